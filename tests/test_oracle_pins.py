@@ -1,0 +1,242 @@
+"""Pins of the CPU oracle to facts fixed by the paper or by mathematics
+(no GPU).  Each test names the passage it follows."""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle.oracle import OracleSim, gumbel, log32, philox4x32_10
+from paper_2603_25068_b300 import scenario as S
+
+PRECISIONS = ["fp64", "fp32"]
+
+
+# ---------------------------------------------------------------- random numbers
+def test_philox_known_answers():
+    """Philox4x32-10 known-answer vectors published with Random123
+    (Salmon et al., SC'11)."""
+    assert list(philox4x32_10([0, 0, 0, 0], [0, 0])) == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
+    assert list(philox4x32_10([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2)) == [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]
+    assert list(philox4x32_10([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344],
+                              [0xA4093822, 0x299F31D0])) == [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]
+
+
+def test_log32_error_bound():
+    """The float logarithm used for Gumbel keys stays within 2 ulp of log."""
+    rng = np.random.default_rng(0)
+    xs = np.concatenate([rng.uniform(2 ** -24, 1.0, 4000), rng.uniform(1e-7, 20.0, 4000),
+                         np.float32(1.0) - np.arange(1, 200, dtype=np.float32) * np.float32(2 ** -24),
+                         np.array([2 ** -24, 0.5, 1.0 - 2 ** -24, 16.6, 1.4142135, 1.4142137])])
+    xs = xs.astype(np.float32)
+    worst = 0.0
+    for x in xs:
+        got = log32(float(x))
+        ref = math.log(float(x))
+        ulp = np.spacing(np.float32(abs(ref))) if ref != 0 else np.float32(2 ** -149)
+        worst = max(worst, abs(got - ref) / float(ulp))
+    assert worst <= 2.0, worst
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_gumbel_distribution(prec):
+    """g = -log(-log U) is Gumbel(0,1): mean = Euler-Mascheroni constant,
+    variance pi^2/6, and exp(-exp(-g)) is uniform (SI-B, Eq. gumbel)."""
+    n = 40000
+    g = np.array([gumbel(12345, 7, i, 3, 0, k, prec) for i in range(n // 4) for k in range(4)])
+    se = math.pi / math.sqrt(6) / math.sqrt(n)
+    assert abs(g.mean() - 0.5772156649) < 4 * se
+    assert abs(g.var() - math.pi ** 2 / 6) < 0.05
+    u = np.exp(-np.exp(-g))
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+
+
+# ---------------------------------------------------------------- car-following
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("length,u", [(100.0, 13.9), (100.0, 10.0), (237.0, 8.3), (60.0, 25.0)])
+def test_lone_vehicle_link_time(prec, length, u):
+    """A lone vehicle moves at free-flow speed (Eq. newell_model, first term) and
+    is capped at the link end by the TG clip (Eq. eq:tg); it is at the end after
+    ceil((L - eps)/(u dt)) steps and leaves in that step."""
+    sc = S.line_network(n_links=3, length=length, u=u, N=1, T=200)
+    o = OracleSim(sc, prec)
+    out = o.rollout()
+    k = math.ceil((np.float32(length) - 0.01) / np.float32(u))
+    arr = np.nonzero(out["n_arrived"])[0][0]
+    assert arr == 1 + 3 * k            # departs at step 0, enters link 0 at t = 1
+    tt = out["travel_time"][0]
+    np.testing.assert_allclose(tt[:3], k, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("dt", [1.0, 0.1, 0.02])
+def test_lone_vehicle_small_dt_limit(dt):
+    """With dt = tau dn, tau = 1 (Methods), the link time of a lone vehicle
+    tends to L/u as dt -> 0: |TT - L/u| <= dt."""
+    length, u = 100.0, 13.9
+    T = int(round(60 / dt))
+    sc = S.line_network(n_links=1, length=length, u=u, N=1, T=T).copy(dt=dt, dn=dt, obs_every=T)
+    o = OracleSim(sc, "fp64")
+    out = o.rollout()
+    tt = out["travel_time"][0][0]
+    assert abs(tt - length / u) <= dt + 1e-9
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("u,kappa", [(10.0, 0.2), (13.9, 0.2), (20.0, 0.4)])
+def test_entry_flow_equals_newell_capacity(prec, u, kappa):
+    """A saturated origin feeds a long link at the capacity of Newell's model
+    with dt = tau dn, tau = 1: q = u kappa / (1 + u kappa) (Eq. newell_model with
+    the vacancy rule X_min > dn/kappa of SI-B)."""
+    N = 600
+    sc = S.line_network(n_links=1, length=5000.0, u=u, kappa=kappa, q=1.0, N=N, T=500)
+    o = OracleSim(sc, prec)
+    out = o.rollout()
+    entered = N - out["n_waiting"]
+    rate = (entered[450] - entered[50]) / 400.0
+    cap = u * kappa / (1.0 + u * kappa)
+    assert abs(rate - cap) < 0.01, (rate, cap)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_exit_flow_limited_by_outflow_credit(prec):
+    """The outflow credit (0.5 veh/s) bounds the discharge of a saturated link."""
+    N = 300
+    sc = S.line_network(n_links=2, length=300.0, u=13.9, kappa=0.2, q=0.5, N=N, T=600)
+    o = OracleSim(sc, prec)
+    out = o.rollout()
+    arr = out["n_arrived"]
+    rate = (arr[500] - arr[200]) / 300.0
+    assert abs(rate - 0.5) < 0.01
+
+
+# ---------------------------------------------------------------- invariants
+def _per_step_invariants(sc, prec):
+    o = OracleSim(sc, prec)
+    o.reset()
+    prev_exits = np.zeros(sc.L, np.int64)
+    s = (np.float64(sc.dn) / sc.kappa.astype(np.float64))
+    for t in range(sc.T):
+        o.step()
+        st = o.state()
+        link, pos, rank, entry = st["veh_link"], st["veh_pos"], st["veh_rank"], st["veh_entry"]
+        on = link >= 0
+        # positions inside the link (SI-A: no backward motion, inside boundaries)
+        assert np.all(pos[on] >= 0) and np.all(pos[on] <= sc.length[link[on]] + 1e-9)
+        # FIFO / no overtaking: queue order by position equals order of entry
+        for j in np.unique(link[on]):
+            ids = np.nonzero(link == j)[0]
+            order = ids[np.argsort(rank[ids])]
+            assert np.all(np.diff(entry[order]) > 0)
+            gaps = -np.diff(pos[order])
+            assert np.all(gaps >= s[j] * (1 - 1e-5) - 1e-4), (t, j, gaps.min(), s[j])
+            assert len(ids) <= math.floor(sc.length[j] / s[j]) + 1
+        # at most one exit per link per step, never above the credit
+        d = st["link_exits"] - prev_exits
+        assert d.min() >= 0 and d.max() <= 1
+        prev_exits = st["link_exits"].copy()
+        assert np.all(st["link_credit"] >= 0)
+    out = o.outputs()
+    tot = out["n_waiting"] + out["n_on"] + out["n_arrived"]
+    assert np.all(tot == sc.N)
+    # counts of the final state agree with the state itself
+    return out
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_invariants_tiny_grid(prec):
+    sc = S.tiny_grid()
+    out = _per_step_invariants(sc.copy(T=150, obs_every=150), prec)
+    assert out["n_on"].max() > 100
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_invariants_dense_small(prec):
+    sc = S.random_small(seed=3, side=3, n_vehicles=120, T=120)
+    _per_step_invariants(sc, prec)
+
+
+# ---------------------------------------------------------------- choice model
+def _star(beta, n_veh, tau=0.5, seed=0):
+    k = len(beta)
+    tail = [0] * k + list(range(1, k + 1))
+    head = list(range(1, k + 1)) + [0] * k
+    b = np.concatenate([beta, np.zeros(k)])
+    # every leaf is in the destination zone: a vehicle leaves at the end of its
+    # first link, so the origin queue head is the only candidate of each step
+    zone = [0] + [1] * k
+    # one departure every 2 steps: an entrant has always moved past the jam
+    # spacing before the next candidate comes, so no choice is ever blocked
+    return S.custom(tail, head, length=500.0, origin=np.zeros(n_veh), dest_node=np.ones(n_veh),
+                    dep_step=2 * np.arange(n_veh), u=20.0, beta=b, T=2 * n_veh + 40, tau=tau,
+                    seed=seed, node_zone=zone)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_choice_frequencies_are_softmax(prec):
+    """argmax(V + g) with Gumbel noise samples the logit probabilities
+    z = softmax(V) (SI-B, Eqs. softmax and gumbel): chi-square test."""
+    beta = np.array([0.0, 1.0, 2.0])
+    n = 3000
+    sc = _star(beta, n)
+    o = OracleSim(sc, prec)
+    o.rollout()
+    first = np.array([o.route(i)[1][0] for i in range(n)])
+    obs = np.bincount(first, minlength=3)[:3]
+    p = np.exp(beta) / np.exp(beta).sum()
+    chi2 = ((obs - n * p) ** 2 / (n * p)).sum()
+    assert stats.chi2.sf(chi2, 2) > 1e-3, (obs, n * p)
+
+
+def test_forward_is_temperature_free():
+    """The one-hot of the Gumbel-softmax sample is argmax(log z + g), which does
+    not depend on the temperature (Eqs. gumbel, straigththrough)."""
+    sc = S.random_small(seed=5, n_vehicles=60, T=80)
+    a = OracleSim(sc.copy(tau=0.5), "fp64").rollout()
+    b = OracleSim(sc.copy(tau=0.01), "fp64").rollout()
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def _fork_merge(seed, betaX, betaY, alphaA, alphaB):
+    # A=0, B=1, C=2, D1=3, D2=4; links 0:A->C 1:B->C 2:C->D1 (X) 3:C->D2 (Y) 4:D1->A 5:D2->B
+    tail = [0, 1, 2, 2, 3, 4]
+    head = [2, 2, 3, 4, 0, 1]
+    beta = [0, 0, betaX, betaY, 0, 0]
+    alpha = [alphaA, alphaB, 1, 1, 1, 1]
+    return S.custom(tail, head, length=100.0, origin=[0, 1], dest_node=[3, 3], dep_step=[0, 0],
+                    u=10.0, beta=beta, alpha=alpha, T=40, seed=seed)
+
+
+def test_brute_force_fork_and_merge():
+    """Two vehicles reach a fork at the same step.  Enumerating the decision
+    sequences (link choice, merge, re-draw with fresh noise) gives exact
+    probabilities of (link entered by vehicle 0, link entered by vehicle 1);
+    the oracle's empirical frequencies over seeds must match (SI-B link and
+    merge choice)."""
+    bX, bY, aA, aB = 0.3, 1.0, 1.0, 2.0
+    pX = math.exp(bX) / (math.exp(bX) + math.exp(bY))
+    pY = 1 - pX
+    P0 = math.exp(aA) / (math.exp(aA) + math.exp(aB))      # vehicle 0 wins a merge
+    P1 = 1 - P0
+    exact = {(2, 2): 0.0, (2, 3): 0.0, (3, 2): 0.0, (3, 3): 0.0}
+    # different picks: both enter; same pick: the winner enters, the loser re-draws
+    exact[(2, 3)] += pX * pY
+    exact[(3, 2)] += pY * pX
+    for same, p in ((2, pX), (3, pY)):
+        for loser_pick, q in ((2, pX), (3, pY)):
+            exact[(same, loser_pick)] += p * p * P0 * q      # vehicle 0 won
+            exact[(loser_pick, same)] += p * p * P1 * q      # vehicle 1 won
+    n = 3000
+    obs = {k: 0 for k in exact}
+    for s in range(n):
+        o = OracleSim(_fork_merge(s, bX, bY, aA, aB), "fp64")
+        o.reset(20)
+        o.step(20)
+        r0, r1 = o.route(0)[1], o.route(1)[1]
+        obs[(int(r0[1]), int(r1[1]))] += 1
+    keys = sorted(exact)
+    e = np.array([exact[k] for k in keys]) * n
+    ob = np.array([obs[k] for k in keys])
+    assert abs(sum(exact.values()) - 1) < 1e-12
+    chi2 = ((ob - e) ** 2 / e).sum()
+    assert stats.chi2.sf(chi2, 3) > 1e-3, (ob, e)
