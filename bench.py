@@ -1,0 +1,371 @@
+"""Benchmark of the simulator hot path on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One benchmark step = one forward rollout of the city-scale workload
+(12,000 nodes / 36,000 links, 1,000,000 vehicles, 3,600 steps of dt = 1 s):
+every simulator step of the path (departures, car-following, credit and arrival,
+link choice, merge, transfer, observation) runs in the CUDA kernels.  The
+metric is vehicle-steps per second (N * T / rollout time); x-real-time is
+T dt / rollout time.  Prints one JSON line on rank 0.
+
+Timing: W untimed rollouts, then K rollouts each timed with CUDA events on the
+stream the kernels run on; the ~40 MB working set is smaller than L2, so L2 is
+flushed (256 MB write) before every timed rollout.  Under torchrun every rank
+runs an independent replica (the single-scenario path does not shard) and the
+slowest rank's time is used.
+
+--impl reference times the CPU oracle (double precision, one thread) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("city-scale forward rollout: random planar graph 12,000 nodes / 36,000 links, "
+            "1,000,000 vehicles from 10,240 OD parameters departing over 30 min, 3,600 steps of dt=1 s")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--T", type=int, default=3600)
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work per sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--small", action="store_true", help="small network (for profiling captures)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_scenario(args):
+    from paper_2603_25068_b300 import scenario as S
+    if args.small:
+        sc = S.city(seed=1, n_nodes=3000, n_links=9000, n_vehicles=250_000, T=args.T,
+                    n_origin_zones=20, n_dest_zones=32, name="city_quarter")
+    else:
+        sc = S.city(seed=1, T=args.T)
+    return sc
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(sc, budget_s):
+    """Run the double-precision oracle from t = 0 until the budget is spent."""
+    from oracle.oracle import OracleSim
+    o = OracleSim(sc, "fp64")
+    o.reset(sc.T)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < sc.T and time.perf_counter() - t0 < budget_s:
+        o.step(10)
+        steps += 10
+    wall = time.perf_counter() - t0
+    return steps, wall
+
+
+def cpu_cores_used():
+    return 1
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    sc = make_scenario(args)
+    times = []
+    steps_done = []
+    for k in range(args.warmup + args.steps):
+        steps, wall = oracle_sample(sc, args.cpu_budget / max(1, args.steps))
+        if k >= args.warmup:
+            times.append(wall)
+            steps_done.append(steps)
+    vs = sum(sc.N * s for s in steps_done) / sum(times)
+    sample = (f"oracle fp64 from t=0, {steps_done[0]} of {sc.T} steps per timed sample "
+              f"(~{args.cpu_budget / max(1, args.steps):.0f} s of CPU work each)")
+    line = {
+        "impl": "reference", "metric": "vehicle-steps/s", "value": vs, "unit": "vehicle-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step": "bounded sample of the rollout"},
+        "cpu_baseline": {"value": vs, "unit": "vehicle-steps/s", "cores": cpu_cores_used(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": vs, "unit": "vehicle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                out, _ = self.p.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(k)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ byte model
+def avg_choice_degree(sc):
+    deg = np.bincount(sc.tail, minlength=sc.V)
+    # choice set after a link: out-degree of its head minus the U-turn
+    d = deg[sc.head].astype(np.float64)
+    has_u = np.zeros(sc.L)
+    key = set(zip(sc.tail.tolist(), sc.head.tolist()))
+    for j in range(sc.L):
+        has_u[j] = (int(sc.head[j]), int(sc.tail[j])) in key
+    d = np.where(d - has_u > 0, d - has_u, d)
+    return float(d.mean())
+
+
+def kernel_a_bytes(sc, n_on, n_cand, deg):
+    """Algorithmic bytes of the node-model / car-following kernel for one step:
+    8 B per vehicle on the network (read + write its position), 32 B per link
+    (queue head/length, credit, length/speed/spacing), 8 B per origin queue
+    (pointer, head departure step), and 60 + 24 deg B per node-model candidate
+    (vehicle, destination, choice set, per-candidate-link utility terms,
+    destination feature and vacancy, merge word)."""
+    return 8.0 * n_on + 32.0 * sc.L + 8.0 * sc.V + (60.0 + 24.0 * deg) * n_cand
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2603_25068_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload_key, launch_units):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel, {}).get(workload_key)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    # scale a smaller capture to one launch of this workload by units processed
+    return e["dram_bytes_per_launch"] * launch_units / e["units_per_launch"]
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2603_25068_b300.sim import Simulator
+    from paper_2603_25068_b300 import native as nat
+
+    sc = make_scenario(args)
+    stream = torch.cuda.current_stream(dev)
+    sim = Simulator(sc, device=local, stream=stream)
+    T, N = sc.T, sc.N
+    nb = sim.n_bins(T)
+    out = dict(counts=torch.empty((nb, sc.L), dtype=torch.int32, device=dev),
+               speed=torch.empty((nb, sc.L), dtype=torch.float32, device=dev),
+               travel_time=torch.empty((nb, sc.L), dtype=torch.float32, device=dev))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        sim.rollout(T, device=True, out=out)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            dist.barrier()
+        for k in range(args.steps):
+            flush.fill_(float(k))                      # evict the working set from L2
+            ev[k][0].record(stream)
+            sim.rollout(T, device=True, out=out)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            dist.barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per = total_ms / args.steps
+    value = ws * N * T * args.steps / (total_ms / 1000.0)
+    launches_per_rollout = 2 * T + 2        # reset + (node model, transfer) per step + final observation
+
+    # ---- instrumented pass: per-kernel device time for the roofline
+    kms = np.zeros(3)
+    kl = np.zeros(3, np.int64)
+    import ctypes as C
+    o = nat.sim_outputs(on_device=0)
+    nat.check(sim.lib.sim_profile_rollout(sim.h, T, C.byref(o), kms.ctypes.data_as(C.c_void_p),
+                                          kl.ctypes.data_as(C.c_void_p)), sim.h)
+    res = sim.outputs()
+    cnt = np.zeros(4 * T, np.int32)
+    nat.check(sim.lib.sim_step_counters(sim.h, cnt.ctypes.data_as(C.c_void_p)), sim.h)
+    cnt = cnt.reshape(T, 4)
+    n_on = res["n_on"][:T].astype(np.float64)            # vehicles on links at the start of each step
+    deg = avg_choice_degree(sc)
+    bytes_a = float(np.sum(kernel_a_bytes(sc, n_on, cnt[:, 2].astype(np.float64), deg)))
+    ms_a = float(kms[0])
+    achieved = bytes_a / (ms_a / 1000.0) / 1e9
+    peak, peak_kind = load_peaks()
+    units_per_launch = float(np.mean(n_on))
+    traffic = ncu_traffic("k_step_a", "city_1M", units_per_launch)
+
+    line = {
+        "metric": "vehicle-steps/s", "value": value, "unit": "vehicle-steps/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if not args.small else "city_quarter (profiling case)",
+                   "step": f"one {T}-step forward rollout", "vehicles": N, "links": sc.L,
+                   "l2": "flushed (256 MB write) before each timed rollout", "parallelism": f"replicas x{ws}"},
+        "x_real_time": T * sc.dt / (ms_per / 1000.0),
+        "active_vehicle_steps_per_s": float(np.sum(n_on)) * ws / (ms_per / 1000.0),
+        "per_rollout_ms": ms,
+        "roofline": {"bound": "hbm", "kernel": "k_step_a (node model + car-following)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_a / T,
+                     "avg_launch_us": 1000.0 * ms_a / T,
+                     "kernel_share": {"k_step_a": kms[0] / kms.sum(), "k_step_b": kms[1] / kms.sum(),
+                                      "obs_final": kms[2] / kms.sum()},
+                     "instrumented_rollout_ms": float(kms.sum())},
+        "gpu_launches": launches_per_rollout * args.steps,
+        "clocks": clk.summary(),
+    }
+
+    # ---- end to end through the public API with host buffers
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        params = dict(u=pin(sc.u), kappa=pin(sc.kappa), alpha=pin(sc.alpha), beta=pin(sc.beta),
+                      cost=pin(sc.cost), w=pin(sc.w))
+        host = dict(counts=torch.empty((nb, sc.L), dtype=torch.int32).pin_memory().numpy(),
+                    speed=torch.empty((nb, sc.L), dtype=torch.float32).pin_memory().numpy(),
+                    travel_time=torch.empty((nb, sc.L), dtype=torch.float32).pin_memory().numpy())
+        h2d = sum(v.nbytes for v in params.values())
+        d2h = sum(v.nbytes for v in host.values())
+
+        def e2e_step():
+            sim.set_params(**params)
+            o = nat.sim_outputs(counts=C.c_void_p(host["counts"].ctypes.data),
+                                speed=C.c_void_p(host["speed"].ctypes.data),
+                                travel_time=C.c_void_p(host["travel_time"].ctypes.data), on_device=0)
+            nat.check(sim.lib.sim_rollout(sim.h, T, C.byref(o)), sim.h)
+
+        e2e_step()                                  # captures the graph after the params change
+        torch.cuda.synchronize(dev)
+        t_e2e = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            e2e_step()
+            t_e2e.append(time.perf_counter() - t0)
+        tot = sum(t_e2e)
+        if ws > 1:
+            t = torch.tensor([tot], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        line["e2e"] = {"value": ws * N * T * args.steps / tot, "unit": "vehicle-steps/s",
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "ms_per_step": 1000 * tot / args.steps,
+                       "note": "sim_set_params from pinned host arrays + sim_rollout into pinned host outputs"}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        steps, wall = oracle_sample(sc, args.cpu_budget)
+        line["cpu_baseline"] = {"value": N * steps / wall, "unit": "vehicle-steps/s",
+                                "cores": cpu_cores_used(), "kind": "oracle",
+                                "sample": f"oracle fp64 from t=0, first {steps} of {T} steps of the same "
+                                          f"workload ({wall:.1f} s, 1 thread; host has {os.cpu_count()} cores)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * trafficsim.h -- C ABI of the B300 (sm_103a) differentiable agent-based traffic
+ * simulator (Makinoshima et al., "Ultra-fast Traffic Nowcasting and Control via
+ * Differentiable Agent-based Simulation").
+ *
+ * One simulator step is phi = g o f (Results, "Differentiable agent-based traffic
+ * simulation"): f is Newell's car-following update applied to every vehicle of
+ * every link (Methods Eq. newell_model; SI-A), g is the node model that lets the
+ * leading vehicle of a link choose its next link with a Gumbel-softmax /
+ * straight-through sample (SI-B "Link choice", Eqs. softmax, gumbel,
+ * straigththrough), resolves competing entrants by a second Gumbel sample over
+ * merge priorities (SI-B "Merge choice") and transfers the winners with
+ * trajectory grafting (SI-B Eq. transfer; SI-C).  Link counts at the midpoint
+ * follow SI-D.  The reverse-mode adjoint is that of the straight-through /
+ * trajectory-grafting surrogate the paper differentiates with jax.grad (Methods,
+ * "Optimization").
+ *
+ * Conventions
+ *  - All sizes are int32 unless noted; all real data is float32.
+ *  - Arrays passed to sim_create / sim_set_params are HOST pointers owned by the
+ *    caller; the library copies them and keeps no reference.
+ *  - The handle owns every device buffer it allocates (cudaMalloc) and frees
+ *    them in sim_destroy.
+ *  - Output buffers belong to the caller; `on_device` says whether they are
+ *    device pointers (written asynchronously on the handle's stream) or host
+ *    pointers (the call returns after the copy).
+ *  - All device work is enqueued on the handle's stream: the caller's
+ *    `sim_options.stream` if non-NULL, else a stream the handle creates.
+ *  - Every call returns SIM_OK (0) or a SIM_E* code; sim_last_error() gives the
+ *    text.  No call aborts the process; device-side failures (queue overflow,
+ *    route-log overflow, bounded waits) are reported through an error word,
+ *    never by trapping the GPU.
+ *  - A handle is not thread safe; distinct handles are independent.
+ */
+#ifndef TRAFFICSIM_H
+#define TRAFFICSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SIM_API __attribute__((visibility("default")))
+#else
+#define SIM_API
+#endif
+
+#define SIM_OK        0
+#define SIM_EINVAL    1   /* bad argument, shape, index or network          */
+#define SIM_ENOMEM    2   /* device allocation failed                        */
+#define SIM_ECUDA     3   /* CUDA runtime error                              */
+#define SIM_ETIMEOUT  4   /* a bounded device wait expired                   */
+#define SIM_ESTATE    5   /* call not valid in the handle's current state    */
+#define SIM_EOVERFLOW 6   /* a fixed-capacity device buffer would overflow   */
+
+/* Fixed point of the outflow credit: one vehicle = 65536 units. */
+#define SIM_FX_ONE 65536
+
+typedef struct sim_ctx *sim_handle;
+
+/* Road network (SI-A, SI-B).  Links are directed tail -> head.
+ * q_fx: outflow credit added per step, in 1/65536 vehicle (capacity q * dt).
+ * phi, psi: [L * F] row-major link features; the utility of turning into link m
+ *   for a vehicle bound for zone z is  beta_m / cost_m + sum_f w_f phi[m,f]
+ *   + (sum_f w_f psi[m,f]) * dest_feat[z, head_m]   (SI-B Eq. for V, with the
+ *   origin/destination factors the text allows).
+ * node_zone: [V] destination zone of each node; dest_feat: [Z * V]. */
+typedef struct {
+    int32_t V, L;
+    const int32_t *tail, *head;
+    const float *length;
+    const int32_t *q_fx;
+    int32_t F;
+    const float *phi, *psi;
+    int32_t Z;
+    const int32_t *node_zone;
+    const float *dest_feat;
+} sim_network;
+
+/* Travel demand: vehicle i joins the queue of its origin node at step
+ * dep_step[i] and leaves the network on reaching any node of dest_zone[i].
+ * od[i] in [0, n_od) groups vehicles by OD demand parameter od_lambda. */
+typedef struct {
+    int32_t N;
+    const int32_t *origin, *dest_zone, *dep_step, *od;
+    int32_t n_od;
+    const float *od_lambda;
+} sim_demand;
+
+/* Differentiable parameters (Methods "Experimental setting"): per link free
+ * speed u (m/s), jam density kappa (veh/m), merge priority alpha, cost
+ * sensitivity beta and cost c; route-choice coefficients w [F]; merge priority
+ * of the origin queues. */
+typedef struct {
+    const float *u, *kappa, *alpha, *beta, *cost;
+    const float *w;
+    float alpha_origin;
+} sim_params;
+
+/* Run options.  dt = tau * dn with tau = 1 (Methods, Eq. newell_model); M is the
+ * sentinel of SI-A (99999); eps_arr the arrival tolerance of Alg. S2 (1e-2 m);
+ * eps_tag the relative dead band that tags ties of the car-following min/max for
+ * the adjoint; tau_gumbel the Gumbel-softmax temperature (Eq. gumbel).
+ * Random numbers: Philox4x32-10 keyed by (seed, scenario_id), counter
+ * (vehicle, step, stream, block).  obs_every: steps per observation bin.
+ * ckpt_every: steps between checkpoints kept for sim_backward (0 = forward only).
+ * route_cap: entries of the per-vehicle route log (needed by sim_backward). */
+typedef struct {
+    float dt, dn, tau_gumbel, M, eps_arr, eps_tag;
+    uint64_t seed;
+    uint32_t scenario_id;
+    int32_t obs_every;
+    int32_t ckpt_every;
+    int32_t route_cap;
+    int32_t device;
+    void *stream;          /* cudaStream_t or NULL */
+} sim_options;
+
+/* Rollout outputs, n_bins = ceil(T / obs_every) bins of obs_every steps:
+ * counts[b*L + j]      vehicles passing the midpoint of link j in bin b (SI-D);
+ * speed[b*L + j]       mean speed on link j in bin b (distance / vehicle-time);
+ * travel_time[b*L + j] mean link time of the vehicles leaving j in bin b;
+ * n_waiting/n_on/n_arrived[t], t = 0..T: vehicles not yet on the network, on a
+ * link, and arrived.  Any pointer may be NULL. */
+typedef struct {
+    int32_t *counts;
+    float *speed, *travel_time;
+    int64_t *n_waiting, *n_on, *n_arrived;
+    int32_t on_device;
+} sim_outputs;
+
+/* Gradients of a scalar loss (sim_backward).  Any pointer may be NULL. */
+typedef struct {
+    float *d_u, *d_kappa, *d_alpha, *d_beta, *d_cost;   /* [L] */
+    float *d_w;                                         /* [F] */
+    float *d_alpha_origin;                              /* [1] */
+    float *d_od_lambda;                                 /* [n_od] */
+    int32_t on_device;
+} sim_grads;
+
+/* Exported state (host buffers, any may be NULL): per vehicle its link (-1 not
+ * yet on the network, -2 arrived), position, rank in its link queue (0 = the
+ * leader; -1 off-network) and entry step; per link the outflow credit and
+ * cumulative exits; per node the number of vehicles its origin queue released. */
+typedef struct {
+    int32_t *veh_link;
+    double *veh_pos;
+    int32_t *veh_rank, *veh_entry;
+    int64_t *link_credit, *link_exits;
+    int32_t *fifo_off;
+} sim_state_view;
+
+/* Decisions of the last step (host buffers, any may be NULL): candidate vehicle
+ * and target per link / origin node (-1 none, -2 leaves to its destination,
+ * -3 chosen link not vacant), and the vehicle that entered each link (-1 none). */
+typedef struct {
+    int32_t *link_cand, *link_target, *node_cand, *node_target, *link_in;
+} sim_records;
+
+/* Number of observation bins of a T-step rollout. */
+SIM_API int32_t sim_n_bins(int32_t T, int32_t obs_every);
+
+/* Create a simulator on options->device.  Validates the network (indices,
+ * choice sets of at most 32 links, positive lengths / capacities / costs),
+ * copies every input to the device and leaves the handle at t = 0.
+ * Errors: SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA.  *out is NULL on failure. */
+SIM_API int sim_create(const sim_network *net, const sim_demand *dem, const sim_params *par,
+               const sim_options *opt, sim_handle *out);
+
+/* Replace the differentiable parameters (host arrays, same sizes as at create).
+ * Takes effect at the next reset / rollout. */
+SIM_API int sim_set_params(sim_handle h, const sim_params *par);
+
+/* Reset to t = 0 for a rollout of horizon T (every vehicle waiting, links empty,
+ * full outflow credit).  Errors: SIM_EINVAL (T < 1). */
+SIM_API int sim_reset(sim_handle h, int32_t T);
+
+/* Advance n_steps steps of phi = g o f from the current time; the last step may
+ * not pass the horizon given to sim_reset.  Observation bins close as they
+ * complete.  Errors: SIM_ESTATE (beyond horizon / no reset), SIM_EOVERFLOW. */
+SIM_API int sim_step(sim_handle h, int32_t n_steps);
+
+/* Reset, run T steps, close the last observation bin and write the outputs.
+ * With options.ckpt_every > 0 it also keeps the checkpoints and route log that
+ * sim_backward needs.  The steps are replayed from a CUDA graph captured on the
+ * first rollout of each horizon.  Errors: as sim_reset / sim_step, SIM_ECUDA. */
+SIM_API int sim_rollout(sim_handle h, int32_t T, sim_outputs *out);
+
+/* Copy the outputs of the current run (bins closed so far; counters up to the
+ * current step) -- the rollout outputs when the run was driven by sim_step. */
+SIM_API int sim_get_outputs(sim_handle h, sim_outputs *out);
+
+/* Per-step counters of the current run: counters[4*t + k] for step t, k = 0
+ * vehicles released by origin queues, 1 arrivals, 2 node-model candidates,
+ * 3 link entries.  `counters` is a host array of 4 * (steps so far) int32. */
+SIM_API int sim_step_counters(sim_handle h, int32_t *counters);
+
+/* Instrumented rollout for measurement: the same kernels as sim_rollout,
+ * launched one by one with a CUDA event recorded on the handle's stream before
+ * and after every launch.  kernel_ms[k] receives the summed device time of
+ * kernel class k (0 = node-model/car-following kernel, 1 = transfer kernel,
+ * 2 = final observation) and launches[k] the launch counts.  Outputs as
+ * sim_rollout. */
+SIM_API int sim_profile_rollout(sim_handle h, int32_t T, sim_outputs *out, double *kernel_ms,
+                                int64_t *launches);
+
+/* Reverse-mode gradient of L = sum_{b,j} dL_dcounts[b,j] * counts[b,j] (+ the
+ * optional terms below) through the straight-through / trajectory-grafting
+ * surrogate of the last sim_rollout (SI-B, SI-C, SI-D), recomputing each
+ * checkpoint segment.  dL_dcounts: [n_bins * L]; dL_dxT: optional [N] adjoint
+ * of the final vehicle positions.  Inputs are host or device per on_device.
+ * Errors: SIM_ESTATE (no rollout with ckpt_every > 0 since the last reset). */
+SIM_API int sim_backward(sim_handle h, const float *dL_dcounts, const float *dL_dxT,
+                 int32_t inputs_on_device, sim_grads *out);
+
+/* Copy the current state / last-step decisions to host buffers. */
+SIM_API int sim_get_state(sim_handle h, sim_state_view *out);
+SIM_API int sim_get_records(sim_handle h, sim_records *out);
+
+/* Current time step and device bytes held by the handle. */
+SIM_API int32_t sim_time(sim_handle h);
+SIM_API size_t sim_device_bytes(sim_handle h);
+
+/* Release every resource of the handle (NULL is accepted). */
+SIM_API int sim_destroy(sim_handle h);
+
+/* Text of the last error on this handle (or of the last failed sim_create when
+ * h is NULL).  Valid until the next call on the handle. */
+SIM_API const char *sim_last_error(sim_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRAFFICSIM_H */

@@ -1,0 +1,158 @@
+"""Python front end of the CUDA simulator (marshalling only).
+
+    sim = Simulator(scenario)          # copies the scenario to the GPU
+    out = sim.rollout()                # dict of numpy arrays (host)
+    out = sim.rollout(device=True)     # dict of torch CUDA tensors, async on sim.stream
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional
+
+import numpy as np
+
+from . import native as nat
+
+
+def _p(a):
+    return C.c_void_p(a.ctypes.data) if a is not None else None
+
+
+class Simulator:
+    def __init__(self, sc, device: int = 0, stream=None, ckpt_every: int = 0, route_cap: int = 64):
+        self.sc = sc
+        self.lib = nat.lib()
+        self._keep = []
+        a = self._arr
+        net = nat.sim_network(V=sc.V, L=sc.L, tail=a(sc.tail, np.int32), head=a(sc.head, np.int32),
+                              length=a(sc.length, np.float32), q_fx=a(sc.q_fx, np.int32), F=sc.F,
+                              phi=a(sc.phi, np.float32), psi=a(sc.psi, np.float32), Z=sc.Z,
+                              node_zone=a(sc.node_zone, np.int32), dest_feat=a(sc.dest_feat, np.float32))
+        dem = nat.sim_demand(N=sc.N, origin=a(sc.origin, np.int32), dest_zone=a(sc.dest_zone, np.int32),
+                             dep_step=a(sc.dep_step, np.int32), od=a(sc.od, np.int32), n_od=sc.n_od,
+                             od_lambda=a(sc.od_lambda, np.float32))
+        par = self._params(sc.u, sc.kappa, sc.alpha, sc.beta, sc.cost, sc.w, sc.alpha_origin)
+        if stream is not None and not isinstance(stream, int):
+            stream = stream.cuda_stream
+        self.stream_ptr = stream
+        opt = nat.sim_options(dt=sc.dt, dn=sc.dn, tau_gumbel=sc.tau, M=sc.M, eps_arr=sc.eps_arr,
+                              eps_tag=sc.eps_tag, seed=sc.seed, scenario_id=sc.scenario_id,
+                              obs_every=sc.obs_every, ckpt_every=ckpt_every, route_cap=route_cap,
+                              device=device, stream=stream)
+        h = C.c_void_p()
+        rc = self.lib.sim_create(C.byref(net), C.byref(dem), C.byref(par), C.byref(opt), C.byref(h))
+        nat.check(rc, None)
+        self.h = h
+        self.device = device
+        self.T = None
+        self._keep = []
+
+    def _arr(self, x, dt):
+        x = np.ascontiguousarray(np.asarray(x, dt))
+        self._keep.append(x)
+        return _p(x)
+
+    def _params(self, u, kappa, alpha, beta, cost, w, alpha_origin):
+        a = self._arr
+        return nat.sim_params(u=a(u, np.float32), kappa=a(kappa, np.float32), alpha=a(alpha, np.float32),
+                              beta=a(beta, np.float32), cost=a(cost, np.float32), w=a(w, np.float32),
+                              alpha_origin=float(alpha_origin))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sim_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def _check(self, rc):
+        nat.check(rc, self.h)
+
+    # ------------------------------------------------------------------ params
+    def set_params(self, u=None, kappa=None, alpha=None, beta=None, cost=None, w=None, alpha_origin=None):
+        sc = self.sc
+        self._keep = []
+        par = self._params(sc.u if u is None else u, sc.kappa if kappa is None else kappa,
+                           sc.alpha if alpha is None else alpha, sc.beta if beta is None else beta,
+                           sc.cost if cost is None else cost, sc.w if w is None else w,
+                           sc.alpha_origin if alpha_origin is None else alpha_origin)
+        self._check(self.lib.sim_set_params(self.h, C.byref(par)))
+        self._keep = []
+
+    # ------------------------------------------------------------------ running
+    def n_bins(self, T=None):
+        return self.lib.sim_n_bins(self.sc.T if T is None else T, self.sc.obs_every)
+
+    def reset(self, T=None):
+        self.T = self.sc.T if T is None else T
+        self._check(self.lib.sim_reset(self.h, self.T))
+
+    def step(self, n=1):
+        self._check(self.lib.sim_step(self.h, n))
+
+    @property
+    def t(self):
+        return self.lib.sim_time(self.h)
+
+    def device_bytes(self):
+        return self.lib.sim_device_bytes(self.h)
+
+    def rollout(self, T: Optional[int] = None, device: bool = False, out=None):
+        """Run a whole rollout.  With device=True the outputs are torch CUDA
+        tensors written asynchronously on the simulator's stream (``out`` may
+        supply preallocated ones)."""
+        T = self.sc.T if T is None else T
+        self.T = T
+        nb, L = self.n_bins(T), self.sc.L
+        if device:
+            import torch
+            dev = torch.device("cuda", self.device)
+            if out is None:
+                out = dict(counts=torch.empty((nb, L), dtype=torch.int32, device=dev),
+                           speed=torch.empty((nb, L), dtype=torch.float32, device=dev),
+                           travel_time=torch.empty((nb, L), dtype=torch.float32, device=dev))
+            o = nat.sim_outputs(counts=C.c_void_p(out["counts"].data_ptr()),
+                                speed=C.c_void_p(out["speed"].data_ptr()),
+                                travel_time=C.c_void_p(out["travel_time"].data_ptr()), on_device=1)
+            self._check(self.lib.sim_rollout(self.h, T, C.byref(o)))
+            return out
+        res = dict(counts=np.zeros((nb, L), np.int32), speed=np.zeros((nb, L), np.float32),
+                   travel_time=np.zeros((nb, L), np.float32), n_waiting=np.zeros(T + 1, np.int64),
+                   n_on=np.zeros(T + 1, np.int64), n_arrived=np.zeros(T + 1, np.int64))
+        o = nat.sim_outputs(*(_p(res[k]) for k in ("counts", "speed", "travel_time", "n_waiting",
+                                                   "n_on", "n_arrived")), 0)
+        self._check(self.lib.sim_rollout(self.h, T, C.byref(o)))
+        return res
+
+    def outputs(self):
+        """Outputs of the run so far (a rollout, or reset + steps)."""
+        T = self.T
+        nb, L = self.n_bins(T), self.sc.L
+        res = dict(counts=np.zeros((nb, L), np.int32), speed=np.zeros((nb, L), np.float32),
+                   travel_time=np.zeros((nb, L), np.float32), n_waiting=np.zeros(T + 1, np.int64),
+                   n_on=np.zeros(T + 1, np.int64), n_arrived=np.zeros(T + 1, np.int64))
+        o = nat.sim_outputs(*(_p(res[k]) for k in ("counts", "speed", "travel_time", "n_waiting",
+                                                   "n_on", "n_arrived")), 0)
+        self._check(self.lib.sim_get_outputs(self.h, C.byref(o)))
+        return res
+
+    def state(self):
+        sc = self.sc
+        d = dict(veh_link=np.zeros(sc.N, np.int32), veh_pos=np.zeros(sc.N, np.float64),
+                 veh_rank=np.zeros(sc.N, np.int32), veh_entry=np.zeros(sc.N, np.int32),
+                 link_credit=np.zeros(sc.L, np.int64), link_exits=np.zeros(sc.L, np.int64),
+                 fifo_off=np.zeros(sc.V, np.int32))
+        v = nat.sim_state_view(*(_p(d[k]) for k in ("veh_link", "veh_pos", "veh_rank", "veh_entry",
+                                                     "link_credit", "link_exits", "fifo_off")))
+        self._check(self.lib.sim_get_state(self.h, C.byref(v)))
+        return d
+
+    def records(self):
+        sc = self.sc
+        d = dict(link_cand=np.zeros(sc.L, np.int32), link_target=np.zeros(sc.L, np.int32),
+                 node_cand=np.zeros(sc.V, np.int32), node_target=np.zeros(sc.V, np.int32),
+                 link_in=np.zeros(sc.L, np.int32))
+        r = nat.sim_records(*(_p(d[k]) for k in ("link_cand", "link_target", "node_cand",
+                                                  "node_target", "link_in")))
+        self._check(self.lib.sim_get_records(self.h, C.byref(r)))
+        return d
