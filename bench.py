@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="small network (for profiling captures)")
+    ap.add_argument("--stage", type=int, default=0, help="queue slots per link block (0 = autotune)")
     return ap.parse_args()
 
 
@@ -230,7 +231,10 @@ def run_ours(args):
     from paper_2603_25068_b300 import native as nat
 
     sc = make_scenario(args)
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated stream: the library enqueues everything on it and the CUDA
+    # events below are recorded on the same stream
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     sim = Simulator(sc, device=local, stream=stream)
     T, N = sc.T, sc.N
     nb = sim.n_bins(T)
@@ -238,6 +242,12 @@ def run_ours(args):
                speed=torch.empty((nb, sc.L), dtype=torch.float32, device=dev),
                travel_time=torch.empty((nb, sc.L), dtype=torch.float32, device=dev))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    from paper_2603_25068_b300 import autotune
+    if args.stage:
+        autotune.set_stage(sim, args.stage)
+        stage, stage_ms = args.stage, {}
+    else:
+        stage, stage_ms = autotune.tune_stage(sim, T=min(T, 900))
 
     for _ in range(args.warmup):
         sim.rollout(T, device=True, out=out)
@@ -306,6 +316,7 @@ def run_ours(args):
                                       "obs_final": kms[2] / kms.sum()},
                      "instrumented_rollout_ms": float(kms.sum())},
         "gpu_launches": launches_per_rollout * args.steps,
+        "launch_shape": {"staged_slots_per_block": stage, "autotune_ms_per_900_steps": stage_ms},
         "clocks": clk.summary(),
     }
 

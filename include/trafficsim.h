@@ -143,7 +143,7 @@ typedef struct {
 
 /* Exported state (host buffers, any may be NULL): per vehicle its link (-1 not
  * yet on the network, -2 arrived), position, rank in its link queue (0 = the
- * leader; -1 off-network) and entry step; per link the outflow credit and
+ * leader; -1 off-network) and entry step (-1 off-network); per link the outflow credit and
  * cumulative exits; per node the number of vehicles its origin queue released. */
 typedef struct {
     int32_t *veh_link;
@@ -219,6 +219,11 @@ SIM_API int sim_backward(sim_handle h, const float *dL_dcounts, const float *dL_
 /* Copy the current state / last-step decisions to host buffers. */
 SIM_API int sim_get_state(sim_handle h, sim_state_view *out);
 SIM_API int sim_get_records(sim_handle h, sim_records *out);
+
+/* Launch shape of the node-model kernel: queue slots staged in shared memory
+ * per link block (256..8192, default 2048; links are packed into blocks up to
+ * this many slots).  Results do not depend on it.  Errors: SIM_EINVAL. */
+SIM_API int sim_set_stage(sim_handle h, int32_t slots);
 
 /* Current time step and device bytes held by the handle. */
 SIM_API int32_t sim_time(sim_handle h);

@@ -195,8 +195,8 @@ typedef struct {
     int64_t *vseq;
     /* link state */
     int64_t *credit, *exits;
-    /* observation accumulators */
-    real *acc_dx;
+    /* observation accumulators (distance summed in double in both builds) */
+    double *acc_dx;
     int64_t *acc_n, *tt_sum, *tt_cnt, *C_prev;
     int32_t t, T, n_bins;
     int32_t *out_counts;      /* [n_bins][L] */
@@ -372,7 +372,7 @@ or_sim *or_create(const or_scenario *sc, int keep_hist)
     o->vseq = (int64_t *)xcalloc(N, sizeof(int64_t));
     o->credit = (int64_t *)xcalloc(L, sizeof(int64_t));
     o->exits = (int64_t *)xcalloc(L, sizeof(int64_t));
-    o->acc_dx = (real *)xcalloc(L, sizeof(real));
+    o->acc_dx = (double *)xcalloc(L, sizeof(double));
     o->acc_n = (int64_t *)xcalloc(L, sizeof(int64_t));
     o->tt_sum = (int64_t *)xcalloc(L, sizeof(int64_t));
     o->tt_cnt = (int64_t *)xcalloc(L, sizeof(int64_t));
@@ -522,7 +522,7 @@ int or_step(or_sim *o)
             else if (d >= o->udt[j] - o->dtag[j]) tag = TAG_FREE;
             else tag = TAG_CONG;
             o->tagbuf[i] = tag;
-            o->acc_dx[j] = o->acc_dx[j] + (xn - x);
+            o->acc_dx[j] += (double)(xn - x);
             o->acc_n[j] += 1;
         }
     }
@@ -672,7 +672,7 @@ int or_step(or_sim *o)
             int64_t C = o->exits[j] + past;
             o->out_counts[(size_t)bin * L + j] = (int32_t)(C - o->C_prev[j]);
             o->C_prev[j] = C;
-            o->out_speed[(size_t)bin * L + j] = o->acc_n[j] ? (double)o->acc_dx[j] / ((double)o->acc_n[j] * (double)sc->dt) : 0.0;
+            o->out_speed[(size_t)bin * L + j] = o->acc_n[j] ? o->acc_dx[j] / ((double)o->acc_n[j] * (double)sc->dt) : 0.0;
             o->out_tt[(size_t)bin * L + j] = o->tt_cnt[j] ? (double)o->tt_sum[j] * (double)sc->dt / (double)o->tt_cnt[j] : 0.0;
             o->acc_dx[j] = 0; o->acc_n[j] = 0; o->tt_sum[j] = 0; o->tt_cnt[j] = 0;
         }

@@ -1,24 +1,9 @@
-// trafficsim.cu -- forward step kernels and the C ABI of include/trafficsim.h.
-//
-// One step phi = g o f runs as two kernels:
-//   step_fwd_a  one warp per link: observation (when a bin closes), Newell
-//               car-following of the whole queue (SI-A, Eq. newell_model) from
-//               the time-t positions into the other position buffer, outflow
-//               credit, leader arrival test (Alg. S2), link choice over the
-//               choice set by Gumbel argmax with one lane per candidate link
-//               (SI-B Eqs. softmax/gumbel/straigththrough), and the merge
-//               (SI-B "Merge choice") as a 64-bit atomicMax of (alpha + g',
-//               ~vehicle id) into the target's word.  One lane per origin node
-//               does the same for the head of its origin queue.
-//   step_fwd_b  one thread per link / origin node: applies the transfers of the
-//               step (SI-B Eq. transfer): pops the leader that won or left to
-//               its destination, pushes the winner at x = 0, updates credit,
-//               exits and link times, and precomputes the vacancy flag
-//               X_min > dn/kappa for the next step from the post-f position of
-//               the new queue tail.
-// A rollout is captured once per horizon into a CUDA graph of 2T + 1 kernels.
-#include "ts_sim.cuh"
+// trafficsim.cu -- host side of the simulator and the C ABI of include/trafficsim.h.
+// The step kernels are in ts_step.cuh; a rollout is captured once per horizon
+// into a CUDA graph of 2T + 2 kernels (reset, T x (k_step_a, k_step_b), final
+// observation).
 #include "../../include/trafficsim.h"
+#include "ts_step.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -62,241 +47,31 @@ __global__ void k_reset(DevSim d, const int *fifo_beg) {
     if (i < d.L) {
         const int4 st = d.lst[i];
         d.lq[i] = make_int4(0, 0, st.w, 0);
-        d.vac[i] = 1;
+        d.vac[i] = kFlagVacant;
         d.W0[i] = 0ull;
         d.W1[i] = 0ull;
-        d.acc_dx[i] = 0.0f; d.acc_n[i] = 0; d.tt_sum[i] = 0; d.tt_cnt[i] = 0; d.C_prev[i] = 0;
-        d.cand_tgt[i] = kTgtNone; d.cand_vid[i] = -1;
+        d.lstat[i] = make_int4(0, 0, 0, 0);
+        d.lpos[i] = make_longlong2(0, 0);
+        d.crec[i] = make_int4(-1, kTgtNone, 0, 0);
     }
-    if (i < d.V) { d.fifo_ptr[i] = fifo_beg[i]; d.ncand_tgt[i] = kTgtNone; d.ncand_vid[i] = -1; }
-    if (i < d.N) { d.vstate[i] = kVehWaiting; d.entry[i] = 0; }
+    if (i < d.V) { d.fifo_ptr[i] = fifo_beg[i]; d.nrec[i] = make_int2(-1, kTgtNone); }
+    if (i < d.N) d.vstate[i] = kVehWaiting;
     if (i < 4) d.err[i] = 0;
 }
 
-// Returns (on lane 0) 1 if the link's leader was a candidate of the node model.
-__device__ __forceinline__ int link_warp(const DevSim &d, int j, int lane, int t, bool obs_only) {
-    const int p = t & 1;
-    const float *pc = p ? d.pos1 : d.pos0;
-    float *pn = p ? d.pos0 : d.pos1;
-    const int4 q = d.lq[j];
-    const int4 st = d.lst[j];
-    if (obs_only || (t > 0 && t % d.obs_every == 0)) {
-        observe_link(d, j, lane, t, q, st, pc);
-        if (obs_only) return 0;
+// Choice-slot records (U, G, head, link) of every choice-set entry after a link
+// and of every out-link of a node, from the per-link utility terms.
+__global__ void k_choice_info(DevSim d, const int *lo_idx, int n_lo, const int *no_idx, int n_no) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n_lo) {
+        const int m = lo_idx[e];
+        const float4 ti = d.tinfo[m];
+        const_cast<float4 *>(d.loinfo)[e] = make_float4(ti.x, ti.y, ti.z, __int_as_float(m));
     }
-    const float4 g = d.geo[j];
-    const int n = q.y;
-    // ---- f: car-following of the queue, leader first ----
-    float xl = 0.0f, accdx = 0.0f, carry = 0.0f;
-    for (int base = 0; base < n; base += 32) {
-        const int k = base + lane;
-        float x = 0.0f;
-        int slot = 0;
-        if (k < n) {
-            int idx = q.x + k;
-            if (idx >= st.y) idx -= st.y;
-            slot = st.x + idx;
-            x = pc[slot];
-        }
-        float xa = __shfl_up_sync(kFull, x, 1);
-        if (lane == 0) xa = carry;
-        if (k < n) {
-            const float h = (k == 0) ? d.M : __fsub_rn(xa, x);
-            int tag;
-            const float xn = newell(x, h, g.x, g.y, g.z, g.w, tag);
-            pn[slot] = xn;
-            if (d.tag_tape) d.tag_tape[slot] = (int8_t)tag;
-            accdx += __fsub_rn(xn, x);
-            if (k == 0) xl = xn;
-        }
-        carry = __shfl_sync(kFull, x, 31);
-    }
-    accdx = warp_sumf(accdx);
-    // ---- g: credit, arrival, choice, merge ----
-    int cand = 0, vid = -1, z = 0, credit = 0;
-    int4 nd = make_int4(0, 0, 0, 0);
-    if (lane == 0) {
-        if (n > 0) { d.acc_dx[j] += accdx; d.acc_n[j] += n; }
-        credit = min(q.z + st.z, st.w);
-        reinterpret_cast<int *>(&d.lq[j])[2] = credit;
-        cand = (n > 0) && (xl >= __fsub_rn(g.x, d.eps_arr)) && (credit >= d.dn_fx);
-        if (cand) {
-            vid = d.svid[st.x + q.x];
-            z = d.dest_zone[vid];
-            nd = d.lnode[j];
-        }
-        d.cand_vid[j] = cand ? vid : -1;
-        if (!cand) d.cand_tgt[j] = kTgtNone;
-        else if (nd.y == z) { d.cand_tgt[j] = kTgtSink; cand = 0; }
-    }
-    const int counted = (lane == 0) ? (d.cand_vid[j] >= 0) : 0;
-    cand = __shfl_sync(kFull, cand, 0);
-    if (!cand) return counted;
-    vid = __shfl_sync(kFull, vid, 0);
-    z = __shfl_sync(kFull, z, 0);
-    nd.z = __shfl_sync(kFull, nd.z, 0);
-    nd.w = __shfl_sync(kFull, nd.w, 0);
-    const int deg = nd.w - nd.z;
-    float key = -INFINITY;
-    int m = -1;
-    if (lane < deg) {
-        m = d.lo_idx[nd.z + lane];
-        key = choice_key(d, m, z, vid, t, lane);
-    }
-    // argmax over lanes, ties to the lowest slot
-    int best = lane;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float ok = __shfl_xor_sync(kFull, key, o);
-        const int ob = __shfl_xor_sync(kFull, best, o);
-        if (ok > key || (ok == key && ob < best)) { key = ok; best = ob; }
-    }
-    const int mt = __shfl_sync(kFull, m, best);
-    if (lane == 0) {
-        if (d.vac[mt]) {
-            const float kp = __fadd_rn(d.alpha[j], gumbel(d.key0, d.key1, vid, t, 1, 0));
-            atomicMax(p ? &d.W1[mt] : &d.W0[mt], merge_word(kp, vid));
-            d.cand_tgt[j] = mt;
-        } else {
-            d.cand_tgt[j] = kTgtBlocked;
-        }
-    }
-    return counted;
-}
-
-// Head of the origin queue of node n (a virtual inflow link of length 0).
-// Returns 1 if the node's origin queue had a candidate.
-__device__ __forceinline__ int node_lane(const DevSim &d, int n, int t) {
-    const int p = t & 1;
-    const int ptr = d.fifo_ptr[n];
-    int tgt = kTgtNone, cv = -1;
-    if (ptr < d.fifo_end[n] && d.fifo_dep[ptr] <= t) {
-        cv = d.fifo_list[ptr];
-        const int z = d.dest_zone[cv];
-        if (d.node_zone[n] == z) {
-            tgt = kTgtSink;
-        } else {
-            const int b = d.no_ptr[n], e = d.no_ptr[n + 1];
-            float bk = 0.0f;
-            int mt = -1;
-            for (int k = 0; k < e - b; ++k) {
-                const int m = d.no_idx[b + k];
-                const float key = choice_key(d, m, z, cv, t, k);
-                if (mt < 0 || key > bk) { bk = key; mt = m; }
-            }
-            if (d.vac[mt]) {
-                const float kp = __fadd_rn(d.alpha[d.L], gumbel(d.key0, d.key1, cv, t, 1, 0));
-                atomicMax(p ? &d.W1[mt] : &d.W0[mt], merge_word(kp, cv));
-                tgt = mt;
-            } else {
-                tgt = kTgtBlocked;
-            }
-        }
-    }
-    d.ncand_vid[n] = cv;
-    d.ncand_tgt[n] = tgt;
-    return cv >= 0;
-}
-
-__global__ void __launch_bounds__(128) k_step_a(DevSim d, int t, int obs_only) {
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    int nc = 0;
-    if (gw < d.L) {
-        nc = link_warp(d, gw, lane, t, obs_only != 0);
-    } else if (!obs_only) {
-        const int n = (gw - d.L) * 32 + lane;
-        if (n < d.V) nc = node_lane(d, n, t);
-        nc = warp_sum(nc);
-    }
-    if (lane == 0 && nc) atomicAdd(&d.step_delta[4 * t + 2], nc);
-}
-
-__global__ void __launch_bounds__(256) k_step_b(DevSim d, int t) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int p = t & 1;
-    const unsigned long long *W = p ? d.W1 : d.W0;
-    int released = 0, arrived = 0, entered = 0;
-    if (i < d.L) {
-        const int j = i;
-        float *pn = p ? d.pos0 : d.pos1;
-        int4 q = d.lq[j];
-        const int4 st = d.lst[j];
-        const int tgt = d.cand_tgt[j];
-        const int cv = d.cand_vid[j];
-        bool out = false;
-        if (tgt == kTgtSink) {
-            out = true;
-            d.vstate[cv] = kVehArrived;
-            arrived = 1;
-        } else if (tgt >= 0) {
-            const unsigned long long w = W[tgt];
-            out = (w != 0ull) && merge_vid(w) == cv;
-        }
-        if (out) {
-            d.tt_sum[j] += t + 1 - d.entry[cv];
-            d.tt_cnt[j] += 1;
-            q.x = (q.x + 1 == st.y) ? 0 : q.x + 1;
-            q.y -= 1;
-            q.z -= d.dn_fx;
-            q.w += 1;
-        }
-        const unsigned long long win = W[j];
-        if (win != 0ull) {
-            const int v = merge_vid(win);
-            if (q.y >= st.y) {
-                set_error(d, SIM_EOVERFLOW, j, t);
-            } else {
-                int idx = q.x + q.y;
-                if (idx >= st.y) idx -= st.y;
-                pn[st.x + idx] = 0.0f;
-                d.svid[st.x + idx] = v;
-                q.y += 1;
-                d.entry[v] = t + 1;
-                d.vstate[v] = j;
-                entered = 1;
-            }
-        }
-        (p ? d.W0 : d.W1)[j] = 0ull;
-        d.lq[j] = q;
-        // vacancy of the coming step: post-f position of the queue tail > s
-        int vac = 1;
-        if (q.y > 0) {
-            const float4 g = d.geo[j];
-            int it = q.x + q.y - 1;
-            if (it >= st.y) it -= st.y;
-            const float xt = pn[st.x + it];
-            float h = d.M;
-            if (q.y > 1) {
-                int ip = it - 1;
-                if (ip < 0) ip += st.y;
-                h = __fsub_rn(pn[st.x + ip], xt);
-            }
-            int tag;
-            vac = newell(xt, h, g.x, g.y, g.z, g.w, tag) > g.z;
-        }
-        d.vac[j] = vac;
-    } else if (i < d.L + d.V) {
-        const int n = i - d.L;
-        const int tgt = d.ncand_tgt[n];
-        const int cv = d.ncand_vid[n];
-        if (tgt == kTgtSink) {
-            d.fifo_ptr[n] += 1;
-            d.vstate[cv] = kVehArrived;
-            released = 1;
-            arrived = 1;
-        } else if (tgt >= 0) {
-            const unsigned long long w = W[tgt];
-            if (w != 0ull && merge_vid(w) == cv) { d.fifo_ptr[n] += 1; released = 1; }
-        }
-    }
-    released = warp_sum(released);
-    arrived = warp_sum(arrived);
-    entered = warp_sum(entered);
-    if ((threadIdx.x & 31) == 0) {
-        if (released) atomicAdd(&d.step_delta[4 * t], released);
-        if (arrived) atomicAdd(&d.step_delta[4 * t + 1], arrived);
-        if (entered) atomicAdd(&d.step_delta[4 * t + 3], entered);
+    if (e < n_no) {
+        const int m = no_idx[e];
+        const float4 ti = d.tinfo[m];
+        const_cast<float4 *>(d.noinfo)[e] = make_float4(ti.x, ti.y, ti.z, __int_as_float(m));
     }
 }
 
@@ -320,6 +95,11 @@ struct sim_ctx {
     float *d_len = nullptr, *d_u = nullptr, *d_kappa = nullptr, *d_beta = nullptr, *d_cost = nullptr;
     float *d_phi = nullptr, *d_psi = nullptr, *d_w = nullptr;
     int *d_head = nullptr, *d_fifo_beg = nullptr;
+    int *d_lo_idx = nullptr, *d_no_idx = nullptr;
+    int n_lo = 0, n_no = 0;
+    int stage = 2048;                    // queue slots staged per link block
+    int stage_max = 0;                   // largest staged slot count of a block
+    int *d_blk = nullptr;
     std::vector<void *> allocs;
     size_t bytes = 0;
     // run state
@@ -371,6 +151,36 @@ extern "C" int32_t sim_n_bins(int32_t T, int32_t obs_every) {
     return (T + obs_every - 1) / obs_every;
 }
 
+// Pack consecutive links into link blocks of k_step_a: at most kLinksPerBlock
+// links whose queue capacities add up to at most `stage` slots (a larger link
+// gets a block of its own).
+static int build_blocks(sim_ctx *h) {
+    std::vector<int> blk{0};
+    int slots = 0, nl = 0, smax = 0;
+    for (int j = 0; j < h->L; ++j) {
+        const int cap = h->lst_host[4 * j + 1];
+        if (nl > 0 && (nl == kLinksPerBlock || slots + cap > h->stage)) {
+            blk.push_back(j);
+            smax = std::max(smax, slots);
+            slots = 0;
+            nl = 0;
+        }
+        slots += cap;
+        nl += 1;
+    }
+    blk.push_back(h->L);
+    smax = std::max(smax, slots);
+    if (!h->d_blk) TRY(dalloc(h, &h->d_blk, (size_t)h->L + 1));
+    CU(cudaMemcpyAsync(h->d_blk, blk.data(), blk.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    h->d.blk_links = h->d_blk;
+    h->d.nblk = (int)blk.size() - 1;
+    h->stage_max = smax;
+    const size_t smem = (size_t)2 * smax * sizeof(float);
+    CU(cudaFuncSetAttribute(k_step_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return SIM_OK;
+}
+
 static int upload_params(sim_ctx *h, const sim_params *par) {
     const int L = h->L, F = h->F;
     for (int j = 0; j < L; ++j) {
@@ -398,6 +208,8 @@ static int upload_params(sim_ctx *h, const sim_params *par) {
     k_params<<<(L + 255) / 256, 256, 0, h->stream>>>(h->d, h->d_len, h->d_u, h->d_kappa, h->d_beta, h->d_cost,
                                                      h->d_phi, h->d_psi, h->d_w, h->d_head, h->opt.dn,
                                                      h->opt.eps_tag);
+    const int ne = std::max(h->n_lo, h->n_no);
+    k_choice_info<<<(ne + 255) / 256, 256, 0, h->stream>>>(h->d, h->d_lo_idx, h->n_lo, h->d_no_idx, h->n_no);
     CU(cudaGetLastError());
     // the captured graphs read the parameters from device memory and stay valid;
     // host copies of the parameters must outlive the asynchronous uploads
@@ -413,6 +225,8 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
     if (V <= 0 || L <= 0 || N < 0 || F < 0 || Z <= 0) return fail(h, SIM_EINVAL, "bad sizes");
     if (!(opt->dt > 0) || !(opt->dn > 0) || opt->obs_every <= 0 || !(opt->tau_gumbel > 0))
         return fail(h, SIM_EINVAL, "bad options");
+    for (int j = 0; j < L; ++j)
+        if (!((double)par->u[j] * opt->dt < 2000.0)) return fail(h, SIM_EINVAL, "u dt must be below 2000 m");
     h->V = V; h->L = L; h->N = N; h->F = F; h->Z = Z; h->n_od = dem->n_od;
     h->opt = *opt;
     h->device = opt->device;
@@ -480,7 +294,7 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
     h->S = (int)S;
     h->lst_host = lst;
     // origin queues sorted by (origin, departure step, id)
-    std::vector<int> fifo(N), fifo_beg(V + 1, 0), fifo_dep(N);
+    std::vector<int> fifo(N), fifo_beg(V + 1, 0), fifo_dep(N), fifo_aux(2 * (size_t)N);
     std::iota(fifo.begin(), fifo.end(), 0);
     std::stable_sort(fifo.begin(), fifo.end(), [&](int a, int b) {
         if (dem->origin[a] != dem->origin[b]) return dem->origin[a] < dem->origin[b];
@@ -489,7 +303,11 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
     });
     for (int i = 0; i < N; ++i) fifo_beg[dem->origin[i] + 1]++;
     for (int n = 0; n < V; ++n) fifo_beg[n + 1] += fifo_beg[n];
-    for (int k = 0; k < N; ++k) fifo_dep[k] = dem->dep_step[fifo[k]];
+    for (int k = 0; k < N; ++k) {
+        fifo_dep[k] = dem->dep_step[fifo[k]];
+        fifo_aux[2 * k] = fifo[k];
+        fifo_aux[2 * k + 1] = dem->dest_zone[fifo[k]];
+    }
     std::vector<int> fifo_end(fifo_beg.begin() + 1, fifo_beg.end());
     h->fifo_beg = fifo_beg;
     h->fifo_list = fifo;
@@ -517,12 +335,18 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
     float *alpha_d;
     TRY(dalloc(h, &alpha_d, L + 1)); d.alpha = alpha_d;     // [L] = origin queues
     int *p;
-    TRY(upload(h, &p, lo_idx.data(), lo_idx.size())); d.lo_idx = p;
+    TRY(upload(h, &h->d_lo_idx, lo_idx.data(), lo_idx.size()));
     TRY(upload(h, &p, no_ptr.data(), no_ptr.size())); d.no_ptr = p;
-    TRY(upload(h, &p, no_idx.data(), no_idx.size())); d.no_idx = p;
+    TRY(upload(h, &h->d_no_idx, no_idx.data(), no_idx.size()));
+    h->n_lo = (int)lo_idx.size();
+    h->n_no = (int)no_idx.size();
+    float4 *lo_info, *no_info;
+    TRY(dalloc(h, &lo_info, lo_idx.size())); d.loinfo = lo_info;
+    TRY(dalloc(h, &no_info, no_idx.size())); d.noinfo = no_info;
     TRY(upload(h, &p, net->node_zone, V)); d.node_zone = p;
     TRY(upload(h, &p, fifo_end.data(), V)); d.fifo_end = p;
-    TRY(upload(h, &p, fifo.data(), N)); d.fifo_list = p;
+    int2 *fa;
+    TRY(upload(h, &fa, (const int2 *)fifo_aux.data(), N)); d.fifo_list = fa;
     TRY(upload(h, &p, fifo_dep.data(), N)); d.fifo_dep = p;
     TRY(upload(h, &p, dem->dest_zone, N)); d.dest_zone = p;
     float *fp;
@@ -544,26 +368,23 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
     TRY(dalloc(h, &d.vac, L));
     TRY(dalloc(h, &d.pos0, S));
     TRY(dalloc(h, &d.pos1, S));
-    TRY(dalloc(h, &d.svid, S));
+    TRY(dalloc(h, &d.saux, S));
+    TRY(dalloc(h, &d.sentry, S));
     TRY(dalloc(h, &d.W0, L));
     TRY(dalloc(h, &d.W1, L));
-    TRY(dalloc(h, &d.cand_vid, L));
-    TRY(dalloc(h, &d.cand_tgt, L));
-    TRY(dalloc(h, &d.ncand_vid, V));
-    TRY(dalloc(h, &d.ncand_tgt, V));
+    TRY(dalloc(h, &d.crec, L));
+    TRY(dalloc(h, &d.nrec, V));
     TRY(dalloc(h, &d.fifo_ptr, V));
-    TRY(dalloc(h, &d.entry, N));
     TRY(dalloc(h, &d.vstate, N));
-    TRY(dalloc(h, &d.acc_dx, L));
-    TRY(dalloc(h, &d.acc_n, L));
-    TRY(dalloc(h, &d.tt_sum, L));
-    TRY(dalloc(h, &d.tt_cnt, L));
-    TRY(dalloc(h, &d.C_prev, L));
+    TRY(dalloc(h, &d.lstat, L));
+    TRY(dalloc(h, &d.lpos, L));
     TRY(dalloc(h, &d.err, 4));
     CU(cudaMemsetAsync(d.pos0, 0, (size_t)S * sizeof(float), h->stream));
     CU(cudaMemsetAsync(d.pos1, 0, (size_t)S * sizeof(float), h->stream));
-    CU(cudaMemsetAsync(d.svid, 0xff, (size_t)S * sizeof(int), h->stream));
+    CU(cudaMemsetAsync(d.saux, 0xff, (size_t)S * sizeof(int2), h->stream));
+    CU(cudaMemsetAsync(d.sentry, 0, (size_t)S * sizeof(int), h->stream));
     d.tag_tape = nullptr;
+    TRY(build_blocks(h));
     TRY(upload_params(h, par));
     CU(cudaStreamSynchronize(h->stream));
     return SIM_OK;
@@ -626,15 +447,22 @@ static void enqueue_reset(sim_ctx *h, int T) {
     k_reset<<<(nmax + 255) / 256, 256, 0, h->stream>>>(h->d, h->d_fifo_beg);
 }
 
-static void enqueue_step(sim_ctx *h, int t) {
-    const int warps = h->L + (h->V + 31) / 32;
-    k_step_a<<<(warps * 32 + 127) / 128, 128, 0, h->stream>>>(h->d, t, 0);
+static void enqueue_a(sim_ctx *h, int t, int obs_only) {
+    const int node_blocks = obs_only ? 0 : (h->V + kBlockA - 1) / kBlockA;
+    const size_t smem = (size_t)2 * h->stage_max * sizeof(float);
+    k_step_a<<<h->d.nblk + node_blocks, kBlockA, smem, h->stream>>>(h->d, t, obs_only);
+}
+
+static void enqueue_b(sim_ctx *h, int t) {
     k_step_b<<<(h->L + h->V + 255) / 256, 256, 0, h->stream>>>(h->d, t);
 }
 
-static void enqueue_obs_final(sim_ctx *h, int T) {
-    k_step_a<<<(h->L * 32 + 127) / 128, 128, 0, h->stream>>>(h->d, T, 1);
+static void enqueue_step(sim_ctx *h, int t) {
+    enqueue_a(h, t, 0);
+    enqueue_b(h, t);
 }
+
+static void enqueue_obs_final(sim_ctx *h, int T) { enqueue_a(h, T, 1); }
 
 static int check_device_error(sim_ctx *h) {
     int e[4];
@@ -760,13 +588,12 @@ extern "C" int sim_profile_rollout(sim_handle h, int32_t T, sim_outputs *out, do
     std::vector<cudaEvent_t> ev((size_t)4 * T + 2);
     for (auto &e : ev) CU(cudaEventCreate(&e));
     enqueue_reset(h, T);
-    const int warps = h->L + (h->V + 31) / 32;
     for (int t = 0; t < T; ++t) {
         CU(cudaEventRecord(ev[4 * t + 0], h->stream));
-        k_step_a<<<(warps * 32 + 127) / 128, 128, 0, h->stream>>>(h->d, t, 0);
+        enqueue_a(h, t, 0);
         CU(cudaEventRecord(ev[4 * t + 1], h->stream));
         CU(cudaEventRecord(ev[4 * t + 2], h->stream));
-        k_step_b<<<(h->L + h->V + 255) / 256, 256, 0, h->stream>>>(h->d, t);
+        enqueue_b(h, t);
         CU(cudaEventRecord(ev[4 * t + 3], h->stream));
     }
     CU(cudaEventRecord(ev[4 * T], h->stream));
@@ -814,11 +641,12 @@ extern "C" int sim_get_state(sim_handle h, sim_state_view *out) {
     const int L = h->L, N = h->N, V = h->V, S = h->S;
     std::vector<int4> lq(L);
     std::vector<float> pos(S);
-    std::vector<int> svid(S), entry(N), vstate(N), fptr(V);
+    std::vector<int2> saux(S);
+    std::vector<int> sentry(S), vstate(N), fptr(V);
     CU(cudaMemcpyAsync(lq.data(), h->d.lq, L * sizeof(int4), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaMemcpyAsync(pos.data(), (h->t & 1) ? h->d.pos1 : h->d.pos0, S * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaMemcpyAsync(svid.data(), h->d.svid, S * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaMemcpyAsync(entry.data(), h->d.entry, N * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(saux.data(), h->d.saux, S * sizeof(int2), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(sentry.data(), h->d.sentry, S * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaMemcpyAsync(vstate.data(), h->d.vstate, N * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaMemcpyAsync(fptr.data(), h->d.fifo_ptr, V * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
@@ -827,18 +655,19 @@ extern "C" int sim_get_state(sim_handle h, sim_state_view *out) {
         if (out->veh_link) out->veh_link[i] = s;
         if (out->veh_pos) out->veh_pos[i] = 0.0;
         if (out->veh_rank) out->veh_rank[i] = -1;
-        if (out->veh_entry) out->veh_entry[i] = entry[i];
+        if (out->veh_entry) out->veh_entry[i] = -1;
     }
     for (int j = 0; j < L; ++j) {
         const int base = h->lst_host[4 * j], cap = h->lst_host[4 * j + 1];
         for (int k = 0; k < lq[j].y; ++k) {
             int idx = lq[j].x + k;
             if (idx >= cap) idx -= cap;
-            const int v = svid[base + idx];
+            const int v = saux[base + idx].x;
             if (v < 0 || v >= N) return fail(h, SIM_ESTATE, "corrupt queue");
             if (out->veh_link) out->veh_link[v] = j;
             if (out->veh_pos) out->veh_pos[v] = pos[base + idx];
             if (out->veh_rank) out->veh_rank[v] = k;
+            if (out->veh_entry) out->veh_entry[v] = sentry[base + idx];
         }
         if (out->link_credit) out->link_credit[j] = lq[j].z;
         if (out->link_exits) out->link_exits[j] = lq[j].w;
@@ -852,23 +681,35 @@ extern "C" int sim_get_records(sim_handle h, sim_records *out) {
     if (!h || !out) return SIM_EINVAL;
     CU(cudaSetDevice(h->device));
     const int L = h->L, V = h->V;
-    std::vector<int> lc(L), lt(L), nc(V), nt(V);
+    std::vector<int4> lc(L);
+    std::vector<int2> nc(V);
     std::vector<unsigned long long> W(L);
     const int p = (h->t - 1) & 1;
-    CU(cudaMemcpyAsync(lc.data(), h->d.cand_vid, L * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaMemcpyAsync(lt.data(), h->d.cand_tgt, L * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaMemcpyAsync(nc.data(), h->d.ncand_vid, V * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaMemcpyAsync(nt.data(), h->d.ncand_tgt, V * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(lc.data(), h->d.crec, L * sizeof(int4), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(nc.data(), h->d.nrec, V * sizeof(int2), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaMemcpyAsync(W.data(), p ? h->d.W1 : h->d.W0, L * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     for (int j = 0; j < L; ++j) {
-        if (out->link_cand) out->link_cand[j] = lt[j] == kTgtNone ? -1 : lc[j];
-        if (out->link_target) out->link_target[j] = lt[j];
+        if (out->link_cand) out->link_cand[j] = lc[j].y == kTgtNone ? -1 : lc[j].x;
+        if (out->link_target) out->link_target[j] = lc[j].y;
         if (out->link_in) out->link_in[j] = W[j] ? (int)(~(uint32_t)(W[j] & 0xffffffffull)) : -1;
     }
     for (int n = 0; n < V; ++n) {
-        if (out->node_cand) out->node_cand[n] = nt[n] == kTgtNone ? -1 : nc[n];
-        if (out->node_target) out->node_target[n] = nt[n];
+        if (out->node_cand) out->node_cand[n] = nc[n].y == kTgtNone ? -1 : nc[n].x;
+        if (out->node_target) out->node_target[n] = nc[n].y;
+    }
+    return SIM_OK;
+}
+
+/* queue slots staged in shared memory per link block of k_step_a */
+extern "C" int sim_set_stage(sim_handle h, int32_t slots) {
+    if (!h) return SIM_EINVAL;
+    if (slots < 256 || slots > 8192) return fail(h, SIM_EINVAL, "stage must be in [256, 8192] slots");
+    if (slots != h->stage) {
+        h->stage = slots;
+        TRY(build_blocks(h));
+        for (auto &g : h->graphs) cudaGraphExecDestroy(g.second);
+        h->graphs.clear();
     }
     return SIM_OK;
 }

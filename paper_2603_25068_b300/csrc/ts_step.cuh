@@ -1,0 +1,453 @@
+// Step kernels of one simulator instance (sm_103a).
+//
+// One step phi = g o f runs as two kernels.
+//
+// k_step_a -- link blocks and origin-node blocks.
+//   A link block owns a contiguous set of links whose queue capacities add up to
+//   at most the block's shared-memory stage (links are packed on the host; a link
+//   larger than the stage gets a block of its own).  Four phases separated by
+//   barriers, each issuing one round of independent global loads:
+//   P1  one thread per link: queue state, link data, statistics and flags of the
+//       step; outflow credit; candidate = leader flagged as arriving with credit.
+//   P2  all threads: every queue position of the block's links into shared
+//       memory (kU coalesced loads in flight per thread whatever the queue
+//       lengths); the leader's (vehicle, zone, entry step) and the choice-set
+//       records of candidates.
+//   P3  all threads: Newell car-following of every vehicle (SI-A, Eq.
+//       newell_model) from the staged time-t positions into the other position
+//       buffer; the utility + Gumbel key of every staged choice slot (SI-B Eqs.
+//       softmax, gumbel, straigththrough) with the destination feature and the
+//       vacancy of the slot's link; the merge key alpha + g' of each candidate.
+//       At observation steps also the per-link midpoint count and position sum
+//       (one segmented warp reduction per 32 staged elements).
+//   P4  one thread per link: observation output when a bin closes (SI-D); argmax
+//       over the slots (ties to the lowest slot) and the merge (SI-B "Merge
+//       choice") as a 64-bit atomicMax of (alpha + g', ~vehicle id) into the
+//       target's word; the vacancy X_min > dn/kappa and leader-arrival flags of
+//       the next step for each of the four (pop, push) outcomes of this step.
+//   Origin-node blocks: one thread per node handles the head of its origin queue
+//   (a virtual inflow link of length 0) the same way.
+// k_step_b -- one thread per link / origin node: applies the transfers (SI-B Eq.
+//   transfer): pops the leader that won its merge or left to its destination,
+//   pushes the merge winner at x = 0, updates credit, exits and link times, and
+//   selects the next step's vacancy / arrival flags.
+//
+// Mean speed of a bin needs the distance sum sum_t sum_i (x_i(t+1) - x_i(t)) over
+// the link's vehicles.  It telescopes: with P(t) the sum of the positions on the
+// link at time t, the bin's distance is P(end) - P(start) + the post-f positions
+// of the vehicles that left during the bin, so positions are summed only when a
+// bin closes (fixed point 2^-16 m, exact integer sums in any order).
+#pragma once
+#include "ts_sim.cuh"
+
+namespace ts {
+
+// flags of link j for the coming step: bit 0 vacant, bit 1 leader arrives
+constexpr int kFlagVacant = 1, kFlagArrive = 2;
+constexpr int kLinksPerBlock = 64;     // at most this many links per link block
+constexpr int kMaxSlotsStaged = 4;     // choice slots per link evaluated in P3
+constexpr int kBlockA = 256;           // threads of k_step_a
+constexpr int kU = 8;                  // staged elements per thread per pass
+constexpr float kPosScale = 65536.0f;  // position sums: fixed point 2^-16 m
+
+__device__ __forceinline__ bool vacant_after(float x, float h, float4 g) {
+    int tag;
+    return newell(x, h, g.x, g.y, g.z, g.w, tag) > g.z;
+}
+__device__ __forceinline__ bool arrives_after(float x, float4 g, float M, float eps) {
+    int tag;
+    return newell(x, M, g.x, g.y, g.z, g.w, tag) >= __fsub_rn(g.x, eps);
+}
+__device__ __forceinline__ long long pos_fx(float x) { return __float2ll_rn(__fmul_rn(x, kPosScale)); }
+
+struct ABlockSmem {
+    int4 q[kLinksPerBlock];             // queue head, length, credit, exits
+    int4 st[kLinksPerBlock];            // queue base, capacity, q_fx, credit cap
+    float4 g[kLinksPerBlock];           // length, u dt, s, tag band
+    int4 nd[kLinksPerBlock];            // head node, head zone, choice begin/end
+    int4 stat[kLinksPerBlock];          // vehicle-steps, link-time sum, leavers, C_prev
+    longlong2 ps[kLinksPerBlock];       // position sum at bin start, leavers' positions
+    int off[kLinksPerBlock + 1];        // first staged element of each link
+    int cand[kLinksPerBlock];           // 1 candidate, 0 none
+    int credit[kLinksPerBlock];
+    float alpha[kLinksPerBlock];
+    int2 lead[kLinksPerBlock];          // candidate (vehicle, zone)
+    int ent[kLinksPerBlock];            // candidate entry step
+    float mkey[kLinksPerBlock];         // candidate merge key alpha + g'
+    int past[kLinksPerBlock];           // vehicles past the midpoint (observation)
+    unsigned long long psum[kLinksPerBlock];  // position sum (observation)
+    float4 lo[kLinksPerBlock][kMaxSlotsStaged];
+    float key[kLinksPerBlock][kMaxSlotsStaged];
+    int vacm[kLinksPerBlock][kMaxSlotsStaged];
+};
+
+// element e of the block's staged queues -> local link index (binary search)
+__device__ __forceinline__ int link_of(const int *off, int nl, int e) {
+    int lo = 0, hi = nl - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ float choice_key(const DevSim &d, float4 e, int zone, int vid, int t, int slot) {
+    const float df = d.dest_feat[(size_t)zone * d.V + __float_as_int(e.z)];
+    const float v = __fadd_rn(e.x, __fmul_rn(e.y, df));
+    return __fadd_rn(v, gumbel(d.key0, d.key1, vid, t, 0, slot));
+}
+
+__device__ __forceinline__ void link_block(const DevSim &d, int b, int t, bool obs_only, float *xs) {
+    __shared__ ABlockSmem S;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int j0 = d.blk_links[b];
+    const int nl = d.blk_links[b + 1] - j0;
+    const int p = t & 1;
+    const float *pc = p ? d.pos1 : d.pos0;
+    float *pn = p ? d.pos0 : d.pos1;
+    const bool obs = obs_only || (t > 0 && t % d.obs_every == 0);
+    // ---------------- P1: link data, statistics, credit, candidate ----------------
+    if (tid < nl) {
+        const int j = j0 + tid;
+        const int4 q = d.lq[j];
+        const int4 st = d.lst[j];
+        const int flags = d.vac[j];
+        S.q[tid] = q;
+        S.st[tid] = st;
+        S.g[tid] = d.geo[j];
+        S.nd[tid] = d.lnode[j];
+        S.stat[tid] = d.lstat[j];
+        S.ps[tid] = d.lpos[j];
+        S.alpha[tid] = d.alpha[j];
+        const int credit = min(q.z + st.z, st.w);
+        S.credit[tid] = credit;
+        S.cand[tid] = !obs_only && (flags & kFlagArrive) && credit >= d.dn_fx;
+        S.past[tid] = 0;
+        S.psum[tid] = 0ull;
+        S.ent[tid] = 0;
+        S.lead[tid] = make_int2(-1, -1);
+    }
+    __syncthreads();
+    if (tid < 32) {          // exclusive scan of queue lengths (nl <= 64)
+        const int a = tid < nl ? S.q[tid].y : 0;
+        const int c = tid + 32 < nl ? S.q[tid + 32].y : 0;
+        int sa = a, sc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ya = __shfl_up_sync(kFull, sa, o), yc = __shfl_up_sync(kFull, sc, o);
+            if (tid >= o) { sa += ya; sc += yc; }
+        }
+        const int tot_a = __shfl_sync(kFull, sa, 31);
+        if (tid < nl) S.off[tid] = sa - a;
+        if (tid + 32 < nl) S.off[tid + 32] = tot_a + sc - c;
+        if (tid == 31) S.off[nl] = tot_a + sc;
+    }
+    __syncthreads();
+    const int total = S.off[nl];
+    // ---------------- P2: stage positions, leader and choice records ----------------
+    // Warp w stages elements [pass + 32 kU w, pass + 32 kU (w + 1)); the link of
+    // an element is tracked linearly from a binary search on the first one.
+    for (int pass = 0; pass < total; pass += kBlockA * kU) {
+        const int wbase = pass + (tid >> 5) * 32 * kU;
+        if (wbase >= total) break;
+        int li = link_of(S.off, nl, min(wbase + lane, total - 1));
+        float v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int e = wbase + u * 32 + lane;
+            v[u] = 0.0f;
+            if (e < total) {
+                while (S.off[li + 1] <= e) ++li;
+                const int4 q = S.q[li], st = S.st[li];
+                int idx = q.x + (e - S.off[li]);
+                if (idx >= st.y) idx -= st.y;
+                v[u] = pc[st.x + idx];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int e = wbase + u * 32 + lane;
+            if (e < total) xs[e] = v[u];
+        }
+    }
+    if (tid < nl && S.cand[tid]) {
+        const int4 q = S.q[tid], st = S.st[tid];
+        S.lead[tid] = d.saux[st.x + q.x];
+        S.ent[tid] = d.sentry[st.x + q.x];
+    }
+    if (!obs_only) {
+        for (int c = tid; c < nl * kMaxSlotsStaged; c += kBlockA) {
+            const int li = c / kMaxSlotsStaged, k = c % kMaxSlotsStaged;
+            const int4 nd = S.nd[li];
+            if (S.cand[li] && k < nd.w - nd.z) S.lo[li][k] = d.loinfo[nd.z + k];
+        }
+    }
+    __syncthreads();
+    // ---------------- P3: car-following, choice and merge keys ----------------
+    float *xn_s = xs + total;
+    if (!obs_only) {
+        for (int c = tid; c < nl * kMaxSlotsStaged; c += kBlockA) {
+            const int li = c / kMaxSlotsStaged, k = c % kMaxSlotsStaged;
+            if (!S.cand[li]) continue;
+            const int4 nd = S.nd[li];
+            const int2 lead = S.lead[li];
+            if (k == 0) S.mkey[li] = __fadd_rn(S.alpha[li], gumbel(d.key0, d.key1, lead.x, t, 1, 0));
+            if (k >= nd.w - nd.z || nd.y == lead.y) continue;     // no slot / leaves to its destination
+            const float4 e = S.lo[li][k];
+            S.key[li][k] = choice_key(d, e, lead.y, lead.x, t, k);
+            S.vacm[li][k] = d.vac[__float_as_int(e.w)] & kFlagVacant;
+        }
+    }
+    for (int pass = 0; pass < total; pass += kBlockA * kU) {
+        const int wbase = pass + (tid >> 5) * 32 * kU;
+        if (wbase >= total) break;
+        int li = link_of(S.off, nl, min(wbase + lane, total - 1));
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int e = wbase + u * 32 + lane;
+            const bool act = e < total;
+            float x = 0.0f;
+            if (act) {
+                while (S.off[li + 1] <= e) ++li;
+                x = xs[e];
+                if (!obs_only) {
+                    const int k = e - S.off[li];
+                    const int4 q = S.q[li], st = S.st[li];
+                    const float4 g = S.g[li];
+                    const float h = (k == 0) ? d.M : __fsub_rn(xs[e - 1], x);
+                    int tag;
+                    const float xn = newell(x, h, g.x, g.y, g.z, g.w, tag);
+                    int idx = q.x + k;
+                    if (idx >= st.y) idx -= st.y;
+                    pn[st.x + idx] = xn;
+                    if (d.tag_tape) d.tag_tape[st.x + idx] = (int8_t)tag;
+                    xn_s[e] = xn;
+                }
+            }
+            if (obs) {      // block-uniform: midpoint count and position sum per link
+                const unsigned seg = __match_any_sync(kFull, act ? li : -1);
+                const unsigned past = act && x >= __fmul_rn(S.g[li].x, 0.5f) ? 1u : 0u;
+                const unsigned sp = __reduce_add_sync(seg, past);
+                const long long xf = act ? pos_fx(x) : 0;
+                const unsigned slo = __reduce_add_sync(seg, (unsigned)(xf & 0xffffffffll));
+                const unsigned shi = __reduce_add_sync(seg, (unsigned)(xf >> 32));
+                if (act && lane == __ffs(seg) - 1) {
+                    if (sp) atomicAdd(&S.past[li], (int)sp);
+                    atomicAdd(&S.psum[li], (unsigned long long)slo + ((unsigned long long)shi << 32));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // ---------------- P4: per link: observation, choice, merge, flags ----------------
+    if (tid >= nl) return;
+    const int li = tid, j = j0 + tid;
+    const int4 q = S.q[li];
+    const int n = q.y;
+    int4 stat = S.stat[li];
+    longlong2 ps = S.ps[li];
+    if (obs) {
+        const int bin = (t - 1) / d.obs_every;
+        const size_t o = (size_t)bin * d.L + j;
+        const int C = q.w + S.past[li];
+        d.out_counts[o] = C - stat.w;
+        const long long pnow = (long long)S.psum[li];
+        const long long dist = pnow - ps.x + ps.y;
+        d.out_speed[o] = stat.x ? (float)((double)dist / (double)kPosScale / ((double)stat.x * (double)d.dt)) : 0.0f;
+        d.out_tt[o] = stat.z ? (float)((double)stat.y * (double)d.dt / (double)stat.z) : 0.0f;
+        stat = make_int4(0, 0, 0, C);
+        ps = make_longlong2(pnow, 0);
+        d.lpos[j] = ps;
+        if (obs_only) { d.lstat[j] = stat; return; }
+    }
+    stat.x += n;
+    d.lstat[j] = stat;
+    const float4 g = S.g[li];
+    const int4 nd = S.nd[li];
+    int tgt = kTgtNone;
+    const int2 lead = S.lead[li];
+    if (S.cand[li]) {
+        if (nd.y == lead.y) {
+            tgt = kTgtSink;
+        } else {
+            const int deg = nd.w - nd.z;
+            float bk = -INFINITY;
+            int bm = -1, bv = 0;
+            for (int k = 0; k < deg; ++k) {
+                float key;
+                int m, vm;
+                if (k < kMaxSlotsStaged) {
+                    key = S.key[li][k];
+                    m = __float_as_int(S.lo[li][k].w);
+                    vm = S.vacm[li][k];
+                } else {
+                    const float4 e = d.loinfo[nd.z + k];
+                    key = choice_key(d, e, lead.y, lead.x, t, k);
+                    m = __float_as_int(e.w);
+                    vm = d.vac[m] & kFlagVacant;
+                }
+                if (bm < 0 || key > bk) { bk = key; bm = m; bv = vm; }
+            }
+            if (bv) {
+                atomicMax(p ? &d.W1[bm] : &d.W0[bm], merge_word(S.mkey[li], lead.x));
+                tgt = bm;
+            } else {
+                tgt = kTgtBlocked;
+            }
+        }
+    }
+    d.lq[j].z = S.credit[li];
+    // flags of the next step for each outcome o = pop | push << 1
+    const float M = d.M;
+    const int off = S.off[li];
+    const float x0 = n >= 1 ? xn_s[off] : 0.0f;
+    const float x1 = n >= 2 ? xn_s[off + 1] : 0.0f;
+    const float xt = n >= 1 ? xn_s[off + n - 1] : 0.0f;
+    const float xpt = n >= 2 ? xn_s[off + n - 2] : 0.0f;
+    int bits = 0;
+    bits |= (n == 0 || vacant_after(xt, n >= 2 ? __fsub_rn(xpt, xt) : M, g)) << 0;
+    bits |= (n <= 1 || vacant_after(xt, n >= 3 ? __fsub_rn(xpt, xt) : M, g)) << 1;
+    bits |= vacant_after(0.0f, n >= 1 ? xt : M, g) << 2;
+    bits |= vacant_after(0.0f, n >= 2 ? xt : M, g) << 3;
+    bits |= (n >= 1 && arrives_after(x0, g, M, d.eps_arr)) << 4;
+    bits |= (n >= 2 && arrives_after(x1, g, M, d.eps_arr)) << 5;
+    bits |= arrives_after(n >= 1 ? x0 : 0.0f, g, M, d.eps_arr) << 6;
+    bits |= arrives_after(n >= 2 ? x1 : 0.0f, g, M, d.eps_arr) << 7;
+    const int cand = S.cand[li];
+    d.crec[j] = make_int4(cand ? lead.x : -1, cand ? tgt : kTgtNone, (S.ent[li] << 8) | bits, __float_as_int(x0));
+}
+
+// Head of the origin queue of node n (a virtual inflow link of length 0).
+__device__ __forceinline__ void node_lane(const DevSim &d, int n, int t) {
+    const int p = t & 1;
+    const int ptr = d.fifo_ptr[n];
+    int tgt = kTgtNone, cv = -1;
+    if (ptr < d.fifo_end[n] && d.fifo_dep[ptr] <= t) {
+        const int2 a = d.fifo_list[ptr];
+        cv = a.x;
+        const int z = a.y;
+        if (d.node_zone[n] == z) {
+            tgt = kTgtSink;
+        } else {
+            const int b = d.no_ptr[n], e = d.no_ptr[n + 1];
+            float bk = 0.0f;
+            int mt = -1;
+            for (int k = 0; k < e - b; ++k) {
+                const float4 in = d.noinfo[b + k];
+                const float key = choice_key(d, in, z, cv, t, k);
+                if (mt < 0 || key > bk) { bk = key; mt = __float_as_int(in.w); }
+            }
+            if (d.vac[mt] & kFlagVacant) {
+                const float kp = __fadd_rn(d.alpha[d.L], gumbel(d.key0, d.key1, cv, t, 1, 0));
+                atomicMax(p ? &d.W1[mt] : &d.W0[mt], merge_word(kp, cv));
+                tgt = mt;
+            } else {
+                tgt = kTgtBlocked;
+            }
+        }
+    }
+    d.nrec[n] = make_int2(cv, tgt);
+}
+
+__global__ void __launch_bounds__(kBlockA, 6) k_step_a(DevSim d, int t, int obs_only) {
+    extern __shared__ float xs[];
+    if ((int)blockIdx.x < d.nblk) {
+        link_block(d, blockIdx.x, t, obs_only != 0, xs);
+    } else if (!obs_only) {
+        const int n = ((int)blockIdx.x - d.nblk) * kBlockA + (int)threadIdx.x;
+        if (n < d.V) node_lane(d, n, t);
+    }
+}
+
+// Sum of v over the block added to *dst by one atomic (every thread must call).
+__device__ __forceinline__ void block_count(int v, int *dst, int *smem) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) smem[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int k = 0; k < nw; ++k) s += smem[k];
+        if (s) atomicAdd(dst, s);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_step_b(DevSim d, int t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = t & 1;
+    const unsigned long long *W = p ? d.W1 : d.W0;
+    int released = 0, arrived = 0, entered = 0, cands = 0;
+    if (i < d.L) {
+        const int j = i;
+        float *pn = p ? d.pos0 : d.pos1;
+        int4 q = d.lq[j];
+        const int4 st = d.lst[j];
+        const int4 c = d.crec[j];
+        const unsigned long long win = W[j];
+        bool pop = false;
+        cands = c.x >= 0;
+        if (c.y == kTgtSink) {
+            pop = true;
+            d.vstate[c.x] = kVehArrived;
+            arrived = 1;
+        } else if (c.y >= 0) {
+            const unsigned long long w = W[c.y];
+            pop = (w != 0ull) && merge_vid(w) == c.x;
+        }
+        if (pop) {
+            int4 stat = d.lstat[j];
+            longlong2 ps = d.lpos[j];
+            stat.y += t + 1 - (c.z >> 8);
+            stat.z += 1;
+            ps.y += pos_fx(__int_as_float(c.w));
+            d.lstat[j] = stat;
+            d.lpos[j] = ps;
+            q.x = (q.x + 1 == st.y) ? 0 : q.x + 1;
+            q.y -= 1;
+            q.z -= d.dn_fx;
+            q.w += 1;
+        }
+        const bool push = win != 0ull;
+        if (push) {
+            const int v = merge_vid(win);
+            if (q.y >= st.y) {
+                set_error(d, SIM_EOVERFLOW, j, t);
+            } else {
+                int idx = q.x + q.y;
+                if (idx >= st.y) idx -= st.y;
+                pn[st.x + idx] = 0.0f;
+                d.saux[st.x + idx] = make_int2(v, d.dest_zone[v]);
+                d.sentry[st.x + idx] = t + 1;
+                q.y += 1;
+                d.vstate[v] = j;
+                entered = 1;
+            }
+        }
+        (p ? d.W0 : d.W1)[j] = 0ull;
+        d.lq[j] = q;
+        const int o = (pop ? 1 : 0) | (push ? 2 : 0);
+        d.vac[j] = ((c.z >> o) & 1) | (((c.z >> (4 + o)) & 1) << 1);
+    } else if (i < d.L + d.V) {
+        const int n = i - d.L;
+        const int2 c = d.nrec[n];
+        cands = c.x >= 0;
+        if (c.y == kTgtSink) {
+            d.fifo_ptr[n] += 1;
+            d.vstate[c.x] = kVehArrived;
+            released = 1;
+            arrived = 1;
+        } else if (c.y >= 0) {
+            const unsigned long long w = W[c.y];
+            if (w != 0ull && merge_vid(w) == c.x) { d.fifo_ptr[n] += 1; released = 1; }
+        }
+    }
+    __shared__ int smem[8];
+    block_count(released, &d.step_delta[4 * t + 0], smem);
+    block_count(arrived, &d.step_delta[4 * t + 1], smem);
+    block_count(cands, &d.step_delta[4 * t + 2], smem);
+    block_count(entered, &d.step_delta[4 * t + 3], smem);
+}
+
+}  // namespace ts

@@ -75,6 +75,7 @@ SIGNATURES = {
     "sim_backward": (C.c_int, [P, P, P, C.c_int32, C.POINTER(sim_grads)]),
     "sim_get_state": (C.c_int, [P, C.POINTER(sim_state_view)]),
     "sim_get_records": (C.c_int, [P, C.POINTER(sim_records)]),
+    "sim_set_stage": (C.c_int, [P, C.c_int32]),
     "sim_time": (C.c_int32, [P]),
     "sim_device_bytes": (C.c_size_t, [P]),
     "sim_destroy": (C.c_int, [P]),

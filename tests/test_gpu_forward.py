@@ -42,8 +42,10 @@ def assert_outputs_equal(g, o, T):
     np.testing.assert_allclose(g["speed"], o["speed"], rtol=RTOL, atol=1e-5)
 
 
-def lockstep(Simulator, sc, T, check_every=1):
+def lockstep(Simulator, sc, T, check_every=1, stage=2048):
     g = Simulator(sc)
+    from paper_2603_25068_b300.autotune import set_stage
+    set_stage(g, stage)
     o = OracleSim(sc, "fp32")
     g.reset(T)
     o.reset(T)
@@ -69,16 +71,20 @@ def test_lockstep_dense_small(Simulator, seed):
     lockstep(Simulator, sc.copy(obs_every=40), 150)
 
 
-def test_lockstep_long_queues(Simulator):
-    # queues far longer than a warp (the carry between 32-vehicle chunks) and
-    # ring-buffer wrap-around of the slot arena
-    sc = S.line_network(n_links=2, length=600.0, u=13.9, kappa=0.2, q=0.5, N=400, T=500)
-    lockstep(Simulator, sc.copy(obs_every=70), 500, check_every=7)
+@pytest.mark.parametrize("stage", [256, 2048])
+def test_lockstep_long_queues(Simulator, stage):
+    # queues longer than a block's thread count, links larger than the stage
+    # (a block of their own) and ring-buffer wrap-around of the slot arena
+    sc = S.line_network(n_links=2, length=1500.0, u=13.9, kappa=0.2, q=0.5, N=700, T=900)
+    lockstep(Simulator, sc.copy(obs_every=70), 900, check_every=9, stage=stage)
 
 
-def test_rollout_graph_matches_oracle_city_small(Simulator):
+@pytest.mark.parametrize("stage", [256, 1024, 4096])
+def test_rollout_graph_matches_oracle_city_small(Simulator, stage):
     sc = S.city_small()
     g = Simulator(sc)
+    from paper_2603_25068_b300.autotune import set_stage
+    set_stage(g, stage)
     out = g.rollout()
     o = OracleSim(sc, "fp32")
     ref = o.rollout()
