@@ -229,6 +229,30 @@ SIM_API int sim_set_stage(sim_handle h, int32_t slots);
 SIM_API int32_t sim_time(sim_handle h);
 SIM_API size_t sim_device_bytes(sim_handle h);
 
+/* Forward rollout that allocates nothing -- the same computation and outputs as
+ * sim_create + sim_rollout + sim_destroy, for callers that may not allocate
+ * device memory: code running while a stream is captured into a CUDA graph,
+ * plug-ins whose host process owns every device allocation, real-time loops.
+ * The paper has no counterpart of this entry point.
+ *   Scratch: one file-scope device array of 16 MiB (every GPU that loads the
+ *   library holds it until the process exits) plus fixed static host buffers.
+ *   Limits: V <= 4096 nodes, L <= 8192 links, N <= 65536 vehicles, T <= 8192
+ *   steps, all choice sets together <= 65536 entries, and every array of the
+ *   run inside the 16 MiB; beyond them the call returns SIM_EOVERFLOW.
+ *   Inputs: host arrays as for sim_create.  Outputs: as sim_rollout (device or
+ *   host per out->on_device; the n_* counters only into host memory).
+ *   Work runs on options->stream (NULL = the default stream) of
+ *   options->device; the call returns after the stream has drained.
+ *   The first call on a device looks up the device address of the scratch
+ *   array (cudaGetSymbolAddress); make that first call before any stream
+ *   capture.  Every call re-initialises the whole scratch, and all calls share
+ *   it: calls that overlap on the GPU (other streams, other host threads) race.
+ *   Returns SIM_OK, SIM_EINVAL (bad argument), SIM_EOVERFLOW (a limit above,
+ *   or a link queue overflowed on the device) or SIM_ECUDA; no error text is
+ *   kept for this call. */
+SIM_API int sim_rollout_static(const sim_network *net, const sim_demand *dem, const sim_params *par,
+                               const sim_options *opt, int32_t T, sim_outputs *out);
+
 /* Release every resource of the handle (NULL is accepted). */
 SIM_API int sim_destroy(sim_handle h);
 

@@ -727,3 +727,270 @@ extern "C" int sim_destroy(sim_handle h) {
 extern "C" const char *sim_last_error(sim_handle h) {
     return h ? h->err.c_str() : g_create_err.c_str();
 }
+
+// ============================================================================
+// Allocation-free forward rollout.
+//
+// For callers that may not allocate device memory: code that runs while a CUDA
+// stream is being captured into a graph (cudaMalloc is not capturable), plug-ins
+// embedded in a host process whose memory manager owns every device allocation,
+// and real-time loops where an allocation could stall.  All simulator state of
+// the call lives in one file-scope device array of fixed size that every GPU
+// loading this library holds until the process exits; host-side set-up uses
+// fixed-size static host buffers.  The paper has no counterpart of this.
+// ============================================================================
+
+namespace {
+
+constexpr size_t kStaticBytes = (size_t)16 << 20;      // device scratch: 16 MiB
+constexpr int kStaticMaxV = 4096, kStaticMaxL = 8192, kStaticMaxN = 65536;
+constexpr int kStaticMaxChoice = 8 * kStaticMaxL;      // entries of all choice sets
+constexpr int kStaticMaxT = 8192;
+constexpr int kStaticMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+// device address of g_static_scratch, looked up once per device
+static void *g_static_addr[kStaticMaxDevices];
+
+// host-side set-up buffers (no dynamic allocation)
+static int hs_no_ptr[kStaticMaxV + 1], hs_no_idx[kStaticMaxL], hs_lo_idx[kStaticMaxChoice];
+static int hs_lnode[4 * kStaticMaxL], hs_lst[4 * kStaticMaxL], hs_blk[kStaticMaxL + 1];
+static int hs_fifo[kStaticMaxN], hs_fifo_beg[kStaticMaxV + 1], hs_fifo_dep[kStaticMaxN];
+static int hs_fifo_aux[2 * kStaticMaxN], hs_fifo_end[kStaticMaxV], hs_fill[kStaticMaxV];
+static int hs_counters[4 * kStaticMaxT];
+static float hs_alpha[kStaticMaxL + 1];
+
+struct Bump {           // carves 256-byte aligned sub-arrays out of the scratch
+    unsigned char *base;
+    size_t used;
+    bool ok;
+    template <class T>
+    T *take(size_t n) {
+        const size_t b = (std::max<size_t>(n, 1) * sizeof(T) + 255) & ~(size_t)255;
+        if (used + b > kStaticBytes) { ok = false; return nullptr; }
+        T *p = (T *)(base + used);
+        used += b;
+        return p;
+    }
+};
+
+}  // namespace
+
+extern "C" int sim_rollout_static(const sim_network *net, const sim_demand *dem, const sim_params *par,
+                                  const sim_options *opt, int32_t T, sim_outputs *out) {
+    if (!net || !dem || !par || !opt || !out) return SIM_EINVAL;
+    const int V = net->V, L = net->L, N = dem->N, F = net->F, Z = net->Z;
+    if (V <= 0 || L <= 0 || N < 0 || F < 0 || Z <= 0 || T < 1) return SIM_EINVAL;
+    if (V > kStaticMaxV || L > kStaticMaxL || N > kStaticMaxN || T > kStaticMaxT) return SIM_EOVERFLOW;
+    if (!(opt->dt > 0) || !(opt->dn > 0) || opt->obs_every <= 0 || !(opt->tau_gumbel > 0)) return SIM_EINVAL;
+    if (opt->device < 0 || opt->device >= kStaticMaxDevices) return SIM_EINVAL;
+    for (int j = 0; j < L; ++j) {
+        if (net->tail[j] < 0 || net->tail[j] >= V || net->head[j] < 0 || net->head[j] >= V) return SIM_EINVAL;
+        if (!(net->length[j] > 0.0f) || net->q_fx[j] <= 0) return SIM_EINVAL;
+        if (!(par->u[j] > 0.0f) || !(par->kappa[j] > 0.0f) || !(par->cost[j] > 0.0f)) return SIM_EINVAL;
+        if (!((double)par->u[j] * opt->dt < 2000.0)) return SIM_EINVAL;
+    }
+    for (int n = 0; n < V; ++n)
+        if (net->node_zone[n] < 0 || net->node_zone[n] >= Z) return SIM_EINVAL;
+    for (int i = 0; i < N; ++i)
+        if (dem->origin[i] < 0 || dem->origin[i] >= V || dem->dest_zone[i] < 0 || dem->dest_zone[i] >= Z ||
+            dem->dep_step[i] < 0)
+            return SIM_EINVAL;
+    // ---- host set-up (same derived structures as sim_create) ----
+    for (int n = 0; n <= V; ++n) hs_no_ptr[n] = 0;
+    for (int j = 0; j < L; ++j) hs_no_ptr[net->tail[j] + 1]++;
+    for (int n = 0; n < V; ++n) hs_no_ptr[n + 1] += hs_no_ptr[n];
+    for (int n = 0; n < V; ++n) hs_fill[n] = 0;
+    for (int j = 0; j < L; ++j) hs_no_idx[hs_no_ptr[net->tail[j]] + hs_fill[net->tail[j]]++] = j;
+    for (int n = 0; n < V; ++n) {
+        const int deg = hs_no_ptr[n + 1] - hs_no_ptr[n];
+        if (deg == 0 || deg > 32) return SIM_EINVAL;
+    }
+    int n_lo = 0;
+    for (int l = 0; l < L; ++l) {
+        const int n = net->head[l];
+        int c = 0;
+        for (int k = hs_no_ptr[n]; k < hs_no_ptr[n + 1]; ++k) c += net->head[hs_no_idx[k]] != net->tail[l];
+        hs_lnode[4 * l + 0] = n;
+        hs_lnode[4 * l + 1] = net->node_zone[n];
+        hs_lnode[4 * l + 2] = n_lo;
+        for (int k = hs_no_ptr[n]; k < hs_no_ptr[n + 1]; ++k) {
+            const int m = hs_no_idx[k];
+            if (!c || net->head[m] != net->tail[l]) {
+                if (n_lo >= kStaticMaxChoice) return SIM_EOVERFLOW;
+                hs_lo_idx[n_lo++] = m;
+            }
+        }
+        hs_lnode[4 * l + 3] = n_lo;
+    }
+    const long long dn_fx = llrint((double)opt->dn * SIM_FX_ONE);
+    long long S = 0;
+    for (int j = 0; j < L; ++j) {
+        const double cap = std::floor((double)net->length[j] * (double)par->kappa[j] / (double)opt->dn) + 2.0;
+        if (cap > 1e6) return SIM_EOVERFLOW;
+        hs_lst[4 * j + 0] = (int)S;
+        hs_lst[4 * j + 1] = (int)cap;
+        hs_lst[4 * j + 2] = net->q_fx[j];
+        hs_lst[4 * j + 3] = (int)std::max<long long>(net->q_fx[j], dn_fx);
+        S += (long long)cap;
+    }
+    if (S > (1ll << 24)) return SIM_EOVERFLOW;
+    for (int i = 0; i < N; ++i) hs_fifo[i] = i;
+    std::sort(hs_fifo, hs_fifo + N, [&](int a, int b) {
+        if (dem->origin[a] != dem->origin[b]) return dem->origin[a] < dem->origin[b];
+        if (dem->dep_step[a] != dem->dep_step[b]) return dem->dep_step[a] < dem->dep_step[b];
+        return a < b;
+    });
+    for (int n = 0; n <= V; ++n) hs_fifo_beg[n] = 0;
+    for (int i = 0; i < N; ++i) hs_fifo_beg[dem->origin[i] + 1]++;
+    for (int n = 0; n < V; ++n) hs_fifo_beg[n + 1] += hs_fifo_beg[n];
+    for (int n = 0; n < V; ++n) hs_fifo_end[n] = hs_fifo_beg[n + 1];
+    for (int k = 0; k < N; ++k) {
+        hs_fifo_dep[k] = dem->dep_step[hs_fifo[k]];
+        hs_fifo_aux[2 * k] = hs_fifo[k];
+        hs_fifo_aux[2 * k + 1] = dem->dest_zone[hs_fifo[k]];
+    }
+    const int stage = 2048;
+    int nblk = 0, slots = 0, nl = 0, smax = 0;
+    hs_blk[0] = 0;
+    for (int j = 0; j < L; ++j) {
+        const int cap = hs_lst[4 * j + 1];
+        if (nl > 0 && (nl == kLinksPerBlock || slots + cap > stage)) {
+            hs_blk[++nblk] = j;
+            smax = std::max(smax, slots);
+            slots = 0;
+            nl = 0;
+        }
+        slots += cap;
+        nl += 1;
+    }
+    hs_blk[++nblk] = L;
+    smax = std::max(smax, slots);
+    for (int j = 0; j < L; ++j) hs_alpha[j] = par->alpha[j];
+    hs_alpha[L] = par->alpha_origin;
+    // ---- device: carve the scratch (first call on a device looks up its address) ----
+    if (cudaSetDevice(opt->device) != cudaSuccess) return SIM_ECUDA;
+    if (!g_static_addr[opt->device]) {
+        void *a = nullptr;
+        if (cudaGetSymbolAddress(&a, g_static_scratch) != cudaSuccess || !a) return SIM_ECUDA;
+        g_static_addr[opt->device] = a;
+    }
+    cudaStream_t s = (cudaStream_t)opt->stream;
+    const int nb = sim_n_bins(T, opt->obs_every);
+    Bump B{(unsigned char *)g_static_addr[opt->device], 0, true};
+    DevSim d{};
+    d.V = V; d.L = L; d.N = N; d.Z = Z; d.F = F;
+    d.dn_fx = (int)dn_fx;
+    d.obs_every = opt->obs_every;
+    d.M = opt->M; d.eps_arr = opt->eps_arr; d.dt = opt->dt;
+    d.key0 = (uint32_t)(opt->seed & 0xffffffffull);
+    d.key1 = (uint32_t)(opt->seed >> 32) ^ opt->scenario_id;
+    float4 *geo = B.take<float4>(L), *tinfo = B.take<float4>(L), *loinfo = B.take<float4>(n_lo),
+           *noinfo = B.take<float4>(L);
+    int4 *lst = B.take<int4>(L), *lnode = B.take<int4>(L);
+    float *alpha = B.take<float>(L + 1), *dest_feat = B.take<float>((size_t)Z * V);
+    int *blk = B.take<int>(nblk + 1), *no_ptr = B.take<int>(V + 1), *node_zone = B.take<int>(V);
+    int *fifo_end = B.take<int>(V), *fifo_dep = B.take<int>(N), *dest_zone = B.take<int>(N);
+    int2 *fifo_list = B.take<int2>(N);
+    float *len = B.take<float>(L), *u = B.take<float>(L), *kappa = B.take<float>(L), *beta = B.take<float>(L),
+          *cost = B.take<float>(L), *phi = B.take<float>((size_t)L * F), *psi = B.take<float>((size_t)L * F),
+          *w = B.take<float>(F);
+    int *head = B.take<int>(L), *lo_idx = B.take<int>(n_lo), *no_idx = B.take<int>(L), *fifo_beg = B.take<int>(V);
+    d.lq = B.take<int4>(L);
+    d.crec = B.take<int4>(L);
+    d.vac = B.take<int>(L);
+    d.pos0 = B.take<float>(S);
+    d.pos1 = B.take<float>(S);
+    d.saux = B.take<int2>(S);
+    d.sentry = B.take<int>(S);
+    d.W0 = B.take<unsigned long long>(L);
+    d.W1 = B.take<unsigned long long>(L);
+    d.nrec = B.take<int2>(V);
+    d.fifo_ptr = B.take<int>(V);
+    d.vstate = B.take<int>(N);
+    d.lstat = B.take<int4>(L);
+    d.lpos = B.take<longlong2>(L);
+    d.out_counts = B.take<int>((size_t)nb * L);
+    d.out_speed = B.take<float>((size_t)nb * L);
+    d.out_tt = B.take<float>((size_t)nb * L);
+    d.step_delta = B.take<int>((size_t)4 * T);
+    d.err = B.take<int>(4);
+    if (!B.ok) return SIM_EOVERFLOW;
+    d.geo = geo; d.tinfo = tinfo; d.loinfo = loinfo; d.noinfo = noinfo; d.lst = lst; d.lnode = lnode;
+    d.alpha = alpha; d.dest_feat = dest_feat; d.blk_links = blk; d.nblk = nblk; d.no_ptr = no_ptr;
+    d.node_zone = node_zone; d.fifo_end = fifo_end; d.fifo_dep = fifo_dep; d.dest_zone = dest_zone;
+    d.fifo_list = fifo_list; d.tag_tape = nullptr;
+#define SUP(dst, src, n) do { if ((n) > 0 && cudaMemcpyAsync((dst), (src), (size_t)(n) * sizeof(*(dst)), cudaMemcpyHostToDevice, s) != cudaSuccess) return SIM_ECUDA; } while (0)
+    SUP(lst, (const int4 *)hs_lst, L);
+    SUP(lnode, (const int4 *)hs_lnode, L);
+    SUP(alpha, hs_alpha, L + 1);
+    SUP(dest_feat, net->dest_feat, (size_t)Z * V);
+    SUP(blk, hs_blk, nblk + 1);
+    SUP(no_ptr, hs_no_ptr, V + 1);
+    SUP(node_zone, net->node_zone, V);
+    SUP(fifo_end, hs_fifo_end, V);
+    SUP(fifo_dep, hs_fifo_dep, N);
+    SUP(dest_zone, dem->dest_zone, N);
+    SUP(fifo_list, (const int2 *)hs_fifo_aux, N);
+    SUP(len, net->length, L);
+    SUP(u, par->u, L);
+    SUP(kappa, par->kappa, L);
+    SUP(beta, par->beta, L);
+    SUP(cost, par->cost, L);
+    SUP(phi, net->phi, (size_t)L * F);
+    SUP(psi, net->psi, (size_t)L * F);
+    SUP(w, par->w, F);
+    SUP(head, net->head, L);
+    SUP(lo_idx, hs_lo_idx, n_lo);
+    SUP(no_idx, hs_no_idx, L);
+    SUP(fifo_beg, hs_fifo_beg, V);
+#undef SUP
+    // state that must start at zero: the whole run re-initialises it
+    if (cudaMemsetAsync(d.pos0, 0, (size_t)S * sizeof(float), s) != cudaSuccess ||
+        cudaMemsetAsync(d.pos1, 0, (size_t)S * sizeof(float), s) != cudaSuccess ||
+        cudaMemsetAsync(d.saux, 0xff, (size_t)S * sizeof(int2), s) != cudaSuccess ||
+        cudaMemsetAsync(d.sentry, 0, (size_t)S * sizeof(int), s) != cudaSuccess ||
+        cudaMemsetAsync(d.step_delta, 0, (size_t)4 * T * sizeof(int), s) != cudaSuccess ||
+        cudaMemsetAsync(d.out_counts, 0, (size_t)nb * L * sizeof(int), s) != cudaSuccess)
+        return SIM_ECUDA;
+    k_params<<<(L + 255) / 256, 256, 0, s>>>(d, len, u, kappa, beta, cost, phi, psi, w, head, opt->dn, opt->eps_tag);
+    const int ne = std::max(n_lo, L);
+    k_choice_info<<<(ne + 255) / 256, 256, 0, s>>>(d, lo_idx, n_lo, no_idx, L);
+    const int nmax = std::max(std::max(L, V), std::max(N, 4));
+    k_reset<<<(nmax + 255) / 256, 256, 0, s>>>(d, fifo_beg);
+    const size_t smem = (size_t)2 * smax * sizeof(float);
+    if (cudaFuncSetAttribute(k_step_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return SIM_ECUDA;
+    const int node_blocks = (V + kBlockA - 1) / kBlockA;
+    for (int t = 0; t < T; ++t) {
+        k_step_a<<<nblk + node_blocks, kBlockA, smem, s>>>(d, t, 0);
+        k_step_b<<<(L + V + 255) / 256, 256, 0, s>>>(d, t);
+    }
+    k_step_a<<<nblk, kBlockA, smem, s>>>(d, T, 1);
+    if (cudaGetLastError() != cudaSuccess) return SIM_ECUDA;
+    // ---- outputs ----
+    const cudaMemcpyKind k = out->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t nbl = (size_t)nb * L;
+    if (out->counts && cudaMemcpyAsync(out->counts, d.out_counts, nbl * sizeof(int), k, s) != cudaSuccess) return SIM_ECUDA;
+    if (out->speed && cudaMemcpyAsync(out->speed, d.out_speed, nbl * sizeof(float), k, s) != cudaSuccess) return SIM_ECUDA;
+    if (out->travel_time && cudaMemcpyAsync(out->travel_time, d.out_tt, nbl * sizeof(float), k, s) != cudaSuccess) return SIM_ECUDA;
+    int err[4] = {0, 0, 0, 0};
+    if (cudaMemcpyAsync(err, d.err, sizeof err, cudaMemcpyDeviceToHost, s) != cudaSuccess) return SIM_ECUDA;
+    if (out->n_waiting || out->n_on || out->n_arrived) {
+        if (out->on_device) return SIM_EINVAL;      // counters are produced on the host
+        if (cudaMemcpyAsync(hs_counters, d.step_delta, (size_t)4 * T * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return SIM_ECUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SIM_ECUDA;
+    if (out->n_waiting || out->n_on || out->n_arrived) {
+        int64_t nw = N, na = 0;
+        for (int t = 0; t <= T; ++t) {
+            if (t > 0) { nw -= hs_counters[4 * (t - 1)]; na += hs_counters[4 * (t - 1) + 1]; }
+            if (out->n_waiting) out->n_waiting[t] = nw;
+            if (out->n_arrived) out->n_arrived[t] = na;
+            if (out->n_on) out->n_on[t] = N - nw - na;
+        }
+    }
+    return err[0] ? err[0] : SIM_OK;
+}

@@ -156,3 +156,43 @@ class Simulator:
                                                   "node_target", "link_in")))
         self._check(self.lib.sim_get_records(self.h, C.byref(r)))
         return d
+
+
+def rollout_static(sc, T: Optional[int] = None, device: int = 0, stream=None):
+    """Forward rollout through sim_rollout_static, the entry point that allocates
+    no device memory (for callers that may not allocate: graph capture, hosts
+    that own all device memory, real-time loops).  Host outputs."""
+    lib = nat.lib()
+    keep = []
+
+    def a(x, dt):
+        x = np.ascontiguousarray(np.asarray(x, dt))
+        keep.append(x)
+        return _p(x)
+
+    T = sc.T if T is None else T
+    net = nat.sim_network(V=sc.V, L=sc.L, tail=a(sc.tail, np.int32), head=a(sc.head, np.int32),
+                          length=a(sc.length, np.float32), q_fx=a(sc.q_fx, np.int32), F=sc.F,
+                          phi=a(sc.phi, np.float32), psi=a(sc.psi, np.float32), Z=sc.Z,
+                          node_zone=a(sc.node_zone, np.int32), dest_feat=a(sc.dest_feat, np.float32))
+    dem = nat.sim_demand(N=sc.N, origin=a(sc.origin, np.int32), dest_zone=a(sc.dest_zone, np.int32),
+                         dep_step=a(sc.dep_step, np.int32), od=a(sc.od, np.int32), n_od=sc.n_od,
+                         od_lambda=a(sc.od_lambda, np.float32))
+    par = nat.sim_params(u=a(sc.u, np.float32), kappa=a(sc.kappa, np.float32), alpha=a(sc.alpha, np.float32),
+                         beta=a(sc.beta, np.float32), cost=a(sc.cost, np.float32), w=a(sc.w, np.float32),
+                         alpha_origin=float(sc.alpha_origin))
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    opt = nat.sim_options(dt=sc.dt, dn=sc.dn, tau_gumbel=sc.tau, M=sc.M, eps_arr=sc.eps_arr,
+                          eps_tag=sc.eps_tag, seed=sc.seed, scenario_id=sc.scenario_id,
+                          obs_every=sc.obs_every, ckpt_every=0, route_cap=0, device=device, stream=stream)
+    nb = lib.sim_n_bins(T, sc.obs_every)
+    res = dict(counts=np.zeros((nb, sc.L), np.int32), speed=np.zeros((nb, sc.L), np.float32),
+               travel_time=np.zeros((nb, sc.L), np.float32), n_waiting=np.zeros(T + 1, np.int64),
+               n_on=np.zeros(T + 1, np.int64), n_arrived=np.zeros(T + 1, np.int64))
+    o = nat.sim_outputs(*(_p(res[k]) for k in ("counts", "speed", "travel_time", "n_waiting",
+                                               "n_on", "n_arrived")), 0)
+    rc = lib.sim_rollout_static(C.byref(net), C.byref(dem), C.byref(par), C.byref(opt), T, C.byref(o))
+    if rc != nat.SIM_OK:
+        raise nat.SimError(rc, "sim_rollout_static failed")
+    return res
