@@ -6,7 +6,7 @@ from __future__ import annotations
 
 from . import native as nat
 
-STAGES = (1024, 2048, 4096)
+STAGES = (2048, 4096, 6144)
 
 
 def set_stage(sim, slots: int) -> None:

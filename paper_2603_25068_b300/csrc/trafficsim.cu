@@ -97,9 +97,10 @@ struct sim_ctx {
     int *d_head = nullptr, *d_fifo_beg = nullptr;
     int *d_lo_idx = nullptr, *d_no_idx = nullptr;
     int n_lo = 0, n_no = 0;
-    int stage = 2048;                    // queue slots staged per link block
+    int stage = 4096;                    // queue slots staged per link block
     int stage_max = 0;                   // largest staged slot count of a block
     int *d_blk = nullptr;
+    int cap_blk = 0;
     std::vector<void *> allocs;
     size_t bytes = 0;
     // run state
@@ -170,13 +171,21 @@ static int build_blocks(sim_ctx *h) {
     }
     blk.push_back(h->L);
     smax = std::max(smax, slots);
-    if (!h->d_blk) TRY(dalloc(h, &h->d_blk, (size_t)h->L + 1));
+    // origin queues are spread over the blocks, at most kNodesPerBlock each
+    const int nlink_blocks = (int)blk.size() - 1;
+    const int nblk = std::max(nlink_blocks, (h->V + kNodesPerBlock - 1) / kNodesPerBlock);
+    while ((int)blk.size() < nblk + 1) blk.push_back(h->L);
+    if (!h->d_blk || h->cap_blk < (int)blk.size()) {
+        h->cap_blk = std::max((int)blk.size(), h->L + 1);
+        TRY(dalloc(h, &h->d_blk, (size_t)h->cap_blk));
+    }
     CU(cudaMemcpyAsync(h->d_blk, blk.data(), blk.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     h->d.blk_links = h->d_blk;
-    h->d.nblk = (int)blk.size() - 1;
+    h->d.nblk = nblk;
+    h->d.npb = (h->V + nblk - 1) / nblk;
     h->stage_max = smax;
-    const size_t smem = (size_t)2 * smax * sizeof(float);
+    const size_t smem = (size_t)smax * sizeof(float);
     CU(cudaFuncSetAttribute(k_step_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return SIM_OK;
 }
@@ -448,9 +457,8 @@ static void enqueue_reset(sim_ctx *h, int T) {
 }
 
 static void enqueue_a(sim_ctx *h, int t, int obs_only) {
-    const int node_blocks = obs_only ? 0 : (h->V + kBlockA - 1) / kBlockA;
-    const size_t smem = (size_t)2 * h->stage_max * sizeof(float);
-    k_step_a<<<h->d.nblk + node_blocks, kBlockA, smem, h->stream>>>(h->d, t, obs_only);
+    const size_t smem = (size_t)h->stage_max * sizeof(float);
+    k_step_a<<<h->d.nblk, kBlockA, smem, h->stream>>>(h->d, t, obs_only);
 }
 
 static void enqueue_b(sim_ctx *h, int t) {
@@ -851,7 +859,7 @@ extern "C" int sim_rollout_static(const sim_network *net, const sim_demand *dem,
         hs_fifo_aux[2 * k] = hs_fifo[k];
         hs_fifo_aux[2 * k + 1] = dem->dest_zone[hs_fifo[k]];
     }
-    const int stage = 2048;
+    const int stage = 4096;
     int nblk = 0, slots = 0, nl = 0, smax = 0;
     hs_blk[0] = 0;
     for (int j = 0; j < L; ++j) {
@@ -867,6 +875,9 @@ extern "C" int sim_rollout_static(const sim_network *net, const sim_demand *dem,
     }
     hs_blk[++nblk] = L;
     smax = std::max(smax, slots);
+    const int nblk_all = std::max(nblk, (V + kNodesPerBlock - 1) / kNodesPerBlock);
+    if (nblk_all > kStaticMaxL) return SIM_EOVERFLOW;
+    while (nblk < nblk_all) hs_blk[++nblk] = L;
     for (int j = 0; j < L; ++j) hs_alpha[j] = par->alpha[j];
     hs_alpha[L] = par->alpha_origin;
     // ---- device: carve the scratch (first call on a device looks up its address) ----
@@ -919,6 +930,7 @@ extern "C" int sim_rollout_static(const sim_network *net, const sim_demand *dem,
     if (!B.ok) return SIM_EOVERFLOW;
     d.geo = geo; d.tinfo = tinfo; d.loinfo = loinfo; d.noinfo = noinfo; d.lst = lst; d.lnode = lnode;
     d.alpha = alpha; d.dest_feat = dest_feat; d.blk_links = blk; d.nblk = nblk; d.no_ptr = no_ptr;
+    d.npb = (V + nblk - 1) / nblk;
     d.node_zone = node_zone; d.fifo_end = fifo_end; d.fifo_dep = fifo_dep; d.dest_zone = dest_zone;
     d.fifo_list = fifo_list; d.tag_tape = nullptr;
 #define SUP(dst, src, n) do { if ((n) > 0 && cudaMemcpyAsync((dst), (src), (size_t)(n) * sizeof(*(dst)), cudaMemcpyHostToDevice, s) != cudaSuccess) return SIM_ECUDA; } while (0)
@@ -959,12 +971,11 @@ extern "C" int sim_rollout_static(const sim_network *net, const sim_demand *dem,
     k_choice_info<<<(ne + 255) / 256, 256, 0, s>>>(d, lo_idx, n_lo, no_idx, L);
     const int nmax = std::max(std::max(L, V), std::max(N, 4));
     k_reset<<<(nmax + 255) / 256, 256, 0, s>>>(d, fifo_beg);
-    const size_t smem = (size_t)2 * smax * sizeof(float);
+    const size_t smem = (size_t)smax * sizeof(float);
     if (cudaFuncSetAttribute(k_step_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SIM_ECUDA;
-    const int node_blocks = (V + kBlockA - 1) / kBlockA;
     for (int t = 0; t < T; ++t) {
-        k_step_a<<<nblk + node_blocks, kBlockA, smem, s>>>(d, t, 0);
+        k_step_a<<<nblk, kBlockA, smem, s>>>(d, t, 0);
         k_step_b<<<(L + V + 255) / 256, 256, 0, s>>>(d, t);
     }
     k_step_a<<<nblk, kBlockA, smem, s>>>(d, T, 1);

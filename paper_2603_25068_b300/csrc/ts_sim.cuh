@@ -39,8 +39,9 @@ struct DevSim {
     const float4 *tinfo;
     const float *alpha;            // [L + 1]: merge priority; [L] = origin queues
     const float4 *loinfo;
-    const int *blk_links;          // [nblk + 1] first link of each link block
-    int nblk;                      // link blocks of k_step_a
+    const int *blk_links;          // [nblk + 1] first link of each block of k_step_a
+    int nblk;                      // blocks of k_step_a
+    int npb;                       // origin queues per block of k_step_a
     // static node / vehicle data
     const int *no_ptr, *node_zone;
     const float4 *noinfo;

@@ -44,7 +44,8 @@ namespace ts {
 
 // flags of link j for the coming step: bit 0 vacant, bit 1 leader arrives
 constexpr int kFlagVacant = 1, kFlagArrive = 2;
-constexpr int kLinksPerBlock = 64;     // at most this many links per link block
+constexpr int kLinksPerBlock = 64;     // at most this many links per block
+constexpr int kNodesPerBlock = 32;     // at most this many origin queues per block
 constexpr int kMaxSlotsStaged = 4;     // choice slots per link evaluated in P3
 constexpr int kBlockA = 256;           // threads of k_step_a
 constexpr int kU = 8;                  // staged elements per thread per pass
@@ -76,9 +77,18 @@ struct ABlockSmem {
     float mkey[kLinksPerBlock];         // candidate merge key alpha + g'
     int past[kLinksPerBlock];           // vehicles past the midpoint (observation)
     unsigned long long psum[kLinksPerBlock];  // position sum (observation)
+    float4 x4[kLinksPerBlock];          // new positions of vehicles 0, 1, n-2, n-1
     float4 lo[kLinksPerBlock][kMaxSlotsStaged];
     float key[kLinksPerBlock][kMaxSlotsStaged];
     int vacm[kLinksPerBlock][kMaxSlotsStaged];
+    // origin queues of the block's nodes
+    int4 nq[kNodesPerBlock];            // next vehicle, end of queue, out-links begin/end
+    int2 nlead[kNodesPerBlock];         // head (vehicle, zone); vehicle -1 if none departed
+    int nzone[kNodesPerBlock];          // zone of the node
+    float nmkey[kNodesPerBlock];
+    float4 nlo[kNodesPerBlock][kMaxSlotsStaged];
+    float nkey[kNodesPerBlock][kMaxSlotsStaged];
+    int nvacm[kNodesPerBlock][kMaxSlotsStaged];
 };
 
 // element e of the block's staged queues -> local link index (binary search)
@@ -97,17 +107,47 @@ __device__ __forceinline__ float choice_key(const DevSim &d, float4 e, int zone,
     return __fadd_rn(v, gumbel(d.key0, d.key1, vid, t, 0, slot));
 }
 
-__device__ __forceinline__ void link_block(const DevSim &d, int b, int t, bool obs_only, float *xs) {
+// Node-model choice of one candidate from its staged slots: argmax of the keys
+// (ties to the lowest slot), slots past the stage evaluated inline.  Returns the
+// target link, or kTgtBlocked when the chosen link is not vacant.
+__device__ __forceinline__ int choose(const DevSim &d, const float4 *lo, const float *key, const int *vacm,
+                                      const float4 *info, int deg, int zone, int vid, int t) {
+    float bk = -INFINITY;
+    int bm = -1, bv = 0;
+    for (int k = 0; k < deg; ++k) {
+        float kk;
+        int m, vm;
+        if (k < kMaxSlotsStaged) {
+            kk = key[k];
+            m = __float_as_int(lo[k].w);
+            vm = vacm[k];
+        } else {
+            const float4 e = info[k];
+            kk = choice_key(d, e, zone, vid, t, k);
+            m = __float_as_int(e.w);
+            vm = d.vac[m] & kFlagVacant;
+        }
+        if (bm < 0 || kk > bk) { bk = kk; bm = m; bv = vm; }
+    }
+    return bv ? bm : kTgtBlocked;
+}
+
+// One block of k_step_a: links [blk_links[b], blk_links[b+1]) and origin queues
+// [b npb, (b+1) npb), phase by phase (see the file header).
+__device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool obs_only, float *xs) {
     __shared__ ABlockSmem S;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int j0 = d.blk_links[b];
     const int nl = d.blk_links[b + 1] - j0;
+    const int n0 = b * d.npb;
+    const int nn = obs_only ? 0 : max(0, min(d.npb, d.V - n0));
+    const int ni = tid - kLinksPerBlock;             // origin-queue index of this thread
     const int p = t & 1;
     const float *pc = p ? d.pos1 : d.pos0;
     float *pn = p ? d.pos0 : d.pos1;
     const bool obs = obs_only || (t > 0 && t % d.obs_every == 0);
-    // ---------------- P1: link data, statistics, credit, candidate ----------------
+    // ---------------- P1: link data, statistics, credit, candidate; queue pointers ----------------
     if (tid < nl) {
         const int j = j0 + tid;
         const int4 q = d.lq[j];
@@ -127,6 +167,11 @@ __device__ __forceinline__ void link_block(const DevSim &d, int b, int t, bool o
         S.psum[tid] = 0ull;
         S.ent[tid] = 0;
         S.lead[tid] = make_int2(-1, -1);
+    } else if (ni >= 0 && ni < nn) {
+        const int n = n0 + ni;
+        S.nq[ni] = make_int4(d.fifo_ptr[n], d.fifo_end[n], d.no_ptr[n], d.no_ptr[n + 1]);
+        S.nzone[ni] = d.node_zone[n];
+        S.nlead[ni] = make_int2(-1, -1);
     }
     __syncthreads();
     if (tid < 32) {          // exclusive scan of queue lengths (nl <= 64)
@@ -145,7 +190,7 @@ __device__ __forceinline__ void link_block(const DevSim &d, int b, int t, bool o
     }
     __syncthreads();
     const int total = S.off[nl];
-    // ---------------- P2: stage positions, leader and choice records ----------------
+    // ---------------- P2: stage positions, leaders, queue heads and choice records ----------------
     // Warp w stages elements [pass + 32 kU w, pass + 32 kU (w + 1)); the link of
     // an element is tracked linearly from a binary search on the first one.
     for (int pass = 0; pass < total; pass += kBlockA * kU) {
@@ -175,28 +220,55 @@ __device__ __forceinline__ void link_block(const DevSim &d, int b, int t, bool o
         const int4 q = S.q[tid], st = S.st[tid];
         S.lead[tid] = d.saux[st.x + q.x];
         S.ent[tid] = d.sentry[st.x + q.x];
+    } else if (ni >= 0 && ni < nn) {
+        const int4 nq = S.nq[ni];
+        if (nq.x < nq.y) {                       // both loads issued before the test
+            const int dep = d.fifo_dep[nq.x];
+            const int2 head = d.fifo_list[nq.x];
+            if (dep <= t) S.nlead[ni] = head;
+        }
     }
     if (!obs_only) {
-        for (int c = tid; c < nl * kMaxSlotsStaged; c += kBlockA) {
-            const int li = c / kMaxSlotsStaged, k = c % kMaxSlotsStaged;
-            const int4 nd = S.nd[li];
-            if (S.cand[li] && k < nd.w - nd.z) S.lo[li][k] = d.loinfo[nd.z + k];
+        for (int c = tid; c < (kLinksPerBlock + kNodesPerBlock) * kMaxSlotsStaged; c += kBlockA) {
+            const int r = c / kMaxSlotsStaged, k = c % kMaxSlotsStaged;
+            if (r < kLinksPerBlock) {
+                if (r >= nl) continue;
+                const int4 nd = S.nd[r];
+                if (S.cand[r] && k < nd.w - nd.z) S.lo[r][k] = d.loinfo[nd.z + k];
+            } else {
+                const int q = r - kLinksPerBlock;
+                if (q >= nn) continue;
+                const int4 nq = S.nq[q];          // queue not empty: stage speculatively
+                if (nq.x < nq.y && k < nq.w - nq.z) S.nlo[q][k] = d.noinfo[nq.z + k];
+            }
         }
     }
     __syncthreads();
     // ---------------- P3: car-following, choice and merge keys ----------------
-    float *xn_s = xs + total;
     if (!obs_only) {
-        for (int c = tid; c < nl * kMaxSlotsStaged; c += kBlockA) {
-            const int li = c / kMaxSlotsStaged, k = c % kMaxSlotsStaged;
-            if (!S.cand[li]) continue;
-            const int4 nd = S.nd[li];
-            const int2 lead = S.lead[li];
-            if (k == 0) S.mkey[li] = __fadd_rn(S.alpha[li], gumbel(d.key0, d.key1, lead.x, t, 1, 0));
-            if (k >= nd.w - nd.z || nd.y == lead.y) continue;     // no slot / leaves to its destination
-            const float4 e = S.lo[li][k];
-            S.key[li][k] = choice_key(d, e, lead.y, lead.x, t, k);
-            S.vacm[li][k] = d.vac[__float_as_int(e.w)] & kFlagVacant;
+        for (int c = tid; c < (kLinksPerBlock + kNodesPerBlock) * kMaxSlotsStaged; c += kBlockA) {
+            const int r = c / kMaxSlotsStaged, k = c % kMaxSlotsStaged;
+            if (r < kLinksPerBlock) {
+                if (r >= nl || !S.cand[r]) continue;
+                const int4 nd = S.nd[r];
+                const int2 lead = S.lead[r];
+                if (k == 0) S.mkey[r] = __fadd_rn(S.alpha[r], gumbel(d.key0, d.key1, lead.x, t, 1, 0));
+                if (k >= nd.w - nd.z || nd.y == lead.y) continue;   // no slot / leaves to its destination
+                const float4 e = S.lo[r][k];
+                S.key[r][k] = choice_key(d, e, lead.y, lead.x, t, k);
+                S.vacm[r][k] = d.vac[__float_as_int(e.w)] & kFlagVacant;
+            } else {
+                const int q = r - kLinksPerBlock;
+                if (q >= nn) continue;
+                const int2 lead = S.nlead[q];
+                if (lead.x < 0) continue;
+                const int4 nq = S.nq[q];
+                if (k == 0) S.nmkey[q] = __fadd_rn(d.alpha[d.L], gumbel(d.key0, d.key1, lead.x, t, 1, 0));
+                if (k >= nq.w - nq.z || S.nzone[q] == lead.y) continue;
+                const float4 e = S.nlo[q][k];
+                S.nkey[q][k] = choice_key(d, e, lead.y, lead.x, t, k);
+                S.nvacm[q][k] = d.vac[__float_as_int(e.w)] & kFlagVacant;
+            }
         }
     }
     for (int pass = 0; pass < total; pass += kBlockA * kU) {
@@ -222,7 +294,11 @@ __device__ __forceinline__ void link_block(const DevSim &d, int b, int t, bool o
                     if (idx >= st.y) idx -= st.y;
                     pn[st.x + idx] = xn;
                     if (d.tag_tape) d.tag_tape[st.x + idx] = (int8_t)tag;
-                    xn_s[e] = xn;
+                    // keep the new positions of the first two and last two vehicles
+                    if (k == 0) S.x4[li].x = xn;
+                    if (k == 1) S.x4[li].y = xn;
+                    if (k == q.y - 2) S.x4[li].z = xn;
+                    if (k == q.y - 1) S.x4[li].w = xn;
                 }
             }
             if (obs) {      // block-uniform: midpoint count and position sum per link
@@ -240,7 +316,23 @@ __device__ __forceinline__ void link_block(const DevSim &d, int b, int t, bool o
         }
     }
     __syncthreads();
-    // ---------------- P4: per link: observation, choice, merge, flags ----------------
+    // ---------------- P4: observation, choice, merge, next-step flags ----------------
+    if (ni >= 0 && ni < nn) {            // origin queue heads
+        const int n = n0 + ni;
+        const int2 lead = S.nlead[ni];
+        int tgt = kTgtNone;
+        if (lead.x >= 0) {
+            if (S.nzone[ni] == lead.y) {
+                tgt = kTgtSink;
+            } else {
+                const int4 nq = S.nq[ni];
+                tgt = choose(d, S.nlo[ni], S.nkey[ni], S.nvacm[ni], d.noinfo + nq.z, nq.w - nq.z, lead.y, lead.x, t);
+                if (tgt >= 0) atomicMax(p ? &d.W1[tgt] : &d.W0[tgt], merge_word(S.nmkey[ni], lead.x));
+            }
+        }
+        d.nrec[n] = make_int2(lead.x, tgt);
+        return;
+    }
     if (tid >= nl) return;
     const int li = tid, j = j0 + tid;
     const int4 q = S.q[li];
@@ -271,40 +363,18 @@ __device__ __forceinline__ void link_block(const DevSim &d, int b, int t, bool o
         if (nd.y == lead.y) {
             tgt = kTgtSink;
         } else {
-            const int deg = nd.w - nd.z;
-            float bk = -INFINITY;
-            int bm = -1, bv = 0;
-            for (int k = 0; k < deg; ++k) {
-                float key;
-                int m, vm;
-                if (k < kMaxSlotsStaged) {
-                    key = S.key[li][k];
-                    m = __float_as_int(S.lo[li][k].w);
-                    vm = S.vacm[li][k];
-                } else {
-                    const float4 e = d.loinfo[nd.z + k];
-                    key = choice_key(d, e, lead.y, lead.x, t, k);
-                    m = __float_as_int(e.w);
-                    vm = d.vac[m] & kFlagVacant;
-                }
-                if (bm < 0 || key > bk) { bk = key; bm = m; bv = vm; }
-            }
-            if (bv) {
-                atomicMax(p ? &d.W1[bm] : &d.W0[bm], merge_word(S.mkey[li], lead.x));
-                tgt = bm;
-            } else {
-                tgt = kTgtBlocked;
-            }
+            tgt = choose(d, S.lo[li], S.key[li], S.vacm[li], d.loinfo + nd.z, nd.w - nd.z, lead.y, lead.x, t);
+            if (tgt >= 0) atomicMax(p ? &d.W1[tgt] : &d.W0[tgt], merge_word(S.mkey[li], lead.x));
         }
     }
     d.lq[j].z = S.credit[li];
     // flags of the next step for each outcome o = pop | push << 1
     const float M = d.M;
-    const int off = S.off[li];
-    const float x0 = n >= 1 ? xn_s[off] : 0.0f;
-    const float x1 = n >= 2 ? xn_s[off + 1] : 0.0f;
-    const float xt = n >= 1 ? xn_s[off + n - 1] : 0.0f;
-    const float xpt = n >= 2 ? xn_s[off + n - 2] : 0.0f;
+    const float4 x4 = S.x4[li];
+    const float x0 = n >= 1 ? x4.x : 0.0f;
+    const float x1 = n >= 2 ? x4.y : 0.0f;
+    const float xt = n >= 1 ? x4.w : 0.0f;
+    const float xpt = n >= 2 ? x4.z : 0.0f;
     int bits = 0;
     bits |= (n == 0 || vacant_after(xt, n >= 2 ? __fsub_rn(xpt, xt) : M, g)) << 0;
     bits |= (n <= 1 || vacant_after(xt, n >= 3 ? __fsub_rn(xpt, xt) : M, g)) << 1;
@@ -318,46 +388,9 @@ __device__ __forceinline__ void link_block(const DevSim &d, int b, int t, bool o
     d.crec[j] = make_int4(cand ? lead.x : -1, cand ? tgt : kTgtNone, (S.ent[li] << 8) | bits, __float_as_int(x0));
 }
 
-// Head of the origin queue of node n (a virtual inflow link of length 0).
-__device__ __forceinline__ void node_lane(const DevSim &d, int n, int t) {
-    const int p = t & 1;
-    const int ptr = d.fifo_ptr[n];
-    int tgt = kTgtNone, cv = -1;
-    if (ptr < d.fifo_end[n] && d.fifo_dep[ptr] <= t) {
-        const int2 a = d.fifo_list[ptr];
-        cv = a.x;
-        const int z = a.y;
-        if (d.node_zone[n] == z) {
-            tgt = kTgtSink;
-        } else {
-            const int b = d.no_ptr[n], e = d.no_ptr[n + 1];
-            float bk = 0.0f;
-            int mt = -1;
-            for (int k = 0; k < e - b; ++k) {
-                const float4 in = d.noinfo[b + k];
-                const float key = choice_key(d, in, z, cv, t, k);
-                if (mt < 0 || key > bk) { bk = key; mt = __float_as_int(in.w); }
-            }
-            if (d.vac[mt] & kFlagVacant) {
-                const float kp = __fadd_rn(d.alpha[d.L], gumbel(d.key0, d.key1, cv, t, 1, 0));
-                atomicMax(p ? &d.W1[mt] : &d.W0[mt], merge_word(kp, cv));
-                tgt = mt;
-            } else {
-                tgt = kTgtBlocked;
-            }
-        }
-    }
-    d.nrec[n] = make_int2(cv, tgt);
-}
-
 __global__ void __launch_bounds__(kBlockA, 6) k_step_a(DevSim d, int t, int obs_only) {
     extern __shared__ float xs[];
-    if ((int)blockIdx.x < d.nblk) {
-        link_block(d, blockIdx.x, t, obs_only != 0, xs);
-    } else if (!obs_only) {
-        const int n = ((int)blockIdx.x - d.nblk) * kBlockA + (int)threadIdx.x;
-        if (n < d.V) node_lane(d, n, t);
-    }
+    step_block(d, blockIdx.x, t, obs_only != 0, xs);
 }
 
 // Sum of v over the block added to *dst by one atomic (every thread must call).

@@ -79,7 +79,7 @@ def test_lockstep_long_queues(Simulator, stage):
     lockstep(Simulator, sc.copy(obs_every=70), 900, check_every=9, stage=stage)
 
 
-@pytest.mark.parametrize("stage", [256, 1024, 4096])
+@pytest.mark.parametrize("stage", [256, 1024, 4096, 8192])
 def test_rollout_graph_matches_oracle_city_small(Simulator, stage):
     sc = S.city_small()
     g = Simulator(sc)
