@@ -78,6 +78,8 @@ def _lib(precision: str):
             lib.or_gumbel.restype = C.c_double
             lib.or_gumbel.argtypes = [C.c_uint64, C.c_uint32, C.c_int32, C.c_int32, C.c_int, C.c_int]
             lib.or_philox4x32_10.argtypes = [P, P, P]
+            lib.or_backward.argtypes = [P, P, P, C.c_int] + [P] * 8
+            lib.or_positions.argtypes = [P, P]
             lib.or_log32.restype = C.c_float
             lib.or_log32.argtypes = [C.c_float]
             _loaded[precision] = lib
@@ -193,6 +195,26 @@ class OracleSim:
         self.lib.or_records(self.h, *(_p(d[k]) for k in ("link_cand", "link_target", "node_cand", "node_target",
                                                          "link_in", "link_margin", "node_margin", "merge_margin")))
         return d
+
+    def backward(self, ybar, xbarT=None, no_tg=False):
+        """Reverse mode of the last rollout (needs keep_history=True).  ybar:
+        [n_bins, L] adjoint of the bin counts; xbarT: optional [N] adjoint of the
+        final positions.  Returns a dict of parameter gradients (float64)."""
+        sc = self.sc
+        yb = np.ascontiguousarray(np.asarray(ybar, np.float64))
+        xb = None if xbarT is None else np.ascontiguousarray(np.asarray(xbarT, np.float64))
+        g = dict(u=np.zeros(sc.L), kappa=np.zeros(sc.L), alpha=np.zeros(sc.L), alpha_origin=np.zeros(1),
+                 beta=np.zeros(sc.L), cost=np.zeros(sc.L), w=np.zeros(sc.F), od_lambda=np.zeros(sc.n_od))
+        rc = self.lib.or_backward(self.h, _p(yb), _p(xb), 1 if no_tg else 0,
+                                  *(_p(g[k]) for k in ("u", "kappa", "alpha", "alpha_origin", "beta", "cost",
+                                                       "w", "od_lambda")))
+        self._check(rc)
+        return g
+
+    def positions(self):
+        x = np.zeros(self.sc.N, np.float64)
+        self.lib.or_positions(self.h, _p(x))
+        return x
 
     def route(self, i):
         n = self.lib.or_route(self.h, i, None, None, 0)

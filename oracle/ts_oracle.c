@@ -777,3 +777,249 @@ void or_destroy(or_sim *o)
     free(o->route_len); free(o->route_cap); free(o->route_t); free(o->route_m);
     free(o);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Reverse mode of the straight-through / trajectory-grafting surrogate       */
+/* ------------------------------------------------------------------------- */
+/*
+ * Every discrete decision of the recorded rollout is frozen (argmaxes, masks,
+ * comparisons, car-following branch tags) and every stop_gradient(v) is the
+ * recorded value; the result is the derivative jax.grad takes of the dense
+ * formulation (SI-A Alg. S1, SI-B Alg. S2) with the readings in the file header.
+ * The dense state X[i, j] (agent i on link j, -M elsewhere) is represented by
+ *   xbar[i]     the adjoint of agent i's valid entry (its current link, or its
+ *               origin queue = a virtual inflow link of length 0), and
+ *   eadj[i][r]  the adjoint of X[i, m_r] right after agent i's r-th entry: by
+ *               the identity of an invalid slot through time, the adjoint of
+ *               the slot (i, m) at any earlier time since i last left m is the
+ *               adjoint right after i's next entry into m (0 if it never enters).
+ * Reverse step t, from the state after the step back to its start:
+ *   (1) observation at t+1 (SI-D): dC_j/dx_i = s sigma (1 - sigma), s = 5/L_j;
+ *       demand weights 1 + (lambda - sg lambda)/lambda give dC/dlambda;
+ *   (2) node model (SI-B): for the valid candidates of each target m,
+ *       abar_i = M (Ebar_i(m) - Xbar_i(l_i)) - x_i Xbar_i(l_i)   (Eq. transfer),
+ *       merge softmax pi' over (alpha_src + g')/tau -> alpha, lbar;
+ *       link-choice softmax pi over (V + g)/tau -> U_m = beta/c + w.phi, G_m = w.psi;
+ *       the winner's old entry receives its new entry's adjoint (grafting);
+ *   (3) car-following (SI-A) by tag: free x' = x + u dt, cong x' = x_lead - s,
+ *       stop x' = x; the TG clip passes the adjoint unchanged.
+ */
+static double sigmoid_d(double z) { return 1.0 / (1.0 + exp(-z)); }
+
+/* adjoint right after vehicle i's first entry into link m at a step > t
+ * (entries are in step order); 0 if it never enters m again */
+static double next_entry_adj(const or_sim *o, double **eadj, int i, int m, int t)
+{
+    for (int r = 0; r < o->route_len[i]; ++r)
+        if (o->route_t[i][r] > t && o->route_m[i][r] == m) return eadj[i][r];
+    return 0.0;
+}
+
+int or_backward(or_sim *o, const double *ybar, const double *xbarT, int no_tg,
+                double *d_u, double *d_kappa, double *d_alpha, double *d_alpha_origin,
+                double *d_beta, double *d_cost, double *d_w, double *d_lambda)
+{
+    const or_scenario *sc = &o->sc;
+    const int N = sc->N, L = sc->L, V = sc->V, F = sc->F, T = o->T;
+    if (!o->keep_hist || !o->hist || o->t != T) { fail(o, "backward needs a full recorded rollout", o->t, T); return -1; }
+    const double M = (double)sc->M, tau = (double)sc->tau, dt = (double)sc->dt;
+    const int nb = o->n_bins;
+    double *xbar = (double *)xcalloc(N, sizeof(double));
+    double **eadj = (double **)xcalloc(N, sizeof(double *));
+    for (int i = 0; i < N; ++i) eadj[i] = (double *)xcalloc(o->route_len[i] ? o->route_len[i] : 1, sizeof(double));
+    double *gu = (double *)xcalloc(L, sizeof(double)), *gs = (double *)xcalloc(L, sizeof(double));
+    double *ga = (double *)xcalloc(L, sizeof(double)), *gU = (double *)xcalloc(L, sizeof(double));
+    double *gG = (double *)xcalloc(L, sizeof(double)), *glam = (double *)xcalloc(sc->n_od ? sc->n_od : 1, sizeof(double));
+    double gao = 0.0;
+    /* adjoint of C_j at the end of each bin: Cbar[b][j] = ybar[b][j] - ybar[b+1][j] */
+    double *Cbar = (double *)xcalloc((size_t)nb * L, sizeof(double));
+    for (int b = 0; b < nb; ++b)
+        for (int j = 0; j < L; ++j)
+            Cbar[(size_t)b * L + j] = ybar[(size_t)b * L + j] - (b + 1 < nb ? ybar[(size_t)(b + 1) * L + j] : 0.0);
+    /* exits at step t count in every C_j(t_b) with t_b >= t + 1: suffix of Cbar */
+    double *Csuf = (double *)xcalloc((size_t)(nb + 1) * L, sizeof(double));
+    for (int b = nb - 1; b >= 0; --b)
+        for (int j = 0; j < L; ++j) Csuf[(size_t)b * L + j] = Csuf[(size_t)(b + 1) * L + j] + Cbar[(size_t)b * L + j];
+    if (xbarT)
+        for (int i = 0; i < N; ++i) if (o->vlink[i] >= 0) xbar[i] = xbarT[i];
+    int *order = (int *)xcalloc(N, sizeof(int));
+    int *cnt = (int *)xcalloc(L + 1, sizeof(int));
+    double *xn = (double *)xcalloc(N, sizeof(double));
+
+    for (int t = T - 1; t >= 0; --t) {
+        or_hist *H = &o->hist[t];
+        const int32_t *vl1 = (t + 1 < T) ? o->hist[t + 1].vlink : o->vlink;
+        const real *x1 = (t + 1 < T) ? o->hist[t + 1].xpre : o->vx;
+        /* (1) observation at time t + 1 */
+        if ((t + 1) % sc->obs_every == 0 || t + 1 == T) {
+            const int b = t / sc->obs_every;
+            for (int i = 0; i < N; ++i) {
+                const int j = vl1[i];
+                if (j < 0) continue;
+                const double cb = Cbar[(size_t)b * L + j];
+                const double len = (double)o->length[j], s5 = 5.0 / len;
+                const double x = (double)x1[i];
+                const double sg = sigmoid_d(s5 * (x - 0.5 * len));
+                xbar[i] += cb * s5 * sg * (1.0 - sg);
+                if (x >= (double)o->half_len[j]) glam[o->od[i]] += cb / (double)o->od_lambda[o->od[i]];
+            }
+        }
+        /* (2) node model of step t */
+        or_cand *cand = H->cand;
+        const int nc = H->n_cand;
+        /* entries of step t: record the adjoint right after the entry */
+        for (int ci = 0; ci < nc; ++ci) {
+            or_cand *c = &cand[ci];
+            if (!c->won) continue;
+            const int i = c->vid;
+            for (int r = 0; r < o->route_len[i]; ++r)
+                if (o->route_t[i][r] == t) { eadj[i][r] = xbar[i]; break; }
+        }
+        /* exits of step t (transfers and sinks): demand weight of the exit count */
+        for (int ci = 0; ci < nc; ++ci) {
+            or_cand *c = &cand[ci];
+            if (c->src_link < 0 || !(c->won || c->target == TGT_SINK)) continue;
+            const int b0 = t / sc->obs_every;      /* bins whose end is >= t + 1 */
+            glam[o->od[c->vid]] += Csuf[(size_t)b0 * L + c->src_link] / (double)o->od_lambda[o->od[c->vid]];
+        }
+        for (int m = 0; m < L; ++m) {
+            /* valid candidates of target m */
+            int nm = 0;
+            for (int ci = 0; ci < nc; ++ci) if (cand[ci].target == m && cand[ci].valid) nm++;
+            if (nm == 0) continue;
+            double *key = (double *)xcalloc(nm, sizeof(double));
+            double *abar = (double *)xcalloc(nm, sizeof(double));
+            int *idx = (int *)xcalloc(nm, sizeof(int));
+            int k = 0;
+            double kmax = -INFINITY;
+            for (int ci = 0; ci < nc; ++ci) {
+                or_cand *c = &cand[ci];
+                if (c->target != m || !c->valid) continue;
+                const int i = c->vid;
+                const double al = c->src_link >= 0 ? (double)o->alpha[c->src_link] : (double)sc->alpha_origin;
+                key[k] = (al + (double)gumbel(sc->seed, sc->scenario_id, i, t, 1, 0)) / tau;
+                if (key[k] > kmax) kmax = key[k];
+                double Enew, Xold;
+                if (c->won) {
+                    int rw = -1;
+                    for (int r = 0; r < o->route_len[i]; ++r) if (o->route_t[i][r] == t) { rw = r; break; }
+                    Enew = xbar[i];
+                    Xold = 0.0;
+                    if (c->src_link >= 0)
+                        for (int r = rw + 1; r < o->route_len[i]; ++r)
+                            if (o->route_m[i][r] == c->src_link) { Xold = eadj[i][r]; break; }
+                } else {
+                    Enew = next_entry_adj(o, eadj, i, m, t);
+                    Xold = xbar[i];
+                }
+                abar[k] = M * (Enew - Xold) - (double)c->x * Xold;
+                idx[k] = ci;
+                k++;
+            }
+            double zs = 0.0;
+            for (k = 0; k < nm; ++k) { key[k] = exp(key[k] - kmax); zs += key[k]; }
+            double S = 0.0;
+            for (k = 0; k < nm; ++k) { key[k] /= zs; S += key[k] * abar[k]; }
+            for (k = 0; k < nm; ++k) {
+                or_cand *c = &cand[idx[k]];
+                const double vbar = key[k] * (abar[k] - S) / tau;         /* adjoint of V'_i = p_i */
+                const double al = c->src_link >= 0 ? (double)o->alpha[c->src_link] : (double)sc->alpha_origin;
+                if (c->src_link >= 0) ga[c->src_link] += vbar; else gao += vbar;
+                const double lbar = al * vbar;                            /* adjoint of l_i at m */
+                /* link choice of this candidate: pi = softmax((V + g)/tau) over its choice set */
+                const int i = c->vid, z = o->dest_zone[i];
+                const int32_t *set; int deg;
+                if (c->src_link >= 0) { set = o->lo_idx + o->lo_ptr[c->src_link]; deg = o->lo_ptr[c->src_link + 1] - o->lo_ptr[c->src_link]; }
+                else { set = o->no_idx + o->no_ptr[c->src_node]; deg = o->no_ptr[c->src_node + 1] - o->no_ptr[c->src_node]; }
+                double *pk = (double *)xcalloc(deg, sizeof(double));
+                double pmax = -INFINITY, ps = 0.0;
+                for (int q = 0; q < deg; ++q) {
+                    pk[q] = ((double)utility(o, set[q], z) + (double)gumbel(sc->seed, sc->scenario_id, i, t, 0, q)) / tau;
+                    if (pk[q] > pmax) pmax = pk[q];
+                }
+                for (int q = 0; q < deg; ++q) { pk[q] = exp(pk[q] - pmax); ps += pk[q]; }
+                for (int q = 0; q < deg; ++q) pk[q] /= ps;
+                for (int q = 0; q < deg; ++q) {
+                    const double Vbar = pk[q] * ((q == c->slot ? 1.0 : 0.0) - pk[c->slot]) * lbar / tau;
+                    const int mq = set[q];
+                    gU[mq] += Vbar;
+                    gG[mq] += Vbar * (double)o->dest_feat[(size_t)z * V + o->head[mq]];
+                }
+                free(pk);
+            }
+            free(key); free(abar); free(idx);
+        }
+        /* grafting: a winner's old entry gets its new entry's adjoint (xbar[i]
+         * carries over unchanged); without TG the old entry gets nothing */
+        if (no_tg)
+            for (int ci = 0; ci < nc; ++ci) if (cand[ci].won) xbar[cand[ci].vid] = 0.0;
+        /* (3) car-following of step t, per link in the order of argsort(-x) */
+        memset(cnt, 0, (size_t)(L + 1) * sizeof(int));
+        for (int i = 0; i < N; ++i) if (H->vlink[i] >= 0) cnt[H->vlink[i] + 1]++;
+        for (int j = 0; j < L; ++j) cnt[j + 1] += cnt[j];
+        {
+            int *fill = (int *)xcalloc(L, sizeof(int));
+            for (int i = 0; i < N; ++i) {
+                const int j = H->vlink[i];
+                if (j >= 0) order[cnt[j] + fill[j]++] = i;
+            }
+            free(fill);
+        }
+        for (int j = 0; j < L; ++j) {
+            const int b = cnt[j], e = cnt[j + 1];
+            /* sort this link's vehicles by time-t position, descending */
+            for (int a = b + 1; a < e; ++a) {
+                int v = order[a], q = a - 1;
+                while (q >= b && (H->xpre[order[q]] < H->xpre[v])) { order[q + 1] = order[q]; --q; }
+                order[q + 1] = v;
+            }
+            for (int q = b; q < e; ++q) {
+                const int i = order[q];
+                double g = xbar[i];
+                if (no_tg) {
+                    const real xa = (q == b) ? (real)sc->M : H->xpre[order[q - 1]] - H->xpre[i];
+                    const real dd = xa - o->s[j];
+                    const real dx = rmin(o->udt[j], rmax(dd, (real)0));
+                    if (H->xpre[i] + dx > o->len[j]) g = 0.0;         /* clipped: constant L */
+                }
+                xn[i] = g;
+            }
+            for (int q = b; q < e; ++q) {
+                const int i = order[q];
+                const int tag = H->tag[i];
+                double pre = (tag == TAG_CONG) ? 0.0 : xn[i];
+                if (q + 1 < e && H->tag[order[q + 1]] == TAG_CONG) pre += xn[order[q + 1]];
+                if (tag == TAG_FREE) gu[j] += dt * xn[i];
+                if (tag == TAG_CONG) gs[j] -= xn[i];
+                xbar[i] = pre;
+            }
+        }
+    }
+    for (int j = 0; j < L; ++j) {
+        const double kap = (double)o->kappa[j], c = (double)o->cost[j], be = (double)o->beta[j];
+        if (d_u) d_u[j] = gu[j];
+        if (d_kappa) d_kappa[j] = gs[j] * (-(double)sc->dn / (kap * kap));
+        if (d_alpha) d_alpha[j] = ga[j];
+        if (d_beta) d_beta[j] = gU[j] / c;
+        if (d_cost) d_cost[j] = -gU[j] * be / (c * c);
+    }
+    if (d_alpha_origin) *d_alpha_origin = gao;
+    if (d_w)
+        for (int f = 0; f < F; ++f) {
+            double s = 0.0;
+            for (int j = 0; j < L; ++j)
+                s += gU[j] * (double)o->phi[(size_t)j * F + f] + gG[j] * (double)o->psi[(size_t)j * F + f];
+            d_w[f] = s;
+        }
+    if (d_lambda) for (int k = 0; k < sc->n_od; ++k) d_lambda[k] = glam[k];
+    for (int i = 0; i < N; ++i) free(eadj[i]);
+    free(eadj); free(xbar); free(gu); free(gs); free(ga); free(gU); free(gG); free(glam);
+    free(Cbar); free(Csuf); free(order); free(cnt); free(xn);
+    return 0;
+}
+
+/* positions of the current state per vehicle (0 off-network) */
+void or_positions(const or_sim *o, double *x)
+{
+    for (int i = 0; i < o->sc.N; ++i) x[i] = o->vlink[i] >= 0 ? (double)o->vx[i] : 0.0;
+}
