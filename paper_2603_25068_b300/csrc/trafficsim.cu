@@ -3,7 +3,7 @@
 // into a CUDA graph of 2T + 2 kernels (reset, T x (k_step_a, k_step_b), final
 // observation).
 #include "../../include/trafficsim.h"
-#include "ts_step.cuh"
+#include "ts_backward.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -109,6 +109,26 @@ struct sim_ctx {
     int cap_T = 0;                       // capacity of the per-T output buffers
     std::map<int, cudaGraphExec_t> graphs;
     std::string err;
+    // reverse mode (options.ckpt_every > 0)
+    int K = 0;                           // steps per checkpoint segment
+    int route_cap = 0;
+    bool tape_ready = false;             // last call was a recorded sim_rollout
+    int cap_seg = 0;                     // checkpoints allocated
+    BwdDev b{};
+    struct Ckpt {
+        int4 *lq = nullptr, *lstat = nullptr;
+        int *vac = nullptr, *sentry = nullptr, *fifo = nullptr, *vstate = nullptr;
+        float *pos = nullptr;
+        int2 *saux = nullptr;
+        longlong2 *lpos = nullptr;
+    } ck;
+    int *d_dummy = nullptr;              // step counters of recomputed steps
+    int *d_od = nullptr;
+    float *d_od_lambda = nullptr;
+    double *d_Cbar = nullptr, *d_Csuf = nullptr;
+    int cap_bins = 0;
+    float *d_dxT = nullptr, *d_ybar = nullptr;
+    float *d_gout = nullptr;             // staging of gradient outputs
 };
 
 static std::string g_create_err;
@@ -393,6 +413,47 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
     CU(cudaMemsetAsync(d.saux, 0xff, (size_t)S * sizeof(int2), h->stream));
     CU(cudaMemsetAsync(d.sentry, 0, (size_t)S * sizeof(int), h->stream));
     d.tag_tape = nullptr;
+    d.route_log = nullptr;
+    d.route_len = nullptr;
+    d.route_cap = 0;
+    if (opt->ckpt_every > 0) {
+        if (opt->route_cap <= 0) return fail(h, SIM_EINVAL, "route_cap must be positive with ckpt_every > 0");
+        h->K = opt->ckpt_every;
+        h->route_cap = opt->route_cap;
+        const int K = h->K;
+        BwdDev &b = h->b;
+        b.S = (int)S; b.K = K; b.cap = h->route_cap; b.n_od = dem->n_od;
+        b.tau = opt->tau_gumbel;
+        b.inv_tau = 1.0 / (double)opt->tau_gumbel;
+        TRY(dalloc(h, &d.route_log, (size_t)N * h->route_cap));
+        TRY(dalloc(h, &d.route_len, N));
+        d.route_cap = h->route_cap;
+        b.route_log = d.route_log;
+        b.route_len = d.route_len;
+        TRY(dalloc(h, &b.tpos, (size_t)(K + 1) * S));
+        TRY(dalloc(h, &b.tvid, (size_t)(K + 1) * S));
+        TRY(dalloc(h, &b.tlq, (size_t)(K + 1) * L));
+        TRY(dalloc(h, &b.ttag, (size_t)K * S));
+        TRY(dalloc(h, &b.tcrec, (size_t)K * L));
+        TRY(dalloc(h, &b.tnrec, (size_t)K * V));
+        TRY(dalloc(h, &b.tW, (size_t)K * L));
+        TRY(dalloc(h, &b.xbar, N));
+        TRY(dalloc(h, &b.eadj, (size_t)N * h->route_cap));
+        TRY(dalloc(h, &b.gu, L)); TRY(dalloc(h, &b.gs, L)); TRY(dalloc(h, &b.ga, L));
+        TRY(dalloc(h, &b.gU, L)); TRY(dalloc(h, &b.gG, L)); TRY(dalloc(h, &b.gao, 1));
+        TRY(dalloc(h, &b.glam, std::max(dem->n_od, 1)));
+        TRY(dalloc(h, &b.Z, L)); TRY(dalloc(h, &b.SA, L));
+        TRY(dalloc(h, &b.ebuf, (size_t)L + V)); TRY(dalloc(h, &b.abuf, (size_t)L + V));
+        TRY(upload(h, &h->d_od, dem->od, N));
+        TRY(upload(h, &h->d_od_lambda, dem->od_lambda, std::max(dem->n_od, 1)));
+        for (int k = 0; k < dem->n_od; ++k)
+            if (!(dem->od_lambda[k] > 0.0f)) return fail(h, SIM_EINVAL, "od_lambda must be positive");
+        for (int i = 0; i < N; ++i)
+            if (dem->od[i] < 0 || dem->od[i] >= dem->n_od) return fail(h, SIM_EINVAL, "od out of range");
+        b.od = h->d_od;
+        b.od_lambda = h->d_od_lambda;
+        TRY(dalloc(h, &h->d_gout, (size_t)5 * L + std::max(F, 1) + 1 + std::max(dem->n_od, 1)));
+    }
     TRY(build_blocks(h));
     TRY(upload_params(h, par));
     CU(cudaStreamSynchronize(h->stream));
@@ -436,16 +497,54 @@ extern "C" int sim_set_params(sim_handle h, const sim_params *par) {
 // per-horizon buffers: outputs and step counters
 static int ensure_T(sim_ctx *h, int T) {
     if (T <= h->cap_T) return SIM_OK;
+    const int nb = sim_n_bins(T, h->opt.obs_every);
     // outputs are re-pointed: cached graphs bake the old pointers
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.second);
     h->graphs.clear();
-    const int nb = sim_n_bins(T, h->opt.obs_every);
     TRY(dalloc(h, &h->d.out_counts, (size_t)nb * h->L));
     TRY(dalloc(h, &h->d.out_speed, (size_t)nb * h->L));
     TRY(dalloc(h, &h->d.out_tt, (size_t)nb * h->L));
     TRY(dalloc(h, &h->d.step_delta, (size_t)4 * T));
+    if (h->K > 0) {
+        TRY(dalloc(h, &h->d_dummy, (size_t)4 * T));
+        const int nseg = (T + h->K - 1) / h->K;
+        if (nseg > h->cap_seg) {
+            const size_t L = h->L, S = h->S, V = h->V, N = h->N;
+            TRY(dalloc(h, &h->ck.lq, nseg * L)); TRY(dalloc(h, &h->ck.lstat, nseg * L));
+            TRY(dalloc(h, &h->ck.vac, nseg * L)); TRY(dalloc(h, &h->ck.sentry, nseg * S));
+            TRY(dalloc(h, &h->ck.fifo, nseg * V)); TRY(dalloc(h, &h->ck.vstate, nseg * N));
+            TRY(dalloc(h, &h->ck.pos, nseg * S)); TRY(dalloc(h, &h->ck.saux, nseg * S));
+            TRY(dalloc(h, &h->ck.lpos, nseg * L));
+            h->cap_seg = nseg;
+        }
+        if (nb > h->cap_bins) {
+            TRY(dalloc(h, &h->d_Cbar, (size_t)nb * h->L));
+            TRY(dalloc(h, &h->d_Csuf, (size_t)(nb + 1) * h->L));
+            TRY(dalloc(h, &h->d_ybar, (size_t)nb * h->L));
+            h->cap_bins = nb;
+        }
+    }
     h->cap_T = T;
     return SIM_OK;
+}
+
+// checkpoint s <-> dynamic state at the start of step s K (positions in buffer cur)
+static void ckpt_copy(sim_ctx *h, int s, int cur, bool save) {
+    const size_t L = h->L, S = h->S, V = h->V, N = h->N;
+    auto cp = [&](void *state, void *ck, size_t bytes) {
+        if (save) cudaMemcpyAsync(ck, state, bytes, cudaMemcpyDeviceToDevice, h->stream);
+        else cudaMemcpyAsync(state, ck, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    };
+    DevSim &d = h->d;
+    cp(d.lq, h->ck.lq + s * L, L * sizeof(int4));
+    cp(d.lstat, h->ck.lstat + s * L, L * sizeof(int4));
+    cp(d.vac, h->ck.vac + s * L, L * sizeof(int));
+    cp(d.sentry, h->ck.sentry + s * S, S * sizeof(int));
+    cp(d.fifo_ptr, h->ck.fifo + s * V, V * sizeof(int));
+    cp(d.vstate, h->ck.vstate + s * N, N * sizeof(int));
+    cp(cur ? d.pos1 : d.pos0, h->ck.pos + s * S, S * sizeof(float));
+    cp(d.saux, h->ck.saux + s * S, S * sizeof(int2));
+    cp(d.lpos, h->ck.lpos + s * L, L * sizeof(longlong2));
 }
 
 static void enqueue_reset(sim_ctx *h, int T) {
@@ -454,6 +553,7 @@ static void enqueue_reset(sim_ctx *h, int T) {
     const int nb = sim_n_bins(T, h->opt.obs_every);
     cudaMemsetAsync(h->d.out_counts, 0, (size_t)nb * h->L * sizeof(int), h->stream);
     k_reset<<<(nmax + 255) / 256, 256, 0, h->stream>>>(h->d, h->d_fifo_beg);
+    if (h->d.route_len) cudaMemsetAsync(h->d.route_len, 0, (size_t)h->N * sizeof(int), h->stream);
 }
 
 static void enqueue_a(sim_ctx *h, int t, int obs_only) {
@@ -492,6 +592,7 @@ extern "C" int sim_reset(sim_handle h, int32_t T) {
     TRY(ensure_T(h, T));
     enqueue_reset(h, T);
     CU(cudaGetLastError());
+    h->tape_ready = false;
     h->t = 0;
     h->T = T;
     h->n_bins = sim_n_bins(T, h->opt.obs_every);
@@ -557,7 +658,10 @@ extern "C" int sim_rollout(sim_handle h, int32_t T, sim_outputs *out) {
         cudaGraph_t g;
         CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         enqueue_reset(h, T);
-        for (int t = 0; t < T; ++t) enqueue_step(h, t);
+        for (int t = 0; t < T; ++t) {
+            if (h->K > 0 && t % h->K == 0) ckpt_copy(h, t / h->K, t & 1, true);
+            enqueue_step(h, t);
+        }
         enqueue_obs_final(h, T);
         cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
         if (ce != cudaSuccess) return fail(h, SIM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
@@ -572,6 +676,7 @@ extern "C" int sim_rollout(sim_handle h, int32_t T, sim_outputs *out) {
     h->T = T;
     h->n_bins = sim_n_bins(T, h->opt.obs_every);
     h->reset_done = true;
+    h->tape_ready = h->K > 0;
     TRY(copy_outputs(h, out));
     if (out && out->on_device) return SIM_OK;    // asynchronous: no host sync
     return check_device_error(h);
@@ -595,6 +700,7 @@ extern "C" int sim_profile_rollout(sim_handle h, int32_t T, sim_outputs *out, do
     TRY(ensure_T(h, T));
     std::vector<cudaEvent_t> ev((size_t)4 * T + 2);
     for (auto &e : ev) CU(cudaEventCreate(&e));
+    h->tape_ready = false;
     enqueue_reset(h, T);
     for (int t = 0; t < T; ++t) {
         CU(cudaEventRecord(ev[4 * t + 0], h->stream));
@@ -638,9 +744,98 @@ extern "C" int sim_get_outputs(sim_handle h, sim_outputs *out) {
     return copy_outputs(h, out);
 }
 
-extern "C" int sim_backward(sim_handle h, const float *, const float *, int32_t, sim_grads *) {
-    if (!h) return SIM_EINVAL;
-    return fail(h, SIM_ESTATE, "sim_backward: no recorded rollout");
+extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *dL_dxT,
+                            int32_t inputs_on_device, sim_grads *out) {
+    if (!h || !dL_dcounts || !out) return SIM_EINVAL;
+    if (h->K <= 0) return fail(h, SIM_ESTATE, "sim_backward needs options.ckpt_every > 0");
+    if (!h->tape_ready) return fail(h, SIM_ESTATE, "sim_backward needs a recorded sim_rollout just before");
+    CU(cudaSetDevice(h->device));
+    TRY(check_device_error(h));
+    const int T = h->T, K = h->K, L = h->L, V = h->V, N = h->N, S = h->S, F = h->F;
+    const int nb = h->n_bins, obs = h->opt.obs_every;
+    const int nseg = (T + K - 1) / K;
+    // adjoint of C_j at the end of each bin and its suffix sums (host, small)
+    std::vector<float> yb((size_t)nb * L);
+    CU(cudaMemcpyAsync(yb.data(), dL_dcounts, yb.size() * sizeof(float),
+                       inputs_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    std::vector<double> cb((size_t)nb * L), cs((size_t)(nb + 1) * L, 0.0);
+    for (int bb = 0; bb < nb; ++bb)
+        for (int j = 0; j < L; ++j)
+            cb[(size_t)bb * L + j] = (double)yb[(size_t)bb * L + j] -
+                                     (bb + 1 < nb ? (double)yb[(size_t)(bb + 1) * L + j] : 0.0);
+    for (int bb = nb - 1; bb >= 0; --bb)
+        for (int j = 0; j < L; ++j) cs[(size_t)bb * L + j] = cs[(size_t)(bb + 1) * L + j] + cb[(size_t)bb * L + j];
+    CU(cudaMemcpyAsync(h->d_Cbar, cb.data(), cb.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(h->d_Csuf, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    BwdDev b = h->b;
+    b.Cbar = h->d_Cbar;
+    b.Csuf = h->d_Csuf;
+    const float *dxT = nullptr;
+    if (dL_dxT) {
+        if (!h->d_dxT) TRY(dalloc(h, &h->d_dxT, N));
+        CU(cudaMemcpyAsync(h->d_dxT, dL_dxT, (size_t)N * sizeof(float),
+                           inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+        dxT = h->d_dxT;
+    }
+    for (double *p : {b.gu, b.gs, b.ga, b.gU, b.gG}) CU(cudaMemsetAsync(p, 0, (size_t)L * sizeof(double), h->stream));
+    CU(cudaMemsetAsync(b.gao, 0, sizeof(double), h->stream));
+    CU(cudaMemsetAsync(b.glam, 0, (size_t)std::max(b.n_od, 1) * sizeof(double), h->stream));
+    CU(cudaMemsetAsync(b.eadj, 0, (size_t)N * h->route_cap * sizeof(double), h->stream));
+    k_bwd_init<<<(N + 255) / 256, 256, 0, h->stream>>>(h->d, b, dxT);
+    // recomputation: no route log, counters into a scratch array
+    DevSim dr = h->d;
+    dr.route_log = nullptr;
+    dr.step_delta = h->d_dummy;
+    const size_t smem_a = (size_t)h->stage_max * sizeof(float);
+    const size_t smem_cf = (size_t)h->stage_max * (sizeof(double) + sizeof(int) + 1);
+    CU(cudaFuncSetAttribute(k_bwd_cf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cf));
+    const int gS = (std::max(S, L) + 255) / 256, gLV = (L + V + 255) / 256, gN = (std::max(L, V) + 255) / 256;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int t0 = sg * K, t1 = std::min(T, t0 + K);
+        ckpt_copy(h, sg, t0 & 1, false);
+        CU(cudaMemsetAsync((t0 & 1) ? h->d.W1 : h->d.W0, 0, (size_t)L * sizeof(unsigned long long), h->stream));
+        k_tape_pre<<<gS, 256, 0, h->stream>>>(dr, b, 0, t0 & 1);
+        for (int t = t0; t < t1; ++t) {
+            dr.tag_tape = b.ttag + (size_t)(t - t0) * S;
+            k_step_a<<<dr.nblk, kBlockA, smem_a, h->stream>>>(dr, t, 0);
+            k_step_b<<<(L + V + 255) / 256, 256, 0, h->stream>>>(dr, t);
+            k_tape_post<<<gN, 256, 0, h->stream>>>(dr, b, t - t0, t & 1);
+            k_tape_pre<<<gS, 256, 0, h->stream>>>(dr, b, t - t0 + 1, (t + 1) & 1);
+        }
+        for (int t = t1 - 1; t >= t0; --t) {
+            const int rec = t - t0;
+            if ((t + 1) % obs == 0 || t + 1 == T)
+                k_bwd_obs<<<(L * 32 + 255) / 256, 256, 0, h->stream>>>(dr, b, rec + 1, t / obs);
+            CU(cudaMemsetAsync(b.Z, 0, (size_t)L * sizeof(double), h->stream));
+            CU(cudaMemsetAsync(b.SA, 0, (size_t)L * sizeof(double), h->stream));
+            k_bwd_node_z<<<gLV, 256, 0, h->stream>>>(dr, b, t, rec, t / obs);
+            k_bwd_node_g<<<gLV, 256, 0, h->stream>>>(dr, b, t, rec);
+            k_bwd_cf<<<dr.nblk, kBlockA, smem_cf, h->stream>>>(dr, b, rec);
+        }
+        CU(cudaGetLastError());
+    }
+    // parameter gradients
+    float *go = h->d_gout;
+    float *gu = go, *gk = go + L, *ga = go + 2 * L, *gbeta = go + 3 * L, *gc = go + 4 * L, *gw = go + 5 * L;
+    float *gao = gw + std::max(F, 1), *gl = gao + 1;
+    const int nfin = std::max(std::max(L, F), std::max(b.n_od, 1));
+    k_bwd_finalize<<<(nfin + 255) / 256, 256, 0, h->stream>>>(h->d, b, h->d_kappa, h->d_beta, h->d_cost, h->d_phi,
+                                                               h->d_psi, h->opt.dn, gu, gk, ga, gbeta, gc, gw, gao, gl);
+    CU(cudaGetLastError());
+    const cudaMemcpyKind kd = out->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const std::pair<float *, const float *> outs[] = {
+        {out->d_u, gu}, {out->d_kappa, gk}, {out->d_alpha, ga}, {out->d_beta, gbeta}, {out->d_cost, gc}};
+    for (auto &o : outs)
+        if (o.first) CU(cudaMemcpyAsync(o.first, o.second, (size_t)L * sizeof(float), kd, h->stream));
+    if (out->d_w && F) CU(cudaMemcpyAsync(out->d_w, gw, (size_t)F * sizeof(float), kd, h->stream));
+    if (out->d_alpha_origin) CU(cudaMemcpyAsync(out->d_alpha_origin, gao, sizeof(float), kd, h->stream));
+    if (out->d_od_lambda && b.n_od) CU(cudaMemcpyAsync(out->d_od_lambda, gl, (size_t)b.n_od * sizeof(float), kd, h->stream));
+    // the recomputation left the state of an earlier time: a new run must reset
+    h->tape_ready = false;
+    h->reset_done = false;
+    CU(cudaStreamSynchronize(h->stream));
+    return check_device_error(h);
 }
 
 extern "C" int sim_get_state(sim_handle h, sim_state_view *out) {

@@ -1,0 +1,396 @@
+// Reverse-mode kernels of the simulator (sm_103a).
+//
+// The derivative is that of the straight-through / trajectory-grafting surrogate
+// the method differentiates (Methods "Optimization": jax.grad of the dense
+// formulation of SI-A Alg. S1 and SI-B Alg. S2): every discrete decision of the
+// recorded rollout is frozen and stop_gradient(v) is the recorded value.  The
+// dense state X[i, j] is represented by
+//   xbar[i]           adjoint of vehicle i's valid entry (its link, or its origin
+//                     queue, a virtual inflow link of length 0), and
+//   eadj[i, r]        adjoint of X[i, m_r] right after vehicle i's r-th entry; an
+//                     invalid slot is the identity through time, so its adjoint at
+//                     an earlier time is that of the next entry into the link.
+// Per step t, in reverse (a segment of K steps is first recomputed from its
+// checkpoint, recording the tape that these kernels read):
+//   k_bwd_obs     observation at t + 1 (SI-D): dC_j/dx_i = s sigma (1 - sigma),
+//                 s = 5/L_j; demand weight 1 + (lambda - sg lambda)/lambda;
+//   k_bwd_node_z  per merge candidate: abar = M (Ebar - Xbar_old) - x Xbar_old
+//                 (SI-B Eq. transfer) and its merge-softmax weight; per-target
+//                 sums; the winners' entry adjoints; demand weight of exits;
+//   k_bwd_node_g  merge softmax Jacobian -> alpha, lbar; link-choice softmax
+//                 Jacobian (Eqs. gumbel, straigththrough) -> U = beta/c + w.phi,
+//                 G = w.psi;
+//   k_bwd_cf      car-following (SI-A) by branch tag: free x' = x + u dt,
+//                 congested x' = x_leader - dn/kappa, stopped x' = x; the TG clip
+//                 passes the adjoint; the winner's old entry receives its new
+//                 entry's adjoint unchanged (grafting, SI-C).
+// Accumulators are double precision.
+#pragma once
+#include "ts_step.cuh"
+
+namespace ts {
+
+struct BwdDev {
+    int S, K, cap, n_od;
+    float tau, inv_tau;
+    // tape of the current segment: K steps, K + 1 state records
+    float *tpos;                 // [(K+1) S] positions at the start of each step
+    int *tvid;                   // [(K+1) S] vehicle of each slot
+    int4 *tlq;                   // [(K+1) L] queue state at the start of each step
+    int8_t *ttag;                // [K S]     car-following tags
+    int4 *tcrec;                 // [K L]     link candidates
+    int2 *tnrec;                 // [K V]     origin-queue candidates
+    unsigned long long *tW;      // [K L]     merge words
+    // adjoints
+    double *xbar;                // [N]
+    double *eadj;                // [N cap]
+    const int2 *route_log;       // [N cap]
+    const int *route_len;        // [N]
+    const double *Cbar;          // [n_bins L] adjoint of C_j at the end of each bin
+    const double *Csuf;          // [(n_bins + 1) L] suffix sums of Cbar
+    double *gu, *gs, *ga, *gU, *gG;   // [L]
+    double *gao;                 // [1]
+    double *glam;                // [n_od]
+    double *Z, *SA;              // [L] per-target merge sums
+    double *ebuf, *abuf;         // [L + V] per-source merge weight and abar
+    const int *od;               // [N]
+    const float *od_lambda;      // [n_od]
+};
+
+__device__ __forceinline__ float merge_key_of(unsigned long long w) {
+    const uint32_t o = (uint32_t)(w >> 32);
+    const uint32_t b = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+    return __uint_as_float(b);
+}
+
+// adjoint right after vehicle v's first entry into link m at a step > t (0 if none)
+__device__ __forceinline__ double next_entry(const BwdDev &b, int v, int m, int t) {
+    const int n = b.route_len[v];
+    const int2 *r = b.route_log + (size_t)v * b.cap;
+    for (int k = 0; k < n; ++k) {
+        const int2 e = r[k];
+        if (e.x > t && e.y == m) return b.eadj[(size_t)v * b.cap + k];
+    }
+    return 0.0;
+}
+
+__device__ __forceinline__ int entry_at(const BwdDev &b, int v, int t) {
+    const int n = b.route_len[v];
+    const int2 *r = b.route_log + (size_t)v * b.cap;
+    for (int k = 0; k < n; ++k)
+        if (r[k].x == t) return k;
+    return -1;
+}
+
+// copy the state at the start of step (t0 + rec) into the tape
+__global__ void k_tape_pre(DevSim d, BwdDev b, int rec, int cur) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const float *pc = cur ? d.pos1 : d.pos0;
+    if (i < b.S) {
+        b.tpos[(size_t)rec * b.S + i] = pc[i];
+        b.tvid[(size_t)rec * b.S + i] = d.saux[i].x;
+    }
+    if (i < d.L) b.tlq[(size_t)rec * d.L + i] = d.lq[i];
+}
+
+// copy the decisions of step t0 + rec into the tape
+__global__ void k_tape_post(DevSim d, BwdDev b, int rec, int p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < d.L) {
+        b.tcrec[(size_t)rec * d.L + i] = d.crec[i];
+        b.tW[(size_t)rec * d.L + i] = (p ? d.W1 : d.W0)[i];
+    }
+    if (i < d.V) b.tnrec[(size_t)rec * d.V + i] = d.nrec[i];
+}
+
+// adjoint of the final positions (vehicles on a link at the end of the rollout)
+__global__ void k_bwd_init(DevSim d, BwdDev b, const float *dxT) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.N) return;
+    b.xbar[i] = (dxT && d.vstate[i] >= 0) ? (double)dxT[i] : 0.0;
+}
+
+// (1) observation at time t + 1 = the state of tape record rec: one warp per link
+__global__ void k_bwd_obs(DevSim d, BwdDev b, int rec, int bin) {
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= d.L) return;
+    const double cb = b.Cbar[(size_t)bin * d.L + j];
+    if (cb == 0.0) return;
+    const int4 q = b.tlq[(size_t)rec * d.L + j];
+    const int4 st = d.lst[j];
+    const double len = (double)d.geo[j].x, s5 = 5.0 / len, half = 0.5 * len;
+    for (int k = lane; k < q.y; k += 32) {
+        int idx = q.x + k;
+        if (idx >= st.y) idx -= st.y;
+        const size_t o = (size_t)rec * b.S + st.x + idx;
+        const int v = b.tvid[o];
+        const double x = (double)b.tpos[o];
+        const double sg = 1.0 / (1.0 + exp(-s5 * (x - half)));
+        b.xbar[v] += cb * s5 * sg * (1.0 - sg);
+        if (x >= half) {
+            const int k2 = b.od[v];
+            atomicAdd(&b.glam[k2], cb / (double)b.od_lambda[k2]);
+        }
+    }
+}
+
+struct Cand {
+    int vid, tgt, src;        // src: link id, or L + node
+    float x, alpha;
+    bool won;
+};
+
+__device__ __forceinline__ Cand load_cand(const DevSim &d, const BwdDev &b, int i, int rec) {
+    Cand c;
+    const unsigned long long *W = b.tW + (size_t)rec * d.L;
+    if (i < d.L) {
+        const int4 r = b.tcrec[(size_t)rec * d.L + i];
+        c.vid = r.x; c.tgt = r.y; c.x = __int_as_float(r.w); c.alpha = d.alpha[i];
+    } else {
+        const int2 r = b.tnrec[(size_t)rec * d.V + (i - d.L)];
+        c.vid = r.x; c.tgt = r.y; c.x = 0.0f; c.alpha = d.alpha[d.L];
+    }
+    c.src = i;
+    c.won = c.vid >= 0 && c.tgt >= 0 && W[c.tgt] != 0ull && merge_vid(W[c.tgt]) == c.vid;
+    return c;
+}
+
+// (2a) merge candidates of step t: abar, softmax weight, per-target sums
+__global__ void k_bwd_node_z(DevSim d, BwdDev b, int t, int rec, int bin0) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.L + d.V) return;
+    const Cand c = load_cand(d, b, i, rec);
+    if (c.vid < 0) return;
+    const int v = c.vid;
+    if (i < d.L && (c.won || c.tgt == kTgtSink)) {          // an exit from link i
+        const int k2 = b.od[v];
+        atomicAdd(&b.glam[k2], b.Csuf[(size_t)bin0 * d.L + i] / (double)b.od_lambda[k2]);
+    }
+    int rw = -1;
+    if (c.won) {                                             // adjoint right after this entry
+        rw = entry_at(b, v, t);
+        if (rw >= 0) b.eadj[(size_t)v * b.cap + rw] = b.xbar[v];
+    }
+    if (c.tgt < 0) return;
+    const double key = ((double)c.alpha + (double)gumbel(d.key0, d.key1, v, t, 1, 0)) * (double)b.inv_tau;
+    const double kmax = (double)merge_key_of(b.tW[(size_t)rec * d.L + c.tgt]) * (double)b.inv_tau;
+    const double e = exp(key - kmax);
+    double Enew, Xold;
+    if (c.won) {
+        Enew = b.xbar[v];
+        Xold = 0.0;
+        if (i < d.L && rw >= 0) {                            // next re-entry into the source link
+            const int n = b.route_len[v];
+            const int2 *r = b.route_log + (size_t)v * b.cap;
+            for (int k = rw + 1; k < n; ++k)
+                if (r[k].y == i) { Xold = b.eadj[(size_t)v * b.cap + k]; break; }
+        }
+    } else {
+        Enew = next_entry(b, v, c.tgt, t);
+        Xold = b.xbar[v];
+    }
+    const double abar = (double)d.M * (Enew - Xold) - (double)c.x * Xold;
+    b.ebuf[i] = e;
+    b.abuf[i] = abar;
+    atomicAdd(&b.Z[c.tgt], e);
+    atomicAdd(&b.SA[c.tgt], e * abar);
+}
+
+// (2b) merge and link-choice Jacobians of step t
+__global__ void k_bwd_node_g(DevSim d, BwdDev b, int t, int rec) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.L + d.V) return;
+    const Cand c = load_cand(d, b, i, rec);
+    if (c.vid < 0 || c.tgt < 0) return;
+    const double Z = b.Z[c.tgt];
+    const double pi = b.ebuf[i] / Z;
+    const double S = b.SA[c.tgt] / Z;
+    const double vbar = pi * (b.abuf[i] - S) * (double)b.inv_tau;   // adjoint of V'_i
+    if (i < d.L) atomicAdd(&b.ga[i], vbar); else atomicAdd(b.gao, vbar);
+    const double lbar = (double)c.alpha * vbar;                      // adjoint of l_i at the target
+    if (lbar == 0.0) return;
+    // choice set of the candidate
+    const int v = c.vid;
+    const int zone = d.dest_zone[v];
+    const float4 *info;
+    int deg;
+    if (i < d.L) {
+        const int4 nd = d.lnode[i];
+        info = d.loinfo + nd.z;
+        deg = nd.w - nd.z;
+    } else {
+        const int n = i - d.L;
+        info = d.noinfo + d.no_ptr[n];
+        deg = d.no_ptr[n + 1] - d.no_ptr[n];
+    }
+    double key[32];
+    double kmax = -INFINITY;
+    int ks = 0;
+    for (int k = 0; k < deg; ++k) {
+        const float4 e = info[k];
+        const float df = d.dest_feat[(size_t)zone * d.V + __float_as_int(e.z)];
+        const float util = __fadd_rn(e.x, __fmul_rn(e.y, df));
+        key[k] = ((double)util + (double)gumbel(d.key0, d.key1, v, t, 0, k)) * (double)b.inv_tau;
+        kmax = fmax(kmax, key[k]);
+        if (__float_as_int(e.w) == c.tgt) ks = k;
+    }
+    double zs = 0.0;
+    for (int k = 0; k < deg; ++k) { key[k] = exp(key[k] - kmax); zs += key[k]; }
+    const double pks = key[ks] / zs;
+    for (int k = 0; k < deg; ++k) {
+        const double pk = key[k] / zs;
+        const double Vbar = pk * ((k == ks ? 1.0 : 0.0) - pks) * lbar * (double)b.inv_tau;
+        const float4 e = info[k];
+        const int m = __float_as_int(e.w);
+        const float df = d.dest_feat[(size_t)zone * d.V + __float_as_int(e.z)];
+        atomicAdd(&b.gU[m], Vbar);
+        atomicAdd(&b.gG[m], Vbar * (double)df);
+    }
+}
+
+// inclusive sum over lanes of one contiguous segment of equal keys
+__device__ __forceinline__ double seg_sum(double v, int key, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(kFull, v, o);
+        const int ky = __shfl_up_sync(kFull, key, o);
+        if (lane >= o && ky == key) v += y;
+    }
+    return v;
+}
+
+struct BwdCfSmem {
+    int4 q[kLinksPerBlock];
+    int4 st[kLinksPerBlock];
+    float udt[kLinksPerBlock];
+    int off[kLinksPerBlock + 1];
+    double su[kLinksPerBlock], ss[kLinksPerBlock];
+};
+
+// (3) car-following of step (t0 + rec), block layout of k_step_a: stage each
+// queue's vehicles, tags and adjoints, then write the adjoints at time t.
+__global__ void __launch_bounds__(kBlockA) k_bwd_cf(DevSim d, BwdDev b, int rec) {
+    extern __shared__ unsigned char bsm[];
+    __shared__ BwdCfSmem S;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int j0 = d.blk_links[blockIdx.x];
+    const int nl = d.blk_links[blockIdx.x + 1] - j0;
+    if (tid < nl) {
+        S.q[tid] = b.tlq[(size_t)rec * d.L + j0 + tid];
+        S.st[tid] = d.lst[j0 + tid];
+        S.udt[tid] = d.geo[j0 + tid].y;
+        S.su[tid] = 0.0;
+        S.ss[tid] = 0.0;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        const int a = tid < nl ? S.q[tid].y : 0;
+        const int c = tid + 32 < nl ? S.q[tid + 32].y : 0;
+        int sa = a, sc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ya = __shfl_up_sync(kFull, sa, o), yc = __shfl_up_sync(kFull, sc, o);
+            if (tid >= o) { sa += ya; sc += yc; }
+        }
+        const int tot_a = __shfl_sync(kFull, sa, 31);
+        if (tid < nl) S.off[tid] = sa - a;
+        if (tid + 32 < nl) S.off[tid + 32] = tot_a + sc - c;
+        if (tid == 31) S.off[nl] = tot_a + sc;
+    }
+    __syncthreads();
+    const int total = S.off[nl];
+    double *sxb = (double *)bsm;
+    int *svid = (int *)(sxb + total);
+    int8_t *stag = (int8_t *)(svid + total);
+    const size_t tbase = (size_t)rec * b.S;
+    // stage vehicles, tags and their adjoints
+    for (int pass = 0; pass < total; pass += kBlockA * kU) {
+        const int wbase = pass + (tid >> 5) * 32 * kU;
+        if (wbase >= total) break;
+        int li = link_of(S.off, nl, min(wbase + lane, total - 1));
+        int vv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int e = wbase + u * 32 + lane;
+            vv[u] = -1;
+            if (e < total) {
+                while (S.off[li + 1] <= e) ++li;
+                const int4 q = S.q[li], st = S.st[li];
+                int idx = q.x + (e - S.off[li]);
+                if (idx >= st.y) idx -= st.y;
+                vv[u] = b.tvid[tbase + st.x + idx];
+                stag[e] = b.ttag[tbase + st.x + idx];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int e = wbase + u * 32 + lane;
+            if (e < total) { svid[e] = vv[u]; sxb[e] = b.xbar[vv[u]]; }
+        }
+    }
+    __syncthreads();
+    // adjoints at time t and per-link parameter sums
+    for (int pass = 0; pass < total; pass += kBlockA * kU) {
+        const int wbase = pass + (tid >> 5) * 32 * kU;
+        if (wbase >= total) break;
+        int li = link_of(S.off, nl, min(wbase + lane, total - 1));
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int e = wbase + u * 32 + lane;
+            const bool act = e < total;
+            double fu = 0.0, fs = 0.0;
+            if (act) {
+                while (S.off[li + 1] <= e) ++li;
+                const int k = e - S.off[li];
+                const int n = S.q[li].y;
+                const int tag = stag[e];
+                const double g = sxb[e];
+                double pre = (tag == kTagCong) ? 0.0 : g;
+                if (k + 1 < n && stag[e + 1] == kTagCong) pre += sxb[e + 1];
+                b.xbar[svid[e]] = pre;
+                if (tag == kTagFree) fu = g * (double)d.dt;
+                if (tag == kTagCong) fs = -g;
+            }
+            const int key = act ? li : -1;
+            const double su = seg_sum(fu, key, lane);
+            const double ss = seg_sum(fs, key, lane);
+            const int knext = __shfl_down_sync(kFull, key, 1);
+            if (act && (lane == 31 || knext != key)) {
+                if (su != 0.0) atomicAdd(&S.su[li], su);
+                if (ss != 0.0) atomicAdd(&S.ss[li], ss);
+            }
+        }
+    }
+    __syncthreads();
+    if (tid < nl) {
+        b.gu[j0 + tid] += S.su[tid];
+        b.gs[j0 + tid] += S.ss[tid];
+    }
+}
+
+// parameter gradients from the accumulators: u dt, s = dn / kappa,
+// U = beta / c + w.phi, G = w.psi
+__global__ void k_bwd_finalize(DevSim d, BwdDev b, const float *kappa, const float *beta, const float *cost,
+                               const float *phi, const float *psi, float dn, float *gu_o, float *gk_o,
+                               float *ga_o, float *gb_o, float *gc_o, float *gw_o, float *gao_o, float *gl_o) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < d.L) {
+        const double kap = kappa[j], c = cost[j], be = beta[j];
+        if (gu_o) gu_o[j] = (float)b.gu[j];
+        if (gk_o) gk_o[j] = (float)(b.gs[j] * (-(double)dn / (kap * kap)));
+        if (ga_o) ga_o[j] = (float)b.ga[j];
+        if (gb_o) gb_o[j] = (float)(b.gU[j] / c);
+        if (gc_o) gc_o[j] = (float)(-b.gU[j] * be / (c * c));
+    }
+    if (j < d.F && gw_o) {
+        double s = 0.0;
+        for (int l = 0; l < d.L; ++l)
+            s += b.gU[l] * (double)phi[(size_t)l * d.F + j] + b.gG[l] * (double)psi[(size_t)l * d.F + j];
+        gw_o[j] = (float)s;
+    }
+    if (j == 0 && gao_o) *gao_o = (float)*b.gao;
+    if (j < b.n_od && gl_o) gl_o[j] = (float)b.glam[j];
+}
+
+}  // namespace ts

@@ -67,7 +67,10 @@ struct DevSim {
     int *step_delta;               // [T][4]: origin releases, arrivals, candidates, entries
     int *err;                      // [4]
     // tape (backward); null when not recording
-    int8_t *tag_tape;              // [S] tag of the slot's vehicle in the last step
+    int8_t *tag_tape;              // [S] car-following tag of each slot's vehicle this step
+    int2 *route_log;               // [N * route_cap] (step, link) of every entry; null = off
+    int *route_len;                // [N] entries so far
+    int route_cap;
 };
 
 __device__ __forceinline__ void set_error(const DevSim &d, int code, int a, int b) {

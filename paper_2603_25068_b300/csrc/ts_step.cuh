@@ -456,6 +456,15 @@ __global__ void __launch_bounds__(256) k_step_b(DevSim d, int t) {
                 q.y += 1;
                 d.vstate[v] = j;
                 entered = 1;
+                if (d.route_log) {                 // route log for the reverse pass
+                    const int r = d.route_len[v];
+                    if (r < d.route_cap) {
+                        d.route_log[(size_t)v * d.route_cap + r] = make_int2(t, j);
+                        d.route_len[v] = r + 1;
+                    } else {
+                        set_error(d, SIM_EOVERFLOW, -1 - v, t);
+                    }
+                }
             }
         }
         (p ? d.W0 : d.W1)[j] = 0ull;

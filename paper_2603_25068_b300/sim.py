@@ -136,6 +136,21 @@ class Simulator:
         self._check(self.lib.sim_get_outputs(self.h, C.byref(o)))
         return res
 
+    def backward(self, dL_dcounts, dL_dxT=None):
+        """Gradient of sum(dL_dcounts * counts) (+ sum(dL_dxT * final positions))
+        with respect to the parameters, through the last rollout (needs
+        ckpt_every > 0).  Host arrays in, dict of float32 numpy arrays out."""
+        sc = self.sc
+        yb = np.ascontiguousarray(np.asarray(dL_dcounts, np.float32))
+        xb = None if dL_dxT is None else np.ascontiguousarray(np.asarray(dL_dxT, np.float32))
+        g = dict(u=np.zeros(sc.L, np.float32), kappa=np.zeros(sc.L, np.float32), alpha=np.zeros(sc.L, np.float32),
+                 beta=np.zeros(sc.L, np.float32), cost=np.zeros(sc.L, np.float32), w=np.zeros(sc.F, np.float32),
+                 alpha_origin=np.zeros(1, np.float32), od_lambda=np.zeros(sc.n_od, np.float32))
+        o = nat.sim_grads(*(_p(g[k]) for k in ("u", "kappa", "alpha", "beta", "cost", "w", "alpha_origin",
+                                               "od_lambda")), 0)
+        self._check(self.lib.sim_backward(self.h, _p(yb), _p(xb), 0, C.byref(o)))
+        return g
+
     def state(self):
         sc = self.sc
         d = dict(veh_link=np.zeros(sc.N, np.int32), veh_pos=np.zeros(sc.N, np.float64),

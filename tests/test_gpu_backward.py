@@ -1,0 +1,86 @@
+"""Parity of the CUDA reverse pass (sim_backward) with the oracle's reverse mode.
+
+Both differentiate the same frozen-decision surrogate through the same float32
+forward (the oracle's float build takes every decision in the kernel's
+precision), with double-precision accumulators on both sides; the GPU returns
+float32 gradients.  Tolerance: 1e-4 of the largest gradient of each parameter
+family (the M-scaled merge terms make absolute scales differ by ~1e5)."""
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleSim
+from paper_2603_25068_b300 import scenario as S
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("u", "kappa", "alpha", "alpha_origin", "beta", "cost", "w", "od_lambda")
+
+
+@pytest.fixture(scope="module")
+def Simulator():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2603_25068_b300.sim import Simulator
+    return Simulator
+
+
+def compare(Simulator, sc, K, seed=0, with_xT=True, rtol=1e-4):
+    rng = np.random.default_rng(seed)
+    g = Simulator(sc, ckpt_every=K, route_cap=64)
+    out = g.rollout()
+    nb = out["counts"].shape[0]
+    ybar = rng.normal(size=(nb, sc.L)).astype(np.float32)
+    xT = rng.normal(size=sc.N).astype(np.float32) if with_xT else None
+    st = g.state()
+    gg = g.backward(ybar, xT)
+    o = OracleSim(sc, "fp32", keep_history=True)
+    ref = o.rollout()
+    np.testing.assert_array_equal(out["counts"], ref["counts"])
+    on = o.state()["veh_link"] >= 0
+    go = o.backward(ybar.astype(np.float64), None if xT is None else np.where(on, xT, 0).astype(np.float64))
+    for k in KEYS:
+        scale = max(np.abs(go[k]).max(), 1e-6)
+        np.testing.assert_allclose(gg[k], go[k], rtol=0, atol=rtol * scale, err_msg=k)
+    return go
+
+
+@pytest.mark.parametrize("K", [300, 7])
+def test_backward_tiny_grid(Simulator, K):
+    sc = S.tiny_grid(T=150).copy(obs_every=50)
+    compare(Simulator, sc, K)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 7])
+def test_backward_dense_small(Simulator, seed):
+    sc = S.random_small(seed=seed, side=3, n_vehicles=160, T=90).copy(obs_every=30)
+    go = compare(Simulator, sc, 13, seed=seed)
+    assert np.count_nonzero(go["alpha"]) > 0 and np.count_nonzero(go["beta"]) > 0
+
+
+def test_backward_city_small(Simulator):
+    sc = S.city_small(T=240).copy(obs_every=60)
+    compare(Simulator, sc, 60, seed=5, with_xT=False)
+
+
+def test_backward_tg_toy(Simulator):
+    sc = S.tg_toy(2.0, 1.0)
+    g = Simulator(sc, ckpt_every=4, route_cap=8)
+    g.rollout()
+    x = g.state()["veh_pos"]
+    gg = g.backward(np.zeros((1, sc.L), np.float32), (2 * x).astype(np.float32))
+    np.testing.assert_allclose(gg["u"][:2], [32.0, 8.0], rtol=1e-6)
+
+
+def test_backward_needs_a_recorded_rollout(Simulator):
+    from paper_2603_25068_b300.native import SimError, SIM_ESTATE
+    sc = S.tiny_grid(n_vehicles=50, T=20)
+    g = Simulator(sc)                                   # forward only
+    g.rollout()
+    with pytest.raises(SimError) as e:
+        g.backward(np.zeros((1, sc.L), np.float32))
+    assert e.value.code == SIM_ESTATE
+    g = Simulator(sc, ckpt_every=5)
+    g.reset(20)
+    g.step(20)                                          # the step path records no tape
+    with pytest.raises(SimError):
+        g.backward(np.zeros((1, sc.L), np.float32))
