@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="small network (for profiling captures)")
     ap.add_argument("--stage", type=int, default=0, help="queue slots per link block (0 = autotune)")
+    ap.add_argument("--no-fwd-bwd", action="store_true", help="skip the calibration-gradient leg")
     return ap.parse_args()
 
 
@@ -217,6 +218,54 @@ def ncu_traffic(kernel, workload_key, launch_units):
     return e["dram_bytes_per_launch"] * launch_units / e["units_per_launch"]
 
 
+# ------------------------------------------------------------------ fwd + bwd
+def run_fwd_bwd(args, dev, stream, flush, ws):
+    """Calibration-gradient workload: 1,800-step rollout of the city network with
+    the reverse pass (checkpoints every 60 steps) of the squared error of
+    5-minute counts on 2,000 sensor links against a hidden ground-truth draw."""
+    import torch
+    import torch.distributed as dist
+    from paper_2603_25068_b300 import scenario as S
+    from paper_2603_25068_b300.sim import Simulator
+    if args.small:
+        model, truth = S.calibration(n_sensors=500, n_nodes=3000, n_links=9000, n_vehicles=250_000,
+                                     n_origin_zones=20, n_dest_zones=32)
+    else:
+        model, truth = S.calibration()
+    T = model.T
+    y_obs = Simulator(truth, device=dev.index, stream=stream).rollout()["counts"]
+    sim = Simulator(model, device=dev.index, stream=stream, ckpt_every=60, route_cap=256)
+    nb = sim.n_bins(T)
+    sens = model.sensors
+    times = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        out = sim.rollout(T)
+        ybar = np.zeros((nb, model.L), np.float32)
+        diff = out["counts"][:, sens].astype(np.float32) - y_obs[:, sens]
+        ybar[:, sens] = 2.0 * diff / diff.size
+        g = sim.backward(ybar)
+        torch.cuda.synchronize(dev)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    if ws > 1:
+        t = torch.tensor([tot], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    ms = 1000 * tot / args.steps
+    return {"metric": "vehicle-steps/s (forward + reverse pass)", "value": ws * model.N * T / (ms / 1000),
+            "unit": "vehicle-steps/s", "ms_per_iteration": ms, "x_real_time": T * model.dt / (ms / 1000),
+            "workload": f"calibration gradient: city network, {model.N:,} vehicles, {T} steps, checkpoints every 60, "
+                        f"{len(sens)} sensor links, gradient w.r.t. {model.n_od} demand and {model.F} route-choice "
+                        "parameters (and every link parameter)",
+            "timing": "host wall clock per iteration (rollout with host outputs, host loss, sim_backward to host), "
+                      "L2 flushed before each",
+            "grad_norm_w": float(np.linalg.norm(g["w"])), "grad_norm_lambda": float(np.linalg.norm(g["od_lambda"]))}
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args):
     import torch
@@ -356,6 +405,9 @@ def run_ours(args):
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "ms_per_step": 1000 * tot / args.steps,
                        "note": "sim_set_params from pinned host arrays + sim_rollout into pinned host outputs"}
+
+    if not args.no_fwd_bwd:
+        line["fwd_bwd"] = run_fwd_bwd(args, dev, stream, flush, ws)
 
     if rank == 0 and not args.no_cpu_baseline:
         steps, wall = oracle_sample(sc, args.cpu_budget)

@@ -1,0 +1,45 @@
+"""torch.autograd.Function over the C ABI: bin counts of a rollout as a
+differentiable function of the simulator's parameters.
+
+The forward value is the simulated (integer) count of each link and bin; the
+backward is sim_backward, the reverse pass of the straight-through /
+trajectory-grafting surrogate (SI-B, SI-C, SI-D).  PyTorch provides the tensors
+and the stream only; both passes run in the library's CUDA kernels.
+
+    counts = rollout_counts(sim, u, kappa, alpha, beta, cost, w, alpha_origin, od_lambda)
+    loss = ((counts[:, sensors] - observed) ** 2).mean()
+    loss.backward()
+"""
+from __future__ import annotations
+
+import torch
+
+PARAMS = ("u", "kappa", "alpha", "beta", "cost", "w", "alpha_origin", "od_lambda")
+
+
+class RolloutCounts(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, sim, T, u, kappa, alpha, beta, cost, w, alpha_origin, od_lambda):
+        host = lambda x: x.detach().to("cpu", torch.float32).numpy()
+        sim.set_params(u=host(u), kappa=host(kappa), alpha=host(alpha), beta=host(beta), cost=host(cost),
+                       w=host(w), alpha_origin=float(alpha_origin.detach().reshape(-1)[0]))
+        out = sim.rollout(T, device=True)
+        ctx.sim = sim
+        ctx.od_dtype = od_lambda.dtype
+        return out["counts"].to(torch.float32)
+
+    @staticmethod
+    def backward(ctx, g_counts):
+        g = ctx.sim.backward_device(g_counts)
+        return (None, None, g["u"], g["kappa"], g["alpha"], g["beta"], g["cost"], g["w"],
+                g["alpha_origin"].reshape(()), g["od_lambda"])
+
+
+def rollout_counts(sim, u, kappa, alpha, beta, cost, w, alpha_origin, od_lambda, T=None):
+    """Counts [n_bins, L] (float32, on the simulator's device); differentiable in
+    every parameter.  od_lambda enters through the demand weights only: the
+    simulated vehicles stay those of the scenario."""
+    T = sim.sc.T if T is None else T
+    if not torch.is_tensor(alpha_origin):
+        alpha_origin = torch.tensor(float(alpha_origin))
+    return RolloutCounts.apply(sim, T, u, kappa, alpha, beta, cost, w, alpha_origin, od_lambda)

@@ -255,8 +255,12 @@ def city(seed: int = 1, n_nodes: int = 12000, n_links: int = 36000,
          n_vehicles: int = 1_000_000, T: int = 3600, tau: float = 0.5,
          n_origin_zones: int = 80, n_dest_zones: int = 128,
          dep_window: float = 1800.0, capacity_mult: Optional[np.ndarray] = None,
-         name: str = "city") -> Scenario:
-    """Random planar city network with zone-based OD demand (see module doc)."""
+         name: str = "city", demand_mult: Optional[np.ndarray] = None,
+         demand_seed: Optional[int] = None) -> Scenario:
+    """Random planar city network with zone-based OD demand (see module doc).
+    demand_mult scales the OD demand parameters and demand_seed (default: seed)
+    draws the vehicles from them, so that a second draw of the demand can share
+    the network of the first."""
     rng = np.random.default_rng(seed)
     pts, und = _planar_graph(rng, n_nodes, n_links // 2)
     tail = _i32(np.concatenate([und[:, 0], und[:, 1]]))
@@ -284,6 +288,11 @@ def city(seed: int = 1, n_nodes: int = 12000, n_links: int = 36000,
     n_od = n_origin_zones * n_dest_zones
     lam = rng.lognormal(0.0, 1.0, size=n_od)
     lam = lam / lam.sum() * n_vehicles
+    if demand_mult is not None:
+        lam = lam * demand_mult
+        lam = lam / lam.sum() * n_vehicles
+    if demand_seed is not None:
+        rng = np.random.default_rng(demand_seed)
     counts = rng.multinomial(n_vehicles, lam / lam.sum())
     od = _i32(np.repeat(np.arange(n_od), counts))
     oz = od // n_dest_zones
@@ -439,3 +448,18 @@ def custom(tail, head, length, origin, dest_node, dep_step, u=10.0, kappa=0.2, a
                     origin=origin, dest_zone=_i32(dz), dep_step=_i32(dep_step),
                     od=_i32(np.zeros(N)), n_od=1, od_lambda=_f32([float(N)]), T=T, tau=tau,
                     seed=seed, obs_every=T)
+
+
+def calibration(n_sensors: int = 2000, T: int = 1800, seed_truth: int = 2, **kw):
+    """Calibration-gradient workload: the city network and 30-minute rollouts
+    with 5-minute counts on n_sensors links; observations come from a hidden
+    ground-truth draw of the 10,240 demand parameters (lambda* = lambda
+    exp(N(0, 0.3^2))) and the 16 route-choice coefficients (w* = w + N(0, 0.5^2)).
+    Returns (model scenario at the mean parameters, truth scenario)."""
+    model = city(T=T, name="calibration", **kw)
+    rng = np.random.default_rng(seed_truth)
+    mult = np.exp(rng.normal(0.0, 0.3, size=model.n_od))
+    truth = city(T=T, name="calibration_truth", demand_mult=mult, demand_seed=seed_truth, **kw)
+    truth = truth.copy(w=_f32(model.w + rng.normal(0.0, 0.5, size=model.F)))
+    sensors = _i32(np.sort(rng.choice(model.L, size=min(n_sensors, model.L), replace=False)))
+    return model.copy(sensors=sensors), truth.copy(sensors=sensors)

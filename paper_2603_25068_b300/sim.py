@@ -151,6 +151,24 @@ class Simulator:
         self._check(self.lib.sim_backward(self.h, _p(yb), _p(xb), 0, C.byref(o)))
         return g
 
+    def backward_device(self, dL_dcounts, dL_dxT=None):
+        """As backward() with torch CUDA tensors in and out (no host copies of
+        the gradients)."""
+        import torch
+        sc = self.sc
+        dev = torch.device("cuda", self.device)
+        yb = dL_dcounts.to(device=dev, dtype=torch.float32).contiguous()
+        xb = None if dL_dxT is None else dL_dxT.to(device=dev, dtype=torch.float32).contiguous()
+        g = dict(u=torch.empty(sc.L, device=dev), kappa=torch.empty(sc.L, device=dev),
+                 alpha=torch.empty(sc.L, device=dev), beta=torch.empty(sc.L, device=dev),
+                 cost=torch.empty(sc.L, device=dev), w=torch.empty(sc.F, device=dev),
+                 alpha_origin=torch.empty(1, device=dev), od_lambda=torch.empty(sc.n_od, device=dev))
+        o = nat.sim_grads(*(C.c_void_p(g[k].data_ptr()) for k in ("u", "kappa", "alpha", "beta", "cost", "w",
+                                                                   "alpha_origin", "od_lambda")), 1)
+        self._check(self.lib.sim_backward(self.h, C.c_void_p(yb.data_ptr()),
+                                          None if xb is None else C.c_void_p(xb.data_ptr()), 1, C.byref(o)))
+        return g
+
     def state(self):
         sc = self.sc
         d = dict(veh_link=np.zeros(sc.N, np.int32), veh_pos=np.zeros(sc.N, np.float64),
