@@ -229,6 +229,38 @@ SIM_API int sim_set_stage(sim_handle h, int32_t slots);
 SIM_API int32_t sim_time(sim_handle h);
 SIM_API size_t sim_device_bytes(sim_handle h);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many simulators advanced together, one launch per phase and step
+ * for all of them.  Members keep their own network, demand, parameters, state,
+ * step counter and horizon; results of a member are the same as when it runs
+ * alone (its decisions depend on its own random key and state only).  While
+ * batched, members use the batch's stream (that of the first member) and must
+ * not be stepped, reset or reshaped through their own handles; their outputs,
+ * state and sim_backward (after they finished) remain available.
+ * ------------------------------------------------------------------------- */
+typedef struct sim_batch_ctx *sim_batch;
+
+/* Group n distinct handles of one device.  Errors: SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA. */
+SIM_API int sim_batch_create(const sim_handle *members, int32_t n, sim_batch *out);
+
+/* Reset member k for a rollout of horizon T; it joins at the next step boundary
+ * of sim_batch_advance (continuous batching). */
+SIM_API int sim_batch_start(sim_batch b, int32_t k, int32_t T);
+
+/* Advance every running member by n_steps steps (a member reaching its horizon
+ * closes its last bin in the following step and then stays idle).  finished:
+ * optional [n] flags, 1 for members done with their horizon.  Runs of 8 or more
+ * steps are replayed from a CUDA graph captured once per length.  Returns after
+ * the stream has drained. */
+SIM_API int sim_batch_advance(sim_batch b, int32_t n_steps, int32_t *finished);
+
+/* Start every member with horizon T and run all of them to the end. */
+SIM_API int sim_batch_rollout(sim_batch b, int32_t T);
+
+/* Release the batch (the member handles stay valid and get their streams back). */
+SIM_API int sim_batch_destroy(sim_batch b);
+SIM_API const char *sim_batch_last_error(sim_batch b);
+
 /* Forward rollout that allocates nothing -- the same computation and outputs as
  * sim_create + sim_rollout + sim_destroy, for callers that may not allocate
  * device memory: code running while a stream is captured into a CUDA graph,

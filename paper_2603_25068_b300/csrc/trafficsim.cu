@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -125,11 +126,18 @@ struct sim_ctx {
     int *d_dummy = nullptr;              // step counters of recomputed steps
     int *d_od = nullptr;
     float *d_od_lambda = nullptr;
-    double *d_Cbar = nullptr, *d_Csuf = nullptr;
-    int cap_bins = 0;
-    float *d_dxT = nullptr, *d_ybar = nullptr;
-    float *d_gout = nullptr;             // staging of gradient outputs
 };
+
+// Workspace of the reverse pass (tape of one segment, adjoints, accumulators),
+// shared by every handle of a device: sim_backward holds the device's lock for
+// the whole call, grows the workspace when a handle needs more and returns only
+// after its stream has drained.  It is released when the process exits.
+struct BwdPool {
+    std::mutex mu;
+    void *buf = nullptr;
+    size_t cap = 0;
+};
+static BwdPool g_bwd_pool[64];
 
 static std::string g_create_err;
 
@@ -172,6 +180,21 @@ extern "C" int32_t sim_n_bins(int32_t T, int32_t obs_every) {
     return (T + obs_every - 1) / obs_every;
 }
 
+// The dynamic shared-memory limit is an attribute of a kernel function, shared by
+// every handle: raise it monotonically (per device) to the largest size needed.
+static std::mutex g_attr_mu;
+static size_t g_attr_a[64], g_attr_cf[64], g_attr_ba[64];
+
+template <class K>
+static cudaError_t raise_smem_attr(K kernel, size_t *cur, int device, size_t bytes) {
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    if (bytes <= cur[device]) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur[device] = bytes;
+    return e;
+}
+
 // Pack consecutive links into link blocks of k_step_a: at most kLinksPerBlock
 // links whose queue capacities add up to at most `stage` slots (a larger link
 // gets a block of its own).
@@ -205,8 +228,7 @@ static int build_blocks(sim_ctx *h) {
     h->d.nblk = nblk;
     h->d.npb = (h->V + nblk - 1) / nblk;
     h->stage_max = smax;
-    const size_t smem = (size_t)smax * sizeof(float);
-    CU(cudaFuncSetAttribute(k_step_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CU(raise_smem_attr(k_step_a, g_attr_a, h->device, (size_t)smax * sizeof(float)));
     return SIM_OK;
 }
 
@@ -408,6 +430,7 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
     TRY(dalloc(h, &d.lstat, L));
     TRY(dalloc(h, &d.lpos, L));
     TRY(dalloc(h, &d.err, 4));
+    CU(cudaMemsetAsync(d.err, 0, 4 * sizeof(int), h->stream));
     CU(cudaMemsetAsync(d.pos0, 0, (size_t)S * sizeof(float), h->stream));
     CU(cudaMemsetAsync(d.pos1, 0, (size_t)S * sizeof(float), h->stream));
     CU(cudaMemsetAsync(d.saux, 0xff, (size_t)S * sizeof(int2), h->stream));
@@ -430,20 +453,6 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
         d.route_cap = h->route_cap;
         b.route_log = d.route_log;
         b.route_len = d.route_len;
-        TRY(dalloc(h, &b.tpos, (size_t)(K + 1) * S));
-        TRY(dalloc(h, &b.tvid, (size_t)(K + 1) * S));
-        TRY(dalloc(h, &b.tlq, (size_t)(K + 1) * L));
-        TRY(dalloc(h, &b.ttag, (size_t)K * S));
-        TRY(dalloc(h, &b.tcrec, (size_t)K * L));
-        TRY(dalloc(h, &b.tnrec, (size_t)K * V));
-        TRY(dalloc(h, &b.tW, (size_t)K * L));
-        TRY(dalloc(h, &b.xbar, N));
-        TRY(dalloc(h, &b.eadj, (size_t)N * h->route_cap));
-        TRY(dalloc(h, &b.gu, L)); TRY(dalloc(h, &b.gs, L)); TRY(dalloc(h, &b.ga, L));
-        TRY(dalloc(h, &b.gU, L)); TRY(dalloc(h, &b.gG, L)); TRY(dalloc(h, &b.gao, 1));
-        TRY(dalloc(h, &b.glam, std::max(dem->n_od, 1)));
-        TRY(dalloc(h, &b.Z, L)); TRY(dalloc(h, &b.SA, L));
-        TRY(dalloc(h, &b.ebuf, (size_t)L + V)); TRY(dalloc(h, &b.abuf, (size_t)L + V));
         TRY(upload(h, &h->d_od, dem->od, N));
         TRY(upload(h, &h->d_od_lambda, dem->od_lambda, std::max(dem->n_od, 1)));
         for (int k = 0; k < dem->n_od; ++k)
@@ -452,7 +461,6 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
             if (dem->od[i] < 0 || dem->od[i] >= dem->n_od) return fail(h, SIM_EINVAL, "od out of range");
         b.od = h->d_od;
         b.od_lambda = h->d_od_lambda;
-        TRY(dalloc(h, &h->d_gout, (size_t)5 * L + std::max(F, 1) + 1 + std::max(dem->n_od, 1)));
     }
     TRY(build_blocks(h));
     TRY(upload_params(h, par));
@@ -516,12 +524,6 @@ static int ensure_T(sim_ctx *h, int T) {
             TRY(dalloc(h, &h->ck.pos, nseg * S)); TRY(dalloc(h, &h->ck.saux, nseg * S));
             TRY(dalloc(h, &h->ck.lpos, nseg * L));
             h->cap_seg = nseg;
-        }
-        if (nb > h->cap_bins) {
-            TRY(dalloc(h, &h->d_Cbar, (size_t)nb * h->L));
-            TRY(dalloc(h, &h->d_Csuf, (size_t)(nb + 1) * h->L));
-            TRY(dalloc(h, &h->d_ybar, (size_t)nb * h->L));
-            h->cap_bins = nb;
         }
     }
     h->cap_T = T;
@@ -766,17 +768,60 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
                                      (bb + 1 < nb ? (double)yb[(size_t)(bb + 1) * L + j] : 0.0);
     for (int bb = nb - 1; bb >= 0; --bb)
         for (int j = 0; j < L; ++j) cs[(size_t)bb * L + j] = cs[(size_t)(bb + 1) * L + j] + cb[(size_t)bb * L + j];
-    CU(cudaMemcpyAsync(h->d_Cbar, cb.data(), cb.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    CU(cudaMemcpyAsync(h->d_Csuf, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (h->device < 0 || h->device >= 64) return fail(h, SIM_EINVAL, "device index");
+    BwdPool &pool = g_bwd_pool[h->device];
+    std::lock_guard<std::mutex> lock(pool.mu);
+    // carve the shared workspace
+    size_t need = 0;
+    auto room = [&](size_t n, size_t sz) { need += (std::max<size_t>(n, 1) * sz + 255) & ~(size_t)255; };
+    room((size_t)(K + 1) * S, sizeof(float)); room((size_t)(K + 1) * S, sizeof(int));
+    room((size_t)(K + 1) * L, sizeof(int4)); room((size_t)K * S, 1); room((size_t)K * L, sizeof(int4));
+    room((size_t)K * V, sizeof(int2)); room((size_t)K * L, sizeof(unsigned long long));
+    room(N, sizeof(double)); room((size_t)N * h->route_cap, sizeof(double));
+    for (int k = 0; k < 7; ++k) room(L, sizeof(double));
+    room(1, sizeof(double)); room(std::max(h->n_od, 1), sizeof(double));
+    room((size_t)L + V, sizeof(double)); room((size_t)L + V, sizeof(double));
+    room((size_t)nb * L, sizeof(double)); room((size_t)(nb + 1) * L, sizeof(double));
+    room(N, sizeof(float)); room((size_t)5 * L + std::max(F, 1) + 1 + std::max(h->n_od, 1), sizeof(float));
+    if (need > pool.cap) {
+        if (pool.buf) { cudaDeviceSynchronize(); cudaFree(pool.buf); pool.buf = nullptr; pool.cap = 0; }
+        cudaError_t e = cudaMalloc(&pool.buf, need);
+        if (e != cudaSuccess) { pool.buf = nullptr; return fail(h, SIM_ENOMEM, "reverse-pass workspace: " + std::string(cudaGetErrorString(e))); }
+        pool.cap = need;
+    }
+    unsigned char *wp = (unsigned char *)pool.buf;
+    auto take = [&](size_t n, size_t sz) { void *p = wp; wp += (std::max<size_t>(n, 1) * sz + 255) & ~(size_t)255; return p; };
     BwdDev b = h->b;
-    b.Cbar = h->d_Cbar;
-    b.Csuf = h->d_Csuf;
+    b.tpos = (float *)take((size_t)(K + 1) * S, sizeof(float));
+    b.tvid = (int *)take((size_t)(K + 1) * S, sizeof(int));
+    b.tlq = (int4 *)take((size_t)(K + 1) * L, sizeof(int4));
+    b.ttag = (int8_t *)take((size_t)K * S, 1);
+    b.tcrec = (int4 *)take((size_t)K * L, sizeof(int4));
+    b.tnrec = (int2 *)take((size_t)K * V, sizeof(int2));
+    b.tW = (unsigned long long *)take((size_t)K * L, sizeof(unsigned long long));
+    b.xbar = (double *)take(N, sizeof(double));
+    b.eadj = (double *)take((size_t)N * h->route_cap, sizeof(double));
+    b.gu = (double *)take(L, sizeof(double)); b.gs = (double *)take(L, sizeof(double));
+    b.ga = (double *)take(L, sizeof(double)); b.gU = (double *)take(L, sizeof(double));
+    b.gG = (double *)take(L, sizeof(double)); b.Z = (double *)take(L, sizeof(double));
+    b.SA = (double *)take(L, sizeof(double));
+    b.gao = (double *)take(1, sizeof(double));
+    b.glam = (double *)take(std::max(h->n_od, 1), sizeof(double));
+    b.ebuf = (double *)take((size_t)L + V, sizeof(double));
+    b.abuf = (double *)take((size_t)L + V, sizeof(double));
+    double *d_Cbar = (double *)take((size_t)nb * L, sizeof(double));
+    double *d_Csuf = (double *)take((size_t)(nb + 1) * L, sizeof(double));
+    float *d_dxT_w = (float *)take(N, sizeof(float));
+    float *d_gout = (float *)take((size_t)5 * L + std::max(F, 1) + 1 + std::max(h->n_od, 1), sizeof(float));
+    CU(cudaMemcpyAsync(d_Cbar, cb.data(), cb.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(d_Csuf, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    b.Cbar = d_Cbar;
+    b.Csuf = d_Csuf;
     const float *dxT = nullptr;
     if (dL_dxT) {
-        if (!h->d_dxT) TRY(dalloc(h, &h->d_dxT, N));
-        CU(cudaMemcpyAsync(h->d_dxT, dL_dxT, (size_t)N * sizeof(float),
+        CU(cudaMemcpyAsync(d_dxT_w, dL_dxT, (size_t)N * sizeof(float),
                            inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
-        dxT = h->d_dxT;
+        dxT = d_dxT_w;
     }
     for (double *p : {b.gu, b.gs, b.ga, b.gU, b.gG}) CU(cudaMemsetAsync(p, 0, (size_t)L * sizeof(double), h->stream));
     CU(cudaMemsetAsync(b.gao, 0, sizeof(double), h->stream));
@@ -789,7 +834,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     dr.step_delta = h->d_dummy;
     const size_t smem_a = (size_t)h->stage_max * sizeof(float);
     const size_t smem_cf = (size_t)h->stage_max * (sizeof(double) + sizeof(int) + 1);
-    CU(cudaFuncSetAttribute(k_bwd_cf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cf));
+    CU(raise_smem_attr(k_bwd_cf, g_attr_cf, h->device, smem_cf));
     const int gS = (std::max(S, L) + 255) / 256, gLV = (L + V + 255) / 256, gN = (std::max(L, V) + 255) / 256;
     for (int sg = nseg - 1; sg >= 0; --sg) {
         const int t0 = sg * K, t1 = std::min(T, t0 + K);
@@ -816,7 +861,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         CU(cudaGetLastError());
     }
     // parameter gradients
-    float *go = h->d_gout;
+    float *go = d_gout;
     float *gu = go, *gk = go + L, *ga = go + 2 * L, *gbeta = go + 3 * L, *gc = go + 4 * L, *gw = go + 5 * L;
     float *gao = gw + std::max(F, 1), *gl = gao + 1;
     const int nfin = std::max(std::max(L, F), std::max(b.n_od, 1));
@@ -930,6 +975,221 @@ extern "C" int sim_destroy(sim_handle h) {
 extern "C" const char *sim_last_error(sim_handle h) {
     return h ? h->err.c_str() : g_create_err.c_str();
 }
+
+// ============================================================================
+// Batches: many handles advanced by one launch per phase and step
+// ============================================================================
+
+struct sim_batch_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<sim_ctx *> m;
+    std::vector<cudaStream_t> saved_streams;
+    DevSim *d_ds = nullptr;
+    int2 *d_bmapA = nullptr, *d_bmapB = nullptr;
+    int *d_t = nullptr, *d_T = nullptr, *d_mode = nullptr;
+    CkDev *d_ck = nullptr;
+    int nA = 0, nB = 0, maxS = 0;
+    size_t smem = 0;
+    bool any_tape = false;
+    std::vector<int> hT, hmode;
+    std::map<int, cudaGraphExec_t> graphs;
+    std::vector<void *> allocs;
+    std::string err;
+};
+
+static int bfail(sim_batch_ctx *b, int code, const std::string &msg) {
+    if (b) b->err = msg; else g_create_err = msg;
+    return code;
+}
+
+#define BCU(call)                                                                  \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) return bfail(b, SIM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+static int balloc(sim_batch_ctx *b, T **p, size_t n) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) return bfail(b, SIM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    b->allocs.push_back(q);
+    *p = (T *)q;
+    return SIM_OK;
+}
+
+static int batch_upload_member(sim_batch_ctx *b, int k) {
+    sim_ctx *h = b->m[k];
+    BCU(cudaMemcpyAsync(b->d_ds + k, &h->d, sizeof(DevSim), cudaMemcpyHostToDevice, b->stream));
+    CkDev c{};
+    if (h->K > 0) {
+        c.K = h->K; c.L = h->L; c.S = h->S; c.V = h->V; c.N = h->N;
+        c.lq = h->ck.lq; c.lstat = h->ck.lstat; c.vac = h->ck.vac; c.sentry = h->ck.sentry; c.fifo = h->ck.fifo;
+        c.vstate = h->ck.vstate; c.pos = h->ck.pos; c.saux = h->ck.saux; c.lpos = h->ck.lpos;
+    }
+    BCU(cudaMemcpyAsync(b->d_ck + k, &c, sizeof(CkDev), cudaMemcpyHostToDevice, b->stream));
+    return SIM_OK;
+}
+
+static void batch_release(sim_batch_ctx *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.second);
+    b->graphs.clear();
+    for (void *p : b->allocs) cudaFree(p);
+    b->allocs.clear();
+    for (size_t k = 0; k < b->m.size() && k < b->saved_streams.size(); ++k) b->m[k]->stream = b->saved_streams[k];
+}
+
+extern "C" int sim_batch_create(const sim_handle *members, int32_t n, sim_batch *out) {
+    if (!out) return bfail(nullptr, SIM_EINVAL, "null output");
+    *out = nullptr;
+    if (!members || n <= 0) return bfail(nullptr, SIM_EINVAL, "empty batch");
+    sim_batch_ctx *b = new sim_batch_ctx();
+    b->device = members[0]->device;
+    b->stream = members[0]->stream;
+    std::vector<int2> bmA, bmB;
+    for (int k = 0; k < n; ++k) {
+        sim_ctx *h = members[k];
+        if (!h || h->device != b->device) { delete b; return bfail(nullptr, SIM_EINVAL, "members must be distinct handles on one device"); }
+        for (int q = 0; q < k; ++q) if (members[q] == h) { delete b; return bfail(nullptr, SIM_EINVAL, "a handle appears twice"); }
+        b->m.push_back(h);
+        b->saved_streams.push_back(h->stream);
+        for (int x = 0; x < h->d.nblk; ++x) bmA.push_back(make_int2(k, x));
+        const int nb = (h->L + h->V + 255) / 256;
+        for (int x = 0; x < nb; ++x) bmB.push_back(make_int2(k, x));
+        b->smem = std::max(b->smem, (size_t)h->stage_max * sizeof(float));
+        b->any_tape = b->any_tape || h->K > 0;
+        b->maxS = std::max(b->maxS, std::max(h->S, std::max(h->L, h->N)));
+    }
+    int rc = SIM_OK;
+    auto fin = [&](int code) { batch_release(b); g_create_err = b->err; delete b; return code; };
+    if (cudaSetDevice(b->device) != cudaSuccess) return fin(bfail(b, SIM_ECUDA, "cudaSetDevice"));
+    // every member works on the batch's stream while batched
+    cudaStreamSynchronize(b->stream);
+    for (int k = 0; k < n; ++k) { cudaStreamSynchronize(b->m[k]->stream); b->m[k]->stream = b->stream; }
+    b->nA = (int)bmA.size();
+    b->nB = (int)bmB.size();
+    if ((rc = balloc(b, &b->d_ds, n)) || (rc = balloc(b, &b->d_ck, n)) || (rc = balloc(b, &b->d_bmapA, b->nA)) ||
+        (rc = balloc(b, &b->d_bmapB, b->nB)) || (rc = balloc(b, &b->d_t, n)) || (rc = balloc(b, &b->d_T, n)) ||
+        (rc = balloc(b, &b->d_mode, n)))
+        return fin(rc);
+    b->hT.assign(n, 0);
+    b->hmode.assign(n, kModeDone);
+    if (cudaMemcpyAsync(b->d_bmapA, bmA.data(), bmA.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream) ||
+        cudaMemcpyAsync(b->d_bmapB, bmB.data(), bmB.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream) ||
+        cudaMemsetAsync(b->d_t, 0, n * sizeof(int), b->stream) || cudaMemsetAsync(b->d_T, 0, n * sizeof(int), b->stream) ||
+        cudaMemcpyAsync(b->d_mode, b->hmode.data(), n * sizeof(int), cudaMemcpyHostToDevice, b->stream))
+        return fin(bfail(b, SIM_ECUDA, "batch set-up copies"));
+    for (int k = 0; k < n; ++k)
+        if ((rc = batch_upload_member(b, k))) return fin(rc);
+    if (raise_smem_attr(k_batch_a, g_attr_ba, b->device, b->smem) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return fin(bfail(b, SIM_ECUDA, "batch set-up"));
+    *out = b;
+    return SIM_OK;
+}
+
+extern "C" int sim_batch_start(sim_batch b, int32_t k, int32_t T) {
+    if (!b || k < 0 || k >= (int)b->m.size()) return SIM_EINVAL;
+    if (T < 1) return bfail(b, SIM_EINVAL, "horizon must be >= 1");
+    sim_ctx *h = b->m[k];
+    BCU(cudaSetDevice(b->device));
+    int rc = ensure_T(h, T);
+    if (rc) return bfail(b, rc, h->err);
+    enqueue_reset(h, T);
+    BCU(cudaGetLastError());
+    if ((rc = batch_upload_member(b, k))) return rc;
+    const int zero = 0, run = kModeRun;
+    BCU(cudaMemcpyAsync(b->d_t + k, &zero, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->d_T + k, &T, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->d_mode + k, &run, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaStreamSynchronize(b->stream));
+    b->hT[k] = T;
+    b->hmode[k] = kModeRun;
+    h->t = 0;
+    h->T = T;
+    h->n_bins = sim_n_bins(T, h->opt.obs_every);
+    h->reset_done = false;           // reachable through the batch only until it finishes
+    h->tape_ready = false;
+    return SIM_OK;
+}
+
+static void batch_enqueue_steps(sim_batch_ctx *b, int n_steps) {
+    const int n = (int)b->m.size();
+    for (int s = 0; s < n_steps; ++s) {
+        if (b->any_tape) k_batch_ckpt<<<dim3(64, n), 256, 0, b->stream>>>(b->d_ds, b->d_ck, b->d_t, b->d_mode);
+        k_batch_a<<<b->nA, kBlockA, b->smem, b->stream>>>(b->d_ds, b->d_bmapA, b->d_t, b->d_mode);
+        k_batch_b<<<b->nB, 256, 0, b->stream>>>(b->d_ds, b->d_bmapB, b->d_t, b->d_mode);
+        k_batch_tick<<<(n + 255) / 256, 256, 0, b->stream>>>(n, b->d_t, b->d_T, b->d_mode);
+    }
+}
+
+extern "C" int sim_batch_advance(sim_batch b, int32_t n_steps, int32_t *finished) {
+    if (!b || n_steps < 0) return SIM_EINVAL;
+    BCU(cudaSetDevice(b->device));
+    const int n = (int)b->m.size();
+    if (n_steps > 0) {
+        auto it = b->graphs.find(n_steps);
+        if (it == b->graphs.end() && n_steps >= 8) {
+            cudaGraph_t g;
+            BCU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            batch_enqueue_steps(b, n_steps);
+            cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+            if (ce != cudaSuccess) return bfail(b, SIM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+            cudaGraphExec_t ge;
+            ce = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) return bfail(b, SIM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+            it = b->graphs.emplace(n_steps, ge).first;
+        }
+        if (it != b->graphs.end()) BCU(cudaGraphLaunch(it->second, b->stream));
+        else batch_enqueue_steps(b, n_steps);
+        BCU(cudaGetLastError());
+    }
+    std::vector<int> mode(n), tv(n);
+    BCU(cudaMemcpyAsync(mode.data(), b->d_mode, n * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    BCU(cudaMemcpyAsync(tv.data(), b->d_t, n * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    BCU(cudaStreamSynchronize(b->stream));
+    for (int k = 0; k < n; ++k) {
+        sim_ctx *h = b->m[k];
+        if (mode[k] == kModeDone && b->hmode[k] != kModeDone) {        // finished its horizon
+            h->t = h->T;
+            h->reset_done = true;
+            h->tape_ready = h->K > 0;
+        } else if (mode[k] != kModeDone) {
+            h->t = tv[k];
+        }
+        b->hmode[k] = mode[k];
+        if (finished) finished[k] = mode[k] == kModeDone;
+    }
+    for (int k = 0; k < n; ++k) {
+        if (b->hT[k] == 0) continue;                 // never started in this batch
+        const int rc = check_device_error(b->m[k]);
+        if (rc) return bfail(b, rc, b->m[k]->err);
+    }
+    return SIM_OK;
+}
+
+extern "C" int sim_batch_rollout(sim_batch b, int32_t T) {
+    if (!b) return SIM_EINVAL;
+    for (int k = 0; k < (int)b->m.size(); ++k) {
+        const int rc = sim_batch_start(b, k, T);
+        if (rc) return rc;
+    }
+    return sim_batch_advance(b, T + 1, nullptr);
+}
+
+extern "C" int sim_batch_destroy(sim_batch b) {
+    if (!b) return SIM_OK;
+    cudaSetDevice(b->device);
+    batch_release(b);
+    delete b;
+    return SIM_OK;
+}
+
+extern "C" const char *sim_batch_last_error(sim_batch b) { return b ? b->err.c_str() : g_create_err.c_str(); }
 
 // ============================================================================
 // Allocation-free forward rollout.
@@ -1167,8 +1427,7 @@ extern "C" int sim_rollout_static(const sim_network *net, const sim_demand *dem,
     const int nmax = std::max(std::max(L, V), std::max(N, 4));
     k_reset<<<(nmax + 255) / 256, 256, 0, s>>>(d, fifo_beg);
     const size_t smem = (size_t)smax * sizeof(float);
-    if (cudaFuncSetAttribute(k_step_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return SIM_ECUDA;
+    if (raise_smem_attr(k_step_a, g_attr_a, opt->device, smem) != cudaSuccess) return SIM_ECUDA;
     for (int t = 0; t < T; ++t) {
         k_step_a<<<nblk, kBlockA, smem, s>>>(d, t, 0);
         k_step_b<<<(L + V + 255) / 256, 256, 0, s>>>(d, t);

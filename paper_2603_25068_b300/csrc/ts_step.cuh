@@ -407,8 +407,8 @@ __device__ __forceinline__ void block_count(int v, int *dst, int *smem) {
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) k_step_b(DevSim d, int t) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Transfers of step t for link / origin node i (every thread of the block calls).
+__device__ __forceinline__ void step_b(const DevSim &d, int i, int t) {
     const int p = t & 1;
     const unsigned long long *W = p ? d.W1 : d.W0;
     int released = 0, arrived = 0, entered = 0, cands = 0;
@@ -490,6 +490,94 @@ __global__ void __launch_bounds__(256) k_step_b(DevSim d, int t) {
     block_count(arrived, &d.step_delta[4 * t + 1], smem);
     block_count(cands, &d.step_delta[4 * t + 2], smem);
     block_count(entered, &d.step_delta[4 * t + 3], smem);
+}
+
+
+__global__ void __launch_bounds__(256) k_step_b(DevSim d, int t) {
+    step_b(d, blockIdx.x * blockDim.x + threadIdx.x, t);
+}
+
+// ---------------------------------------------------------------------------
+// Batched launches: one kernel per phase over the blocks of many simulator
+// instances (members), each block belonging to one member.  Members carry their
+// own step counter and mode in device memory, so that they can have different
+// horizons and join or leave at step boundaries.
+// ---------------------------------------------------------------------------
+constexpr int kModeRun = 0, kModeFinal = 1, kModeDone = 2;
+
+__device__ __forceinline__ void load_member(DevSim &sd, const DevSim *ds, int m) {
+    const int nw = (int)(sizeof(DevSim) / sizeof(int));
+    for (int k = threadIdx.x; k < nw; k += blockDim.x) reinterpret_cast<int *>(&sd)[k] = reinterpret_cast<const int *>(ds + m)[k];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBlockA, 6) k_batch_a(const DevSim *ds, const int2 *bmap, const int *tvec,
+                                                        const int *mode) {
+    extern __shared__ float xs[];
+    __shared__ DevSim sd;
+    const int2 m = bmap[blockIdx.x];
+    const int md = mode[m.x];
+    if (md == kModeDone) return;
+    load_member(sd, ds, m.x);
+    step_block(sd, m.y, tvec[m.x], md == kModeFinal, xs);
+}
+
+__global__ void __launch_bounds__(256) k_batch_b(const DevSim *ds, const int2 *bmap, const int *tvec, const int *mode) {
+    __shared__ DevSim sd;
+    const int2 m = bmap[blockIdx.x];
+    if (mode[m.x] != kModeRun) return;
+    load_member(sd, ds, m.x);
+    step_b(sd, m.y * 256 + (int)threadIdx.x, tvec[m.x]);
+}
+
+// after each batched step: running members advance; a member reaching its
+// horizon closes its last bin in the next step's pass, then stops
+__global__ void k_batch_tick(int n, int *tvec, const int *Tvec, int *mode) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const int md = mode[m];
+    if (md == kModeRun) {
+        const int t = tvec[m] + 1;
+        tvec[m] = t;
+        if (t >= Tvec[m]) mode[m] = kModeFinal;
+    } else if (md == kModeFinal) {
+        mode[m] = kModeDone;
+    }
+}
+
+// checkpoint of the members recording a tape (every K steps, before the step)
+struct CkDev {
+    int K, L, S, V, N;
+    int4 *lq, *lstat;
+    int *vac, *sentry, *fifo, *vstate;
+    float *pos;
+    int2 *saux;
+    longlong2 *lpos;
+};
+
+__global__ void k_batch_ckpt(const DevSim *ds, const CkDev *cks, const int *tvec, const int *mode) {
+    const int m = blockIdx.y;
+    const CkDev c = cks[m];
+    if (c.K <= 0 || mode[m] != kModeRun) return;
+    const int t = tvec[m];
+    if (t % c.K != 0) return;
+    const DevSim &d = ds[m];
+    const size_t s = t / c.K;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const float *pc = (t & 1) ? d.pos1 : d.pos0;
+    for (size_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)c.S; i += stride) {
+        c.pos[s * c.S + i] = pc[i];
+        c.saux[s * c.S + i] = d.saux[i];
+        c.sentry[s * c.S + i] = d.sentry[i];
+    }
+    for (size_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)c.L; i += stride) {
+        c.lq[s * c.L + i] = d.lq[i];
+        c.lstat[s * c.L + i] = d.lstat[i];
+        c.vac[s * c.L + i] = d.vac[i];
+        c.lpos[s * c.L + i] = d.lpos[i];
+    }
+    for (size_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)c.V; i += stride) c.fifo[s * c.V + i] = d.fifo_ptr[i];
+    for (size_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)c.N; i += stride) c.vstate[s * c.N + i] = d.vstate[i];
 }
 
 }  // namespace ts

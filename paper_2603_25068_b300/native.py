@@ -76,6 +76,12 @@ SIGNATURES = {
     "sim_get_state": (C.c_int, [P, C.POINTER(sim_state_view)]),
     "sim_get_records": (C.c_int, [P, C.POINTER(sim_records)]),
     "sim_set_stage": (C.c_int, [P, C.c_int32]),
+    "sim_batch_create": (C.c_int, [C.POINTER(P), C.c_int32, C.POINTER(P)]),
+    "sim_batch_start": (C.c_int, [P, C.c_int32, C.c_int32]),
+    "sim_batch_advance": (C.c_int, [P, C.c_int32, P]),
+    "sim_batch_rollout": (C.c_int, [P, C.c_int32]),
+    "sim_batch_destroy": (C.c_int, [P]),
+    "sim_batch_last_error": (C.c_char_p, [P]),
     "sim_rollout_static": (C.c_int, [C.POINTER(sim_network), C.POINTER(sim_demand), C.POINTER(sim_params),
                                      C.POINTER(sim_options), C.c_int32, C.POINTER(sim_outputs)]),
     "sim_time": (C.c_int32, [P]),

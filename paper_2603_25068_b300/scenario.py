@@ -463,3 +463,28 @@ def calibration(n_sensors: int = 2000, T: int = 1800, seed_truth: int = 2, **kw)
     truth = truth.copy(w=_f32(model.w + rng.normal(0.0, 0.5, size=model.F)))
     sensors = _i32(np.sort(rng.choice(model.L, size=min(n_sensors, model.L), replace=False)))
     return model.copy(sensors=sensors), truth.copy(sensors=sensors)
+
+
+def batched_scenarios(n: int = 64, seed: int = 3, n_min: int = 10_000, n_max: int = 200_000,
+                      n_perturbed: int = 500, T: int = 1800, **city_kw):
+    """Control-candidate scenarios on one city network: vehicle counts
+    log-uniform over [n_min, n_max], and in each scenario the outflow capacity
+    of n_perturbed random links scaled by U(0.7, 1.0); each scenario has its own
+    demand draw and random key."""
+    rng = np.random.default_rng(seed)
+    base = city(T=T, **city_kw)
+    out = []
+    for k in range(n):
+        nk = int(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+        mult = np.ones(base.L)
+        links = rng.choice(base.L, size=min(n_perturbed, base.L), replace=False)
+        mult[links] = rng.uniform(0.7, 1.0, size=len(links))
+        q = np.rint(base.q_fx.astype(np.float64) * mult)
+        r = np.random.default_rng([seed, k])
+        idx = r.choice(base.N, size=min(nk, base.N), replace=False)
+        idx.sort()
+        sc = base.copy(name=f"candidate_{k}", q_fx=_i32(np.maximum(q, 1)), N=len(idx),
+                       origin=base.origin[idx], dest_zone=base.dest_zone[idx], dep_step=base.dep_step[idx],
+                       od=base.od[idx], seed=int(base.seed) + 1000 * (k + 1), scenario_id=k)
+        out.append(sc)
+    return out

@@ -156,3 +156,18 @@ def test_fp32_against_fp64_error_statement(Simulator):
         steps_equal = t + 1
     assert steps_equal >= 100
     assert worst < 1e-4, worst
+
+
+def test_handles_with_different_launch_shapes_coexist(Simulator):
+    """A handle created after another with a smaller shared-memory stage must not
+    break the first one (the kernel attribute is shared by all handles)."""
+    big = S.line_network(n_links=2, length=3000.0, kappa=0.8, N=50, T=60)
+    small = S.tiny_grid(n_vehicles=50, T=60)
+    g1 = Simulator(big)
+    g2 = Simulator(small)
+    o1 = g1.rollout()
+    o2 = g2.rollout()
+    r1 = OracleSim(big, "fp32").rollout()
+    r2 = OracleSim(small, "fp32").rollout()
+    assert_outputs_equal(o1, r1, 60)
+    assert_outputs_equal(o2, r2, 60)
