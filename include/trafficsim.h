@@ -225,6 +225,11 @@ SIM_API int sim_get_records(sim_handle h, sim_records *out);
  * this many slots).  Results do not depend on it.  Errors: SIM_EINVAL. */
 SIM_API int sim_set_stage(sim_handle h, int32_t slots);
 
+/* Move the handle's work to another stream of its device (the old stream is
+ * drained first; a stream the handle created is destroyed).  NULL: only drain.
+ * Not for a handle that is a member of a live batch. */
+SIM_API int sim_set_stream(sim_handle h, void *stream);
+
 /* Current time step and device bytes held by the handle. */
 SIM_API int32_t sim_time(sim_handle h);
 SIM_API size_t sim_device_bytes(sim_handle h);

@@ -114,6 +114,7 @@ struct sim_ctx {
     int K = 0;                           // steps per checkpoint segment
     int route_cap = 0;
     bool tape_ready = false;             // last call was a recorded sim_rollout
+    int bmode = 2;                       // batch mode (running / closing last bin / idle)
     int cap_seg = 0;                     // checkpoints allocated
     BwdDev b{};
     struct Ckpt {
@@ -949,6 +950,18 @@ extern "C" int sim_get_records(sim_handle h, sim_records *out) {
     return SIM_OK;
 }
 
+extern "C" int sim_set_stream(sim_handle h, void *stream) {
+    if (!h) return SIM_EINVAL;
+    CU(cudaSetDevice(h->device));
+    CU(cudaStreamSynchronize(h->stream));
+    if (stream) {
+        if (h->own_stream) CU(cudaStreamDestroy(h->stream));
+        h->own_stream = false;
+        h->stream = (cudaStream_t)stream;
+    }
+    return SIM_OK;
+}
+
 /* queue slots staged in shared memory per link block of k_step_a */
 extern "C" int sim_set_stage(sim_handle h, int32_t slots) {
     if (!h) return SIM_EINVAL;
@@ -1075,11 +1088,20 @@ extern "C" int sim_batch_create(const sim_handle *members, int32_t n, sim_batch 
         (rc = balloc(b, &b->d_bmapB, b->nB)) || (rc = balloc(b, &b->d_t, n)) || (rc = balloc(b, &b->d_T, n)) ||
         (rc = balloc(b, &b->d_mode, n)))
         return fin(rc);
+    // members already running in an earlier batch continue where they are
+    std::vector<int> ht(n);
     b->hT.assign(n, 0);
     b->hmode.assign(n, kModeDone);
+    for (int k = 0; k < n; ++k) {
+        sim_ctx *h = b->m[k];
+        b->hmode[k] = h->bmode;
+        b->hT[k] = h->bmode == kModeDone ? 0 : h->T;
+        ht[k] = h->bmode == kModeDone ? 0 : h->t;
+    }
     if (cudaMemcpyAsync(b->d_bmapA, bmA.data(), bmA.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream) ||
         cudaMemcpyAsync(b->d_bmapB, bmB.data(), bmB.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream) ||
-        cudaMemsetAsync(b->d_t, 0, n * sizeof(int), b->stream) || cudaMemsetAsync(b->d_T, 0, n * sizeof(int), b->stream) ||
+        cudaMemcpyAsync(b->d_t, ht.data(), n * sizeof(int), cudaMemcpyHostToDevice, b->stream) ||
+        cudaMemcpyAsync(b->d_T, b->hT.data(), n * sizeof(int), cudaMemcpyHostToDevice, b->stream) ||
         cudaMemcpyAsync(b->d_mode, b->hmode.data(), n * sizeof(int), cudaMemcpyHostToDevice, b->stream))
         return fin(bfail(b, SIM_ECUDA, "batch set-up copies"));
     for (int k = 0; k < n; ++k)
@@ -1108,6 +1130,7 @@ extern "C" int sim_batch_start(sim_batch b, int32_t k, int32_t T) {
     BCU(cudaStreamSynchronize(b->stream));
     b->hT[k] = T;
     b->hmode[k] = kModeRun;
+    h->bmode = kModeRun;
     h->t = 0;
     h->T = T;
     h->n_bins = sim_n_bins(T, h->opt.obs_every);
@@ -1162,6 +1185,7 @@ extern "C" int sim_batch_advance(sim_batch b, int32_t n_steps, int32_t *finished
             h->t = tv[k];
         }
         b->hmode[k] = mode[k];
+        h->bmode = mode[k];
         if (finished) finished[k] = mode[k] == kModeDone;
     }
     for (int k = 0; k < n; ++k) {

@@ -76,6 +76,7 @@ SIGNATURES = {
     "sim_get_state": (C.c_int, [P, C.POINTER(sim_state_view)]),
     "sim_get_records": (C.c_int, [P, C.POINTER(sim_records)]),
     "sim_set_stage": (C.c_int, [P, C.c_int32]),
+    "sim_set_stream": (C.c_int, [P, P]),
     "sim_batch_create": (C.c_int, [C.POINTER(P), C.c_int32, C.POINTER(P)]),
     "sim_batch_start": (C.c_int, [P, C.c_int32, C.c_int32]),
     "sim_batch_advance": (C.c_int, [P, C.c_int32, P]),

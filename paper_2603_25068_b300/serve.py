@@ -1,0 +1,283 @@
+"""Serving loop: continuous batching of simulation requests on one GPU.
+
+Requests (nowcast rollouts, calibration-gradient rollouts, control-candidate
+rollouts) arrive over time.  The engine
+  * admits a request as soon as its device memory fits in the HBM budget
+    (sim_device_bytes of the created handle plus its reverse-pass needs),
+  * runs every admitted forward rollout in one batch: one launch per phase and
+    step for all of them (sim_batch_*), a new request joining at the next step
+    boundary, finished ones leaving it,
+  * runs the reverse pass of a finished gradient request on a worker thread with
+    its own stream, so that it overlaps the batched forward work on the device,
+  * records each request's latency from arrival to result.
+Each request's result is the one it would get alone: batching changes neither
+its random key nor its state.
+"""
+from __future__ import annotations
+
+import dataclasses
+import queue
+import threading
+import time
+from typing import List, Optional
+
+import numpy as np
+
+from . import native as nat
+from .batch import Batch
+from .sim import Simulator
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    kind: str                 # "nowcast" | "calibration" | "control"
+    scenario: object          # scenario.Scenario (its T is the horizon)
+    arrival: float            # seconds after the stream starts
+    observed: Optional[np.ndarray] = None     # [n_bins, n_sensors] calibration targets
+    target_link: int = 0      # control: link whose count is to be halved
+    # filled by the engine
+    admitted: float = float("nan")
+    finished: float = float("nan")
+    result: Optional[dict] = None
+
+    @property
+    def needs_grad(self):
+        return self.kind in ("calibration", "control")
+
+    @property
+    def vehicle_steps(self):
+        return self.scenario.N * self.scenario.T
+
+
+def loss_cotangent(req: Request, counts: np.ndarray) -> np.ndarray:
+    """dL/dcounts of the request's loss: calibration -- mean squared error of the
+    sensor counts against the observations (Methods "Optimization"); control --
+    squared error of the target link's total count against half its value."""
+    sc = req.scenario
+    yb = np.zeros(counts.shape, np.float32)
+    if req.kind == "calibration":
+        s = sc.sensors
+        diff = counts[:, s].astype(np.float32) - req.observed
+        yb[:, s] = 2.0 * diff / diff.size
+    elif req.kind == "control":
+        tot = float(counts[:, req.target_link].sum())
+        yb[:, req.target_link] = 2.0 * (tot - 0.5 * tot)
+    return yb
+
+
+def run_request_alone(req: Request, device: int = 0, ckpt_every: int = 180, route_cap: int = 256) -> dict:
+    """The same request processed on its own (the reference for mix parity and
+    for serial execution)."""
+    sc = req.scenario
+    sim = Simulator(sc, device=device, ckpt_every=ckpt_every if req.needs_grad else 0, route_cap=route_cap)
+    out = sim.rollout(sc.T)
+    res = dict(counts=out["counts"], speed=out["speed"], travel_time=out["travel_time"])
+    if req.needs_grad:
+        res["grad"] = sim.backward(loss_cotangent(req, out["counts"]))
+    sim.close()
+    return res
+
+
+class Engine:
+    def __init__(self, device: int = 0, hbm_budget: float = 150e9, chunk: int = 60, ckpt_every: int = 180,
+                 route_cap: int = 256):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.budget = hbm_budget
+        self.chunk = chunk
+        self.ckpt_every = ckpt_every
+        self.route_cap = route_cap
+        self.stream = torch.cuda.Stream(device=device)
+        self.bwd_stream = torch.cuda.Stream(device=device)
+        self.active: List[tuple] = []          # (request, simulator, bytes)
+        self.batch: Optional[Batch] = None
+        self.batch_members: List[int] = []
+        self.used = 0.0
+        self.bwd_q: "queue.Queue" = queue.Queue()
+        self.bwd_thread = threading.Thread(target=self._bwd_worker, daemon=True)
+        self.bwd_thread.start()
+        self.lock = threading.Lock()
+        self.t0 = None
+
+    # -------------------------------------------------------------- helpers
+    def now(self):
+        return time.perf_counter() - self.t0
+
+    def _estimate_extra(self, req: Request) -> float:
+        """Device bytes beyond the handle: reverse-pass workspace share."""
+        if not req.needs_grad:
+            return 0.0
+        sc = req.scenario
+        slots = float(np.sum(np.floor(sc.length.astype(np.float64) * sc.kappa / sc.dn) + 2))
+        return 9.0 * (self.ckpt_every + 1) * slots + 16.0 * sc.N * self.route_cap
+
+    def _bwd_worker(self):
+        torch = self.torch
+        while True:
+            item = self.bwd_q.get()
+            if item is None:
+                return
+            req, sim, nbytes = item
+            with torch.cuda.device(self.device):
+                sim.set_stream(self.bwd_stream)          # overlaps the batched forward work
+                out = sim.outputs()
+                g = sim.backward(loss_cotangent(req, out["counts"]))
+                req.result = dict(counts=out["counts"], speed=out["speed"], travel_time=out["travel_time"], grad=g)
+                sim.close()
+            with self.lock:
+                self.used -= nbytes
+            req.finished = self.now()
+
+    def _rebuild(self, new=()):
+        if self.batch is not None:
+            self.batch.close()
+            self.batch = None
+        if self.active:
+            self.batch = Batch([s for (_, s, _) in self.active])
+            for req in new:
+                i = next(i for i, (r, _, _) in enumerate(self.active) if r is req)
+                self.batch.start(i, req.scenario.T)
+
+    def _admit(self, req: Request) -> bool:
+        sc = req.scenario
+        extra = self._estimate_extra(req)
+        with self.lock:
+            if self.used + extra >= self.budget:
+                return False
+        sim = Simulator(sc, device=self.device, stream=self.stream,
+                        ckpt_every=self.ckpt_every if req.needs_grad else 0, route_cap=self.route_cap)
+        nbytes = float(sim.device_bytes()) + extra
+        with self.lock:
+            if self.used + nbytes > self.budget and self.active:
+                ok = False
+            else:
+                self.used += nbytes
+                ok = True
+        if not ok:
+            sim.close()
+            return False
+        req.admitted = self.now()
+        self.active.append((req, sim, nbytes))
+        return True
+
+    # -------------------------------------------------------------- main loop
+    def run(self, requests: List[Request], poll: float = 0.0005):
+        """Serve the requests (arrival times in seconds from now); returns them
+        with results and timings."""
+        torch = self.torch
+        pending = sorted(requests, key=lambda r: r.arrival)
+        self.t0 = time.perf_counter()
+        k = 0
+        waiting: List[Request] = []
+        with torch.cuda.device(self.device):
+            while True:
+                while k < len(pending) and pending[k].arrival <= self.now():
+                    waiting.append(pending[k])
+                    k += 1
+                new = []
+                still = []
+                for req in waiting:
+                    (new if self._admit(req) else still).append(req)
+                waiting = still
+                if new:
+                    self._rebuild(new)
+                if not self.active:
+                    if all(np.isfinite(r.finished) for r in requests):
+                        break
+                    time.sleep(poll)
+                    continue
+                fin = self.batch.advance(self.chunk)
+                if fin.any():
+                    done = [self.active[i] for i in np.nonzero(fin)[0]]
+                    self.active = [a for i, a in enumerate(self.active) if not fin[i]]
+                    self._rebuild()
+                    for req, sim, nbytes in done:
+                        if req.needs_grad:
+                            self.bwd_q.put((req, sim, nbytes))
+                        else:
+                            out = sim.outputs()
+                            req.result = dict(counts=out["counts"], speed=out["speed"],
+                                              travel_time=out["travel_time"])
+                            sim.close()
+                            with self.lock:
+                                self.used -= nbytes
+                            req.finished = self.now()
+            self.bwd_q.put(None)
+            self.bwd_thread.join()
+        return requests
+
+
+def latency_stats(reqs: List[Request]) -> dict:
+    lat = np.array([r.finished - r.arrival for r in reqs])
+    return dict(p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
+                mean_s=float(lat.mean()), max_s=float(lat.max()))
+
+
+def run_serial(requests: List[Request], device: int = 0, ckpt_every: int = 180) -> List[dict]:
+    """Serial single-scenario execution in arrival order (each request alone,
+    one after another), with the same arrival times."""
+    t0 = time.perf_counter()
+    out = []
+    for req in sorted(requests, key=lambda r: r.arrival):
+        now = time.perf_counter() - t0
+        if now < req.arrival:
+            time.sleep(req.arrival - now)
+        res = run_request_alone(req, device=device, ckpt_every=ckpt_every)
+        fin = time.perf_counter() - t0
+        out.append(dict(rid=req.rid, arrival=req.arrival, finished=fin, result=res))
+    return out
+
+
+_NETWORK_CACHE = {}
+
+
+def network_family(n_links: int, seed: int = 4):
+    """A network of the serving family (same generator as the city workload,
+    n_links / 3 nodes), with 1,000,000 vehicles to draw requests from; cached."""
+    from . import scenario as S
+    key = (n_links, seed)
+    if key not in _NETWORK_CACHE:
+        n_nodes = max(30, n_links // 3)
+        zo = max(4, min(80, n_nodes // 150))
+        zd = max(6, min(128, n_nodes // 94))
+        _NETWORK_CACHE[key] = S.city(seed=seed + n_links, n_nodes=n_nodes, n_links=n_links, n_vehicles=1_000_000,
+                                     T=3600, n_origin_zones=zo, n_dest_zones=zd, name=f"net{n_links}")
+    return _NETWORK_CACHE[key]
+
+
+def make_request_stream(n: int = 256, rate: float = 4.0, seed: int = 4,
+                        sizes=(2000, 4500, 9000, 18000, 36000), n_range=(50_000, 1_000_000),
+                        horizons=None, n_sensors: int = 200):
+    """Poisson request stream: 50% one-hour nowcasts (3,600-step forward), 25%
+    30-minute calibration gradients, 25% 30-minute control candidates (gradient
+    w.r.t. link costs); networks drawn from the family, vehicle counts
+    log-uniform over n_range.  Calibration targets are synthetic counts (a fixed
+    Poisson draw per sensor and bin); control candidates get cost sensitivities
+    beta ~ U(0, 5) and a target link."""
+    from .scenario import _i32, _f32
+    horizons = horizons or {"nowcast": 3600, "calibration": 1800, "control": 1800}
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for rid in range(n):
+        t += rng.exponential(1.0 / rate)
+        kind = rng.choice(["nowcast", "nowcast", "calibration", "control"])
+        base = network_family(int(rng.choice(sizes)), seed)
+        nv = int(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1]))))
+        idx = np.sort(rng.choice(base.N, size=min(nv, base.N), replace=False))
+        T = horizons[kind]
+        sc = base.copy(name=f"{kind}_{rid}", N=len(idx), origin=base.origin[idx], dest_zone=base.dest_zone[idx],
+                       dep_step=base.dep_step[idx], od=base.od[idx], T=T, seed=1000 + rid, scenario_id=rid)
+        req = Request(rid=rid, kind=str(kind), scenario=sc, arrival=t)
+        if kind == "calibration":
+            sens = _i32(np.sort(rng.choice(sc.L, size=min(n_sensors, sc.L), replace=False)))
+            req.scenario = sc.copy(sensors=sens)
+            nb = (T + sc.obs_every - 1) // sc.obs_every
+            req.observed = rng.poisson(20.0, size=(nb, len(sens))).astype(np.float32)
+        elif kind == "control":
+            req.scenario = sc.copy(beta=_f32(rng.uniform(0.0, 5.0, size=sc.L)))
+            req.target_link = int(rng.integers(0, sc.L))
+        out.append(req)
+    return out

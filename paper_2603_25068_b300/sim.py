@@ -94,6 +94,13 @@ class Simulator:
     def t(self):
         return self.lib.sim_time(self.h)
 
+    def set_stream(self, stream):
+        """Move the handle's work to another stream (torch.cuda.Stream or handle)."""
+        if stream is not None and not isinstance(stream, int):
+            stream = stream.cuda_stream
+        self._check(self.lib.sim_set_stream(self.h, stream))
+        self.stream_ptr = stream
+
     def device_bytes(self):
         return self.lib.sim_device_bytes(self.h)
 

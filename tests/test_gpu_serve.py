@@ -1,0 +1,44 @@
+"""Serving with continuous batching: requests of different kinds, networks and
+sizes arrive while others run; each result equals the result of the same request
+processed alone (forward outputs bitwise; gradients up to the order of double
+additions in the reverse pass)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_served_results_equal_results_alone():
+    from paper_2603_25068_b300 import serve
+    reqs = serve.make_request_stream(n=8, rate=40.0, seed=7, sizes=(600, 1200), n_range=(3000, 20000),
+                                     horizons={"nowcast": 400, "calibration": 300, "control": 300}, n_sensors=50)
+    kinds = {r.kind for r in reqs}
+    assert {"nowcast"} < kinds
+    eng = serve.Engine(hbm_budget=20e9, chunk=25, ckpt_every=60)
+    eng.run(reqs)
+    st = serve.latency_stats(reqs)
+    assert st["p99_s"] >= st["p50_s"] > 0
+    # several requests were in flight together
+    overlap = sum(1 for a in reqs for b in reqs if a is not b and a.admitted < b.finished and b.admitted < a.finished)
+    assert overlap > 0
+    for r in reqs:
+        alone = serve.run_request_alone(r, ckpt_every=60)
+        for k in ("counts", "speed", "travel_time"):
+            np.testing.assert_array_equal(r.result[k], alone[k], err_msg=f"{r.kind} {k}")
+        if r.needs_grad:
+            for k, g in alone["grad"].items():
+                scale = max(1e-6, float(np.abs(g).max()))
+                np.testing.assert_allclose(r.result["grad"][k], g, rtol=0, atol=1e-5 * scale, err_msg=f"{r.kind} {k}")
+
+
+def test_admission_respects_the_budget():
+    from paper_2603_25068_b300 import serve
+    reqs = serve.make_request_stream(n=4, rate=1000.0, seed=8, sizes=(600,), n_range=(3000, 6000),
+                                     horizons={"nowcast": 120, "calibration": 120, "control": 120})
+    one = max(serve.Simulator(r.scenario).device_bytes() for r in reqs)
+    eng = serve.Engine(hbm_budget=1.5 * one + 1e8, chunk=20, ckpt_every=60)   # about one request at a time
+    eng.run(reqs)
+    assert all(np.isfinite(r.finished) for r in reqs)
+    order = sorted(reqs, key=lambda r: r.admitted)
+    # with room for about one request, admissions wait for earlier results
+    assert any(b.admitted >= a.finished - 1e-3 for a, b in zip(order, order[1:]))
