@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--small", action="store_true", help="small network (for profiling captures)")
     ap.add_argument("--stage", type=int, default=0, help="queue slots per link block (0 = autotune)")
     ap.add_argument("--no-fwd-bwd", action="store_true", help="skip the calibration-gradient leg")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-scenario leg")
+    ap.add_argument("--batch-n", type=int, default=64)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-requests", type=int, default=32)
     return ap.parse_args()
 
 
@@ -266,6 +270,97 @@ def run_fwd_bwd(args, dev, stream, flush, ws):
             "grad_norm_w": float(np.linalg.norm(g["w"])), "grad_norm_lambda": float(np.linalg.norm(g["od_lambda"]))}
 
 
+# ------------------------------------------------------------------ batched
+def run_batched(args, dev, stream, flush, ws):
+    """Batched control-candidate scenarios: n scenarios of 10k-200k vehicles on
+    the city network with per-scenario capacity multipliers, 1,800 steps,
+    forward in one batched launch per phase and step, then each scenario's
+    reverse pass; against the same scenarios run one by one."""
+    import torch
+    from paper_2603_25068_b300 import scenario as S
+    from paper_2603_25068_b300.batch import Batch
+    from paper_2603_25068_b300.sim import Simulator
+    kw = dict(n_nodes=3000, n_links=9000, n_vehicles=250_000, n_origin_zones=20, n_dest_zones=32) if args.small else {}
+    scs = S.batched_scenarios(n=args.batch_n, **kw)
+    T = scs[0].T
+    sims = [Simulator(sc, device=dev.index, stream=stream, ckpt_every=180, route_cap=256) for sc in scs]
+    rng = np.random.default_rng(0)
+    ybars = []
+    vs = float(sum(sc.N for sc in scs)) * T
+    # batched: one warm-up batch rollout, then a timed batch forward + reverse passes
+    res = {}
+    with Batch(sims) as b:
+        b.rollout(T)
+        for sc, sm in zip(scs, sims):
+            ybars.append(rng.normal(size=(sm.n_bins(T), sc.L)).astype(np.float32))
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        b.rollout(T)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        for sm, yb in zip(sims, ybars):
+            sm.backward(yb)
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
+    res["batched_forward_s"] = t1 - t0
+    res["batched_forward_plus_reverse_s"] = t2 - t0
+    # serial single-scenario path
+    flush.fill_(2.0)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for sm in sims:
+        sm.rollout(T)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    for sm, yb in zip(sims, ybars):
+        sm.rollout(T)
+        sm.backward(yb)
+    torch.cuda.synchronize(dev)
+    t2 = time.perf_counter()
+    res["serial_forward_s"] = t1 - t0
+    res["serial_forward_plus_reverse_s"] = t2 - t1
+    for s_ in sims:
+        s_.close()
+    return {"metric": "vehicle-steps/s", "unit": "vehicle-steps/s",
+            "workload": f"{len(scs)} control-candidate scenarios on the {scs[0].L}-link city network, "
+                        f"{int(sum(sc.N for sc in scs)):,} vehicles in total ({min(sc.N for sc in scs):,}-"
+                        f"{max(sc.N for sc in scs):,} per scenario), {T} steps, capacity x U(0.7,1.0) on 500 links",
+            "batched_forward": vs / res["batched_forward_s"],
+            "serial_forward": vs / res["serial_forward_s"],
+            "batched_forward_plus_reverse": vs / res["batched_forward_plus_reverse_s"],
+            "serial_forward_plus_reverse": vs / res["serial_forward_plus_reverse_s"],
+            "seconds": res,
+            "timing": "host wall clock, device synchronised; reverse passes run one scenario after another"}
+
+
+# ------------------------------------------------------------------ serving
+def run_serving(args, dev, ws):
+    """Poisson stream of nowcast / calibration / control requests on networks of
+    2k-36k links and 50k-1M vehicles, continuous batching under a 150 GB budget,
+    against serial single-scenario execution of the same stream."""
+    from paper_2603_25068_b300 import serve
+    sizes = (600, 1200, 2400) if args.small else (2000, 4500, 9000, 18000, 36000)
+    n_range = (5000, 50000) if args.small else (50_000, 1_000_000)
+    reqs = serve.make_request_stream(n=args.serve_requests, rate=4.0, seed=4, sizes=sizes, n_range=n_range)
+    eng = serve.Engine(device=dev.index, hbm_budget=150e9, chunk=60, ckpt_every=180)
+    t0 = time.perf_counter()
+    eng.run(reqs)
+    makespan = max(r.finished for r in reqs)
+    st = serve.latency_stats(reqs)
+    vs = float(sum(r.vehicle_steps for r in reqs))
+    ser = serve.run_serial(reqs, device=dev.index, ckpt_every=180)
+    lat_s = np.array([x["finished"] - x["arrival"] for x in ser])
+    ser_span = max(x["finished"] for x in ser)
+    return {"requests": len(reqs), "rate_per_s": 4.0,
+            "mix": {k: sum(1 for r in reqs if r.kind == k) for k in ("nowcast", "calibration", "control")},
+            "p50_latency_s": st["p50_s"], "p99_latency_s": st["p99_s"],
+            "vehicle_steps_per_s": vs / makespan,
+            "serial": {"p50_latency_s": float(np.percentile(lat_s, 50)), "p99_latency_s": float(np.percentile(lat_s, 99)),
+                       "vehicle_steps_per_s": vs / ser_span},
+            "hbm_budget_gb": 150, "note": "latency from arrival to result, including simulator creation"}
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args):
     import torch
@@ -408,6 +503,10 @@ def run_ours(args):
 
     if not args.no_fwd_bwd:
         line["fwd_bwd"] = run_fwd_bwd(args, dev, stream, flush, ws)
+    if not args.no_batched:
+        line["batched"] = run_batched(args, dev, stream, flush, ws)
+    if not args.no_serve:
+        line["serving"] = run_serving(args, dev, ws)
 
     if rank == 0 and not args.no_cpu_baseline:
         steps, wall = oracle_sample(sc, args.cpu_budget)

@@ -99,6 +99,7 @@ class Engine:
         self.bwd_thread = threading.Thread(target=self._bwd_worker, daemon=True)
         self.bwd_thread.start()
         self.lock = threading.Lock()
+        self.worker_error = None
         self.t0 = None
 
     # -------------------------------------------------------------- helpers
@@ -120,12 +121,15 @@ class Engine:
             if item is None:
                 return
             req, sim, nbytes = item
-            with torch.cuda.device(self.device):
-                sim.set_stream(self.bwd_stream)          # overlaps the batched forward work
-                out = sim.outputs()
-                g = sim.backward(loss_cotangent(req, out["counts"]))
-                req.result = dict(counts=out["counts"], speed=out["speed"], travel_time=out["travel_time"], grad=g)
-                sim.close()
+            try:
+                with torch.cuda.device(self.device):
+                    out = sim.outputs()
+                    g = sim.backward(loss_cotangent(req, out["counts"]))
+                    req.result = dict(counts=out["counts"], speed=out["speed"], travel_time=out["travel_time"], grad=g)
+                    sim.close()
+            except Exception as e:          # reported by the main loop
+                self.worker_error = e
+                return
             with self.lock:
                 self.used -= nbytes
             req.finished = self.now()
@@ -163,7 +167,7 @@ class Engine:
         return True
 
     # -------------------------------------------------------------- main loop
-    def run(self, requests: List[Request], poll: float = 0.0005):
+    def run(self, requests: List[Request], poll: float = 0.0005, max_seconds: float = 3600.0):
         """Serve the requests (arrival times in seconds from now); returns them
         with results and timings."""
         torch = self.torch
@@ -173,6 +177,10 @@ class Engine:
         waiting: List[Request] = []
         with torch.cuda.device(self.device):
             while True:
+                if self.worker_error is not None or not self.bwd_thread.is_alive():
+                    raise RuntimeError(f"reverse-pass worker failed: {self.worker_error!r}")
+                if self.now() > max_seconds:
+                    raise RuntimeError("serving run exceeded its time limit")
                 while k < len(pending) and pending[k].arrival <= self.now():
                     waiting.append(pending[k])
                     k += 1
@@ -195,6 +203,8 @@ class Engine:
                     self._rebuild()
                     for req, sim, nbytes in done:
                         if req.needs_grad:
+                            # leave the batch's stream here, where nothing is being captured
+                            sim.set_stream(self.bwd_stream)
                             self.bwd_q.put((req, sim, nbytes))
                         else:
                             out = sim.outputs()
