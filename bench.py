@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="small network (for profiling captures)")
     ap.add_argument("--stage", type=int, default=0, help="queue slots per link block (0 = autotune)")
+    ap.add_argument("--executor", default="auto", choices=["auto", "step", "persistent"],
+                    help="forward executor of the timed rollouts")
     ap.add_argument("--no-fwd-bwd", action="store_true", help="skip the calibration-gradient leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-scenario leg")
     ap.add_argument("--batch-n", type=int, default=64)
@@ -387,11 +389,15 @@ def run_ours(args):
                travel_time=torch.empty((nb, sc.L), dtype=torch.float32, device=dev))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     from paper_2603_25068_b300 import autotune
+    sim.set_executor(args.executor)
+    executor = sim.executor
     if args.stage:
         autotune.set_stage(sim, args.stage)
         stage, stage_ms = args.stage, {}
-    else:
+    elif executor == "step":
         stage, stage_ms = autotune.tune_stage(sim, T=min(T, 900))
+    else:
+        stage, stage_ms = None, {}
 
     for _ in range(args.warmup):
         sim.rollout(T, device=True, out=out)
@@ -419,7 +425,9 @@ def run_ours(args):
         total_ms = float(t.item())
     ms_per = total_ms / args.steps
     value = ws * N * T * args.steps / (total_ms / 1000.0)
-    launches_per_rollout = 2 * T + 2        # reset + (node model, transfer) per step + final observation
+    # our kernels per rollout: reset + (node model, transfer) per step + final
+    # observation, or reset + one persistent launch
+    launches_per_rollout = 2 * T + 2 if executor == "step" else 2
 
     # ---- instrumented pass: per-kernel device time for the roofline
     kms = np.zeros(3)
@@ -438,8 +446,15 @@ def run_ours(args):
     ms_a = float(kms[0])
     achieved = bytes_a / (ms_a / 1000.0) / 1e9
     peak, peak_kind = load_peaks()
-    units_per_launch = float(np.mean(n_on))
-    traffic = ncu_traffic("k_step_a", "city_1M", units_per_launch)
+    if executor == "step":
+        kname, kdesc, per_launch = "k_step_a", "k_step_a (node model + car-following)", T
+        units_per_launch = float(np.mean(n_on))            # vehicles on links per launch (one step)
+        share = {"k_step_a": kms[0] / kms.sum(), "k_step_b": kms[1] / kms.sum(), "obs_final": kms[2] / kms.sum()}
+    else:
+        kname, kdesc, per_launch = "k_persist", "k_persist (whole rollout: every step of the path)", 1
+        units_per_launch = float(np.sum(n_on))              # vehicle-steps on links per launch (one rollout)
+        share = {"k_persist": 1.0}
+    traffic = ncu_traffic(kname, "city_1M", units_per_launch)
 
     line = {
         "metric": "vehicle-steps/s", "value": value, "unit": "vehicle-steps/s", "n_gpus": ws,
@@ -451,18 +466,38 @@ def run_ours(args):
         "x_real_time": T * sc.dt / (ms_per / 1000.0),
         "active_vehicle_steps_per_s": float(np.sum(n_on)) * ws / (ms_per / 1000.0),
         "per_rollout_ms": ms,
-        "roofline": {"bound": "hbm", "kernel": "k_step_a (node model + car-following)",
+        "roofline": {"bound": "hbm", "kernel": kdesc,
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
-                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_a / T,
-                     "avg_launch_us": 1000.0 * ms_a / T,
-                     "kernel_share": {"k_step_a": kms[0] / kms.sum(), "k_step_b": kms[1] / kms.sum(),
-                                      "obs_final": kms[2] / kms.sum()},
+                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_a / per_launch,
+                     "avg_launch_us": 1000.0 * ms_a / per_launch, "us_per_step": 1000.0 * ms_a / T,
+                     "kernel_share": share,
                      "instrumented_rollout_ms": float(kms.sum())},
         "gpu_launches": launches_per_rollout * args.steps,
-        "launch_shape": {"staged_slots_per_block": stage, "autotune_ms_per_900_steps": stage_ms},
+        "executor": executor,
+        "launch_shape": ({"staged_slots_per_block": stage, "autotune_ms_per_900_steps": stage_ms}
+                         if executor == "step" else {"ctas": "one per SM (cooperative)", "threads": 1024}),
         "clocks": clk.summary(),
     }
+
+    # ---- the other executor on the same workload, for comparison
+    if executor == "persistent":
+        sim.set_executor("step")
+        st_stage, _ = autotune.tune_stage(sim, T=min(T, 900))
+        sim.rollout(T, device=True, out=out)
+        st_ms = []
+        for k in range(2):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.rollout(T, device=True, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            st_ms.append(e0.elapsed_time(e1))
+        sim.set_executor("auto")
+        line["step_executor"] = {"ms_per_rollout": float(np.mean(st_ms)), "staged_slots_per_block": st_stage,
+                                 "vehicle_steps_per_s": N * T / (float(np.mean(st_ms)) / 1000.0),
+                                 "note": "two kernels per step in a CUDA graph, same workload and outputs"}
 
     # ---- end to end through the public API with host buffers
     if not args.no_e2e:

@@ -225,6 +225,26 @@ SIM_API int sim_get_records(sim_handle h, sim_records *out);
  * this many slots).  Results do not depend on it.  Errors: SIM_EINVAL. */
 SIM_API int sim_set_stage(sim_handle h, int32_t slots);
 
+/* Forward executor of sim_rollout / sim_step (results are bit-identical):
+ *   SIM_EXEC_STEP        two kernels per step (link blocks, then transfers),
+ *                        captured into a CUDA graph per horizon;
+ *   SIM_EXEC_PERSISTENT  the whole run in one cooperative launch, one CTA per
+ *                        SM, every link queue resident in shared memory and one
+ *                        grid-wide barrier per step (the paper has no
+ *                        counterpart: its step is a sequence of XLA ops);
+ *   SIM_EXEC_AUTO        (default) persistent when available, else step.
+ * The persistent executor is available when every queue of the network fits in
+ * the shared memory of the GPU's SMs and the handle records no reverse-pass tape
+ * (ckpt_every = 0).  Errors: SIM_EINVAL (unknown value, or persistent requested
+ * where it is unavailable; the text says why). */
+#define SIM_EXEC_AUTO       0
+#define SIM_EXEC_STEP       1
+#define SIM_EXEC_PERSISTENT 2
+SIM_API int sim_set_executor(sim_handle h, int32_t executor);
+/* Executor the next forward run will use (SIM_EXEC_STEP or SIM_EXEC_PERSISTENT),
+ * -1 for a NULL handle. */
+SIM_API int32_t sim_get_executor(sim_handle h);
+
 /* Move the handle's work to another stream of its device (the old stream is
  * drained first; a stream the handle created is destroyed).  NULL: only drain.
  * Not for a handle that is a member of a live batch. */

@@ -1,9 +1,14 @@
 // trafficsim.cu -- host side of the simulator and the C ABI of include/trafficsim.h.
-// The step kernels are in ts_step.cuh; a rollout is captured once per horizon
-// into a CUDA graph of 2T + 2 kernels (reset, T x (k_step_a, k_step_b), final
-// observation).
+// Two forward executors run the same step:
+//   * per-step kernels (ts_step.cuh): a rollout is captured once per horizon
+//     into a CUDA graph of 2T + 2 kernels (reset, T x (k_step_a, k_step_b),
+//     final observation); used when recording the reverse-pass tape and for
+//     networks whose queues do not fit in shared memory;
+//   * persistent (ts_persist.cuh): the whole run in one cooperative launch with
+//     every queue resident in shared memory, one grid barrier per step.
 #include "../../include/trafficsim.h"
 #include "ts_backward.cuh"
+#include "ts_persist.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -127,6 +132,13 @@ struct sim_ctx {
     int *d_dummy = nullptr;              // step counters of recomputed steps
     int *d_od = nullptr;
     float *d_od_lambda = nullptr;
+    // persistent executor
+    int executor = SIM_EXEC_AUTO;        // requested
+    bool persist_ok = false;             // the network fits (groups, shared memory, co-residency)
+    std::string persist_why;             // reason when it does not
+    int G = 0;                           // CTAs (one per SM at most)
+    size_t persist_smem = 0;
+    PArgs pa{};
 };
 
 // Workspace of the reverse pass (tape of one segment, adjoints, accumulators),
@@ -230,6 +242,112 @@ static int build_blocks(sim_ctx *h) {
     h->d.npb = (h->V + nblk - 1) / nblk;
     h->stage_max = smax;
     CU(raise_smem_attr(k_step_a, g_attr_a, h->device, (size_t)smax * sizeof(float)));
+    return SIM_OK;
+}
+
+// Groups of the persistent executor: consecutive links packed into at most one
+// group per SM, each within kPLinks links and the shared memory left for queue
+// slots, with the largest group weight (slots + 16 per link) made as small as
+// possible (binary search over the bound, greedy packing).
+static size_t g_attr_p[64];
+static int build_groups(sim_ctx *h) {
+    h->persist_ok = false;
+    int nsm = 0, optin = 0;
+    CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    const long long slot_cap = ((long long)optin - (long long)sizeof(PSmem)) / (long long)sizeof(float);
+    const int L = h->L;
+    std::vector<long long> cap(L);
+    long long wsum = 0, wmax = 0;
+    for (int j = 0; j < L; ++j) {
+        cap[j] = h->lst_host[4 * j + 1];
+        if (cap[j] > slot_cap) {
+            h->persist_why = "a link queue is larger than the shared memory of one CTA";
+            return SIM_OK;
+        }
+        wsum += cap[j] + 16;
+        wmax = std::max(wmax, cap[j] + 16);
+    }
+    auto pack = [&](long long bound, std::vector<int> *starts) {
+        int groups = 0, nl = 0;
+        long long w = 0, slots = 0;
+        if (starts) starts->clear();
+        for (int j = 0; j < L; ++j) {
+            const long long wj = cap[j] + 16;
+            if (nl == 0 || nl == kPLinks || w + wj > bound || slots + cap[j] > slot_cap) {
+                if (starts) starts->push_back(j);
+                ++groups;
+                nl = 0; w = 0; slots = 0;
+            }
+            ++nl; w += wj; slots += cap[j];
+        }
+        return groups;
+    };
+    long long lo = std::max(wmax, (wsum + nsm - 1) / nsm), hi = std::max(lo, wsum);
+    if (pack(hi, nullptr) > nsm) {
+        h->persist_why = "the queues do not fit in the shared memory of the GPU";
+        return SIM_OK;
+    }
+    while (lo < hi) {
+        const long long mid = lo + (hi - lo) / 2;
+        if (pack(mid, nullptr) <= nsm) hi = mid; else lo = mid + 1;
+    }
+    std::vector<int> starts;
+    pack(lo, &starts);
+    const int ngl = (int)starts.size();
+    const int G = std::max(ngl, (h->V + kPNodes - 1) / kPNodes);
+    if (G > nsm) {
+        h->persist_why = "too many origin nodes for one CTA per SM";
+        return SIM_OK;
+    }
+    std::vector<int> grp(starts);
+    grp.push_back(L);
+    while ((int)grp.size() < G + 1) grp.push_back(L);
+    long long smax = 0;
+    for (int g = 0; g < G; ++g) {
+        long long sl = 0;
+        for (int j = grp[g]; j < grp[g + 1]; ++j) sl += cap[j];
+        smax = std::max(smax, sl);
+    }
+    const size_t smem = sizeof(PSmem) + (size_t)smax * sizeof(float);
+    CU(raise_smem_attr(k_persist, g_attr_p, h->device, smem));
+    int per_sm = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist, kPT, smem));
+    if (per_sm < 1 || G > per_sm * nsm) {
+        h->persist_why = "the CTAs cannot all be resident at once";
+        return SIM_OK;
+    }
+    int *d_grp = nullptr;
+    TRY(upload(h, &d_grp, grp.data(), grp.size()));
+    if (!h->pa.W3) {
+        TRY(dalloc(h, &h->pa.W3, (size_t)3 * L));
+        TRY(dalloc(h, &h->pa.crec2, (size_t)2 * L));
+        TRY(dalloc(h, &h->pa.bar, 4));
+    }
+    h->pa.grp_links = d_grp;
+    h->pa.npg = (h->V + G - 1) / G;
+    h->G = G;
+    h->persist_smem = smem;
+    h->persist_ok = true;
+    return SIM_OK;
+}
+
+// persistent executor in use for the next forward run of this handle
+static bool use_persist(const sim_ctx *h) {
+    if (h->K > 0 || !h->persist_ok) return false;
+    return h->executor != SIM_EXEC_STEP;
+}
+
+// steps [t0, t1) (+ the observation-only pass at t1) in one cooperative launch
+static int enqueue_persist(sim_ctx *h, int t0, int t1, int final_obs) {
+    PArgs a = h->pa;
+    a.t0 = t0;
+    a.t1 = t1;
+    a.final_obs = final_obs;
+    CU(cudaMemsetAsync(a.W3, 0, (size_t)3 * h->L * sizeof(unsigned long long), h->stream));
+    CU(cudaMemsetAsync(a.bar, 0, sizeof(unsigned), h->stream));
+    void *args[2] = {(void *)&h->d, (void *)&a};
+    CU(cudaLaunchCooperativeKernel((const void *)k_persist, dim3(h->G), dim3(kPT), args, h->persist_smem, h->stream));
     return SIM_OK;
 }
 
@@ -464,6 +582,7 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
         b.od_lambda = h->d_od_lambda;
     }
     TRY(build_blocks(h));
+    TRY(build_groups(h));
     TRY(upload_params(h, par));
     CU(cudaStreamSynchronize(h->stream));
     return SIM_OK;
@@ -608,10 +727,16 @@ extern "C" int sim_step(sim_handle h, int32_t n_steps) {
     if (!h->reset_done) return fail(h, SIM_ESTATE, "sim_reset first");
     if (n_steps < 0 || h->t + n_steps > h->T) return fail(h, SIM_ESTATE, "step beyond the horizon");
     CU(cudaSetDevice(h->device));
-    for (int k = 0; k < n_steps; ++k) {
-        enqueue_step(h, h->t);
-        h->t++;
-        if (h->t == h->T) enqueue_obs_final(h, h->T);
+    if (use_persist(h) && n_steps > 0) {
+        const int t1 = h->t + n_steps;
+        TRY(enqueue_persist(h, h->t, t1, t1 == h->T));
+        h->t = t1;
+    } else {
+        for (int k = 0; k < n_steps; ++k) {
+            enqueue_step(h, h->t);
+            h->t++;
+            if (h->t == h->T) enqueue_obs_final(h, h->T);
+        }
     }
     CU(cudaGetLastError());
     return check_device_error(h);
@@ -656,6 +781,19 @@ extern "C" int sim_rollout(sim_handle h, int32_t T, sim_outputs *out) {
     if (T < 1) return fail(h, SIM_EINVAL, "horizon must be >= 1");
     CU(cudaSetDevice(h->device));
     TRY(ensure_T(h, T));
+    if (use_persist(h)) {
+        enqueue_reset(h, T);
+        TRY(enqueue_persist(h, 0, T, 1));
+        CU(cudaGetLastError());
+        h->t = T;
+        h->T = T;
+        h->n_bins = sim_n_bins(T, h->opt.obs_every);
+        h->reset_done = true;
+        h->tape_ready = false;
+        TRY(copy_outputs(h, out));
+        if (out && out->on_device) return SIM_OK;
+        return check_device_error(h);
+    }
     auto it = h->graphs.find(T);
     if (it == h->graphs.end()) {
         cudaGraph_t g;
@@ -701,9 +839,32 @@ extern "C" int sim_profile_rollout(sim_handle h, int32_t T, sim_outputs *out, do
     if (T < 1) return fail(h, SIM_EINVAL, "horizon must be >= 1");
     CU(cudaSetDevice(h->device));
     TRY(ensure_T(h, T));
+    h->tape_ready = false;
+    if (use_persist(h)) {
+        cudaEvent_t e0, e1;
+        CU(cudaEventCreate(&e0));
+        CU(cudaEventCreate(&e1));
+        enqueue_reset(h, T);
+        CU(cudaEventRecord(e0, h->stream));
+        TRY(enqueue_persist(h, 0, T, 1));
+        CU(cudaEventRecord(e1, h->stream));
+        CU(cudaGetLastError());
+        CU(cudaStreamSynchronize(h->stream));
+        float ms = 0;
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (kernel_ms) { kernel_ms[0] = ms; kernel_ms[1] = 0; kernel_ms[2] = 0; }
+        if (launches) { launches[0] = 1; launches[1] = 0; launches[2] = 0; }
+        h->t = T;
+        h->T = T;
+        h->n_bins = sim_n_bins(T, h->opt.obs_every);
+        h->reset_done = true;
+        TRY(copy_outputs(h, out));
+        return check_device_error(h);
+    }
     std::vector<cudaEvent_t> ev((size_t)4 * T + 2);
     for (auto &e : ev) CU(cudaEventCreate(&e));
-    h->tape_ready = false;
     enqueue_reset(h, T);
     for (int t = 0; t < T; ++t) {
         CU(cudaEventRecord(ev[4 * t + 0], h->stream));
@@ -973,6 +1134,22 @@ extern "C" int sim_set_stage(sim_handle h, int32_t slots) {
         h->graphs.clear();
     }
     return SIM_OK;
+}
+
+extern "C" int sim_set_executor(sim_handle h, int32_t executor) {
+    if (!h) return SIM_EINVAL;
+    if (executor != SIM_EXEC_AUTO && executor != SIM_EXEC_STEP && executor != SIM_EXEC_PERSISTENT)
+        return fail(h, SIM_EINVAL, "unknown executor");
+    if (executor == SIM_EXEC_PERSISTENT && (h->K > 0 || !h->persist_ok))
+        return fail(h, SIM_EINVAL, h->K > 0 ? "the persistent executor records no reverse-pass tape"
+                                           : "persistent executor unavailable: " + h->persist_why);
+    h->executor = executor;
+    return SIM_OK;
+}
+
+extern "C" int32_t sim_get_executor(sim_handle h) {
+    if (!h) return -1;
+    return use_persist(h) ? SIM_EXEC_PERSISTENT : SIM_EXEC_STEP;
 }
 
 extern "C" int32_t sim_time(sim_handle h) { return h ? h->t : -1; }

@@ -104,6 +104,18 @@ class Simulator:
     def device_bytes(self):
         return self.lib.sim_device_bytes(self.h)
 
+    EXECUTORS = {"auto": 0, "step": 1, "persistent": 2}
+
+    def set_executor(self, name: str):
+        """Forward executor: "auto", "step" (two kernels per step, graph per
+        horizon) or "persistent" (one cooperative launch per run)."""
+        self._check(self.lib.sim_set_executor(self.h, self.EXECUTORS[name]))
+
+    @property
+    def executor(self) -> str:
+        """Executor the next forward run uses ("step" or "persistent")."""
+        return {1: "step", 2: "persistent"}[self.lib.sim_get_executor(self.h)]
+
     def rollout(self, T: Optional[int] = None, device: bool = False, out=None):
         """Run a whole rollout.  With device=True the outputs are torch CUDA
         tensors written asynchronously on the simulator's stream (``out`` may

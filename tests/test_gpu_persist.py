@@ -1,0 +1,162 @@
+"""The persistent executor (one cooperative launch per run, queues resident in
+shared memory, one grid barrier per step) against the two-kernel executor and
+against the oracle.
+
+Both executors evaluate every floating-point operation of the step in the same
+order, so every output and every piece of state must be bitwise identical; the
+oracle's float build takes the same decisions, so lockstep comparison against
+it is exact as well.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleSim
+from paper_2603_25068_b300 import scenario as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Simulator():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2603_25068_b300.sim import Simulator
+    return Simulator
+
+
+STATE_KEYS = ("veh_link", "veh_rank", "veh_entry", "veh_pos", "link_credit", "link_exits", "fifo_off")
+OUT_KEYS = ("counts", "speed", "travel_time", "n_waiting", "n_on", "n_arrived")
+REC_KEYS = ("link_cand", "link_target", "node_cand", "node_target", "link_in")
+
+
+def run(Simulator, sc, T, executor, chunks=None):
+    g = Simulator(sc)
+    g.set_executor(executor)
+    if chunks is None:
+        out = g.rollout(T)
+    else:
+        g.reset(T)
+        for c in chunks:
+            g.step(c)
+        out = g.outputs()
+    res = dict(out=out, state=g.state(), rec=g.records(), executor=g.executor)
+    g.close()
+    return res
+
+
+def assert_same(a, b):
+    for k in OUT_KEYS:
+        np.testing.assert_array_equal(a["out"][k], b["out"][k], err_msg=k)
+    for k in STATE_KEYS:
+        np.testing.assert_array_equal(a["state"][k], b["state"][k], err_msg=k)
+    for k in REC_KEYS:
+        np.testing.assert_array_equal(a["rec"][k], b["rec"][k], err_msg=k)
+
+
+SCENARIOS = {
+    "tiny_grid": lambda: S.tiny_grid(),
+    "dense_small": lambda: S.random_small(seed=2, side=3, n_vehicles=150, T=150).copy(obs_every=40),
+    "city_small": lambda: S.city_small(),
+    "line": lambda: S.line_network(n_links=2, length=1500.0, u=13.9, kappa=0.2, q=0.5, N=700, T=900).copy(obs_every=70),
+}
+
+
+def test_executor_selection(Simulator):
+    from paper_2603_25068_b300.native import SimError
+    sc = S.city_small()
+    g = Simulator(sc)
+    assert g.executor == "persistent"
+    g.set_executor("step")
+    assert g.executor == "step"
+    g.set_executor("auto")
+    assert g.executor == "persistent"
+    g.close()
+    g = Simulator(sc, ckpt_every=30)          # records the reverse-pass tape
+    assert g.executor == "step"
+    with pytest.raises(SimError):
+        g.set_executor("persistent")
+    g.close()
+
+
+@pytest.mark.parametrize("name", sorted(SCENARIOS))
+def test_persistent_matches_step_executor(Simulator, name):
+    sc = SCENARIOS[name]()
+    a = run(Simulator, sc, sc.T, "step")
+    b = run(Simulator, sc, sc.T, "persistent")
+    assert (a["executor"], b["executor"]) == ("step", "persistent")
+    assert_same(a, b)
+
+
+@pytest.mark.parametrize("name", ["tiny_grid", "city_small"])
+def test_runs_split_into_launches(Simulator, name):
+    # sim_step in uneven pieces (each piece one launch, the first step of each
+    # reading the vacancy flags written by the previous launch), also with the
+    # executors alternating, equals one whole-run launch
+    sc = SCENARIOS[name]()
+    T = sc.T
+    whole = run(Simulator, sc, T, "persistent")
+    pieces = [1, 7, 33, 2, 60]
+    pieces.append(T - sum(pieces))
+    split = run(Simulator, sc, T, "persistent", chunks=pieces)
+    assert_same(whole, split)
+    g = Simulator(sc)
+    g.reset(T)
+    for i, c in enumerate(pieces):
+        g.set_executor("persistent" if i % 2 == 0 else "step")
+        g.step(c)
+    mixed = dict(out=g.outputs(), state=g.state(), rec=g.records())
+    g.close()
+    assert_same(whole, mixed)
+
+
+def test_lockstep_against_oracle_in_multi_step_launches(Simulator):
+    # launches of 10 steps: steps after the first of a launch derive the
+    # vacancy of other CTAs' links from their records and the merge words
+    sc = S.random_small(seed=3, side=3, n_vehicles=150, T=150).copy(obs_every=40)
+    g = Simulator(sc)
+    g.set_executor("persistent")
+    o = OracleSim(sc, "fp32")
+    g.reset(150)
+    o.reset(150)
+    for _ in range(15):
+        g.step(10)
+        o.step(10)
+        gs, os_ = g.state(), o.state()
+        for k in ("veh_link", "veh_rank", "link_credit", "link_exits", "fifo_off", "veh_pos"):
+            np.testing.assert_array_equal(gs[k], os_[k], err_msg=k)
+    go, oo = g.outputs(), o.outputs()
+    np.testing.assert_array_equal(go["counts"], oo["counts"])
+    np.testing.assert_array_equal(go["n_on"], oo["n_on"])
+    g.close()
+
+
+def test_queue_longer_than_a_chunk(Simulator):
+    # more than 4096 vehicles queued on one link: the car-following update of
+    # one CTA runs in several chunks whose boundary headway is carried over
+    sc = S.line_network(n_links=2, length=12000.0, u=13.9, kappa=0.5, q=0.02, N=5200, T=5600)
+    g = Simulator(sc)
+    g.set_executor("persistent")
+    o = OracleSim(sc, "fp32")
+    g.reset(sc.T)
+    o.reset(sc.T)
+    peak = 0
+    for _ in range(sc.T // 700):
+        g.step(700)
+        o.step(700)
+        gs, os_ = g.state(), o.state()
+        peak = max(peak, int(np.max(np.bincount(gs["veh_link"][gs["veh_link"] >= 0], minlength=sc.L))))
+        for k in ("veh_link", "veh_rank", "link_credit", "link_exits", "veh_pos"):
+            np.testing.assert_array_equal(gs[k], os_[k], err_msg=k)
+    assert peak > 4096
+    np.testing.assert_array_equal(g.outputs()["counts"], o.outputs()["counts"])
+    g.close()
+
+
+def test_city_full_size_executors_agree(Simulator):
+    # 36,000 links and 1,000,000 vehicles, first 900 steps: every output and
+    # every piece of state identical between the executors
+    sc = S.city().copy(T=900)
+    a = run(Simulator, sc, 900, "step")
+    b = run(Simulator, sc, 900, "persistent")
+    assert_same(a, b)
+    assert a["out"]["n_on"][-1] > 100_000
