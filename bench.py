@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--stage", type=int, default=0, help="queue slots per link block (0 = autotune)")
     ap.add_argument("--executor", default="auto", choices=["auto", "step", "persistent"],
                     help="forward executor of the timed rollouts")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other forward executor")
     ap.add_argument("--no-fwd-bwd", action="store_true", help="skip the calibration-gradient leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-scenario leg")
     ap.add_argument("--batch-n", type=int, default=64)
@@ -481,7 +482,7 @@ def run_ours(args):
     }
 
     # ---- the other executor on the same workload, for comparison
-    if executor == "persistent":
+    if executor == "persistent" and not args.no_compare:
         sim.set_executor("step")
         st_stage, _ = autotune.tune_stage(sim, T=min(T, 900))
         sim.rollout(T, device=True, out=out)

@@ -133,6 +133,8 @@ struct sim_ctx {
     int *d_od = nullptr;
     float *d_od_lambda = nullptr;
     // persistent executor
+    std::vector<int> lo_count;           // choice-set size after each link
+    std::vector<int> no_ptr_host;        // out-links of each node (CSR offsets)
     int executor = SIM_EXEC_AUTO;        // requested
     bool persist_ok = false;             // the network fits (groups, shared memory, co-residency)
     std::string persist_why;             // reason when it does not
@@ -255,47 +257,72 @@ static int build_groups(sim_ctx *h) {
     int nsm = 0, optin = 0;
     CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    const long long slot_cap = ((long long)optin - (long long)sizeof(PSmem)) / (long long)sizeof(float);
-    const int L = h->L;
-    std::vector<long long> cap(L);
+    const long long budget = (long long)optin - (long long)sizeof(PSmem);
+    const int L = h->L, V = h->V;
+    // shared-memory bytes of a link: its ring slots and its staged choice records
+    std::vector<long long> cap(L), lob(L);
     long long wsum = 0, wmax = 0;
     for (int j = 0; j < L; ++j) {
         cap[j] = h->lst_host[4 * j + 1];
-        if (cap[j] > slot_cap) {
-            h->persist_why = "a link queue is larger than the shared memory of one CTA";
-            return SIM_OK;
-        }
+        lob[j] = 4 * cap[j] + 16 * (long long)h->lo_count[j];
         wsum += cap[j] + 16;
         wmax = std::max(wmax, cap[j] + 16);
     }
-    auto pack = [&](long long bound, std::vector<int> *starts) {
-        int groups = 0, nl = 0;
-        long long w = 0, slots = 0;
-        if (starts) starts->clear();
-        for (int j = 0; j < L; ++j) {
-            const long long wj = cap[j] + 16;
-            if (nl == 0 || nl == kPLinks || w + wj > bound || slots + cap[j] > slot_cap) {
-                if (starts) starts->push_back(j);
-                ++groups;
-                nl = 0; w = 0; slots = 0;
-            }
-            ++nl; w += wj; slots += cap[j];
+    // the origin queues of a group are the nodes [g npg, (g + 1) npg)
+    auto node_bytes = [&](int G) {
+        const int npg = (V + G - 1) / G;
+        long long worst = 0;
+        for (int g = 0; g < G; ++g) {
+            const int n0 = std::min(V, g * npg), n1 = std::min(V, (g + 1) * npg);
+            worst = std::max(worst, 16LL * (h->no_ptr_host[n1] - h->no_ptr_host[n0]));
         }
-        return groups;
+        return worst;
     };
-    long long lo = std::max(wmax, (wsum + nsm - 1) / nsm), hi = std::max(lo, wsum);
-    if (pack(hi, nullptr) > nsm) {
-        h->persist_why = "the queues do not fit in the shared memory of the GPU";
-        return SIM_OK;
-    }
-    while (lo < hi) {
-        const long long mid = lo + (hi - lo) / 2;
-        if (pack(mid, nullptr) <= nsm) hi = mid; else lo = mid + 1;
-    }
+    long long reserve = node_bytes(std::max(1, std::min(nsm, (V + kPNodes - 1) / kPNodes)));
     std::vector<int> starts;
-    pack(lo, &starts);
-    const int ngl = (int)starts.size();
-    const int G = std::max(ngl, (h->V + kPNodes - 1) / kPNodes);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const long long lbud = budget - reserve - 16;
+        bool fits = true;
+        for (int j = 0; j < L; ++j) fits = fits && lob[j] <= lbud;
+        if (!fits) {
+            h->persist_why = "a link queue is larger than the shared memory of one CTA";
+            return SIM_OK;
+        }
+        auto pack = [&](long long bound, std::vector<int> *out) {
+            int groups = 0, nl = 0;
+            long long w = 0, bytes = 0;
+            if (out) out->clear();
+            for (int j = 0; j < L; ++j) {
+                const long long wj = cap[j] + 16;
+                if (nl == 0 || nl == kPLinks || w + wj > bound || bytes + lob[j] > lbud) {
+                    if (out) out->push_back(j);
+                    ++groups;
+                    nl = 0; w = 0; bytes = 0;
+                }
+                ++nl; w += wj; bytes += lob[j];
+            }
+            return groups;
+        };
+        long long lo = std::max(wmax, (wsum + nsm - 1) / nsm), hi = std::max(lo, wsum);
+        if (pack(hi, nullptr) > nsm) {
+            h->persist_why = "the queues do not fit in the shared memory of the GPU";
+            return SIM_OK;
+        }
+        while (lo < hi) {
+            const long long mid = lo + (hi - lo) / 2;
+            if (pack(mid, nullptr) <= nsm) hi = mid; else lo = mid + 1;
+        }
+        pack(lo, &starts);
+        const int G = std::max((int)starts.size(), (V + kPNodes - 1) / kPNodes);
+        const long long need = node_bytes(G);
+        if (need <= reserve) break;
+        if (attempt == 1) {
+            h->persist_why = "the origin nodes' out-links do not fit in shared memory";
+            return SIM_OK;
+        }
+        reserve = need;
+    }
+    const int G = std::max((int)starts.size(), (V + kPNodes - 1) / kPNodes);
     if (G > nsm) {
         h->persist_why = "too many origin nodes for one CTA per SM";
         return SIM_OK;
@@ -303,13 +330,19 @@ static int build_groups(sim_ctx *h) {
     std::vector<int> grp(starts);
     grp.push_back(L);
     while ((int)grp.size() < G + 1) grp.push_back(L);
-    long long smax = 0;
+    const int npg = (V + G - 1) / G;
+    size_t dmax = 0;
     for (int g = 0; g < G; ++g) {
-        long long sl = 0;
-        for (int j = grp[g]; j < grp[g + 1]; ++j) sl += cap[j];
-        smax = std::max(smax, sl);
+        long long sl = 0, nlo = 0;
+        for (int j = grp[g]; j < grp[g + 1]; ++j) { sl += cap[j]; nlo += h->lo_count[j]; }
+        const int n0 = std::min(V, g * npg), n1 = std::min(V, (g + 1) * npg);
+        dmax = std::max(dmax, p_dyn_bytes(sl, nlo, h->no_ptr_host[n1] - h->no_ptr_host[n0]));
     }
-    const size_t smem = sizeof(PSmem) + (size_t)smax * sizeof(float);
+    const size_t smem = sizeof(PSmem) + dmax;
+    if (smem > (size_t)optin) {
+        h->persist_why = "a group does not fit in the shared memory of one CTA";
+        return SIM_OK;
+    }
     CU(raise_smem_attr(k_persist, g_attr_p, h->device, smem));
     int per_sm = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist, kPT, smem));
@@ -325,7 +358,8 @@ static int build_groups(sim_ctx *h) {
         TRY(dalloc(h, &h->pa.bar, 4));
     }
     h->pa.grp_links = d_grp;
-    h->pa.npg = (h->V + G - 1) / G;
+    h->pa.npg = npg;
+    h->pa.packz = (h->N < (1 << 24) && h->Z <= 256) ? 1 : 0;
     h->G = G;
     h->persist_smem = smem;
     h->persist_ok = true;
@@ -461,6 +495,9 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
         S += (long long)cap;
     }
     if (S > (1ll << 30)) return fail(h, SIM_EINVAL, "queue arena too large");
+    h->lo_count.resize(L);
+    for (int l = 0; l < L; ++l) h->lo_count[l] = lnode[4 * l + 3] - lnode[4 * l + 2];
+    h->no_ptr_host = no_ptr;
     h->S = (int)S;
     h->lst_host = lst;
     // origin queues sorted by (origin, departure step, id)

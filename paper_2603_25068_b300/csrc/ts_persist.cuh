@@ -5,16 +5,28 @@
 // The queues of a CTA's links stay in its shared memory for the whole launch
 // (FIFO rings, leader first, one float position per slot: the order of SI-A's
 // argsort, maintained instead of re-sorted because vehicles never overtake), so
-// that the car-following update reads and writes no global memory.  Across
-// CTAs, the node model of SI-B couples links only through
-//   * the merge words W[target] (64-bit atomicMax of alpha + g', ~vehicle),
-//     three buffers indexed by step mod 3, and
+// that the car-following update reads and writes no global memory.  The
+// (vehicle, zone, entry step) of the first two queue positions of every link
+// and of every origin queue are cached in shared memory too, so that finding
+// the candidates of a step loads nothing.  Across CTAs, the node model of SI-B
+// couples links only through
+//   * the merge words W[target] (64-bit atomicMax of alpha + g' over the
+//     candidates, low half ~(vehicle << 8 | zone) when the sizes allow, so that
+//     the target learns the entrant's zone with the word), three buffers
+//     indexed by step mod 3, and
 //   * each link's record of the step (candidate, target, next-step vacancy /
 //     arrival bits for the four (pop, push) outcomes), two buffers by parity,
 // from which any CTA derives the vacancy of any link for the next step without
 // waiting for the link's owner to apply its transfers.  One grid-wide barrier
-// per step therefore suffices: epoch t = [transfers of step t-1 for own links]
-// [step t: credit, candidates, car-following, link choice, merge] barrier.
+// per step therefore suffices.  Epoch t of a CTA:
+//   T   transfers of step t-1 for its links and origin queues (one round of
+//       merge-word loads), then credit and candidates of step t;
+//   S   one block scan of the choice work -> a compact list of (candidate,
+//       choice slot) pairs;
+//   C|F choice warps evaluate the pairs (utility + Gumbel keys, vacancy of the
+//       slot's link) while the other warps run the Newell update of every
+//       queued vehicle in shared memory, one warp per link at a time;
+//   P   argmax, merge atomicMax, next-step bits, records; barrier.
 //
 // Every floating-point operation is the one of the two-kernel path (same device
 // functions, same order), so both executors give bit-identical results.
@@ -25,15 +37,19 @@
 
 namespace ts {
 
-constexpr int kPT = 1024;        // threads per CTA
-constexpr int kPLinks = 320;     // links per CTA at most
-constexpr int kPNodes = 256;     // origin queues per CTA at most
-constexpr int kPU = 4;           // car-following elements per thread per chunk
-constexpr int kPSlot = 4;        // choice slots per candidate evaluated in parallel
+constexpr int kPT = 1024;                    // threads per CTA
+constexpr int kPLinks = 288;                 // links per CTA at most
+constexpr int kPNodes = 128;                 // origin queues per CTA at most
+constexpr int kPNodeTid = 512;               // thread of origin queue 0 in the per-entity phases
+constexpr int kPSlot = 4;                    // choice slots per candidate evaluated in parallel
+constexpr int kPCW = 16;                     // choice warps
+constexpr int kPCFT = kPT - 32 * kPCW;       // car-following threads
+constexpr int kPPairs = (kPLinks + kPNodes) * (kPSlot + 1);
 
 struct PArgs {
     const int *grp_links;          // [G + 1] first link of each CTA's group
     int npg;                       // origin queues per CTA
+    int packz;                     // merge words carry the entrant's zone
     unsigned long long *W3;        // [3 L] merge words by step mod 3
     int4 *crec2;                   // [2 L] link records by step parity
     unsigned *bar;                 // grid barrier counter (zero at launch)
@@ -45,31 +61,38 @@ struct PSmem {
     int4 q[kPLinks];               // queue head, length, credit, exits
     int4 st[kPLinks];              // global slot base, capacity, q_fx, credit cap
     float4 g[kPLinks];             // length, u dt, s, tag band
-    int4 nd[kPLinks];              // head node, head zone, choice begin/end
+    int4 nd[kPLinks];              // head node, head zone, first staged choice entry, choice count
     int4 stat[kPLinks];            // open-bin statistics
     int4 cr[kPLinks];              // record of the step (candidate, target, entry << 8 | bits, x0)
-    float4 x4[kPLinks];            // new positions of vehicles 0, 1, n-2, n-1
-    int2 lead[kPLinks];            // candidate (vehicle, zone)
+    int4 ld[kPLinks];              // (vehicle, zone) at queue positions 0 and 1
+    int2 le[kPLinks];              // entry steps at queue positions 0 and 1
     int flags[kPLinks];            // vacancy / arrival for the coming step
-    int off[kPLinks + 1];          // first element of each link in the block's element order
-    int past[kPLinks];             // vehicles past the midpoint (observation)
-    float mkey[kPLinks];           // merge key alpha + g' of the candidate
+    int lbase[kPLinks + 1];        // first ring slot of each link in shared memory (static)
+    int past[kPLinks];
+    float mkey[kPLinks];
+    float alpha[kPLinks];
     unsigned long long psum[kPLinks];
-    float key[kPLinks][kPSlot];    // utility + Gumbel of each choice slot
+    float key[kPLinks][kPSlot];
     int tv[kPLinks][kPSlot];       // target << 1 | vacant
-    int4 nq[kPNodes];              // next vehicle, end of queue, out-links begin/end
-    int2 nlead[kPNodes];
+    int4 nq[kPNodes];              // next vehicle, end of queue, first staged out-link entry, out-degree
+    int4 nh[kPNodes];              // (vehicle, zone) at queue positions 0 and 1
+    int2 ndep[kPNodes];            // departure steps at queue positions 0 and 1
     int2 nrec[kPNodes];            // (candidate, target) of the step
     int nzone[kPNodes];
     float nmkey[kPNodes];
     float nkey[kPNodes][kPSlot];
     int ntv[kPNodes][kPSlot];
-    int wsum[32], wpre[32];
+    int plist[kPPairs];            // entity << 3 | (0 merge key, 1 + k choice slot k)
+    int wsum[32];
     int cnt[4];                    // step counters: releases, arrivals, candidates, entries
-    float carry[2];                // old position of the last element of a chunk, by chunk parity
-    int total;
-    int stop;
+    int npairs, stop;
 };
+
+// Shared-memory bytes of a CTA beyond PSmem: ring slots, staged choice records
+// of its links and of its origin nodes' out-links (16-byte aligned sections).
+__host__ __device__ inline size_t p_dyn_bytes(long long slots, long long n_lo, long long n_no) {
+    return (((size_t)slots * 4 + 15) & ~(size_t)15) + (size_t)(n_lo + n_no) * 16;
+}
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
     unsigned v;
@@ -88,7 +111,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ bool grid_sync(const DevSim &d, unsigned *bar, unsigned target, int t, int *stop) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         atomicAdd(bar, 1u);
         const unsigned long long t_start = global_ns();
         int ok = 1;
@@ -102,39 +125,49 @@ __device__ __forceinline__ bool grid_sync(const DevSim &d, unsigned *bar, unsign
                     break;
                 }
             }
-            __nanosleep(20);
         }
-        __threadfence();
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         *stop = !ok;
     }
     __syncthreads();
     return *stop == 0;
 }
 
+// merge words: the key in the high half; ~(vehicle << 8 | zone) or ~vehicle in
+// the low half (the largest key wins, equal keys go to the lowest vehicle)
+__device__ __forceinline__ unsigned long long p_word(float key, int vid, int zone, int packz) {
+    if (!packz) return merge_word(key, vid);
+    const unsigned long long w = merge_word(key, 0);
+    return (w & 0xffffffff00000000ull) | (unsigned long long)(~(((uint32_t)vid << 8) | (uint32_t)zone));
+}
+__device__ __forceinline__ int p_vid(unsigned long long w, int packz) {
+    return packz ? (int)((~(uint32_t)(w & 0xffffffffull)) >> 8) : merge_vid(w);
+}
+
 // Vacancy / arrival flags of link m for step t, from its record of step t-1
 // and the merge words of step t-1 (what its owner will apply).
-__device__ __forceinline__ int derived_flags(const int4 *Cp, const unsigned long long *Wp, int m) {
+__device__ __forceinline__ int derived_flags(const int4 *Cp, const unsigned long long *Wp, int m, int packz) {
     const int4 c = __ldcg(Cp + m);
+    const unsigned long long wm = __ldcg(Wp + m);
     bool pop = c.y == kTgtSink;
     if (c.y >= 0) {
         const unsigned long long w = __ldcg(Wp + c.y);
-        pop = w != 0ull && merge_vid(w) == c.x;
+        pop = w != 0ull && p_vid(w, packz) == c.x;
     }
-    const bool push = __ldcg(Wp + m) != 0ull;
-    const int o = (pop ? 1 : 0) | (push ? 2 : 0);
+    const int o = (pop ? 1 : 0) | (wm != 0ull ? 2 : 0);
     return ((c.z >> o) & 1) | (((c.z >> (4 + o)) & 1) << 1);
 }
 
 __device__ __forceinline__ int vacant_of(const DevSim &d, bool first, const int4 *Cp, const unsigned long long *Wp,
-                                         int m) {
-    return (first ? __ldcg(d.vac + m) : derived_flags(Cp, Wp, m)) & kFlagVacant;
+                                         int m, int packz) {
+    return (first ? __ldcg(d.vac + m) : derived_flags(Cp, Wp, m, packz)) & kFlagVacant;
 }
 
 // argmax of the staged keys (ties to the lowest slot); slots past the stage
 // are evaluated inline.  Returns the target or kTgtBlocked.
 __device__ __forceinline__ int p_choose(const DevSim &d, bool first, const int4 *Cp, const unsigned long long *Wp,
-                                        const float *key, const int *tv, const float4 *info, int deg, int zone,
-                                        int vid, int t) {
+                                        int packz, const float *key, const int *tv, const float4 *info, int deg,
+                                        int zone, int vid, int t) {
     float bk = -INFINITY;
     int bm = -1, bv = 0;
     for (int k = 0; k < deg; ++k) {
@@ -148,64 +181,106 @@ __device__ __forceinline__ int p_choose(const DevSim &d, bool first, const int4 
             const float4 e = info[k];
             kk = choice_key(d, e, zone, vid, t, k);
             m = __float_as_int(e.w);
-            vm = vacant_of(d, first, Cp, Wp, m);
+            vm = vacant_of(d, first, Cp, Wp, m, packz);
         }
         if (bm < 0 || kk > bk) { bk = kk; bm = m; bv = vm; }
     }
     return bv ? bm : kTgtBlocked;
 }
 
-// Transfers of step tb for the CTA's links and origin queues (SI-B Eq.
+// A refill of the second cached queue position, loaded in phase T and stored
+// after the other phases (its value is needed only at the next pop).
+struct PPend {
+    int2 aux;
+    int ent;
+    int on;
+};
+
+__device__ __forceinline__ int2 ld_int2(const int2 *p) {
+    int2 v;
+    asm volatile("ld.global.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int ld_int(const int *p) {
+    int v;
+    asm volatile("ld.global.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+struct PCtx {
+    int j0, nl, n0, nn, base0, nslots;
+    float *P;                      // ring slots
+    const float4 *LO;              // staged choice records of the links
+    const float4 *NO;              // staged out-link records of the origin nodes
+    int lo0, no0;                  // first staged entry (global index)
+};
+
+// Transfers of step tb for this thread's link or origin queue (SI-B Eq.
 // transfer): pop the leader that won its merge or left to its destination, push
-// the merge winner at x = 0, then the flags of step tb + 1.
-__device__ __forceinline__ void p_transfers(const DevSim &d, const PArgs &a, PSmem &S, float *P, int j0, int nl,
-                                            int nn, int base0, int tb) {
+// the merge winner at x = 0, flags of step tb + 1.  Counters accumulate.
+__device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int tb, PPend &pd,
+                                        int *cnt) {
+    const int tid = threadIdx.x;
     const unsigned long long *Wb = a.W3 + (size_t)(tb % 3) * d.L;
-    unsigned long long *Wc = a.W3 + (size_t)((tb + 2) % 3) * d.L;    // words of step tb + 2
-    int released = 0, arrived = 0, cands = 0, entered = 0;
-    for (int li = threadIdx.x; li < nl; li += kPT) {
-        const int j = j0 + li;
+    if (tid < c.nl) {
+        const int li = tid, j = c.j0 + li;
         int4 q = S.q[li];
         const int4 st = S.st[li];
-        const int4 c = S.cr[li];
+        const int4 cr = S.cr[li];
         const unsigned long long win = __ldcg(Wb + j);
+        unsigned long long wt = 0ull;
+        if (cr.y >= 0) wt = __ldcg(Wb + cr.y);
         bool pop = false;
-        cands += c.x >= 0;
-        if (c.y == kTgtSink) {
+        cnt[2] += cr.x >= 0;
+        if (cr.y == kTgtSink) {
             pop = true;
-            d.vstate[c.x] = kVehArrived;
-            arrived += 1;
-        } else if (c.y >= 0) {
-            const unsigned long long w = __ldcg(Wb + c.y);
-            pop = w != 0ull && merge_vid(w) == c.x;
+            d.vstate[cr.x] = kVehArrived;
+            cnt[1] += 1;
+        } else if (cr.y >= 0) {
+            pop = wt != 0ull && p_vid(wt, a.packz) == cr.x;
         }
+        int4 ld = S.ld[li];
+        int2 le = S.le[li];
         if (pop) {
             int4 stat = S.stat[li];
-            stat.y += tb + 1 - (c.z >> 8);
+            stat.y += tb + 1 - (cr.z >> 8);
             stat.z += 1;
             S.stat[li] = stat;
             longlong2 ps = d.lpos[j];
-            ps.y += pos_fx(__int_as_float(c.w));
+            ps.y += pos_fx(__int_as_float(cr.w));
             d.lpos[j] = ps;
             q.x = (q.x + 1 == st.y) ? 0 : q.x + 1;
             q.y -= 1;
             q.z -= d.dn_fx;
             q.w += 1;
+            ld.x = ld.z;
+            ld.y = ld.w;
+            le.x = le.y;
+            if (q.y >= 2) {
+                int idx = q.x + 1;
+                if (idx >= st.y) idx -= st.y;
+                pd.aux = ld_int2(d.saux + st.x + idx);
+                pd.ent = ld_int(d.sentry + st.x + idx);
+                pd.on = 1;
+            }
         }
         const bool push = win != 0ull;
         if (push) {
-            const int v = merge_vid(win);
+            const int v = p_vid(win, a.packz);
             if (q.y >= st.y) {
                 set_error(d, SIM_EOVERFLOW, j, tb);
             } else {
+                const int z = a.packz ? (int)((~(uint32_t)(win & 0xffffffffull)) & 0xffu) : d.dest_zone[v];
                 int idx = q.x + q.y;
                 if (idx >= st.y) idx -= st.y;
-                P[st.x - base0 + idx] = 0.0f;
-                d.saux[st.x + idx] = make_int2(v, d.dest_zone[v]);
+                c.P[st.x - c.base0 + idx] = 0.0f;
+                d.saux[st.x + idx] = make_int2(v, z);
                 d.sentry[st.x + idx] = tb + 1;
+                if (q.y == 0) { ld.x = v; ld.y = z; le.x = tb + 1; }
+                if (q.y == 1) { ld.z = v; ld.w = z; le.y = tb + 1; }
                 q.y += 1;
                 d.vstate[v] = j;
-                entered += 1;
+                cnt[3] += 1;
                 if (d.route_log) {
                     const int r = d.route_len[v];
                     if (r < d.route_cap) {
@@ -218,209 +293,280 @@ __device__ __forceinline__ void p_transfers(const DevSim &d, const PArgs &a, PSm
             }
         }
         S.q[li] = q;
+        S.ld[li] = ld;
+        S.le[li] = le;
         const int o = (pop ? 1 : 0) | (push ? 2 : 0);
-        S.flags[li] = ((c.z >> o) & 1) | (((c.z >> (4 + o)) & 1) << 1);
-        Wc[j] = 0ull;
-    }
-    for (int ni = threadIdx.x; ni < nn; ni += kPT) {
-        const int2 c = S.nrec[ni];
-        cands += c.x >= 0;
-        if (c.y == kTgtSink) {
-            S.nq[ni].x += 1;
-            d.vstate[c.x] = kVehArrived;
-            released += 1;
-            arrived += 1;
-        } else if (c.y >= 0) {
-            const unsigned long long w = __ldcg(Wb + c.y);
-            if (w != 0ull && merge_vid(w) == c.x) { S.nq[ni].x += 1; released += 1; }
+        S.flags[li] = ((cr.z >> o) & 1) | (((cr.z >> (4 + o)) & 1) << 1);
+        a.W3[(size_t)((tb + 2) % 3) * d.L + j] = 0ull;      // words of step tb + 2 start from zero
+    } else if (tid >= kPNodeTid && tid < kPNodeTid + c.nn) {
+        const int ni = tid - kPNodeTid;
+        const int2 cr = S.nrec[ni];
+        cnt[2] += cr.x >= 0;
+        bool rel = false;
+        if (cr.y == kTgtSink) {
+            rel = true;
+            d.vstate[cr.x] = kVehArrived;
+            cnt[1] += 1;
+        } else if (cr.y >= 0) {
+            const unsigned long long w = __ldcg(Wb + cr.y);
+            rel = w != 0ull && p_vid(w, a.packz) == cr.x;
         }
-    }
-    released = warp_sum(released);
-    arrived = warp_sum(arrived);
-    cands = warp_sum(cands);
-    entered = warp_sum(entered);
-    if ((threadIdx.x & 31) == 0) {
-        if (released) atomicAdd(&S.cnt[0], released);
-        if (arrived) atomicAdd(&S.cnt[1], arrived);
-        if (cands) atomicAdd(&S.cnt[2], cands);
-        if (entered) atomicAdd(&S.cnt[3], entered);
-    }
-    __syncthreads();
-    if (threadIdx.x < 4) {
-        const int v = S.cnt[threadIdx.x];
-        if (v) atomicAdd(&d.step_delta[4 * tb + threadIdx.x], v);
-        S.cnt[threadIdx.x] = 0;
+        if (rel) {
+            cnt[0] += 1;
+            int4 nq = S.nq[ni];
+            int4 nh = S.nh[ni];
+            int2 dp = S.ndep[ni];
+            nq.x += 1;
+            nh.x = nh.z;
+            nh.y = nh.w;
+            dp.x = dp.y;
+            if (nq.x + 1 < nq.y) {
+                pd.aux = ld_int2(d.fifo_list + nq.x + 1);
+                pd.ent = ld_int(d.fifo_dep + nq.x + 1);
+                pd.on = 1;
+            }
+            S.nq[ni] = nq;
+            S.nh[ni] = nh;
+            S.ndep[ni] = dp;
+        }
     }
 }
 
-// Step t for the CTA's links and origin queues: credit and candidates, Newell
-// car-following in shared memory, observation at bin ends, link choice and
-// merge.  obs_only: only close the bin ending at t.
-__device__ __forceinline__ void p_step(const DevSim &d, const PArgs &a, PSmem &S, float *P, int j0, int nl, int n0,
-                                       int nn, int base0, int t, bool first, bool obs_only) {
-    const int tid = threadIdx.x, lane = tid & 31;
-    const bool obs = obs_only || (t > 0 && t % d.obs_every == 0);
-    if (obs_only) nn = 0;
-    // ---------------- credit, candidates, queue-length scan ----------------
-    for (int li = tid; li < nl; li += kPT) {
+// the refill loaded by p_apply (second queue position)
+__device__ __forceinline__ void p_refill(PSmem &S, const PCtx &c, const PPend &pd) {
+    if (!pd.on) return;
+    const int tid = threadIdx.x;
+    if (tid < c.nl) {
+        S.ld[tid].z = pd.aux.x;
+        S.ld[tid].w = pd.aux.y;
+        S.le[tid].y = pd.ent;
+    } else {
+        const int ni = tid - kPNodeTid;
+        S.nh[ni].z = pd.aux.x;
+        S.nh[ni].w = pd.aux.y;
+        S.ndep[ni].y = pd.ent;
+    }
+}
+
+// add this thread's step counters to the CTA's (every thread calls)
+__device__ __forceinline__ void p_count(PSmem &S, const int *cnt) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int v = warp_sum(cnt[k]);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&S.cnt[k], v);
+    }
+}
+
+// Step t of this thread's link or origin queue up to the choice: credit,
+// candidate.  Returns its number of choice pairs (merge key + choice slots).
+__device__ __forceinline__ int p_candidate(const DevSim &d, PSmem &S, const PCtx &c, int t, bool obs_only) {
+    const int tid = threadIdx.x;
+    if (tid < c.nl) {
+        const int li = tid;
         S.past[li] = 0;
         S.psum[li] = 0ull;
-        if (obs_only) continue;             // the records of the last step stay
         const int4 q = S.q[li];
+        if (obs_only) return 0;
         const int4 st = S.st[li];
         const int credit = min(q.z + st.z, st.w);
         S.q[li].z = credit;
         const bool cand = (S.flags[li] & kFlagArrive) && credit >= d.dn_fx;
-        int2 lead = make_int2(-1, -1);
-        int ent = 0;
-        if (cand) {
-            lead = d.saux[st.x + q.x];
-            ent = d.sentry[st.x + q.x];
-        }
-        S.lead[li] = lead;
-        S.cr[li] = make_int4(cand ? lead.x : -1, kTgtNone, ent, 0);
+        const int4 nd = S.nd[li];
+        const int4 ld = S.ld[li];
+        S.cr[li] = make_int4(cand ? ld.x : -1, kTgtNone, cand ? S.le[li].x : 0, 0);
+        return (cand && nd.y != ld.y) ? 1 + min(nd.w, kPSlot) : 0;
     }
-    for (int ni = tid; ni < nn; ni += kPT) {
+    if (!obs_only && tid >= kPNodeTid && tid < kPNodeTid + c.nn) {
+        const int ni = tid - kPNodeTid;
         const int4 nq = S.nq[ni];
-        int2 lead = make_int2(-1, -1);
-        if (nq.x < nq.y) {
-            const int dep = d.fifo_dep[nq.x];
-            const int2 head = d.fifo_list[nq.x];
-            if (dep <= t) lead = head;
-        }
-        S.nlead[ni] = lead;
+        const int4 nh = S.nh[ni];
+        const bool cand = nq.x < nq.y && S.ndep[ni].x <= t;
+        S.nrec[ni] = make_int2(cand ? nh.x : -1, kTgtNone);
+        return (cand && S.nzone[ni] != nh.y) ? 1 + min(nq.w, kPSlot) : 0;
     }
-    if (tid < kPLinks) {                    // exclusive scan of queue lengths, per warp
-        const int v = tid < nl ? S.q[tid].y : 0;
-        int s = v;
+    return 0;
+}
+
+// Block scan of every thread's choice-pair count: the compact pair list.
+__device__ __forceinline__ void p_scan(PSmem &S, int v) {
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int s = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, s, o);
+        if (lane >= o) s += y;
+    }
+    if (lane == 31) S.wsum[w] = s;
+    __syncthreads();
+    if (w == 0) {
+        const int x = S.wsum[lane];
+        int r = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, s, o);
-            if (lane >= o) s += y;
+            const int y = __shfl_up_sync(kFull, r, o);
+            if (lane >= o) r += y;
         }
-        if (lane == 31) S.wsum[tid >> 5] = s;
-        S.off[tid] = s - v;
+        S.wsum[lane] = r - x;
+        if (lane == 31) S.npairs = r;
     }
     __syncthreads();
-    if (tid < 32) {
-        const int v = tid < kPLinks / 32 ? S.wsum[tid] : 0;
-        int s = v;
+    const int ex = s - v + S.wsum[w];
+    for (int k = 0; k < v; ++k) S.plist[ex + k] = (tid << 3) | k;
+    __syncthreads();
+}
+
+// The (candidate, slot) pairs of the choice warps, kPP at a time per thread:
+// slot 0 is the candidate's merge key alpha + g', slot 1 + k the utility +
+// Gumbel key of choice slot k and the vacancy of its link.  All global loads of
+// the kPP pairs (destination feature, the slot link's record and merge word,
+// then its candidate's target word) are issued before any is consumed, and the
+// Gumbel draws are computed while they are in flight.
+constexpr int kPP = 1;
+
+__device__ __forceinline__ void p_pairs(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int t, bool first,
+                                        const int4 *Cp, const unsigned long long *Wp, int tfirst, int CT) {
+    const int ct = threadIdx.x - tfirst;
+    const int np = S.npairs;
+    for (int base = ct; base < np; base += CT * kPP) {
+        int pe[kPP], vid[kPP], m[kPP], cx[kPP], cy[kPP], cz[kPP];
+        float ux[kPP], uy[kPP], df[kPP];
+        bool push[kPP];
+        unsigned long long wt[kPP];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, s, o);
-            if (lane >= o) s += y;
-        }
-        S.wpre[tid] = s - v;
-        if (tid == 31) S.total = s;
-    }
-    __syncthreads();
-    if (tid < nl) S.off[tid] += S.wpre[tid >> 5];
-    if (tid == 0) S.off[nl] = S.total;
-    __syncthreads();
-    const int total = S.total;
-    const int4 *Cp = a.crec2 + (size_t)((t + 1) & 1) * d.L;                 // records of step t-1
-    const unsigned long long *Wp = a.W3 + (size_t)((t + 2) % 3) * d.L;     // words of step t-1
-    // ---------------- link-choice and merge keys of the candidates ----------------
-    if (!obs_only) {
-        for (int c = tid; c < (nl + nn) * kPSlot; c += kPT) {
-            const int r = c / kPSlot, k = c % kPSlot;
-            if (r < nl) {
-                const int2 lead = S.lead[r];
-                if (lead.x < 0 || S.cr[r].x < 0) continue;
-                const int4 nd = S.nd[r];
-                if (k == 0) S.mkey[r] = __fadd_rn(d.alpha[j0 + r], gumbel(d.key0, d.key1, lead.x, t, 1, 0));
-                if (k >= nd.w - nd.z || nd.y == lead.y) continue;
-                const float4 e = d.loinfo[nd.z + k];
-                const int m = __float_as_int(e.w);
-                S.key[r][k] = choice_key(d, e, lead.y, lead.x, t, k);
-                S.tv[r][k] = (m << 1) | vacant_of(d, first, Cp, Wp, m);
+        for (int i = 0; i < kPP; ++i) {
+            const int p = base + i * CT;
+            pe[i] = -1;
+            if (p >= np) continue;
+            const int e = S.plist[p];
+            pe[i] = e;
+            const int en = e >> 3, sl = e & 7;
+            const bool isl = en < kPNodeTid;
+            const int4 who = isl ? S.ld[en] : S.nh[en - kPNodeTid];
+            vid[i] = who.x;
+            if (sl == 0) continue;
+            const float4 info = isl ? c.LO[S.nd[en].z + sl - 1] : c.NO[S.nq[en - kPNodeTid].z + sl - 1];
+            ux[i] = info.x;
+            uy[i] = info.y;
+            m[i] = __float_as_int(info.w);
+            df[i] = d.dest_feat[(size_t)who.y * d.V + __float_as_int(info.z)];
+            if (first) {
+                cz[i] = __ldcg(d.vac + m[i]);
             } else {
-                const int q = r - nl;
-                const int2 lead = S.nlead[q];
-                if (lead.x < 0) continue;
-                const int4 nq = S.nq[q];
-                if (k == 0) S.nmkey[q] = __fadd_rn(d.alpha[d.L], gumbel(d.key0, d.key1, lead.x, t, 1, 0));
-                if (k >= nq.w - nq.z || S.nzone[q] == lead.y) continue;
-                const float4 e = d.noinfo[nq.z + k];
-                const int m = __float_as_int(e.w);
-                S.nkey[q][k] = choice_key(d, e, lead.y, lead.x, t, k);
-                S.ntv[q][k] = (m << 1) | vacant_of(d, first, Cp, Wp, m);
+                const int4 cc = __ldcg(Cp + m[i]);
+                cx[i] = cc.x;
+                cy[i] = cc.y;
+                cz[i] = cc.z;
+                push[i] = __ldcg(Wp + m[i]) != 0ull;
+            }
+        }
+        if (!first) {
+#pragma unroll
+            for (int i = 0; i < kPP; ++i) {
+                wt[i] = 0ull;
+                if (pe[i] >= 0 && (pe[i] & 7) != 0 && cy[i] >= 0) wt[i] = __ldcg(Wp + cy[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kPP; ++i) {
+            if (pe[i] < 0) continue;
+            const int en = pe[i] >> 3, sl = pe[i] & 7;
+            const bool isl = en < kPNodeTid;
+            const int ni = en - kPNodeTid;
+            if (sl == 0) {
+                const float g = gumbel(d.key0, d.key1, vid[i], t, 1, 0);
+                const float al = isl ? S.alpha[en] : d.alpha[d.L];
+                if (isl) S.mkey[en] = __fadd_rn(al, g);
+                else S.nmkey[ni] = __fadd_rn(al, g);
+                continue;
+            }
+            const int k = sl - 1;
+            const float g = gumbel(d.key0, d.key1, vid[i], t, 0, k);
+            const float key = __fadd_rn(__fadd_rn(ux[i], __fmul_rn(uy[i], df[i])), g);
+            int vac;
+            if (first) {
+                vac = cz[i] & kFlagVacant;
+            } else {
+                bool pop = cy[i] == kTgtSink;
+                if (cy[i] >= 0) pop = wt[i] != 0ull && p_vid(wt[i], a.packz) == cx[i];
+                const int o = (pop ? 1 : 0) | (push[i] ? 2 : 0);
+                vac = (cz[i] >> o) & 1;
+            }
+            if (isl) {
+                S.key[en][k] = key;
+                S.tv[en][k] = (m[i] << 1) | vac;
+            } else {
+                S.nkey[ni][k] = key;
+                S.ntv[ni][k] = (m[i] << 1) | vac;
             }
         }
     }
-    // ---------------- car-following in shared memory, chunk by chunk ----------------
-    // Warp w of a chunk handles elements [cb + 32 kPU w, cb + 32 kPU (w + 1)),
-    // lane-interleaved; new positions are written after every thread of the
-    // chunk has read its time-t headway.
+}
+
+// Newell car-following of every queued vehicle of the CTA, in shared memory,
+// by warps 0 .. nw - 1: warp w owns links w, w + nw, ...; for a
+// link, lane l updates queue positions l, l + 32, ... (leader first), taking
+// the time-t position of the vehicle ahead from lane l - 1 by a shuffle (from
+// the previous round of 32 for lane 0) before any lane writes.  No barrier is
+// needed: a link's slots are touched by its warp only.  At bin ends the warp
+// also sums the link's vehicles past the midpoint and their positions.
+constexpr int kPCFW = kPCFT / 32;
+
+__device__ __forceinline__ void p_carfollow(const DevSim &d, PSmem &S, const PCtx &c, bool obs, bool obs_only,
+                                            int nw) {
+    const int lane = threadIdx.x & 31;
     const float M = d.M;
-    for (int cb = 0, ci = 0; cb < total; cb += kPT * kPU, ++ci) {
-        const int wbase = cb + (tid >> 5) * 32 * kPU;
-        float xn[kPU];
-        int sidx[kPU];
-        int li = link_of(S.off, nl, min(wbase + lane, total - 1));
-#pragma unroll
-        for (int u = 0; u < kPU; ++u) {
-            const int e = wbase + u * 32 + lane;
-            const bool act = e < total;
-            float x = 0.0f;
-            sidx[u] = -1;
-            xn[u] = 0.0f;
+    for (int li = threadIdx.x >> 5; li < c.nl; li += nw) {
+        const int2 qv = *reinterpret_cast<const int2 *>(&S.q[li]);     // head, length
+        const int n = qv.y;
+        if (n == 0) continue;
+        const int lb = S.lbase[li], cap = S.lbase[li + 1] - lb;
+        const float4 g = S.g[li];
+        float *R = c.P + lb;
+        float ahead = M;                    // time-t position of the vehicle ahead of lane 0
+        int past = 0;
+        long long ps = 0;
+        for (int k0 = 0; k0 < n; k0 += 32) {
+            const int k = k0 + lane;
+            const bool act = k < n;
+            int idx = qv.x + k;
+            if (idx >= cap) idx -= cap;
+            const float x = act ? R[idx] : 0.0f;
+            const float up = __shfl_up_sync(kFull, x, 1);
+            const float last = __shfl_sync(kFull, x, 31);
             if (act) {
-                while (S.off[li + 1] <= e) ++li;
-                const int k = e - S.off[li];
-                const int4 q = S.q[li], st = S.st[li];
-                const int lb = st.x - base0;
-                int idx = q.x + k;
-                if (idx >= st.y) idx -= st.y;
-                x = P[lb + idx];
-                if (e == cb + kPT * kPU - 1) S.carry[(ci + 1) & 1] = x;
+                if (obs) {
+                    past += x >= __fmul_rn(g.x, 0.5f) ? 1 : 0;
+                    ps += pos_fx(x);
+                }
                 if (!obs_only) {
-                    float h;
-                    if (k == 0) {
-                        h = M;
-                    } else if (e == cb) {
-                        h = __fsub_rn(S.carry[ci & 1], x);
-                    } else {
-                        const int ip = idx == 0 ? st.y - 1 : idx - 1;
-                        h = __fsub_rn(P[lb + ip], x);
-                    }
-                    const float4 g = S.g[li];
+                    const float h = k == 0 ? M : __fsub_rn(lane == 0 ? ahead : up, x);
                     int tag;
-                    xn[u] = newell(x, h, g.x, g.y, g.z, g.w, tag);
-                    sidx[u] = lb + idx;
-                    if (k == 0) S.x4[li].x = xn[u];
-                    if (k == 1) S.x4[li].y = xn[u];
-                    if (k == q.y - 2) S.x4[li].z = xn[u];
-                    if (k == q.y - 1) S.x4[li].w = xn[u];
+                    R[idx] = newell(x, h, g.x, g.y, g.z, g.w, tag);
                 }
             }
-            if (obs) {      // block-uniform: midpoint count and position sum per link
-                const unsigned seg = __match_any_sync(kFull, act ? li : -1);
-                const unsigned past = act && x >= __fmul_rn(S.g[li].x, 0.5f) ? 1u : 0u;
-                const unsigned sp = __reduce_add_sync(seg, past);
-                const long long xf = act ? pos_fx(x) : 0;
-                const unsigned slo = __reduce_add_sync(seg, (unsigned)(xf & 0xffffffffll));
-                const unsigned shi = __reduce_add_sync(seg, (unsigned)(xf >> 32));
-                if (act && lane == __ffs(seg) - 1) {
-                    if (sp) atomicAdd(&S.past[li], (int)sp);
-                    atomicAdd(&S.psum[li], (unsigned long long)slo + ((unsigned long long)shi << 32));
-                }
-            }
+            ahead = last;
         }
-        __syncthreads();
-        if (!obs_only) {
+        if (obs) {
+            past = warp_sum(past);
 #pragma unroll
-            for (int u = 0; u < kPU; ++u)
-                if (sidx[u] >= 0) P[sidx[u]] = xn[u];
+            for (int o = 16; o > 0; o >>= 1) ps += __shfl_xor_sync(kFull, ps, o);
+            if (lane == 0) {
+                S.past[li] = past;
+                S.psum[li] = (unsigned long long)ps;
+            }
         }
-        __syncthreads();
     }
-    if (total == 0) __syncthreads();        // the keys above are complete before they are read
-    // ---------------- observation, choice, merge, records ----------------
+}
+
+// Observation at bin ends, choice, merge, next-step bits and records of this
+// thread's link or origin queue.
+__device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int t, bool first,
+                                         bool obs, bool obs_only, const int4 *Cp, const unsigned long long *Wp) {
+    const int tid = threadIdx.x;
     unsigned long long *Wt = a.W3 + (size_t)(t % 3) * d.L;
-    int4 *Ct = a.crec2 + (size_t)(t & 1) * d.L;
-    for (int li = tid; li < nl; li += kPT) {
-        const int j = j0 + li;
+    const float M = d.M;
+    if (tid < c.nl) {
+        const int li = tid, j = c.j0 + li;
         const int4 q = S.q[li];
         const int n = q.y;
         int4 stat = S.stat[li];
@@ -436,28 +582,34 @@ __device__ __forceinline__ void p_step(const DevSim &d, const PArgs &a, PSmem &S
             d.out_tt[o] = stat.z ? (float)((double)stat.y * (double)d.dt / (double)stat.z) : 0.0f;
             stat = make_int4(0, 0, 0, C);
             d.lpos[j] = make_longlong2(pnow, 0);
-            if (obs_only) { S.stat[li] = stat; continue; }
+            if (obs_only) { S.stat[li] = stat; return; }
         }
         stat.x += n;
         S.stat[li] = stat;
         const int4 c0 = S.cr[li];
-        const int2 lead = S.lead[li];
         const int4 nd = S.nd[li];
+        const int4 ld = S.ld[li];
         int tgt = kTgtNone;
         if (c0.x >= 0) {
-            if (nd.y == lead.y) {
+            if (nd.y == ld.y) {
                 tgt = kTgtSink;
             } else {
-                tgt = p_choose(d, first, Cp, Wp, S.key[li], S.tv[li], d.loinfo + nd.z, nd.w - nd.z, lead.y, lead.x, t);
-                if (tgt >= 0) atomicMax(Wt + tgt, merge_word(S.mkey[li], lead.x));
+                tgt = p_choose(d, first, Cp, Wp, a.packz, S.key[li], S.tv[li], c.LO + nd.z, nd.w, ld.y, ld.x, t);
+                if (tgt >= 0) atomicMax(Wt + tgt, p_word(S.mkey[li], ld.x, ld.y, a.packz));
             }
         }
         const float4 g = S.g[li];
-        const float4 x4 = S.x4[li];
-        const float x0 = n >= 1 ? x4.x : 0.0f;
-        const float x1 = n >= 2 ? x4.y : 0.0f;
-        const float xt = n >= 1 ? x4.w : 0.0f;
-        const float xpt = n >= 2 ? x4.z : 0.0f;
+        const int4 st = S.st[li];
+        const int lb = st.x - c.base0;
+        auto at = [&](int k) {
+            int idx = q.x + k;
+            if (idx >= st.y) idx -= st.y;
+            return c.P[lb + idx];
+        };
+        const float x0 = n >= 1 ? at(0) : 0.0f;
+        const float x1 = n >= 2 ? at(1) : 0.0f;
+        const float xt = n >= 1 ? at(n - 1) : 0.0f;
+        const float xpt = n >= 2 ? at(n - 2) : 0.0f;
         int bits = 0;
         bits |= (n == 0 || vacant_after(xt, n >= 2 ? __fsub_rn(xpt, xt) : M, g)) << 0;
         bits |= (n <= 1 || vacant_after(xt, n >= 3 ? __fsub_rn(xpt, xt) : M, g)) << 1;
@@ -469,95 +621,180 @@ __device__ __forceinline__ void p_step(const DevSim &d, const PArgs &a, PSmem &S
         bits |= arrives_after(n >= 2 ? x1 : 0.0f, g, M, d.eps_arr) << 7;
         const int4 rec = make_int4(c0.x, c0.x >= 0 ? tgt : kTgtNone, (c0.z << 8) | bits, __float_as_int(x0));
         S.cr[li] = rec;
-        Ct[j] = rec;
-    }
-    for (int ni = tid; ni < nn; ni += kPT) {
-        const int2 lead = S.nlead[ni];
-        int tgt = kTgtNone;
-        if (lead.x >= 0) {
-            if (S.nzone[ni] == lead.y) {
-                tgt = kTgtSink;
-            } else {
-                const int4 nq = S.nq[ni];
-                tgt = p_choose(d, first, Cp, Wp, S.nkey[ni], S.ntv[ni], d.noinfo + nq.z, nq.w - nq.z, lead.y, lead.x, t);
-                if (tgt >= 0) atomicMax(Wt + tgt, merge_word(S.nmkey[ni], lead.x));
-            }
+        a.crec2[(size_t)(t & 1) * d.L + j] = rec;
+    } else if (!obs_only && tid >= kPNodeTid && tid < kPNodeTid + c.nn) {
+        const int ni = tid - kPNodeTid;
+        const int2 r = S.nrec[ni];
+        if (r.x < 0) return;
+        const int4 nh = S.nh[ni];
+        int tgt;
+        if (S.nzone[ni] == nh.y) {
+            tgt = kTgtSink;
+        } else {
+            const int4 nq = S.nq[ni];
+            tgt = p_choose(d, first, Cp, Wp, a.packz, S.nkey[ni], S.ntv[ni], c.NO + nq.z, nq.w, nh.y, nh.x, t);
+            if (tgt >= 0) atomicMax(Wt + tgt, p_word(S.nmkey[ni], nh.x, nh.y, a.packz));
         }
-        S.nrec[ni] = make_int2(lead.x, tgt);
+        S.nrec[ni] = make_int2(r.x, tgt);
     }
 }
 
 __global__ void __launch_bounds__(kPT, 1) k_persist(DevSim d, PArgs a) {
     extern __shared__ __align__(16) unsigned char p_smem[];
     PSmem &S = *reinterpret_cast<PSmem *>(p_smem);
-    float *P = reinterpret_cast<float *>(p_smem + sizeof(PSmem));
     const int tid = threadIdx.x;
-    const int j0 = a.grp_links[blockIdx.x];
-    const int nl = a.grp_links[blockIdx.x + 1] - j0;
-    const int n0 = blockIdx.x * a.npg;
-    const int nn = max(0, min(a.npg, d.V - n0));
-    const int base0 = nl > 0 ? d.lst[j0].x : 0;
-    const int nslots = nl > 0 ? d.lst[j0 + nl - 1].x + d.lst[j0 + nl - 1].y - base0 : 0;
+    PCtx c;
+    c.j0 = a.grp_links[blockIdx.x];
+    c.nl = a.grp_links[blockIdx.x + 1] - c.j0;
+    c.n0 = blockIdx.x * a.npg;
+    c.nn = max(0, min(a.npg, d.V - c.n0));
+    c.base0 = c.nl > 0 ? d.lst[c.j0].x : 0;
+    const int nslots = c.nl > 0 ? d.lst[c.j0 + c.nl - 1].x + d.lst[c.j0 + c.nl - 1].y - c.base0 : 0;
+    c.nslots = nslots;
+    c.lo0 = c.nl > 0 ? d.lnode[c.j0].z : 0;
+    const int n_lo = c.nl > 0 ? d.lnode[c.j0 + c.nl - 1].w - c.lo0 : 0;
+    c.no0 = c.nn > 0 ? d.no_ptr[c.n0] : 0;
+    const int n_no = c.nn > 0 ? d.no_ptr[c.n0 + c.nn] - c.no0 : 0;
+    unsigned char *dyn = p_smem + sizeof(PSmem);
+    c.P = reinterpret_cast<float *>(dyn);
+    float4 *LO = reinterpret_cast<float4 *>(dyn + p_dyn_bytes(nslots, 0, 0));
+    float4 *NO = LO + n_lo;
+    c.LO = LO;
+    c.NO = NO;
     // ---------------- load the group's state ----------------
-    for (int li = tid; li < nl; li += kPT) {
-        const int j = j0 + li;
-        S.q[li] = d.lq[j];
-        S.st[li] = d.lst[j];
+    const float *pc = (a.t0 & 1) ? d.pos1 : d.pos0;
+    for (int s = tid; s < nslots; s += kPT) c.P[s] = pc[c.base0 + s];
+    for (int e = tid; e < n_lo; e += kPT) LO[e] = d.loinfo[c.lo0 + e];
+    for (int e = tid; e < n_no; e += kPT) NO[e] = d.noinfo[c.no0 + e];
+    for (int li = tid; li < c.nl; li += kPT) {
+        const int j = c.j0 + li;
+        const int4 q = d.lq[j], st = d.lst[j], nd = d.lnode[j];
+        S.q[li] = q;
+        S.st[li] = st;
+        S.lbase[li] = st.x - c.base0;
         S.g[li] = d.geo[j];
-        S.nd[li] = d.lnode[j];
+        S.nd[li] = make_int4(nd.x, nd.y, nd.z - c.lo0, nd.w - nd.z);
         S.stat[li] = d.lstat[j];
         S.flags[li] = d.vac[j];
         S.cr[li] = d.crec[j];
+        S.alpha[li] = d.alpha[j];
+        int4 ld = make_int4(-1, -1, -1, -1);
+        int2 le = make_int2(0, 0);
+        if (q.y >= 1) {
+            const int2 v = d.saux[st.x + q.x];
+            ld.x = v.x;
+            ld.y = v.y;
+            le.x = d.sentry[st.x + q.x];
+        }
+        if (q.y >= 2) {
+            const int idx = q.x + 1 >= st.y ? q.x + 1 - st.y : q.x + 1;
+            const int2 v = d.saux[st.x + idx];
+            ld.z = v.x;
+            ld.w = v.y;
+            le.y = d.sentry[st.x + idx];
+        }
+        S.ld[li] = ld;
+        S.le[li] = le;
     }
-    for (int ni = tid; ni < nn; ni += kPT) {
-        const int n = n0 + ni;
-        S.nq[ni] = make_int4(d.fifo_ptr[n], d.fifo_end[n], d.no_ptr[n], d.no_ptr[n + 1]);
+    for (int ni = tid; ni < c.nn; ni += kPT) {
+        const int n = c.n0 + ni;
+        const int ptr = d.fifo_ptr[n], end = d.fifo_end[n];
+        const int o0 = d.no_ptr[n], o1 = d.no_ptr[n + 1];
+        S.nq[ni] = make_int4(ptr, end, o0 - c.no0, o1 - o0);
         S.nzone[ni] = d.node_zone[n];
         S.nrec[ni] = d.nrec[n];
+        int4 nh = make_int4(-1, -1, -1, -1);
+        int2 dp = make_int2(0, 0);
+        if (ptr < end) {
+            const int2 v = d.fifo_list[ptr];
+            nh.x = v.x;
+            nh.y = v.y;
+            dp.x = d.fifo_dep[ptr];
+        }
+        if (ptr + 1 < end) {
+            const int2 v = d.fifo_list[ptr + 1];
+            nh.z = v.x;
+            nh.w = v.y;
+            dp.y = d.fifo_dep[ptr + 1];
+        }
+        S.nh[ni] = nh;
+        S.ndep[ni] = dp;
     }
-    const float *pc = (a.t0 & 1) ? d.pos1 : d.pos0;
-    for (int s = tid; s < nslots; s += kPT) P[s] = pc[base0 + s];
     if (tid < 4) S.cnt[tid] = 0;
-    if (tid == 0) S.stop = 0;
+    if (tid == 0) {
+        S.stop = 0;
+        S.lbase[c.nl] = nslots;
+    }
     __syncthreads();
     // ---------------- steps ----------------
     unsigned epoch = 0;
     for (int t = a.t0; t < a.t1; ++t) {
-        if (t > a.t0) {
-            p_transfers(d, a, S, P, j0, nl, nn, base0, t - 1);
-            __syncthreads();
+        const bool first = t == a.t0;
+        const bool obs = t > 0 && t % d.obs_every == 0;
+        PPend pd{};
+        int cnt[4] = {0, 0, 0, 0};
+        if (!first) p_apply(d, a, S, c, t - 1, pd, cnt);
+        const int v = p_candidate(d, S, c, t, false);      // reads what this thread's p_apply wrote
+        if (!first) p_count(S, cnt);
+        p_scan(S, v);
+        if (!first && tid < 4) {
+            const int x = S.cnt[tid];
+            if (x) atomicAdd(&d.step_delta[4 * (t - 1) + tid], x);
         }
-        p_step(d, a, S, P, j0, nl, n0, nn, base0, t, t == a.t0, false);
+        const int4 *Cp = a.crec2 + (size_t)((t + 1) & 1) * d.L;                 // records of step t-1
+        const unsigned long long *Wp = a.W3 + (size_t)((t + 2) % 3) * d.L;     // words of step t-1
+        if (tid >= kPCFT) {
+            p_pairs(d, a, S, c, t, first, Cp, Wp, kPCFT, kPT - kPCFT);
+        } else {
+            p_carfollow(d, S, c, obs, false, kPCFW);
+        }
+        __syncthreads();
+        if (tid < 4) S.cnt[tid] = 0;
+        p_decide(d, a, S, c, t, first, obs, false, Cp, Wp);
+        p_refill(S, c, pd);
         ++epoch;
         if (!grid_sync(d, a.bar, epoch * gridDim.x, t, &S.stop)) return;
     }
     if (a.t1 > a.t0) {
-        p_transfers(d, a, S, P, j0, nl, nn, base0, a.t1 - 1);
+        PPend pd{};
+        int cnt[4] = {0, 0, 0, 0};
+        p_apply(d, a, S, c, a.t1 - 1, pd, cnt);
+        p_count(S, cnt);
+        p_refill(S, c, pd);
         __syncthreads();
+        if (tid < 4 && S.cnt[tid]) atomicAdd(&d.step_delta[4 * (a.t1 - 1) + tid], S.cnt[tid]);
     }
     if (a.final_obs) {
-        p_step(d, a, S, P, j0, nl, n0, nn, base0, a.t1, a.t1 == a.t0, true);
         __syncthreads();
+        p_candidate(d, S, c, a.t1, true);
+        __syncthreads();
+        if (tid < kPCFT) p_carfollow(d, S, c, true, true, kPCFW);
+        __syncthreads();
+        p_decide(d, a, S, c, a.t1, false, true, true, nullptr, nullptr);
     }
+    __syncthreads();
     // ---------------- write the group's state back ----------------
     // merge words as the two-kernel executor leaves them: those of the last
-    // step in its parity buffer (read by sim_get_records), the other buffer zero
-    float *pd = (a.t1 & 1) ? d.pos1 : d.pos0;
-    for (int s = tid; s < nslots; s += kPT) pd[base0 + s] = P[s];
+    // step (standard format) in its parity buffer, the other buffer zero
+    float *pdst = (a.t1 & 1) ? d.pos1 : d.pos0;
+    for (int s = tid; s < nslots; s += kPT) pdst[c.base0 + s] = c.P[s];
     const unsigned long long *Wl = a.W3 + (size_t)((a.t1 + 2) % 3) * d.L;
     unsigned long long *Wlast = (a.t1 & 1) ? d.W0 : d.W1;
     unsigned long long *Wnext = (a.t1 & 1) ? d.W1 : d.W0;
-    for (int li = tid; li < nl; li += kPT) {
-        const int j = j0 + li;
+    for (int li = tid; li < c.nl; li += kPT) {
+        const int j = c.j0 + li;
         d.lq[j] = S.q[li];
         d.lstat[j] = S.stat[li];
         d.vac[j] = S.flags[li];
         d.crec[j] = S.cr[li];
-        if (a.t1 > a.t0) Wlast[j] = __ldcg(Wl + j);
+        if (a.t1 > a.t0) {
+            const unsigned long long w = __ldcg(Wl + j);
+            Wlast[j] = w ? ((w & 0xffffffff00000000ull) | (unsigned long long)(~(uint32_t)p_vid(w, a.packz))) : 0ull;
+        }
         Wnext[j] = 0ull;
     }
-    for (int ni = tid; ni < nn; ni += kPT) {
-        const int n = n0 + ni;
+    for (int ni = tid; ni < c.nn; ni += kPT) {
+        const int n = c.n0 + ni;
         d.fifo_ptr[n] = S.nq[ni].x;
         d.nrec[n] = S.nrec[ni];
     }
