@@ -598,7 +598,7 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
     if (opt->ckpt_every > 0) {
         if (opt->route_cap <= 0) return fail(h, SIM_EINVAL, "route_cap must be positive with ckpt_every > 0");
         h->K = opt->ckpt_every;
-        h->route_cap = opt->route_cap;
+        h->route_cap = (opt->route_cap + 7) & ~7;     // rows of 64-byte multiples: 16-byte loads in the reverse pass
         const int K = h->K;
         BwdDev &b = h->b;
         b.S = (int)S; b.K = K; b.cap = h->route_cap; b.n_od = dem->n_od;

@@ -63,23 +63,35 @@ __device__ __forceinline__ float merge_key_of(unsigned long long w) {
     return __uint_as_float(b);
 }
 
+// First index k in [k0, n) of vehicle v's route log whose entry (step, link)
+// satisfies pred, or -1.  Entries are read eight at a time with independent
+// 16-byte loads (rows are 64-byte aligned: the capacity is a multiple of 8).
+template <class Pred>
+__device__ __forceinline__ int route_find(const BwdDev &b, int v, int k0, Pred pred) {
+    const int n = b.route_len[v];
+    const int4 *r = reinterpret_cast<const int4 *>(b.route_log + (size_t)v * b.cap);
+    for (int base = k0 & ~7; base < n; base += 8) {
+        int4 w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = base + 2 * q < n ? r[(base >> 1) + q] : make_int4(-1, -1, -1, -1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int ka = base + 2 * q, kb = ka + 1;
+            if (ka >= k0 && ka < n && pred(w[q].x, w[q].y)) return ka;
+            if (kb >= k0 && kb < n && pred(w[q].z, w[q].w)) return kb;
+        }
+    }
+    return -1;
+}
+
 // adjoint right after vehicle v's first entry into link m at a step > t (0 if none)
 __device__ __forceinline__ double next_entry(const BwdDev &b, int v, int m, int t) {
-    const int n = b.route_len[v];
-    const int2 *r = b.route_log + (size_t)v * b.cap;
-    for (int k = 0; k < n; ++k) {
-        const int2 e = r[k];
-        if (e.x > t && e.y == m) return b.eadj[(size_t)v * b.cap + k];
-    }
-    return 0.0;
+    const int k = route_find(b, v, 0, [&](int s, int l) { return s > t && l == m; });
+    return k >= 0 ? b.eadj[(size_t)v * b.cap + k] : 0.0;
 }
 
 __device__ __forceinline__ int entry_at(const BwdDev &b, int v, int t) {
-    const int n = b.route_len[v];
-    const int2 *r = b.route_log + (size_t)v * b.cap;
-    for (int k = 0; k < n; ++k)
-        if (r[k].x == t) return k;
-    return -1;
+    return route_find(b, v, 0, [&](int s, int) { return s == t; });
 }
 
 // copy the state at the start of step (t0 + rec) into the tape
@@ -181,10 +193,8 @@ __global__ void k_bwd_node_z(DevSim d, BwdDev b, int t, int rec, int bin0) {
         Enew = b.xbar[v];
         Xold = 0.0;
         if (i < d.L && rw >= 0) {                            // next re-entry into the source link
-            const int n = b.route_len[v];
-            const int2 *r = b.route_log + (size_t)v * b.cap;
-            for (int k = rw + 1; k < n; ++k)
-                if (r[k].y == i) { Xold = b.eadj[(size_t)v * b.cap + k]; break; }
+            const int k = route_find(b, v, rw + 1, [&](int, int l) { return l == i; });
+            if (k >= 0) Xold = b.eadj[(size_t)v * b.cap + k];
         }
     } else {
         Enew = next_entry(b, v, c.tgt, t);
@@ -224,26 +234,67 @@ __global__ void k_bwd_node_g(DevSim d, BwdDev b, int t, int rec) {
         info = d.noinfo + d.no_ptr[n];
         deg = d.no_ptr[n + 1] - d.no_ptr[n];
     }
-    double key[32];
+    // keys (V_k + g_k)/tau of the first kG slots held in registers (fully
+    // unrolled); slots past kG are recomputed where needed
+    constexpr int kG = 8;
+    auto keyk = [&](int k, int &m, float &df) {
+        const float4 e = info[k];
+        m = __float_as_int(e.w);
+        df = d.dest_feat[(size_t)zone * d.V + __float_as_int(e.z)];
+        const float util = __fadd_rn(e.x, __fmul_rn(e.y, df));
+        return ((double)util + (double)gumbel(d.key0, d.key1, v, t, 0, k)) * (double)b.inv_tau;
+    };
+    double key[kG];
+    float dfs[kG];
+    int ms[kG];
     double kmax = -INFINITY;
     int ks = 0;
-    for (int k = 0; k < deg; ++k) {
-        const float4 e = info[k];
-        const float df = d.dest_feat[(size_t)zone * d.V + __float_as_int(e.z)];
-        const float util = __fadd_rn(e.x, __fmul_rn(e.y, df));
-        key[k] = ((double)util + (double)gumbel(d.key0, d.key1, v, t, 0, k)) * (double)b.inv_tau;
-        kmax = fmax(kmax, key[k]);
-        if (__float_as_int(e.w) == c.tgt) ks = k;
+#pragma unroll
+    for (int k = 0; k < kG; ++k) {
+        if (k < deg) {
+            key[k] = keyk(k, ms[k], dfs[k]);
+            kmax = fmax(kmax, key[k]);
+            if (ms[k] == c.tgt) ks = k;
+        }
     }
-    double zs = 0.0;
-    for (int k = 0; k < deg; ++k) { key[k] = exp(key[k] - kmax); zs += key[k]; }
-    const double pks = key[ks] / zs;
-    for (int k = 0; k < deg; ++k) {
-        const double pk = key[k] / zs;
+    for (int k = kG; k < deg; ++k) {
+        int m;
+        float df;
+        const double kk = keyk(k, m, df);
+        kmax = fmax(kmax, kk);
+        if (m == c.tgt) ks = k;
+    }
+    double zs = 0.0, eks = 0.0;
+#pragma unroll
+    for (int k = 0; k < kG; ++k) {
+        if (k < deg) {
+            key[k] = exp(key[k] - kmax);
+            zs += key[k];
+            if (k == ks) eks = key[k];
+        }
+    }
+    for (int k = kG; k < deg; ++k) {
+        int m;
+        float df;
+        const double ek = exp(keyk(k, m, df) - kmax);
+        zs += ek;
+        if (k == ks) eks = ek;
+    }
+    const double pks = eks / zs;
+#pragma unroll
+    for (int k = 0; k < kG; ++k) {
+        if (k < deg) {
+            const double pk = key[k] / zs;
+            const double Vbar = pk * ((k == ks ? 1.0 : 0.0) - pks) * lbar * (double)b.inv_tau;
+            atomicAdd(&b.gU[ms[k]], Vbar);
+            atomicAdd(&b.gG[ms[k]], Vbar * (double)dfs[k]);
+        }
+    }
+    for (int k = kG; k < deg; ++k) {
+        int m;
+        float df;
+        const double pk = exp(keyk(k, m, df) - kmax) / zs;
         const double Vbar = pk * ((k == ks ? 1.0 : 0.0) - pks) * lbar * (double)b.inv_tau;
-        const float4 e = info[k];
-        const int m = __float_as_int(e.w);
-        const float df = d.dest_feat[(size_t)zone * d.V + __float_as_int(e.z)];
         atomicAdd(&b.gU[m], Vbar);
         atomicAdd(&b.gG[m], Vbar * (double)df);
     }
@@ -315,7 +366,7 @@ __global__ void __launch_bounds__(kBlockA) k_bwd_cf(DevSim d, BwdDev b, int rec)
             const int e = wbase + u * 32 + lane;
             vv[u] = -1;
             if (e < total) {
-                while (S.off[li + 1] <= e) ++li;
+                li = link_advance(S.off, nl, li, e);
                 const int4 q = S.q[li], st = S.st[li];
                 int idx = q.x + (e - S.off[li]);
                 if (idx >= st.y) idx -= st.y;
@@ -341,7 +392,7 @@ __global__ void __launch_bounds__(kBlockA) k_bwd_cf(DevSim d, BwdDev b, int rec)
             const bool act = e < total;
             double fu = 0.0, fs = 0.0;
             if (act) {
-                while (S.off[li + 1] <= e) ++li;
+                li = link_advance(S.off, nl, li, e);
                 const int k = e - S.off[li];
                 const int n = S.q[li].y;
                 const int tag = stag[e];

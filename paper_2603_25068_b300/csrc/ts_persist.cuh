@@ -68,6 +68,7 @@ struct PSmem {
     int2 le[kPLinks];              // entry steps at queue positions 0 and 1
     int flags[kPLinks];            // vacancy / arrival for the coming step
     int lbase[kPLinks + 1];        // first ring slot of each link in shared memory (static)
+    int wl[32 + 1];                // first link of each car-following warp
     int past[kPLinks];
     float mkey[kPLinks];
     float alpha[kPLinks];
@@ -85,7 +86,7 @@ struct PSmem {
     int plist[kPPairs];            // entity << 3 | (0 merge key, 1 + k choice slot k)
     int wsum[32];
     int cnt[4];                    // step counters: releases, arrivals, candidates, entries
-    int npairs, stop;
+    int npairs, ctot, stop;
 };
 
 // Shared-memory bytes of a CTA beyond PSmem: ring slots, staged choice records
@@ -358,7 +359,8 @@ __device__ __forceinline__ void p_count(PSmem &S, const int *cnt) {
 }
 
 // Step t of this thread's link or origin queue up to the choice: credit,
-// candidate.  Returns its number of choice pairs (merge key + choice slots).
+// candidate.  Returns (choice pairs (merge key + choice slots) << 16) | the
+// link's car-following cost (1 + rounds of 32 vehicles).
 __device__ __forceinline__ int p_candidate(const DevSim &d, PSmem &S, const PCtx &c, int t, bool obs_only) {
     const int tid = threadIdx.x;
     if (tid < c.nl) {
@@ -366,15 +368,16 @@ __device__ __forceinline__ int p_candidate(const DevSim &d, PSmem &S, const PCtx
         S.past[li] = 0;
         S.psum[li] = 0ull;
         const int4 q = S.q[li];
-        if (obs_only) return 0;
+        const int cost = 1 + ((q.y + 31) >> 5);           // car-following rounds of the link (+1)
+        if (obs_only) return cost;
         const int4 st = S.st[li];
         const int credit = min(q.z + st.z, st.w);
         S.q[li].z = credit;
-        const bool cand = (S.flags[li] & kFlagArrive) && credit >= d.dn_fx;
+        const bool cand = q.y > 0 && (S.flags[li] & kFlagArrive) && credit >= d.dn_fx;
         const int4 nd = S.nd[li];
         const int4 ld = S.ld[li];
         S.cr[li] = make_int4(cand ? ld.x : -1, kTgtNone, cand ? S.le[li].x : 0, 0);
-        return (cand && nd.y != ld.y) ? 1 + min(nd.w, kPSlot) : 0;
+        return (((cand && nd.y != ld.y) ? 1 + min(nd.w, kPSlot) : 0) << 16) | cost;
     }
     if (!obs_only && tid >= kPNodeTid && tid < kPNodeTid + c.nn) {
         const int ni = tid - kPNodeTid;
@@ -382,13 +385,15 @@ __device__ __forceinline__ int p_candidate(const DevSim &d, PSmem &S, const PCtx
         const int4 nh = S.nh[ni];
         const bool cand = nq.x < nq.y && S.ndep[ni].x <= t;
         S.nrec[ni] = make_int2(cand ? nh.x : -1, kTgtNone);
-        return (cand && S.nzone[ni] != nh.y) ? 1 + min(nq.w, kPSlot) : 0;
+        return ((cand && S.nzone[ni] != nh.y) ? 1 + min(nq.w, kPSlot) : 0) << 16;
     }
     return 0;
 }
 
-// Block scan of every thread's choice-pair count: the compact pair list.
-__device__ __forceinline__ void p_scan(PSmem &S, int v) {
+// Block scan of every thread's (choice pairs << 16 | car-following cost): the
+// compact pair list and the first link of each of the nw car-following warps
+// (contiguous runs of links with equal shares of the total cost).
+__device__ __forceinline__ void p_scan(PSmem &S, const PCtx &c, int v, int nw) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     int s = v;
 #pragma unroll
@@ -407,11 +412,29 @@ __device__ __forceinline__ void p_scan(PSmem &S, int v) {
             if (lane >= o) r += y;
         }
         S.wsum[lane] = r - x;
-        if (lane == 31) S.npairs = r;
+        if (lane == 31) {
+            S.npairs = r >> 16;
+            S.ctot = r & 0xffff;
+        }
     }
     __syncthreads();
     const int ex = s - v + S.wsum[w];
-    for (int k = 0; k < v; ++k) S.plist[ex + k] = (tid << 3) | k;
+    if (tid < c.nl) {
+        // car-following warp q starts at the first link whose cost prefix
+        // reaches q tot / nw: link tid + 1 for the targets in (ex, ex + cost]
+        // q with e0 < floor(tot q / nw) <= e1: q in [ceil((e0 + 1) nw / tot), ((e1 + 1) nw - 1) / tot]
+        const int tot = S.ctot, e0 = ex & 0xffff, e1 = e0 + (v & 0xffff);
+        const int qa = max(1, ((e0 + 1) * nw + tot - 1) / tot), qb = min(nw - 1, ((e1 + 1) * nw - 1) / tot);
+        for (int q = qa; q <= qb; ++q) S.wl[q] = tid + 1;
+    }
+    if (tid == 0) {                         // targets 0 start at link 0 (covers nl = 0)
+        S.wl[0] = 0;
+        S.wl[nw] = c.nl;
+        for (int q = 1; q < nw; ++q)
+            if (S.ctot * q < nw) S.wl[q] = 0;
+    }
+    const int np = v >> 16;
+    for (int k = 0; k < np; ++k) S.plist[(ex >> 16) + k] = (tid << 3) | k;
     __syncthreads();
 }
 
@@ -503,7 +526,8 @@ __device__ __forceinline__ void p_pairs(const DevSim &d, const PArgs &a, PSmem &
 }
 
 // Newell car-following of every queued vehicle of the CTA, in shared memory,
-// by warps 0 .. nw - 1: warp w owns links w, w + nw, ...; for a
+// by warps 0 .. nw - 1: warp w owns a contiguous run of links with an equal
+// share of the total cost (1 + rounds of 32 vehicles per link); for a
 // link, lane l updates queue positions l, l + 32, ... (leader first), taking
 // the time-t position of the vehicle ahead from lane l - 1 by a shuffle (from
 // the previous round of 32 for lane 0) before any lane writes.  No barrier is
@@ -511,48 +535,67 @@ __device__ __forceinline__ void p_pairs(const DevSim &d, const PArgs &a, PSmem &
 // also sums the link's vehicles past the midpoint and their positions.
 constexpr int kPCFW = kPCFT / 32;
 
-__device__ __forceinline__ void p_carfollow(const DevSim &d, PSmem &S, const PCtx &c, bool obs, bool obs_only,
-                                            int nw) {
-    const int lane = threadIdx.x & 31;
+constexpr int kPLG = 1;          // links a car-following warp updates at once
+
+__device__ __forceinline__ void p_carfollow(const DevSim &d, PSmem &S, const PCtx &c, bool obs, bool obs_only) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float M = d.M;
-    for (int li = threadIdx.x >> 5; li < c.nl; li += nw) {
-        const int2 qv = *reinterpret_cast<const int2 *>(&S.q[li]);     // head, length
-        const int n = qv.y;
-        if (n == 0) continue;
-        const int lb = S.lbase[li], cap = S.lbase[li + 1] - lb;
-        const float4 g = S.g[li];
-        float *R = c.P + lb;
-        float ahead = M;                    // time-t position of the vehicle ahead of lane 0
-        int past = 0;
-        long long ps = 0;
-        for (int k0 = 0; k0 < n; k0 += 32) {
-            const int k = k0 + lane;
-            const bool act = k < n;
-            int idx = qv.x + k;
-            if (idx >= cap) idx -= cap;
-            const float x = act ? R[idx] : 0.0f;
-            const float up = __shfl_up_sync(kFull, x, 1);
-            const float last = __shfl_sync(kFull, x, 31);
-            if (act) {
-                if (obs) {
-                    past += x >= __fmul_rn(g.x, 0.5f) ? 1 : 0;
-                    ps += pos_fx(x);
-                }
-                if (!obs_only) {
-                    const float h = k == 0 ? M : __fsub_rn(lane == 0 ? ahead : up, x);
-                    int tag;
-                    R[idx] = newell(x, h, g.x, g.y, g.z, g.w, tag);
-                }
-            }
-            ahead = last;
-        }
-        if (obs) {
-            past = warp_sum(past);
+    const int l0 = S.wl[w], l1 = S.wl[w + 1];
+    for (int lg = l0; lg < l1; lg += kPLG) {
+        int n[kPLG], qh[kPLG], cap[kPLG];
+        unsigned R[kPLG];
+        float4 g[kPLG];
+        float ahead[kPLG];
+        int rounds = 0;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) ps += __shfl_xor_sync(kFull, ps, o);
-            if (lane == 0) {
-                S.past[li] = past;
-                S.psum[li] = (unsigned long long)ps;
+        for (int j = 0; j < kPLG; ++j) {
+            const int li = lg + j;
+            n[j] = 0;
+            ahead[j] = M;
+            if (li < l1) {
+                const int2 qv = *reinterpret_cast<const int2 *>(&S.q[li]);     // head, length
+                n[j] = qv.y;
+                qh[j] = qv.x;
+                const int lb = S.lbase[li];
+                cap[j] = S.lbase[li + 1] - lb;
+                R[j] = (unsigned)lb;
+                g[j] = S.g[li];
+                rounds = max(rounds, (qv.y + 31) >> 5);
+            }
+        }
+        for (int k0 = 0; k0 < rounds * 32; k0 += 32) {
+            const int k = k0 + lane;
+            float x[kPLG];
+            int idx[kPLG];
+#pragma unroll
+            for (int j = 0; j < kPLG; ++j) {
+                idx[j] = qh[j] + k;
+                if (idx[j] >= cap[j]) idx[j] -= cap[j];
+                x[j] = k < n[j] ? c.P[R[j] + idx[j]] : 0.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < kPLG; ++j) {
+                const float up = __shfl_up_sync(kFull, x[j], 1);
+                const float last = __shfl_sync(kFull, x[j], 31);
+                if (obs && k0 < n[j]) {     // bin end: vehicles past the midpoint, position sum (time t)
+                    const bool act = k < n[j];
+                    const int pj = warp_sum(act && x[j] >= __fmul_rn(g[j].x, 0.5f) ? 1 : 0);
+                    long long sj = act ? pos_fx(x[j]) : 0;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(kFull, sj, o);
+                    if (lane == 0) {
+                        S.past[lg + j] += pj;
+                        S.psum[lg + j] += (unsigned long long)sj;
+                    }
+                }
+                if (k < n[j]) {
+                    if (!obs_only) {
+                        const float h = k == 0 ? M : __fsub_rn(lane == 0 ? ahead[j] : up, x[j]);
+                        int tag;
+                        c.P[R[j] + idx[j]] = newell(x[j], h, g[j].x, g[j].y, g[j].z, g[j].w, tag);
+                    }
+                }
+                ahead[j] = last;
             }
         }
     }
@@ -736,7 +779,7 @@ __global__ void __launch_bounds__(kPT, 1) k_persist(DevSim d, PArgs a) {
         if (!first) p_apply(d, a, S, c, t - 1, pd, cnt);
         const int v = p_candidate(d, S, c, t, false);      // reads what this thread's p_apply wrote
         if (!first) p_count(S, cnt);
-        p_scan(S, v);
+        p_scan(S, c, v, kPCFW);
         if (!first && tid < 4) {
             const int x = S.cnt[tid];
             if (x) atomicAdd(&d.step_delta[4 * (t - 1) + tid], x);
@@ -746,7 +789,7 @@ __global__ void __launch_bounds__(kPT, 1) k_persist(DevSim d, PArgs a) {
         if (tid >= kPCFT) {
             p_pairs(d, a, S, c, t, first, Cp, Wp, kPCFT, kPT - kPCFT);
         } else {
-            p_carfollow(d, S, c, obs, false, kPCFW);
+            p_carfollow(d, S, c, obs, false);
         }
         __syncthreads();
         if (tid < 4) S.cnt[tid] = 0;
@@ -766,9 +809,9 @@ __global__ void __launch_bounds__(kPT, 1) k_persist(DevSim d, PArgs a) {
     }
     if (a.final_obs) {
         __syncthreads();
-        p_candidate(d, S, c, a.t1, true);
-        __syncthreads();
-        if (tid < kPCFT) p_carfollow(d, S, c, true, true, kPCFW);
+        const int v = p_candidate(d, S, c, a.t1, true);
+        p_scan(S, c, v, kPCFW);
+        if (tid < kPCFT) p_carfollow(d, S, c, true, true);
         __syncthreads();
         p_decide(d, a, S, c, a.t1, false, true, true, nullptr, nullptr);
     }

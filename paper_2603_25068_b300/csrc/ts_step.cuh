@@ -101,6 +101,18 @@ __device__ __forceinline__ int link_of(const int *off, int nl, int e) {
     return lo;
 }
 
+// advance link index li (the link of an earlier element) to the link of
+// element e: two linear steps, then a binary search (empty links have equal
+// offsets, so the link of a later element can be many links further on)
+__device__ __forceinline__ int link_advance(const int *off, int nl, int li, int e) {
+    if (off[li + 1] > e) return li;
+    ++li;
+    if (off[li + 1] > e) return li;
+    ++li;
+    if (off[li + 1] > e) return li;
+    return link_of(off, nl, e);
+}
+
 __device__ __forceinline__ float choice_key(const DevSim &d, float4 e, int zone, int vid, int t, int slot) {
     const float df = d.dest_feat[(size_t)zone * d.V + __float_as_int(e.z)];
     const float v = __fadd_rn(e.x, __fmul_rn(e.y, df));
@@ -162,7 +174,7 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
         S.alpha[tid] = d.alpha[j];
         const int credit = min(q.z + st.z, st.w);
         S.credit[tid] = credit;
-        S.cand[tid] = !obs_only && (flags & kFlagArrive) && credit >= d.dn_fx;
+        S.cand[tid] = !obs_only && q.y > 0 && (flags & kFlagArrive) && credit >= d.dn_fx;
         S.past[tid] = 0;
         S.psum[tid] = 0ull;
         S.ent[tid] = 0;
@@ -203,7 +215,7 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
             const int e = wbase + u * 32 + lane;
             v[u] = 0.0f;
             if (e < total) {
-                while (S.off[li + 1] <= e) ++li;
+                li = link_advance(S.off, nl, li, e);
                 const int4 q = S.q[li], st = S.st[li];
                 int idx = q.x + (e - S.off[li]);
                 if (idx >= st.y) idx -= st.y;
@@ -281,7 +293,7 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
             const bool act = e < total;
             float x = 0.0f;
             if (act) {
-                while (S.off[li + 1] <= e) ++li;
+                li = link_advance(S.off, nl, li, e);
                 x = xs[e];
                 if (!obs_only) {
                     const int k = e - S.off[li];
