@@ -198,7 +198,7 @@ extern "C" int32_t sim_n_bins(int32_t T, int32_t obs_every) {
 // The dynamic shared-memory limit is an attribute of a kernel function, shared by
 // every handle: raise it monotonically (per device) to the largest size needed.
 static std::mutex g_attr_mu;
-static size_t g_attr_a[64], g_attr_cf[64], g_attr_ba[64];
+static size_t g_attr_a[64], g_attr_at[64], g_attr_cf[64], g_attr_ba[64];
 
 template <class K>
 static cudaError_t raise_smem_attr(K kernel, size_t *cur, int device, size_t bytes) {
@@ -244,6 +244,7 @@ static int build_blocks(sim_ctx *h) {
     h->d.npb = (h->V + nblk - 1) / nblk;
     h->stage_max = smax;
     CU(raise_smem_attr(k_step_a, g_attr_a, h->device, (size_t)smax * sizeof(float)));
+    CU(raise_smem_attr(k_step_a_tape, g_attr_at, h->device, (size_t)smax * sizeof(float)));
     return SIM_OK;
 }
 
@@ -982,6 +983,8 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     room((size_t)L + V, sizeof(double)); room((size_t)L + V, sizeof(double));
     room((size_t)nb * L, sizeof(double)); room((size_t)(nb + 1) * L, sizeof(double));
     room(N, sizeof(float)); room((size_t)5 * L + std::max(F, 1) + 1 + std::max(h->n_od, 1), sizeof(float));
+    const int n_gw = (L + kGwLinks - 1) / kGwLinks;
+    room((size_t)n_gw * std::max(F, 1), sizeof(double));
     if (need > pool.cap) {
         if (pool.buf) { cudaDeviceSynchronize(); cudaFree(pool.buf); pool.buf = nullptr; pool.cap = 0; }
         cudaError_t e = cudaMalloc(&pool.buf, need);
@@ -1012,6 +1015,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     double *d_Csuf = (double *)take((size_t)(nb + 1) * L, sizeof(double));
     float *d_dxT_w = (float *)take(N, sizeof(float));
     float *d_gout = (float *)take((size_t)5 * L + std::max(F, 1) + 1 + std::max(h->n_od, 1), sizeof(float));
+    double *d_gw_part = (double *)take((size_t)n_gw * std::max(F, 1), sizeof(double));
     CU(cudaMemcpyAsync(d_Cbar, cb.data(), cb.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CU(cudaMemcpyAsync(d_Csuf, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     b.Cbar = d_Cbar;
@@ -1034,19 +1038,25 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     const size_t smem_a = (size_t)h->stage_max * sizeof(float);
     const size_t smem_cf = (size_t)h->stage_max * (sizeof(double) + sizeof(int) + 1);
     CU(raise_smem_attr(k_bwd_cf, g_attr_cf, h->device, smem_cf));
-    const int gS = (std::max(S, L) + 255) / 256, gLV = (L + V + 255) / 256, gN = (std::max(L, V) + 255) / 256;
+    const int gS = (std::max(S, L) + 255) / 256, gLV = (L + V + 255) / 256;
     for (int sg = nseg - 1; sg >= 0; --sg) {
         const int t0 = sg * K, t1 = std::min(T, t0 + K);
         ckpt_copy(h, sg, t0 & 1, false);
         CU(cudaMemsetAsync((t0 & 1) ? h->d.W1 : h->d.W0, 0, (size_t)L * sizeof(unsigned long long), h->stream));
-        k_tape_pre<<<gS, 256, 0, h->stream>>>(dr, b, 0, t0 & 1);
-        for (int t = t0; t < t1; ++t) {
-            dr.tag_tape = b.ttag + (size_t)(t - t0) * S;
-            k_step_a<<<dr.nblk, kBlockA, smem_a, h->stream>>>(dr, t, 0);
+        for (int t = t0; t < t1; ++t) {            // each step writes its own tape record
+            const size_t r = (size_t)(t - t0);
+            dr.tag_tape = b.ttag + r * S;
+            dr.tape_pos = b.tpos + r * S;
+            dr.tape_vid = b.tvid + r * S;
+            dr.tape_lq = b.tlq + r * L;
+            dr.tape_crec = b.tcrec + r * L;
+            dr.tape_nrec = b.tnrec + r * V;
+            dr.tape_W = b.tW + r * L;
+            k_step_a_tape<<<dr.nblk, kBlockA, smem_a, h->stream>>>(dr, t);
             k_step_b<<<(L + V + 255) / 256, 256, 0, h->stream>>>(dr, t);
-            k_tape_post<<<gN, 256, 0, h->stream>>>(dr, b, t - t0, t & 1);
-            k_tape_pre<<<gS, 256, 0, h->stream>>>(dr, b, t - t0 + 1, (t + 1) & 1);
         }
+        dr.tape_W = nullptr;
+        k_tape_pre<<<gS, 256, 0, h->stream>>>(dr, b, t1 - t0, t1 & 1);    // state at the end of the segment
         for (int t = t1 - 1; t >= t0; --t) {
             const int rec = t - t0;
             if ((t + 1) % obs == 0 || t + 1 == T)
@@ -1064,8 +1074,9 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     float *gu = go, *gk = go + L, *ga = go + 2 * L, *gbeta = go + 3 * L, *gc = go + 4 * L, *gw = go + 5 * L;
     float *gao = gw + std::max(F, 1), *gl = gao + 1;
     const int nfin = std::max(std::max(L, F), std::max(b.n_od, 1));
-    k_bwd_finalize<<<(nfin + 255) / 256, 256, 0, h->stream>>>(h->d, b, h->d_kappa, h->d_beta, h->d_cost, h->d_phi,
-                                                               h->d_psi, h->opt.dn, gu, gk, ga, gbeta, gc, gw, gao, gl);
+    if (F > 0) k_bwd_gw_part<<<n_gw, kGwLinks, 0, h->stream>>>(h->d, b, h->d_phi, h->d_psi, d_gw_part);
+    k_bwd_finalize<<<(nfin + 255) / 256, 256, 0, h->stream>>>(h->d, b, h->d_kappa, h->d_beta, h->d_cost, d_gw_part,
+                                                               n_gw, h->opt.dn, gu, gk, ga, gbeta, gc, gw, gao, gl);
     CU(cudaGetLastError());
     const cudaMemcpyKind kd = out->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const std::pair<float *, const float *> outs[] = {

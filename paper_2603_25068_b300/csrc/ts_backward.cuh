@@ -105,16 +105,6 @@ __global__ void k_tape_pre(DevSim d, BwdDev b, int rec, int cur) {
     if (i < d.L) b.tlq[(size_t)rec * d.L + i] = d.lq[i];
 }
 
-// copy the decisions of step t0 + rec into the tape
-__global__ void k_tape_post(DevSim d, BwdDev b, int rec, int p) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < d.L) {
-        b.tcrec[(size_t)rec * d.L + i] = d.crec[i];
-        b.tW[(size_t)rec * d.L + i] = (p ? d.W1 : d.W0)[i];
-    }
-    if (i < d.V) b.tnrec[(size_t)rec * d.V + i] = d.nrec[i];
-}
-
 // adjoint of the final positions (vehicles on a link at the end of the rollout)
 __global__ void k_bwd_init(DevSim d, BwdDev b, const float *dxT) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -420,10 +410,30 @@ __global__ void __launch_bounds__(kBlockA) k_bwd_cf(DevSim d, BwdDev b, int rec)
     }
 }
 
+// per-feature partial sums of dL/dw = sum_l gU_l phi_lf + gG_l psi_lf over the
+// 256 links of a block, in a fixed tree order (deterministic)
+constexpr int kGwLinks = 256;
+__global__ void __launch_bounds__(kGwLinks) k_bwd_gw_part(DevSim d, BwdDev b, const float *phi, const float *psi,
+                                                         double *part) {
+    __shared__ double red[kGwLinks];
+    const int tid = threadIdx.x, l = blockIdx.x * kGwLinks + tid;
+    for (int f = 0; f < d.F; ++f) {
+        red[tid] = l < d.L ? b.gU[l] * (double)phi[(size_t)l * d.F + f] + b.gG[l] * (double)psi[(size_t)l * d.F + f]
+                           : 0.0;
+        __syncthreads();
+        for (int st = kGwLinks / 2; st > 0; st >>= 1) {
+            if (tid < st) red[tid] += red[tid + st];
+            __syncthreads();
+        }
+        if (tid == 0) part[(size_t)blockIdx.x * d.F + f] = red[0];
+        __syncthreads();
+    }
+}
+
 // parameter gradients from the accumulators: u dt, s = dn / kappa,
 // U = beta / c + w.phi, G = w.psi
 __global__ void k_bwd_finalize(DevSim d, BwdDev b, const float *kappa, const float *beta, const float *cost,
-                               const float *phi, const float *psi, float dn, float *gu_o, float *gk_o,
+                               const double *gw_part, int n_part, float dn, float *gu_o, float *gk_o,
                                float *ga_o, float *gb_o, float *gc_o, float *gw_o, float *gao_o, float *gl_o) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < d.L) {
@@ -436,8 +446,7 @@ __global__ void k_bwd_finalize(DevSim d, BwdDev b, const float *kappa, const flo
     }
     if (j < d.F && gw_o) {
         double s = 0.0;
-        for (int l = 0; l < d.L; ++l)
-            s += b.gU[l] * (double)phi[(size_t)l * d.F + j] + b.gG[l] * (double)psi[(size_t)l * d.F + j];
+        for (int p = 0; p < n_part; ++p) s += gw_part[(size_t)p * d.F + j];
         gw_o[j] = (float)s;
     }
     if (j == 0 && gao_o) *gao_o = (float)*b.gao;

@@ -68,6 +68,12 @@ struct DevSim {
     int *err;                      // [4]
     // tape (backward); null when not recording
     int8_t *tag_tape;              // [S] car-following tag of each slot's vehicle this step
+    float *tape_pos;               // [S] positions at the start of this step (occupied slots)
+    int *tape_vid;                 // [S] vehicle of each occupied slot at the start of this step
+    int4 *tape_lq;                 // [L] queue state at the start of this step
+    int4 *tape_crec;               // [L] link records of this step
+    int2 *tape_nrec;               // [V] origin-queue records of this step
+    unsigned long long *tape_W;    // [L] merge words of this step
     int2 *route_log;               // [N * route_cap] (step, link) of every entry; null = off
     int *route_len;                // [N] entries so far
     int route_cap;

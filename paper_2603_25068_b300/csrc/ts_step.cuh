@@ -145,7 +145,10 @@ __device__ __forceinline__ int choose(const DevSim &d, const float4 *lo, const f
 }
 
 // One block of k_step_a: links [blk_links[b], blk_links[b+1]) and origin queues
-// [b npb, (b+1) npb), phase by phase (see the file header).
+// [b npb, (b+1) npb), phase by phase (see the file header).  kTape: also write
+// the reverse pass's tape of the step (state at its start for the occupied
+// slots, tags, queue states and records).
+template <bool kTape>
 __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool obs_only, float *xs) {
     __shared__ ABlockSmem S;
     const int tid = threadIdx.x;
@@ -165,6 +168,7 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
         const int4 q = d.lq[j];
         const int4 st = d.lst[j];
         const int flags = d.vac[j];
+        if (kTape) d.tape_lq[j] = q;
         S.q[tid] = q;
         S.st[tid] = st;
         S.g[tid] = d.geo[j];
@@ -210,6 +214,7 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
         if (wbase >= total) break;
         int li = link_of(S.off, nl, min(wbase + lane, total - 1));
         float v[kU];
+        int sl[kTape ? kU : 1], vd[kTape ? kU : 1];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const int e = wbase + u * 32 + lane;
@@ -220,12 +225,22 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
                 int idx = q.x + (e - S.off[li]);
                 if (idx >= st.y) idx -= st.y;
                 v[u] = pc[st.x + idx];
+                if (kTape) {
+                    sl[u] = st.x + idx;
+                    vd[u] = d.saux[st.x + idx].x;
+                }
             }
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const int e = wbase + u * 32 + lane;
-            if (e < total) xs[e] = v[u];
+            if (e < total) {
+                xs[e] = v[u];
+                if (kTape) {
+                    d.tape_pos[sl[u]] = v[u];
+                    d.tape_vid[sl[u]] = vd[u];
+                }
+            }
         }
     }
     if (tid < nl && S.cand[tid]) {
@@ -305,7 +320,7 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
                     int idx = q.x + k;
                     if (idx >= st.y) idx -= st.y;
                     pn[st.x + idx] = xn;
-                    if (d.tag_tape) d.tag_tape[st.x + idx] = (int8_t)tag;
+                    if (kTape) d.tag_tape[st.x + idx] = (int8_t)tag;
                     // keep the new positions of the first two and last two vehicles
                     if (k == 0) S.x4[li].x = xn;
                     if (k == 1) S.x4[li].y = xn;
@@ -343,6 +358,7 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
             }
         }
         d.nrec[n] = make_int2(lead.x, tgt);
+        if (kTape) d.tape_nrec[n] = make_int2(lead.x, tgt);
         return;
     }
     if (tid >= nl) return;
@@ -397,12 +413,20 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
     bits |= arrives_after(n >= 1 ? x0 : 0.0f, g, M, d.eps_arr) << 6;
     bits |= arrives_after(n >= 2 ? x1 : 0.0f, g, M, d.eps_arr) << 7;
     const int cand = S.cand[li];
-    d.crec[j] = make_int4(cand ? lead.x : -1, cand ? tgt : kTgtNone, (S.ent[li] << 8) | bits, __float_as_int(x0));
+    const int4 rec = make_int4(cand ? lead.x : -1, cand ? tgt : kTgtNone, (S.ent[li] << 8) | bits, __float_as_int(x0));
+    d.crec[j] = rec;
+    if (kTape) d.tape_crec[j] = rec;
 }
 
 __global__ void __launch_bounds__(kBlockA, 6) k_step_a(DevSim d, int t, int obs_only) {
     extern __shared__ float xs[];
-    step_block(d, blockIdx.x, t, obs_only != 0, xs);
+    step_block<false>(d, blockIdx.x, t, obs_only != 0, xs);
+}
+
+// the same step, recording the reverse pass's tape (segment recomputation)
+__global__ void __launch_bounds__(kBlockA, 6) k_step_a_tape(DevSim d, int t) {
+    extern __shared__ float xs[];
+    step_block<true>(d, blockIdx.x, t, false, xs);
 }
 
 // Sum of v over the block added to *dst by one atomic (every thread must call).
@@ -431,6 +455,7 @@ __device__ __forceinline__ void step_b(const DevSim &d, int i, int t) {
         const int4 st = d.lst[j];
         const int4 c = d.crec[j];
         const unsigned long long win = W[j];
+        if (d.tape_W) d.tape_W[j] = win;
         bool pop = false;
         cands = c.x >= 0;
         if (c.y == kTgtSink) {
@@ -531,7 +556,7 @@ __global__ void __launch_bounds__(kBlockA, 6) k_batch_a(const DevSim *ds, const 
     const int md = mode[m.x];
     if (md == kModeDone) return;
     load_member(sd, ds, m.x);
-    step_block(sd, m.y, tvec[m.x], md == kModeFinal, xs);
+    step_block<false>(sd, m.y, tvec[m.x], md == kModeFinal, xs);
 }
 
 __global__ void __launch_bounds__(256) k_batch_b(const DevSim *ds, const int2 *bmap, const int *tvec, const int *mode) {
