@@ -198,7 +198,7 @@ extern "C" int32_t sim_n_bins(int32_t T, int32_t obs_every) {
 // The dynamic shared-memory limit is an attribute of a kernel function, shared by
 // every handle: raise it monotonically (per device) to the largest size needed.
 static std::mutex g_attr_mu;
-static size_t g_attr_a[64], g_attr_at[64], g_attr_cf[64], g_attr_ba[64];
+static size_t g_attr_a[64], g_attr_at[64], g_attr_ba[64];
 
 template <class K>
 static cudaError_t raise_smem_attr(K kernel, size_t *cur, int device, size_t bytes) {
@@ -1036,8 +1036,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     dr.route_log = nullptr;
     dr.step_delta = h->d_dummy;
     const size_t smem_a = (size_t)h->stage_max * sizeof(float);
-    const size_t smem_cf = (size_t)h->stage_max * (sizeof(double) + sizeof(int) + 1);
-    CU(raise_smem_attr(k_bwd_cf, g_attr_cf, h->device, smem_cf));
+
     const int gS = (std::max(S, L) + 255) / 256, gLV = (L + V + 255) / 256;
     for (int sg = nseg - 1; sg >= 0; --sg) {
         const int t0 = sg * K, t1 = std::min(T, t0 + K);
@@ -1065,7 +1064,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
             CU(cudaMemsetAsync(b.SA, 0, (size_t)L * sizeof(double), h->stream));
             k_bwd_node_z<<<gLV, 256, 0, h->stream>>>(dr, b, t, rec, t / obs);
             k_bwd_node_g<<<gLV, 256, 0, h->stream>>>(dr, b, t, rec);
-            k_bwd_cf<<<dr.nblk, kBlockA, smem_cf, h->stream>>>(dr, b, rec);
+            k_bwd_cf<<<(L * 32 + kBwdCfThreads - 1) / kBwdCfThreads, kBwdCfThreads, 0, h->stream>>>(dr, b, rec);
         }
         CU(cudaGetLastError());
     }

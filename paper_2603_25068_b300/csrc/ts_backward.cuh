@@ -290,123 +290,69 @@ __global__ void k_bwd_node_g(DevSim d, BwdDev b, int t, int rec) {
     }
 }
 
-// inclusive sum over lanes of one contiguous segment of equal keys
-__device__ __forceinline__ double seg_sum(double v, int key, int lane) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_up_sync(kFull, v, o);
-        const int ky = __shfl_up_sync(kFull, key, o);
-        if (lane >= o && ky == key) v += y;
-    }
-    return v;
-}
+// (3) car-following of step (t0 + rec): one warp per link, lanes over queue
+// positions k = k0 + lane (leader first).  Vehicle k's adjoint at time t is its
+// own adjoint at t + 1 unless its update was congested (then x' depended on the
+// leader only), plus its follower's adjoint when the follower was congested
+// (the follower's headway used x_k); the follower's values come from lane + 1
+// (lane 31 loads the next round's first vehicle).  Every vehicle's adjoint is
+// read before any lane writes it, and a link's vehicles belong to its warp only.
+// Per-link parameter sums: free -> u (x' = x + u dt), congested -> s.
+constexpr int kBwdCfThreads = 256;
 
-struct BwdCfSmem {
-    int4 q[kLinksPerBlock];
-    int4 st[kLinksPerBlock];
-    float udt[kLinksPerBlock];
-    int off[kLinksPerBlock + 1];
-    double su[kLinksPerBlock], ss[kLinksPerBlock];
-};
-
-// (3) car-following of step (t0 + rec), block layout of k_step_a: stage each
-// queue's vehicles, tags and adjoints, then write the adjoints at time t.
-__global__ void __launch_bounds__(kBlockA) k_bwd_cf(DevSim d, BwdDev b, int rec) {
-    extern __shared__ unsigned char bsm[];
-    __shared__ BwdCfSmem S;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int j0 = d.blk_links[blockIdx.x];
-    const int nl = d.blk_links[blockIdx.x + 1] - j0;
-    if (tid < nl) {
-        S.q[tid] = b.tlq[(size_t)rec * d.L + j0 + tid];
-        S.st[tid] = d.lst[j0 + tid];
-        S.udt[tid] = d.geo[j0 + tid].y;
-        S.su[tid] = 0.0;
-        S.ss[tid] = 0.0;
-    }
-    __syncthreads();
-    if (tid < 32) {
-        const int a = tid < nl ? S.q[tid].y : 0;
-        const int c = tid + 32 < nl ? S.q[tid + 32].y : 0;
-        int sa = a, sc = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int ya = __shfl_up_sync(kFull, sa, o), yc = __shfl_up_sync(kFull, sc, o);
-            if (tid >= o) { sa += ya; sc += yc; }
+__global__ void __launch_bounds__(kBwdCfThreads) k_bwd_cf(DevSim d, BwdDev b, int rec) {
+    const int lane = threadIdx.x & 31;
+    const int j = (blockIdx.x * kBwdCfThreads + threadIdx.x) >> 5;
+    if (j >= d.L) return;
+    const int4 q = b.tlq[(size_t)rec * d.L + j];
+    const int n = q.y;
+    if (n == 0) return;
+    const int4 st = d.lst[j];
+    const double dt = (double)d.dt;
+    const size_t tb = (size_t)rec * b.S + st.x;
+    auto slot = [&](int k) {
+        int idx = q.x + k;
+        if (idx >= st.y) idx -= st.y;
+        return idx;
+    };
+    double su = 0.0, ss = 0.0;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const int k = k0 + lane;
+        const bool act = k < n;
+        int v = -1, tag = kTagStop;
+        double g = 0.0;
+        if (act) {
+            const int idx = slot(k);
+            v = b.tvid[tb + idx];
+            tag = b.ttag[tb + idx];
+            g = b.xbar[v];
         }
-        const int tot_a = __shfl_sync(kFull, sa, 31);
-        if (tid < nl) S.off[tid] = sa - a;
-        if (tid + 32 < nl) S.off[tid + 32] = tot_a + sc - c;
-        if (tid == 31) S.off[nl] = tot_a + sc;
-    }
-    __syncthreads();
-    const int total = S.off[nl];
-    double *sxb = (double *)bsm;
-    int *svid = (int *)(sxb + total);
-    int8_t *stag = (int8_t *)(svid + total);
-    const size_t tbase = (size_t)rec * b.S;
-    // stage vehicles, tags and their adjoints
-    for (int pass = 0; pass < total; pass += kBlockA * kU) {
-        const int wbase = pass + (tid >> 5) * 32 * kU;
-        if (wbase >= total) break;
-        int li = link_of(S.off, nl, min(wbase + lane, total - 1));
-        int vv[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int e = wbase + u * 32 + lane;
-            vv[u] = -1;
-            if (e < total) {
-                li = link_advance(S.off, nl, li, e);
-                const int4 q = S.q[li], st = S.st[li];
-                int idx = q.x + (e - S.off[li]);
-                if (idx >= st.y) idx -= st.y;
-                vv[u] = b.tvid[tbase + st.x + idx];
-                stag[e] = b.ttag[tbase + st.x + idx];
-            }
+        // the follower (k + 1): next lane, or the next round's first vehicle
+        int ftag = __shfl_down_sync(kFull, tag, 1);
+        double fg = __shfl_down_sync(kFull, g, 1);
+        if (lane == 31 && k + 1 < n) {
+            const int idx = slot(k + 1);
+            ftag = b.ttag[tb + idx];
+            fg = b.xbar[b.tvid[tb + idx]];
         }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int e = wbase + u * 32 + lane;
-            if (e < total) { svid[e] = vv[u]; sxb[e] = b.xbar[vv[u]]; }
+        double pre = 0.0;
+        if (act) {
+            pre = (tag == kTagCong) ? 0.0 : g;
+            if (k + 1 < n && ftag == kTagCong) pre += fg;
+            if (tag == kTagFree) su += g * dt;
+            if (tag == kTagCong) ss -= g;
         }
+        __syncwarp();                           // every lane has read before any writes
+        if (act) b.xbar[v] = pre;
     }
-    __syncthreads();
-    // adjoints at time t and per-link parameter sums
-    for (int pass = 0; pass < total; pass += kBlockA * kU) {
-        const int wbase = pass + (tid >> 5) * 32 * kU;
-        if (wbase >= total) break;
-        int li = link_of(S.off, nl, min(wbase + lane, total - 1));
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int e = wbase + u * 32 + lane;
-            const bool act = e < total;
-            double fu = 0.0, fs = 0.0;
-            if (act) {
-                li = link_advance(S.off, nl, li, e);
-                const int k = e - S.off[li];
-                const int n = S.q[li].y;
-                const int tag = stag[e];
-                const double g = sxb[e];
-                double pre = (tag == kTagCong) ? 0.0 : g;
-                if (k + 1 < n && stag[e + 1] == kTagCong) pre += sxb[e + 1];
-                b.xbar[svid[e]] = pre;
-                if (tag == kTagFree) fu = g * (double)d.dt;
-                if (tag == kTagCong) fs = -g;
-            }
-            const int key = act ? li : -1;
-            const double su = seg_sum(fu, key, lane);
-            const double ss = seg_sum(fs, key, lane);
-            const int knext = __shfl_down_sync(kFull, key, 1);
-            if (act && (lane == 31 || knext != key)) {
-                if (su != 0.0) atomicAdd(&S.su[li], su);
-                if (ss != 0.0) atomicAdd(&S.ss[li], ss);
-            }
-        }
+    for (int o = 16; o > 0; o >>= 1) {
+        su += __shfl_xor_sync(kFull, su, o);
+        ss += __shfl_xor_sync(kFull, ss, o);
     }
-    __syncthreads();
-    if (tid < nl) {
-        b.gu[j0 + tid] += S.su[tid];
-        b.gs[j0 + tid] += S.ss[tid];
+    if (lane == 0) {
+        if (su != 0.0) b.gu[j] += su;
+        if (ss != 0.0) b.gs[j] += ss;
     }
 }
 
