@@ -218,6 +218,24 @@ SIM_API int sim_backward(sim_handle h, const float *dL_dcounts, const float *dL_
 
 /* Copy the current state / last-step decisions to host buffers. */
 SIM_API int sim_get_state(sim_handle h, sim_state_view *out);
+
+/* Replace the dynamic state by a given one at step t of the current horizon
+ * (0 <= t <= T of the last sim_reset / sim_rollout), e.g. the oracle's state
+ * after a flagged near-tie, so that a lockstep comparison can continue from
+ * it.  *in holds host arrays in the layout of sim_state_view (every field
+ * required): vehicle link (-1 waiting / not yet departed, -2 arrived),
+ * position, rank in its queue (0 = leader), entry step; per link outflow
+ * credit (2^-16 veh) and exits; per origin node the number of vehicles
+ * released.  The next sim_step continues with step t.  The vacancy / arrival
+ * flags of step t are derived from the queues as the step would derive them.
+ * The observation bin containing t restarts at t (its counts, speeds and
+ * travel times cover [t, bin end)); the step counters of earlier steps are
+ * kept.  The paper has no counterpart (its state is a dense tensor one can
+ * assign).  Errors: SIM_ESTATE (no sim_reset yet, t out of range), SIM_EINVAL
+ * (a field out of range, ranks not 0..n-1 per link, a queue over capacity, a
+ * position outside its link, waiting vehicles that do not match the origin
+ * queues). */
+SIM_API int sim_set_state(sim_handle h, const sim_state_view *in, int32_t t);
 SIM_API int sim_get_records(sim_handle h, sim_records *out);
 
 /* Launch shape of the node-model kernel: queue slots staged in shared memory

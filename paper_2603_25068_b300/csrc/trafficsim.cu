@@ -65,6 +65,27 @@ __global__ void k_reset(DevSim d, const int *fifo_beg) {
     if (i < 4) d.err[i] = 0;
 }
 
+// Vacancy / arrival flags of step t of every link from its queue at time t, as
+// k_step_b selects them for an outcome without pop or push (set state).
+__global__ void k_set_flags(DevSim d, int t) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= d.L) return;
+    const int4 q = d.lq[j], st = d.lst[j];
+    const float4 g = d.geo[j];
+    const float *pc = (t & 1) ? d.pos1 : d.pos0;
+    auto at = [&](int k) {
+        int idx = q.x + k;
+        if (idx >= st.y) idx -= st.y;
+        return pc[st.x + idx];
+    };
+    const int n = q.y;
+    const float M = d.M;
+    const float xt = n >= 1 ? at(n - 1) : 0.0f, xpt = n >= 2 ? at(n - 2) : 0.0f, x0 = n >= 1 ? at(0) : 0.0f;
+    const int vac = (n == 0 || vacant_after(xt, n >= 2 ? __fsub_rn(xpt, xt) : M, g)) ? 1 : 0;
+    const int arr = (n >= 1 && arrives_after(x0, g, M, d.eps_arr)) ? 1 : 0;
+    d.vac[j] = vac | (arr << 1);
+}
+
 // Choice-slot records (U, G, head, link) of every choice-set entry after a link
 // and of every out-link of a node, from the per-link utility terms.
 __global__ void k_choice_info(DevSim d, const int *lo_idx, int n_lo, const int *no_idx, int n_no) {
@@ -1131,6 +1152,90 @@ extern "C" int sim_get_state(sim_handle h, sim_state_view *out) {
     }
     if (out->fifo_off)
         for (int n = 0; n < V; ++n) out->fifo_off[n] = fptr[n] - h->fifo_beg[n];
+    return SIM_OK;
+}
+
+extern "C" int sim_set_state(sim_handle h, const sim_state_view *in, int32_t t) {
+    if (!h || !in) return SIM_EINVAL;
+    if (!h->reset_done) return fail(h, SIM_ESTATE, "sim_reset first");
+    if (t < 0 || t > h->T) return fail(h, SIM_ESTATE, "step outside the horizon");
+    if (!in->veh_link || !in->veh_pos || !in->veh_rank || !in->veh_entry || !in->link_credit || !in->link_exits ||
+        !in->fifo_off)
+        return fail(h, SIM_EINVAL, "every field of the state is required");
+    CU(cudaSetDevice(h->device));
+    const int L = h->L, N = h->N, V = h->V, S = h->S;
+    std::vector<int4> lq(L);
+    std::vector<float> pos(S, 0.0f);
+    std::vector<int2> saux(S, make_int2(-1, -1));
+    std::vector<int> sentry(S, 0), vstate(N), fptr(V), cnt(L, 0);
+    std::vector<int4> lstat(L);
+    std::vector<longlong2> lpos(L);
+    std::vector<int> dz(N);
+    CU(cudaMemcpyAsync(dz.data(), h->d.dest_zone, (size_t)N * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    long long waiting = 0, queued = 0;
+    for (int n = 0; n < V; ++n) {
+        const int len = h->fifo_beg[n + 1] - h->fifo_beg[n];
+        if (in->fifo_off[n] < 0 || in->fifo_off[n] > len) return fail(h, SIM_EINVAL, "origin queue offset out of range");
+        fptr[n] = h->fifo_beg[n] + in->fifo_off[n];
+        queued += len - in->fifo_off[n];
+    }
+    for (int i = 0; i < N; ++i) {
+        const int j = in->veh_link[i];
+        if (j < kVehArrived || j >= L) return fail(h, SIM_EINVAL, "vehicle link out of range");
+        vstate[i] = j;
+        if (j == kVehWaiting) { ++waiting; continue; }
+        if (j < 0) continue;
+        const int cap = h->lst_host[4 * j + 1], k = in->veh_rank[i];
+        const double x = in->veh_pos[i];
+        if (k < 0 || k >= cap - 1) return fail(h, SIM_EINVAL, "rank out of range");
+        if (!(x >= 0.0 && x <= (double)h->length[j])) return fail(h, SIM_EINVAL, "position outside its link");
+        const int slot = h->lst_host[4 * j] + k;
+        if (saux[slot].x >= 0) return fail(h, SIM_EINVAL, "two vehicles with the same rank");
+        saux[slot] = make_int2(i, dz[i]);
+        pos[slot] = (float)x;
+        sentry[slot] = in->veh_entry[i];
+        cnt[j] += 1;
+    }
+    if (waiting != queued) return fail(h, SIM_EINVAL, "waiting vehicles do not match the origin queues");
+    for (int j = 0; j < L; ++j) {
+        const int base = h->lst_host[4 * j];
+        for (int k = 0; k < cnt[j]; ++k)
+            if (saux[base + k].x < 0) return fail(h, SIM_EINVAL, "ranks of a link are not 0..n-1");
+        if (in->link_credit[j] < 0 || in->link_credit[j] > h->lst_host[4 * j + 3])
+            return fail(h, SIM_EINVAL, "credit out of range");
+        lq[j] = make_int4(0, cnt[j], (int)in->link_credit[j], (int)in->link_exits[j]);
+        // the open bin restarts at t: C at its start, position sum at t
+        long long past = 0, psum = 0;
+        for (int k = 0; k < cnt[j]; ++k) {
+            const float x = pos[base + k];
+            past += x >= h->length[j] * 0.5f;
+            psum += llrintf(x * 65536.0f);
+        }
+        lstat[j] = make_int4(0, 0, 0, (int)(in->link_exits[j] + past));
+        lpos[j] = make_longlong2(psum, 0);
+    }
+    DevSim &d = h->d;
+    float *pc = (t & 1) ? d.pos1 : d.pos0;
+    CU(cudaMemcpyAsync(d.lq, lq.data(), L * sizeof(int4), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(pc, pos.data(), (size_t)S * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(d.saux, saux.data(), (size_t)S * sizeof(int2), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(d.sentry, sentry.data(), (size_t)S * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(d.vstate, vstate.data(), (size_t)N * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(d.fifo_ptr, fptr.data(), (size_t)V * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(d.lstat, lstat.data(), L * sizeof(int4), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(d.lpos, lpos.data(), L * sizeof(longlong2), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemsetAsync(d.W0, 0, L * sizeof(unsigned long long), h->stream));
+    CU(cudaMemsetAsync(d.W1, 0, L * sizeof(unsigned long long), h->stream));
+    const std::vector<int4> crec(L, make_int4(-1, kTgtNone, 0, 0));
+    const std::vector<int2> nrec(V, make_int2(-1, kTgtNone));
+    CU(cudaMemcpyAsync(d.crec, crec.data(), L * sizeof(int4), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(d.nrec, nrec.data(), V * sizeof(int2), cudaMemcpyHostToDevice, h->stream));
+    k_set_flags<<<(L + 255) / 256, 256, 0, h->stream>>>(d, t);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(h->stream));
+    h->t = t;
+    h->tape_ready = false;
     return SIM_OK;
 }
 

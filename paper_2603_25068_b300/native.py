@@ -75,6 +75,7 @@ SIGNATURES = {
     "sim_backward": (C.c_int, [P, P, P, C.c_int32, C.POINTER(sim_grads)]),
     "sim_get_state": (C.c_int, [P, C.POINTER(sim_state_view)]),
     "sim_get_records": (C.c_int, [P, C.POINTER(sim_records)]),
+    "sim_set_state": (C.c_int, [P, C.POINTER(sim_state_view), C.c_int32]),
     "sim_set_stage": (C.c_int, [P, C.c_int32]),
     "sim_set_stream": (C.c_int, [P, P]),
     "sim_set_executor": (C.c_int, [P, C.c_int32]),

@@ -199,6 +199,21 @@ class Simulator:
         self._check(self.lib.sim_get_state(self.h, C.byref(v)))
         return d
 
+    def set_state(self, state: dict, t: int):
+        """Continue from a given state at step t (the dict layout of state(),
+        e.g. the oracle's); the next step() runs step t."""
+        sc = self.sc
+        arrs = dict(veh_link=np.ascontiguousarray(state["veh_link"], np.int32),
+                    veh_pos=np.ascontiguousarray(state["veh_pos"], np.float64),
+                    veh_rank=np.ascontiguousarray(state["veh_rank"], np.int32),
+                    veh_entry=np.ascontiguousarray(state["veh_entry"], np.int32),
+                    link_credit=np.ascontiguousarray(state["link_credit"], np.int64),
+                    link_exits=np.ascontiguousarray(state["link_exits"], np.int64),
+                    fifo_off=np.ascontiguousarray(state["fifo_off"], np.int32))
+        v = nat.sim_state_view(*(_p(arrs[k]) for k in ("veh_link", "veh_pos", "veh_rank", "veh_entry",
+                                                        "link_credit", "link_exits", "fifo_off")))
+        self._check(self.lib.sim_set_state(self.h, C.byref(v), int(t)))
+
     def records(self):
         sc = self.sc
         d = dict(link_cand=np.zeros(sc.L, np.int32), link_target=np.zeros(sc.L, np.int32),
