@@ -1000,6 +1000,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     room((size_t)K * V, sizeof(int2)); room((size_t)K * L, sizeof(unsigned long long));
     room(N, sizeof(double)); room((size_t)N * h->route_cap, sizeof(double));
     for (int k = 0; k < 7; ++k) room(L, sizeof(double));
+    room(2 * (size_t)L, sizeof(double));                // second parity of the merge sums
     room(1, sizeof(double)); room(std::max(h->n_od, 1), sizeof(double));
     room((size_t)L + V, sizeof(double)); room((size_t)L + V, sizeof(double));
     room((size_t)nb * L, sizeof(double)); room((size_t)(nb + 1) * L, sizeof(double));
@@ -1026,8 +1027,8 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     b.eadj = (double *)take((size_t)N * h->route_cap, sizeof(double));
     b.gu = (double *)take(L, sizeof(double)); b.gs = (double *)take(L, sizeof(double));
     b.ga = (double *)take(L, sizeof(double)); b.gU = (double *)take(L, sizeof(double));
-    b.gG = (double *)take(L, sizeof(double)); b.Z = (double *)take(L, sizeof(double));
-    b.SA = (double *)take(L, sizeof(double));
+    b.gG = (double *)take(L, sizeof(double)); b.Z = (double *)take(2 * (size_t)L, sizeof(double));
+    b.SA = (double *)take(2 * (size_t)L, sizeof(double));
     b.gao = (double *)take(1, sizeof(double));
     b.glam = (double *)take(std::max(h->n_od, 1), sizeof(double));
     b.ebuf = (double *)take((size_t)L + V, sizeof(double));
@@ -1051,6 +1052,8 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     CU(cudaMemsetAsync(b.gao, 0, sizeof(double), h->stream));
     CU(cudaMemsetAsync(b.glam, 0, (size_t)std::max(b.n_od, 1) * sizeof(double), h->stream));
     CU(cudaMemsetAsync(b.eadj, 0, (size_t)N * h->route_cap * sizeof(double), h->stream));
+    CU(cudaMemsetAsync(b.Z, 0, 2 * (size_t)L * sizeof(double), h->stream));
+    CU(cudaMemsetAsync(b.SA, 0, 2 * (size_t)L * sizeof(double), h->stream));
     k_bwd_init<<<(N + 255) / 256, 256, 0, h->stream>>>(h->d, b, dxT);
     // recomputation: no route log, counters into a scratch array
     DevSim dr = h->d;
@@ -1081,11 +1084,9 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
             const int rec = t - t0;
             if ((t + 1) % obs == 0 || t + 1 == T)
                 k_bwd_obs<<<(L * 32 + 255) / 256, 256, 0, h->stream>>>(dr, b, rec + 1, t / obs);
-            CU(cudaMemsetAsync(b.Z, 0, (size_t)L * sizeof(double), h->stream));
-            CU(cudaMemsetAsync(b.SA, 0, (size_t)L * sizeof(double), h->stream));
             k_bwd_node_z<<<gLV, 256, 0, h->stream>>>(dr, b, t, rec, t / obs);
             k_bwd_node_g<<<gLV, 256, 0, h->stream>>>(dr, b, t, rec);
-            k_bwd_cf<<<(L * 32 + kBwdCfThreads - 1) / kBwdCfThreads, kBwdCfThreads, 0, h->stream>>>(dr, b, rec);
+            k_bwd_cf<<<(L * 32 + kBwdCfThreads - 1) / kBwdCfThreads, kBwdCfThreads, 0, h->stream>>>(dr, b, rec, t);
         }
         CU(cudaGetLastError());
     }

@@ -51,7 +51,8 @@ struct BwdDev {
     double *gu, *gs, *ga, *gU, *gG;   // [L]
     double *gao;                 // [1]
     double *glam;                // [n_od]
-    double *Z, *SA;              // [L] per-target merge sums
+    double *Z, *SA;              // [2 L] per-target merge sums, by step parity (the
+                                 // reverse car-following kernel clears the other parity)
     double *ebuf, *abuf;         // [L + V] per-source merge weight and abar
     const int *od;               // [N]
     const float *od_lambda;      // [n_od]
@@ -193,8 +194,9 @@ __global__ void k_bwd_node_z(DevSim d, BwdDev b, int t, int rec, int bin0) {
     const double abar = (double)d.M * (Enew - Xold) - (double)c.x * Xold;
     b.ebuf[i] = e;
     b.abuf[i] = abar;
-    atomicAdd(&b.Z[c.tgt], e);
-    atomicAdd(&b.SA[c.tgt], e * abar);
+    const size_t zo = (size_t)(t & 1) * d.L + c.tgt;
+    atomicAdd(&b.Z[zo], e);
+    atomicAdd(&b.SA[zo], e * abar);
 }
 
 // (2b) merge and link-choice Jacobians of step t
@@ -203,9 +205,10 @@ __global__ void k_bwd_node_g(DevSim d, BwdDev b, int t, int rec) {
     if (i >= d.L + d.V) return;
     const Cand c = load_cand(d, b, i, rec);
     if (c.vid < 0 || c.tgt < 0) return;
-    const double Z = b.Z[c.tgt];
+    const size_t zo = (size_t)(t & 1) * d.L + c.tgt;
+    const double Z = b.Z[zo];
     const double pi = b.ebuf[i] / Z;
-    const double S = b.SA[c.tgt] / Z;
+    const double S = b.SA[zo] / Z;
     const double vbar = pi * (b.abuf[i] - S) * (double)b.inv_tau;   // adjoint of V'_i
     if (i < d.L) atomicAdd(&b.ga[i], vbar); else atomicAdd(b.gao, vbar);
     const double lbar = (double)c.alpha * vbar;                      // adjoint of l_i at the target
@@ -290,20 +293,28 @@ __global__ void k_bwd_node_g(DevSim d, BwdDev b, int t, int rec) {
     }
 }
 
-// (3) car-following of step (t0 + rec): one warp per link, lanes over queue
-// positions k = k0 + lane (leader first).  Vehicle k's adjoint at time t is its
-// own adjoint at t + 1 unless its update was congested (then x' depended on the
-// leader only), plus its follower's adjoint when the follower was congested
-// (the follower's headway used x_k); the follower's values come from lane + 1
-// (lane 31 loads the next round's first vehicle).  Every vehicle's adjoint is
-// read before any lane writes it, and a link's vehicles belong to its warp only.
-// Per-link parameter sums: free -> u (x' = x + u dt), congested -> s.
+// (3) car-following of step (t0 + rec): one warp per link; an iteration covers
+// kCfR rounds of 32 queue positions (leader first), issuing every tape and
+// adjoint load of them (and of the vehicle after them) before using any.
+// Vehicle k's adjoint at time t is its own adjoint at t + 1 unless its update
+// was congested (then x' depended on the leader only), plus its follower's
+// adjoint when the follower was congested (the follower's headway used x_k).
+// The follower's values come from the next lane, or for lane 31 from lane 0 of
+// the next round.  Every adjoint an iteration reads is read before any lane
+// writes, and a link's vehicles belong to its warp only.  Per-link parameter
+// sums: free -> u (x' = x + u dt), congested -> s.
 constexpr int kBwdCfThreads = 256;
+constexpr int kCfR = 4;
 
-__global__ void __launch_bounds__(kBwdCfThreads) k_bwd_cf(DevSim d, BwdDev b, int rec) {
+__global__ void __launch_bounds__(kBwdCfThreads) k_bwd_cf(DevSim d, BwdDev b, int rec, int t) {
     const int lane = threadIdx.x & 31;
     const int j = (blockIdx.x * kBwdCfThreads + threadIdx.x) >> 5;
     if (j >= d.L) return;
+    if (lane == 0) {                                        // merge sums of step t - 1 start from zero
+        const size_t zo = (size_t)((t + 1) & 1) * d.L + j;
+        b.Z[zo] = 0.0;
+        b.SA[zo] = 0.0;
+    }
     const int4 q = b.tlq[(size_t)rec * d.L + j];
     const int n = q.y;
     if (n == 0) return;
@@ -316,34 +327,54 @@ __global__ void __launch_bounds__(kBwdCfThreads) k_bwd_cf(DevSim d, BwdDev b, in
         return idx;
     };
     double su = 0.0, ss = 0.0;
-    for (int k0 = 0; k0 < n; k0 += 32) {
-        const int k = k0 + lane;
-        const bool act = k < n;
-        int v = -1, tag = kTagStop;
-        double g = 0.0;
-        if (act) {
-            const int idx = slot(k);
-            v = b.tvid[tb + idx];
-            tag = b.ttag[tb + idx];
-            g = b.xbar[v];
+    for (int k0 = 0; k0 < n; k0 += 32 * kCfR) {
+        int v[kCfR], tag[kCfR];
+        double g[kCfR];
+#pragma unroll
+        for (int r = 0; r < kCfR; ++r) {
+            const int k = k0 + 32 * r + lane;
+            v[r] = -1;
+            tag[r] = kTagStop;
+            if (k < n) {
+                const int idx = slot(k);
+                v[r] = b.tvid[tb + idx];
+                tag[r] = b.ttag[tb + idx];
+            }
         }
-        // the follower (k + 1): next lane, or the next round's first vehicle
-        int ftag = __shfl_down_sync(kFull, tag, 1);
-        double fg = __shfl_down_sync(kFull, g, 1);
-        if (lane == 31 && k + 1 < n) {
-            const int idx = slot(k + 1);
-            ftag = b.ttag[tb + idx];
-            fg = b.xbar[b.tvid[tb + idx]];
+        const int kx = k0 + 32 * kCfR;                      // the vehicle after this iteration
+        int vx = -1, tx = kTagStop;
+        if (lane == 0 && kx < n) {
+            const int idx = slot(kx);
+            vx = b.tvid[tb + idx];
+            tx = b.ttag[tb + idx];
         }
-        double pre = 0.0;
-        if (act) {
-            pre = (tag == kTagCong) ? 0.0 : g;
-            if (k + 1 < n && ftag == kTagCong) pre += fg;
-            if (tag == kTagFree) su += g * dt;
-            if (tag == kTagCong) ss -= g;
+#pragma unroll
+        for (int r = 0; r < kCfR; ++r) g[r] = v[r] >= 0 ? b.xbar[v[r]] : 0.0;
+        const double gx = vx >= 0 ? b.xbar[vx] : 0.0;
+        double pre[kCfR];
+#pragma unroll
+        for (int r = 0; r < kCfR; ++r) {
+            int ftag = __shfl_down_sync(kFull, tag[r], 1);
+            double fg = __shfl_down_sync(kFull, g[r], 1);
+            const int ntag = __shfl_sync(kFull, r + 1 < kCfR ? tag[r + 1 < kCfR ? r + 1 : r] : tx, 0);
+            const double ng = __shfl_sync(kFull, r + 1 < kCfR ? g[r + 1 < kCfR ? r + 1 : r] : gx, 0);
+            if (lane == 31) {
+                ftag = ntag;
+                fg = ng;
+            }
+            const int k = k0 + 32 * r + lane;
+            pre[r] = 0.0;
+            if (k < n) {
+                pre[r] = (tag[r] == kTagCong) ? 0.0 : g[r];
+                if (k + 1 < n && ftag == kTagCong) pre[r] += fg;
+                if (tag[r] == kTagFree) su += g[r] * dt;
+                if (tag[r] == kTagCong) ss -= g[r];
+            }
         }
-        __syncwarp();                           // every lane has read before any writes
-        if (act) b.xbar[v] = pre;
+        __syncwarp();                                       // every lane has read before any writes
+#pragma unroll
+        for (int r = 0; r < kCfR; ++r)
+            if (v[r] >= 0) b.xbar[v[r]] = pre[r];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
