@@ -252,9 +252,12 @@ SIM_API int sim_set_stage(sim_handle h, int32_t slots);
  *                        counterpart: its step is a sequence of XLA ops);
  *   SIM_EXEC_AUTO        (default) persistent when available, else step.
  * The persistent executor is available when every queue of the network fits in
- * the shared memory of the GPU's SMs and the handle records no reverse-pass tape
- * (ckpt_every = 0).  Errors: SIM_EINVAL (unknown value, or persistent requested
- * where it is unavailable; the text says why). */
+ * the shared memory of the GPU's SMs.  For a handle that records the reverse-pass
+ * tape (ckpt_every > 0) it runs sim_rollout as one launch per checkpoint segment
+ * and the segment recomputation of sim_backward as one recording launch per
+ * segment; sim_step of such a handle uses the two-kernel path.  Errors:
+ * SIM_EINVAL (unknown value, or persistent requested where it is unavailable;
+ * the text says why). */
 #define SIM_EXEC_AUTO       0
 #define SIM_EXEC_STEP       1
 #define SIM_EXEC_PERSISTENT 2

@@ -273,7 +273,7 @@ static int build_blocks(sim_ctx *h) {
 // group per SM, each within kPLinks links and the shared memory left for queue
 // slots, with the largest group weight (slots + 16 per link) made as small as
 // possible (binary search over the bound, greedy packing).
-static size_t g_attr_p[64];
+static size_t g_attr_p[64], g_attr_pt[64];
 static int build_groups(sim_ctx *h) {
     h->persist_ok = false;
     int nsm = 0, optin = 0;
@@ -366,8 +366,11 @@ static int build_groups(sim_ctx *h) {
         return SIM_OK;
     }
     CU(raise_smem_attr(k_persist, g_attr_p, h->device, smem));
-    int per_sm = 0;
+    CU(raise_smem_attr(k_persist_tape, g_attr_pt, h->device, smem));
+    int per_sm = 0, per_sm_t = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist, kPT, smem));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, k_persist_tape, kPT, smem));
+    per_sm = std::min(per_sm, per_sm_t);
     if (per_sm < 1 || G > per_sm * nsm) {
         h->persist_why = "the CTAs cannot all be resident at once";
         return SIM_OK;
@@ -388,23 +391,29 @@ static int build_groups(sim_ctx *h) {
     return SIM_OK;
 }
 
-// persistent executor in use for the next forward run of this handle
-static bool use_persist(const sim_ctx *h) {
-    if (h->K > 0 || !h->persist_ok) return false;
-    return h->executor != SIM_EXEC_STEP;
-}
+// persistent executor in use for the next forward run of this handle (also the
+// checkpointed forward of handles that record the reverse-pass tape and their
+// segment recomputation)
+static bool use_persist(const sim_ctx *h) { return h->persist_ok && h->executor != SIM_EXEC_STEP; }
 
 // steps [t0, t1) (+ the observation-only pass at t1) in one cooperative launch
-static int enqueue_persist(sim_ctx *h, int t0, int t1, int final_obs) {
+// of d (tape: the recording kernel, d's tape pointers the bases of record 0)
+static int enqueue_persist_d(sim_ctx *h, const DevSim &d, int t0, int t1, int final_obs, bool tape) {
     PArgs a = h->pa;
     a.t0 = t0;
     a.t1 = t1;
     a.final_obs = final_obs;
+    a.S = h->S;
     CU(cudaMemsetAsync(a.W3, 0, (size_t)3 * h->L * sizeof(unsigned long long), h->stream));
     CU(cudaMemsetAsync(a.bar, 0, sizeof(unsigned), h->stream));
-    void *args[2] = {(void *)&h->d, (void *)&a};
-    CU(cudaLaunchCooperativeKernel((const void *)k_persist, dim3(h->G), dim3(kPT), args, h->persist_smem, h->stream));
+    DevSim dd = d;
+    void *args[2] = {(void *)&dd, (void *)&a};
+    CU(cudaLaunchCooperativeKernel(tape ? (const void *)k_persist_tape : (const void *)k_persist, dim3(h->G), dim3(kPT),
+                                   args, h->persist_smem, h->stream));
     return SIM_OK;
+}
+static int enqueue_persist(sim_ctx *h, int t0, int t1, int final_obs) {
+    return enqueue_persist_d(h, h->d, t0, t1, final_obs, false);
 }
 
 static int upload_params(sim_ctx *h, const sim_params *par) {
@@ -786,7 +795,7 @@ extern "C" int sim_step(sim_handle h, int32_t n_steps) {
     if (!h->reset_done) return fail(h, SIM_ESTATE, "sim_reset first");
     if (n_steps < 0 || h->t + n_steps > h->T) return fail(h, SIM_ESTATE, "step beyond the horizon");
     CU(cudaSetDevice(h->device));
-    if (use_persist(h) && n_steps > 0) {
+    if (use_persist(h) && h->K == 0 && n_steps > 0) {
         const int t1 = h->t + n_steps;
         TRY(enqueue_persist(h, h->t, t1, t1 == h->T));
         h->t = t1;
@@ -842,13 +851,21 @@ extern "C" int sim_rollout(sim_handle h, int32_t T, sim_outputs *out) {
     TRY(ensure_T(h, T));
     if (use_persist(h)) {
         enqueue_reset(h, T);
-        TRY(enqueue_persist(h, 0, T, 1));
+        if (h->K > 0) {              // one launch per checkpoint segment, the state saved before each
+            for (int t0 = 0; t0 < T; t0 += h->K) {
+                const int t1 = std::min(T, t0 + h->K);
+                ckpt_copy(h, t0 / h->K, t0 & 1, true);
+                TRY(enqueue_persist(h, t0, t1, t1 == T));
+            }
+        } else {
+            TRY(enqueue_persist(h, 0, T, 1));
+        }
         CU(cudaGetLastError());
         h->t = T;
         h->T = T;
         h->n_bins = sim_n_bins(T, h->opt.obs_every);
         h->reset_done = true;
-        h->tape_ready = false;
+        h->tape_ready = h->K > 0;
         TRY(copy_outputs(h, out));
         if (out && out->on_device) return SIM_OK;
         return check_device_error(h);
@@ -899,7 +916,7 @@ extern "C" int sim_profile_rollout(sim_handle h, int32_t T, sim_outputs *out, do
     CU(cudaSetDevice(h->device));
     TRY(ensure_T(h, T));
     h->tape_ready = false;
-    if (use_persist(h)) {
+    if (use_persist(h) && h->K == 0) {
         cudaEvent_t e0, e1;
         CU(cudaEventCreate(&e0));
         CU(cudaEventCreate(&e1));
@@ -1066,17 +1083,28 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         const int t0 = sg * K, t1 = std::min(T, t0 + K);
         ckpt_copy(h, sg, t0 & 1, false);
         CU(cudaMemsetAsync((t0 & 1) ? h->d.W1 : h->d.W0, 0, (size_t)L * sizeof(unsigned long long), h->stream));
-        for (int t = t0; t < t1; ++t) {            // each step writes its own tape record
-            const size_t r = (size_t)(t - t0);
-            dr.tag_tape = b.ttag + r * S;
-            dr.tape_pos = b.tpos + r * S;
-            dr.tape_vid = b.tvid + r * S;
-            dr.tape_lq = b.tlq + r * L;
-            dr.tape_crec = b.tcrec + r * L;
-            dr.tape_nrec = b.tnrec + r * V;
-            dr.tape_W = b.tW + r * L;
-            k_step_a_tape<<<dr.nblk, kBlockA, smem_a, h->stream>>>(dr, t);
-            k_step_b<<<(L + V + 255) / 256, 256, 0, h->stream>>>(dr, t);
+        if (use_persist(h)) {                      // one recording launch for the segment
+            dr.tag_tape = b.ttag;
+            dr.tape_pos = b.tpos;
+            dr.tape_vid = b.tvid;
+            dr.tape_lq = b.tlq;
+            dr.tape_crec = b.tcrec;
+            dr.tape_nrec = b.tnrec;
+            dr.tape_W = b.tW;
+            TRY(enqueue_persist_d(h, dr, t0, t1, 0, true));
+        } else {
+            for (int t = t0; t < t1; ++t) {        // each step writes its own tape record
+                const size_t r = (size_t)(t - t0);
+                dr.tag_tape = b.ttag + r * S;
+                dr.tape_pos = b.tpos + r * S;
+                dr.tape_vid = b.tvid + r * S;
+                dr.tape_lq = b.tlq + r * L;
+                dr.tape_crec = b.tcrec + r * L;
+                dr.tape_nrec = b.tnrec + r * V;
+                dr.tape_W = b.tW + r * L;
+                k_step_a_tape<<<dr.nblk, kBlockA, smem_a, h->stream>>>(dr, t);
+                k_step_b<<<(L + V + 255) / 256, 256, 0, h->stream>>>(dr, t);
+            }
         }
         dr.tape_W = nullptr;
         k_tape_pre<<<gS, 256, 0, h->stream>>>(dr, b, t1 - t0, t1 & 1);    // state at the end of the segment
@@ -1293,9 +1321,8 @@ extern "C" int sim_set_executor(sim_handle h, int32_t executor) {
     if (!h) return SIM_EINVAL;
     if (executor != SIM_EXEC_AUTO && executor != SIM_EXEC_STEP && executor != SIM_EXEC_PERSISTENT)
         return fail(h, SIM_EINVAL, "unknown executor");
-    if (executor == SIM_EXEC_PERSISTENT && (h->K > 0 || !h->persist_ok))
-        return fail(h, SIM_EINVAL, h->K > 0 ? "the persistent executor records no reverse-pass tape"
-                                           : "persistent executor unavailable: " + h->persist_why);
+    if (executor == SIM_EXEC_PERSISTENT && !h->persist_ok)
+        return fail(h, SIM_EINVAL, "persistent executor unavailable: " + h->persist_why);
     h->executor = executor;
     return SIM_OK;
 }

@@ -55,6 +55,7 @@ struct PArgs {
     unsigned *bar;                 // grid barrier counter (zero at launch)
     int t0, t1;                    // steps [t0, t1)
     int final_obs;                 // close the last bin at t1 (observation-only pass)
+    int S;                         // tape stride of the slot records (recording launches)
 };
 
 struct PSmem {
@@ -219,6 +220,7 @@ struct PCtx {
 // Transfers of step tb for this thread's link or origin queue (SI-B Eq.
 // transfer): pop the leader that won its merge or left to its destination, push
 // the merge winner at x = 0, flags of step tb + 1.  Counters accumulate.
+template <bool kTape>
 __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int tb, PPend &pd,
                                         int *cnt) {
     const int tid = threadIdx.x;
@@ -229,6 +231,9 @@ __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &
         const int4 st = S.st[li];
         const int4 cr = S.cr[li];
         const unsigned long long win = __ldcg(Wb + j);
+        if (kTape)                  // the tape keeps merge words in the standard format (~vehicle low half)
+            d.tape_W[(size_t)(tb - a.t0) * d.L + j] =
+                win ? ((win & 0xffffffff00000000ull) | (unsigned long long)(~(uint32_t)p_vid(win, a.packz))) : 0ull;
         unsigned long long wt = 0ull;
         if (cr.y >= 0) wt = __ldcg(Wb + cr.y);
         bool pop = false;
@@ -361,7 +366,8 @@ __device__ __forceinline__ void p_count(PSmem &S, const int *cnt) {
 // Step t of this thread's link or origin queue up to the choice: credit,
 // candidate.  Returns (choice pairs (merge key + choice slots) << 16) | the
 // link's car-following cost (1 + rounds of 32 vehicles).
-__device__ __forceinline__ int p_candidate(const DevSim &d, PSmem &S, const PCtx &c, int t, bool obs_only) {
+template <bool kTape>
+__device__ __forceinline__ int p_candidate(const DevSim &d, PSmem &S, const PCtx &c, int t, int r, bool obs_only) {
     const int tid = threadIdx.x;
     if (tid < c.nl) {
         const int li = tid;
@@ -370,6 +376,7 @@ __device__ __forceinline__ int p_candidate(const DevSim &d, PSmem &S, const PCtx
         const int4 q = S.q[li];
         const int cost = 1 + ((q.y + 31) >> 5);           // car-following rounds of the link (+1)
         if (obs_only) return cost;
+        if (kTape) d.tape_lq[(size_t)r * d.L + c.j0 + li] = q;
         const int4 st = S.st[li];
         const int credit = min(q.z + st.z, st.w);
         S.q[li].z = credit;
@@ -537,7 +544,9 @@ constexpr int kPCFW = kPCFT / 32;
 
 constexpr int kPLG = 1;          // links a car-following warp updates at once
 
-__device__ __forceinline__ void p_carfollow(const DevSim &d, PSmem &S, const PCtx &c, bool obs, bool obs_only) {
+template <bool kTape>
+__device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int r, bool obs,
+                                            bool obs_only) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float M = d.M;
     const int l0 = S.wl[w], l1 = S.wl[w + 1];
@@ -593,6 +602,11 @@ __device__ __forceinline__ void p_carfollow(const DevSim &d, PSmem &S, const PCt
                         const float h = k == 0 ? M : __fsub_rn(lane == 0 ? ahead[j] : up, x[j]);
                         int tag;
                         c.P[R[j] + idx[j]] = newell(x[j], h, g[j].x, g[j].y, g[j].z, g[j].w, tag);
+                        if (kTape) {                // tape: time-t position and branch tag of the slot
+                            const size_t o = (size_t)r * a.S + c.base0 + R[j] + idx[j];
+                            d.tape_pos[o] = x[j];
+                            d.tag_tape[o] = (int8_t)tag;
+                        }
                     }
                 }
                 ahead[j] = last;
@@ -603,6 +617,7 @@ __device__ __forceinline__ void p_carfollow(const DevSim &d, PSmem &S, const PCt
 
 // Observation at bin ends, choice, merge, next-step bits and records of this
 // thread's link or origin queue.
+template <bool kTape>
 __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int t, bool first,
                                          bool obs, bool obs_only, const int4 *Cp, const unsigned long long *Wp) {
     const int tid = threadIdx.x;
@@ -665,10 +680,14 @@ __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem 
         const int4 rec = make_int4(c0.x, c0.x >= 0 ? tgt : kTgtNone, (c0.z << 8) | bits, __float_as_int(x0));
         S.cr[li] = rec;
         a.crec2[(size_t)(t & 1) * d.L + j] = rec;
+        if (kTape) d.tape_crec[(size_t)(t - a.t0) * d.L + j] = rec;
     } else if (!obs_only && tid >= kPNodeTid && tid < kPNodeTid + c.nn) {
         const int ni = tid - kPNodeTid;
         const int2 r = S.nrec[ni];
-        if (r.x < 0) return;
+        if (r.x < 0) {
+            if (kTape) d.tape_nrec[(size_t)(t - a.t0) * d.V + c.n0 + ni] = r;
+            return;
+        }
         const int4 nh = S.nh[ni];
         int tgt;
         if (S.nzone[ni] == nh.y) {
@@ -679,10 +698,29 @@ __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem 
             if (tgt >= 0) atomicMax(Wt + tgt, p_word(S.nmkey[ni], nh.x, nh.y, a.packz));
         }
         S.nrec[ni] = make_int2(r.x, tgt);
+        if (kTape) d.tape_nrec[(size_t)(t - a.t0) * d.V + c.n0 + ni] = make_int2(r.x, tgt);
     }
 }
 
-__global__ void __launch_bounds__(kPT, 1) k_persist(DevSim d, PArgs a) {
+// tape: vehicle of every occupied slot at the start of step t (record r), by
+// threads [tfirst, tfirst + nt) (the choice warps, once their pairs are done)
+__device__ __forceinline__ void p_tape_vid(const DevSim &d, const PArgs &a, const PSmem &S, const PCtx &c, int r,
+                                           int tfirst, int nt) {
+    const int w = (threadIdx.x - tfirst) >> 5, nw = nt >> 5, lane = threadIdx.x & 31;
+    for (int li = w; li < c.nl; li += nw) {
+        const int2 qv = *reinterpret_cast<const int2 *>(&S.q[li]);
+        const int lb = S.lbase[li], cap = S.lbase[li + 1] - lb;
+        for (int k = lane; k < qv.y; k += 32) {
+            int idx = qv.x + k;
+            if (idx >= cap) idx -= cap;
+            const int gs = c.base0 + lb + idx;
+            d.tape_vid[(size_t)r * a.S + gs] = d.saux[gs].x;
+        }
+    }
+}
+
+template <bool kTape>
+__device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
     extern __shared__ __align__(16) unsigned char p_smem[];
     PSmem &S = *reinterpret_cast<PSmem *>(p_smem);
     const int tid = threadIdx.x;
@@ -776,8 +814,8 @@ __global__ void __launch_bounds__(kPT, 1) k_persist(DevSim d, PArgs a) {
         const bool obs = t > 0 && t % d.obs_every == 0;
         PPend pd{};
         int cnt[4] = {0, 0, 0, 0};
-        if (!first) p_apply(d, a, S, c, t - 1, pd, cnt);
-        const int v = p_candidate(d, S, c, t, false);      // reads what this thread's p_apply wrote
+        if (!first) p_apply<kTape>(d, a, S, c, t - 1, pd, cnt);
+        const int v = p_candidate<kTape>(d, S, c, t, t - a.t0, false);   // reads what this thread's p_apply wrote
         if (!first) p_count(S, cnt);
         p_scan(S, c, v, kPCFW);
         if (!first && tid < 4) {
@@ -788,12 +826,13 @@ __global__ void __launch_bounds__(kPT, 1) k_persist(DevSim d, PArgs a) {
         const unsigned long long *Wp = a.W3 + (size_t)((t + 2) % 3) * d.L;     // words of step t-1
         if (tid >= kPCFT) {
             p_pairs(d, a, S, c, t, first, Cp, Wp, kPCFT, kPT - kPCFT);
+            if (kTape) p_tape_vid(d, a, S, c, t - a.t0, kPCFT, kPT - kPCFT);
         } else {
-            p_carfollow(d, S, c, obs, false);
+            p_carfollow<kTape>(d, a, S, c, t - a.t0, obs, false);
         }
         __syncthreads();
         if (tid < 4) S.cnt[tid] = 0;
-        p_decide(d, a, S, c, t, first, obs, false, Cp, Wp);
+        p_decide<kTape>(d, a, S, c, t, first, obs, false, Cp, Wp);
         p_refill(S, c, pd);
         ++epoch;
         if (!grid_sync(d, a.bar, epoch * gridDim.x, t, &S.stop)) return;
@@ -801,7 +840,7 @@ __global__ void __launch_bounds__(kPT, 1) k_persist(DevSim d, PArgs a) {
     if (a.t1 > a.t0) {
         PPend pd{};
         int cnt[4] = {0, 0, 0, 0};
-        p_apply(d, a, S, c, a.t1 - 1, pd, cnt);
+        p_apply<kTape>(d, a, S, c, a.t1 - 1, pd, cnt);
         p_count(S, cnt);
         p_refill(S, c, pd);
         __syncthreads();
@@ -809,11 +848,11 @@ __global__ void __launch_bounds__(kPT, 1) k_persist(DevSim d, PArgs a) {
     }
     if (a.final_obs) {
         __syncthreads();
-        const int v = p_candidate(d, S, c, a.t1, true);
+        const int v = p_candidate<false>(d, S, c, a.t1, 0, true);
         p_scan(S, c, v, kPCFW);
-        if (tid < kPCFT) p_carfollow(d, S, c, true, true);
+        if (tid < kPCFT) p_carfollow<false>(d, a, S, c, 0, true, true);
         __syncthreads();
-        p_decide(d, a, S, c, a.t1, false, true, true, nullptr, nullptr);
+        p_decide<false>(d, a, S, c, a.t1, false, true, true, nullptr, nullptr);
     }
     __syncthreads();
     // ---------------- write the group's state back ----------------
@@ -842,5 +881,11 @@ __global__ void __launch_bounds__(kPT, 1) k_persist(DevSim d, PArgs a) {
         d.nrec[n] = S.nrec[ni];
     }
 }
+
+__global__ void __launch_bounds__(kPT, 1) k_persist(DevSim d, PArgs a) { persist_body<false>(d, a); }
+
+// the same run recording the reverse pass's tape (d.tape_* and d.tag_tape are
+// the bases of record 0 = step a.t0; slot records have stride a.S)
+__global__ void __launch_bounds__(kPT, 1) k_persist_tape(DevSim d, PArgs a) { persist_body<true>(d, a); }
 
 }  // namespace ts

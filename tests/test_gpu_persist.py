@@ -71,11 +71,38 @@ def test_executor_selection(Simulator):
     g.set_executor("auto")
     assert g.executor == "persistent"
     g.close()
-    g = Simulator(sc, ckpt_every=30)          # records the reverse-pass tape
+    g = Simulator(sc, ckpt_every=30)          # records the reverse-pass tape: persistent too
+    assert g.executor == "persistent"
+    g.set_executor("step")
     assert g.executor == "step"
-    with pytest.raises(SimError):
-        g.set_executor("persistent")
     g.close()
+    from paper_2603_25068_b300.native import check
+    g2 = Simulator(sc)
+    with pytest.raises(SimError):
+        check(g2.lib.sim_set_executor(g2.h, 7), g2.h)          # unknown executor
+    g2.close()
+
+
+@pytest.mark.parametrize("name", ["dense_small", "city_small"])
+def test_checkpointed_rollout_and_gradient_match_step_executor(Simulator, name):
+    # the checkpointed forward (one launch per segment) and the recording
+    # recomputation of the reverse pass, persistent vs two-kernel executor
+    sc = SCENARIOS[name]()
+    res = {}
+    for ex in ("step", "persistent"):
+        g = Simulator(sc, ckpt_every=17, route_cap=64)
+        g.set_executor(ex)
+        out = g.rollout(sc.T)
+        rng = np.random.default_rng(3)
+        yb = rng.normal(size=out["counts"].shape).astype(np.float32)
+        res[ex] = (out, g.backward(yb))
+        g.close()
+    (oa, ga), (ob, gb) = res["step"], res["persistent"]
+    for k in OUT_KEYS:
+        np.testing.assert_array_equal(oa[k], ob[k], err_msg=k)
+    for k in ga:
+        scale = np.max(np.abs(ga[k])) + 1e-30
+        assert np.max(np.abs(ga[k].astype(np.float64) - gb[k])) <= 1e-6 * scale, k
 
 
 @pytest.mark.parametrize("name", sorted(SCENARIOS))
