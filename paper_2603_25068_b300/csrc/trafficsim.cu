@@ -44,7 +44,11 @@ __global__ void k_params(DevSim d, const float *len, const float *u, const float
         a = __fadd_rn(a, __fmul_rn(wf, phi[(size_t)j * d.F + f]));
         g = __fadd_rn(g, __fmul_rn(wf, psi[(size_t)j * d.F + f]));
     }
-    const_cast<float4 *>(d.geo)[j] = make_float4(L, udt, s, dtag);
+    const float4 geo = make_float4(L, udt, s, dtag);
+    const_cast<float4 *>(d.geo)[j] = geo;
+    // the bits k_step_a computes for a link with no vehicle (n = 0)
+    const int va = vacant_after(0.0f, d.M, geo) ? 1 : 0, ar = arrives_after(0.0f, geo, d.M, d.eps_arr) ? 1 : 0;
+    const_cast<int *>(d.ebits)[j] = 1 | (1 << 1) | (va << 2) | (va << 3) | (ar << 6) | (ar << 7);
     const_cast<float4 *>(d.tinfo)[j] = make_float4(a, g, __int_as_float(head[j]), __fmul_rn(L, 0.5f));
 }
 
@@ -567,6 +571,8 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
     float4 *geo, *tinfo;
     int4 *lstd, *lnoded;
     TRY(dalloc(h, &geo, L)); d.geo = geo;
+    int *ebits_d;
+    TRY(dalloc(h, &ebits_d, L)); d.ebits = ebits_d;
     TRY(dalloc(h, &tinfo, L)); d.tinfo = tinfo;
     TRY(upload(h, &lstd, (const int4 *)lst.data(), L)); d.lst = lstd;
     TRY(upload(h, &lnoded, (const int4 *)lnode.data(), L)); d.lnode = lnoded;
@@ -1736,6 +1742,7 @@ extern "C" int sim_rollout_static(const sim_network *net, const sim_demand *dem,
     float4 *geo = B.take<float4>(L), *tinfo = B.take<float4>(L), *loinfo = B.take<float4>(n_lo),
            *noinfo = B.take<float4>(L);
     int4 *lst = B.take<int4>(L), *lnode = B.take<int4>(L);
+    int *ebits = B.take<int>(L);
     float *alpha = B.take<float>(L + 1), *dest_feat = B.take<float>((size_t)Z * V);
     int *blk = B.take<int>(nblk + 1), *no_ptr = B.take<int>(V + 1), *node_zone = B.take<int>(V);
     int *fifo_end = B.take<int>(V), *fifo_dep = B.take<int>(N), *dest_zone = B.take<int>(N);
@@ -1764,7 +1771,7 @@ extern "C" int sim_rollout_static(const sim_network *net, const sim_demand *dem,
     d.step_delta = B.take<int>((size_t)4 * T);
     d.err = B.take<int>(4);
     if (!B.ok) return SIM_EOVERFLOW;
-    d.geo = geo; d.tinfo = tinfo; d.loinfo = loinfo; d.noinfo = noinfo; d.lst = lst; d.lnode = lnode;
+    d.geo = geo; d.ebits = ebits; d.tinfo = tinfo; d.loinfo = loinfo; d.noinfo = noinfo; d.lst = lst; d.lnode = lnode;
     d.alpha = alpha; d.dest_feat = dest_feat; d.blk_links = blk; d.nblk = nblk; d.no_ptr = no_ptr;
     d.npb = (V + nblk - 1) / nblk;
     d.node_zone = node_zone; d.fifo_end = fifo_end; d.fifo_dep = fifo_dep; d.dest_zone = dest_zone;

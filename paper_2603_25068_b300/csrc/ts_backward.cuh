@@ -304,7 +304,7 @@ __global__ void k_bwd_node_g(DevSim d, BwdDev b, int t, int rec) {
 // writes, and a link's vehicles belong to its warp only.  Per-link parameter
 // sums: free -> u (x' = x + u dt), congested -> s.
 constexpr int kBwdCfThreads = 256;
-constexpr int kCfR = 4;
+constexpr int kCfR = 2;
 
 __global__ void __launch_bounds__(kBwdCfThreads) k_bwd_cf(DevSim d, BwdDev b, int rec, int t) {
     const int lane = threadIdx.x & 31;
@@ -316,9 +316,9 @@ __global__ void __launch_bounds__(kBwdCfThreads) k_bwd_cf(DevSim d, BwdDev b, in
         b.SA[zo] = 0.0;
     }
     const int4 q = b.tlq[(size_t)rec * d.L + j];
+    const int4 st = d.lst[j];                               // issued with the queue state
     const int n = q.y;
     if (n == 0) return;
-    const int4 st = d.lst[j];
     const double dt = (double)d.dt;
     const size_t tb = (size_t)rec * b.S + st.x;
     auto slot = [&](int k) {

@@ -34,6 +34,7 @@ struct DevSim {
     uint32_t key0, key1;
     // static link data
     const float4 *geo;
+    const int *ebits;              // [L] next-step vacancy/arrival bits of an empty link (from geo)
     const int4 *lst;
     const int4 *lnode;
     const float4 *tinfo;

@@ -171,11 +171,13 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
         if (kTape) d.tape_lq[j] = q;
         S.q[tid] = q;
         S.st[tid] = st;
-        S.g[tid] = d.geo[j];
-        S.nd[tid] = d.lnode[j];
-        S.stat[tid] = d.lstat[j];
-        S.ps[tid] = d.lpos[j];
-        S.alpha[tid] = d.alpha[j];
+        if (q.y > 0 || obs) {              // an empty link off a bin end needs only its credit
+            S.g[tid] = d.geo[j];
+            S.nd[tid] = d.lnode[j];
+            S.stat[tid] = d.lstat[j];
+            S.ps[tid] = d.lpos[j];
+            S.alpha[tid] = d.alpha[j];
+        }
         const int credit = min(q.z + st.z, st.w);
         S.credit[tid] = credit;
         S.cand[tid] = !obs_only && q.y > 0 && (flags & kFlagArrive) && credit >= d.dn_fx;
@@ -365,6 +367,13 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
     const int li = tid, j = j0 + tid;
     const int4 q = S.q[li];
     const int n = q.y;
+    if (n == 0 && !obs) {                  // empty link: credit, and the static bits of an empty queue
+        d.lq[j].z = S.credit[li];
+        const int4 rec = make_int4(-1, kTgtNone, d.ebits[j], 0);
+        d.crec[j] = rec;
+        if (kTape) d.tape_crec[j] = rec;
+        return;
+    }
     int4 stat = S.stat[li];
     longlong2 ps = S.ps[li];
     if (obs) {
