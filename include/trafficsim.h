@@ -266,6 +266,15 @@ SIM_API int sim_set_executor(sim_handle h, int32_t executor);
  * -1 for a NULL handle. */
 SIM_API int32_t sim_get_executor(sim_handle h);
 
+/* Test hook for the bounded waits of the persistent executor: the next
+ * persistent launch of h waits at its grid barriers for `missing` arrivals
+ * that never come, so every CTA gives up after its bounded wait (about 2 s),
+ * the call reports SIM_ETIMEOUT and the device context stays usable; the
+ * handle needs sim_reset (or sim_rollout) before it is used again.  No GPU
+ * fault is involved: the wait simply runs out.  The paper has no counterpart.
+ * Errors: SIM_EINVAL (missing < 0, or no persistent executor for h). */
+SIM_API int sim_test_barrier_timeout(sim_handle h, int32_t missing);
+
 /* Move the handle's work to another stream of its device (the old stream is
  * drained first; a stream the handle created is destroyed).  NULL: only drain.
  * Not for a handle that is a member of a live batch. */

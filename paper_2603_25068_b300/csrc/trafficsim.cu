@@ -161,6 +161,7 @@ struct sim_ctx {
     std::vector<int> lo_count;           // choice-set size after each link
     std::vector<int> no_ptr_host;        // out-links of each node (CSR offsets)
     int executor = SIM_EXEC_AUTO;        // requested
+    int bar_extra = 0;                   // test hook: missing arrivals at the next launch's barriers
     bool persist_ok = false;             // the network fits (groups, shared memory, co-residency)
     std::string persist_why;             // reason when it does not
     int G = 0;                           // CTAs (one per SM at most)
@@ -408,6 +409,8 @@ static int enqueue_persist_d(sim_ctx *h, const DevSim &d, int t0, int t1, int fi
     a.t1 = t1;
     a.final_obs = final_obs;
     a.S = h->S;
+    a.bar_extra = h->bar_extra;
+    h->bar_extra = 0;
     CU(cudaMemsetAsync(a.W3, 0, (size_t)3 * h->L * sizeof(unsigned long long), h->stream));
     CU(cudaMemsetAsync(a.bar, 0, sizeof(unsigned), h->stream));
     DevSim dd = d;
@@ -1330,6 +1333,13 @@ extern "C" int sim_set_executor(sim_handle h, int32_t executor) {
     if (executor == SIM_EXEC_PERSISTENT && !h->persist_ok)
         return fail(h, SIM_EINVAL, "persistent executor unavailable: " + h->persist_why);
     h->executor = executor;
+    return SIM_OK;
+}
+
+extern "C" int sim_test_barrier_timeout(sim_handle h, int32_t missing) {
+    if (!h || missing < 0) return SIM_EINVAL;
+    if (!h->persist_ok) return fail(h, SIM_EINVAL, "persistent executor unavailable: " + h->persist_why);
+    h->bar_extra = missing;
     return SIM_OK;
 }
 

@@ -56,6 +56,8 @@ struct PArgs {
     int t0, t1;                    // steps [t0, t1)
     int final_obs;                 // close the last bin at t1 (observation-only pass)
     int S;                         // tape stride of the slot records (recording launches)
+    int bar_extra;                 // arrivals the first barrier waits for beyond the grid (0; > 0 in
+                                   // tests of the bounded wait: they never come)
 };
 
 struct PSmem {
@@ -835,7 +837,7 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         p_decide<kTape>(d, a, S, c, t, first, obs, false, Cp, Wp);
         p_refill(S, c, pd);
         ++epoch;
-        if (!grid_sync(d, a.bar, epoch * gridDim.x, t, &S.stop)) return;
+        if (!grid_sync(d, a.bar, epoch * gridDim.x + (unsigned)a.bar_extra, t, &S.stop)) return;
     }
     if (a.t1 > a.t0) {
         PPend pd{};

@@ -80,6 +80,7 @@ SIGNATURES = {
     "sim_set_stream": (C.c_int, [P, P]),
     "sim_set_executor": (C.c_int, [P, C.c_int32]),
     "sim_get_executor": (C.c_int32, [P]),
+    "sim_test_barrier_timeout": (C.c_int, [P, C.c_int32]),
     "sim_batch_create": (C.c_int, [C.POINTER(P), C.c_int32, C.POINTER(P)]),
     "sim_batch_start": (C.c_int, [P, C.c_int32, C.c_int32]),
     "sim_batch_advance": (C.c_int, [P, C.c_int32, P]),

@@ -187,3 +187,23 @@ def test_city_full_size_executors_agree(Simulator):
     b = run(Simulator, sc, 900, "persistent")
     assert_same(a, b)
     assert a["out"]["n_on"][-1] > 100_000
+
+
+def test_bounded_barrier_wait_reports_timeout_and_recovers(Simulator):
+    # the wait runs out (arrivals that never come), no fault: SIM_ETIMEOUT,
+    # then the same handle and the device work normally after a reset
+    import time
+    from paper_2603_25068_b300.native import SimError, SIM_ETIMEOUT, check
+    sc = S.tiny_grid()
+    ref = run(Simulator, sc, sc.T, "persistent")
+    g = Simulator(sc)
+    check(g.lib.sim_test_barrier_timeout(g.h, 1), g.h)
+    t0 = time.perf_counter()
+    with pytest.raises(SimError) as e:
+        g.rollout(sc.T)
+    assert e.value.code == SIM_ETIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    out = g.rollout(sc.T)                      # reset by the rollout: a normal run again
+    for k in OUT_KEYS:
+        np.testing.assert_array_equal(out[k], ref["out"][k], err_msg=k)
+    g.close()
