@@ -413,7 +413,7 @@ __device__ __forceinline__ void p_scan(PSmem &S, const PCtx &c, int v, int nw) {
     if (lane == 31) S.wsum[w] = s;
     __syncthreads();
     if (w == 0) {
-        const int x = S.wsum[lane];
+        const int x = lane < kPT / 32 ? S.wsum[lane] : 0;  // only the block's warps wrote a total
         int r = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
