@@ -281,8 +281,8 @@ def run_fwd_bwd(args, dev, stream, flush, ws):
 def run_batched(args, dev, stream, flush, ws):
     """Batched control-candidate scenarios: n scenarios of 10k-200k vehicles on
     the city network with per-scenario capacity multipliers, 1,800 steps,
-    forward in one batched launch per phase and step, then each scenario's
-    reverse pass; against the same scenarios run one by one."""
+    forward by the autotuned batch executor, then each scenario's reverse pass;
+    against the same scenarios run one by one."""
     import torch
     from paper_2603_25068_b300 import scenario as S
     from paper_2603_25068_b300.batch import Batch
@@ -294,9 +294,12 @@ def run_batched(args, dev, stream, flush, ws):
     rng = np.random.default_rng(0)
     ybars = []
     vs = float(sum(sc.N for sc in scs)) * T
-    # batched: one warm-up batch rollout, then a timed batch forward + reverse passes
+    # batched: executor autotuned on a short rollout, one warm-up batch rollout,
+    # then a timed batch forward + reverse passes
+    from paper_2603_25068_b300 import autotune
     res = {}
     with Batch(sims) as b:
+        best, tune_ms = autotune.tune_batch(b, T=min(T, 120))
         b.rollout(T)
         for sc, sm in zip(scs, sims):
             ybars.append(rng.normal(size=(sm.n_bins(T), sc.L)).astype(np.float32))
@@ -310,6 +313,21 @@ def run_batched(args, dev, stream, flush, ws):
             sm.backward(yb)
         torch.cuda.synchronize(dev)
         t2 = time.perf_counter()
+        other = {}
+        for e in autotune.BATCH_EXECUTORS:        # forward of the executor not chosen
+            if e == best:
+                continue
+            try:
+                b.set_executor(e)
+            except Exception:
+                continue
+            b.rollout(T)
+            flush.fill_(3.0)
+            torch.cuda.synchronize(dev)
+            t3 = time.perf_counter()
+            b.rollout(T)
+            torch.cuda.synchronize(dev)
+            other[e] = time.perf_counter() - t3
     res["batched_forward_s"] = t1 - t0
     res["batched_forward_plus_reverse_s"] = t2 - t0
     # serial single-scenario path
@@ -338,6 +356,9 @@ def run_batched(args, dev, stream, flush, ws):
             "batched_forward_plus_reverse": vs / res["batched_forward_plus_reverse_s"],
             "serial_forward_plus_reverse": vs / res["serial_forward_plus_reverse_s"],
             "seconds": res,
+            "executor": best,
+            "autotune_ms_per_rollout": {k: round(v, 2) for k, v in tune_ms.items()},
+            "other_executor_forward_s": other,
             "timing": "host wall clock, device synchronised; reverse passes run one scenario after another"}
 
 

@@ -304,10 +304,37 @@ SIM_API int sim_batch_start(sim_batch b, int32_t k, int32_t T);
 
 /* Advance every running member by n_steps steps (a member reaching its horizon
  * closes its last bin in the following step and then stays idle).  finished:
- * optional [n] flags, 1 for members done with their horizon.  Runs of 8 or more
- * steps are replayed from a CUDA graph captured once per length.  Returns after
- * the stream has drained. */
+ * optional [n] flags, 1 for members done with their horizon.  With the
+ * persistent batch executor the n_steps steps are one cooperative launch;
+ * with the step executor, runs of 8 or more steps are replayed from a CUDA
+ * graph captured once per length.  Returns after the stream has drained.
+ * Errors: a member's device error (its code), SIM_ETIMEOUT when a grid barrier
+ * of the persistent launch gave up (the members' states are then undefined). */
 SIM_API int sim_batch_advance(sim_batch b, int32_t n_steps, int32_t *finished);
+
+/* Executor of the batch (SIM_EXEC_* above):
+ *   SIM_EXEC_STEP        per step a checkpoint kernel, the link-block kernel, the
+ *                        transfer kernel and a counter kernel over all members
+ *                        (graph-captured);
+ *   SIM_EXEC_PERSISTENT  one cooperative launch per advance, one CTA of 1,024
+ *                        threads per SM; a warp takes 32 links (or 32 origin
+ *                        nodes, or 32 transfer elements) of one member through
+ *                        the node model, with a bounded grid barrier after the
+ *                        node model and after the transfers of every step;
+ *   SIM_EXEC_AUTO        (default) persistent when available, else step.
+ * Both give every member bitwise the same outputs and state as its solo run.
+ * Errors: SIM_EINVAL (unknown value; persistent requested but unavailable --
+ * more than 1,024 members, or no cooperative launch on the device). */
+SIM_API int sim_batch_set_executor(sim_batch b, int32_t executor);
+SIM_API int32_t sim_batch_get_executor(sim_batch b);
+
+/* Test hook of the persistent batch executor: every grid barrier of the next
+ * sim_batch_advance waits for `missing` arrivals that never come, so its
+ * bounded wait runs out (about 2 s); the advance reports SIM_ETIMEOUT.  The
+ * running members' states are then undefined until sim_batch_start restarts
+ * them.  No GPU fault is involved.  Errors: SIM_EINVAL (missing < 0, or no
+ * persistent batch executor). */
+SIM_API int sim_batch_test_barrier_timeout(sim_batch b, int32_t missing);
 
 /* Start every member with horizon T and run all of them to the end. */
 SIM_API int sim_batch_rollout(sim_batch b, int32_t T);

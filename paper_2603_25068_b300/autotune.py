@@ -1,7 +1,9 @@
-"""Launch-shape autotuner: times short rollouts for each candidate shape of the
-node-model kernel (queue slots staged in shared memory per link block) on the
-simulator's own stream and keeps the fastest.  Results never depend on the
-shape, only the time does."""
+"""Launch-shape autotuner: times short rollouts for each candidate shape and
+keeps the fastest.  For one simulator: the queue slots staged in shared memory
+per link block of the node-model kernel.  For a batch: the executor (one
+cooperative launch per advance with warp-per-32-links items, or one launch per
+phase and step with link blocks).  Results never depend on the shape, only the
+time does."""
 from __future__ import annotations
 
 from . import native as nat
@@ -30,4 +32,31 @@ def tune_stage(sim, T: int = 600, reps: int = 2, stages=STAGES):
         times[g] = ev[0].elapsed_time(ev[1]) / reps
     best = min(times, key=times.get)
     set_stage(sim, best)
+    return best, times
+
+
+BATCH_EXECUTORS = ("persistent", "step")
+
+
+def tune_batch(batch, T: int = 120, reps: int = 1, executors=BATCH_EXECUTORS):
+    """Times a batch rollout of T steps with each executor and keeps the
+    fastest.  Returns (best executor, {executor: ms per rollout})."""
+    import time
+
+    import torch
+    times = {}
+    for e in executors:
+        try:
+            batch.set_executor(e)
+        except nat.SimError:                      # unavailable on this device
+            continue
+        batch.rollout(T)                          # warm (and graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            batch.rollout(T)
+        torch.cuda.synchronize()
+        times[e] = (time.perf_counter() - t0) * 1e3 / reps
+    best = min(times, key=times.get)
+    batch.set_executor(best)
     return best, times

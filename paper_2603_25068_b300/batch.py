@@ -1,5 +1,6 @@
-"""Batched simulation: many Simulator handles advanced by one launch per phase
-and step (sim_batch_* of the C ABI).  Members keep their own scenario, state,
+"""Batched simulation: many Simulator handles advanced together (sim_batch_* of
+the C ABI), by one cooperative launch per advance (persistent executor) or one
+launch per phase and step (step executor).  Members keep their own scenario, state,
 step counter and horizon, so they can join at any step boundary (continuous
 batching) and each member's result equals its solo result."""
 from __future__ import annotations
@@ -22,6 +23,16 @@ class Batch:
         if rc != nat.SIM_OK:
             raise nat.SimError(rc, self.lib.sim_batch_last_error(None).decode())
         self.h = h
+
+    EXECUTORS = {"auto": 0, "step": 1, "persistent": 2}
+
+    def set_executor(self, name: str):
+        """"persistent", "step" or "auto"; results do not depend on it."""
+        self._check(self.lib.sim_batch_set_executor(self.h, self.EXECUTORS[name]))
+
+    @property
+    def executor(self) -> str:
+        return {1: "step", 2: "persistent"}[self.lib.sim_batch_get_executor(self.h)]
 
     def _check(self, rc):
         if rc != nat.SIM_OK:

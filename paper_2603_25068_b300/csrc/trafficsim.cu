@@ -9,6 +9,7 @@
 #include "../../include/trafficsim.h"
 #include "ts_backward.cuh"
 #include "ts_persist.cuh"
+#include "ts_batch.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -1382,6 +1383,19 @@ struct sim_batch_ctx {
     std::map<int, cudaGraphExec_t> graphs;
     std::vector<void *> allocs;
     std::string err;
+    // persistent batch executor (one cooperative launch per advance)
+    int executor = SIM_EXEC_AUTO;
+    bool bp_ok = false;
+    std::string bp_why;
+    int bp_grid = 0;
+    size_t bp_smem = 0;
+    int2 *d_itA = nullptr, *d_itB = nullptr;
+    int nIA = 0, nIB = 0;
+    unsigned *d_bar = nullptr;
+    int *d_berr = nullptr;
+    unsigned char *d_ckstep = nullptr;
+    int ckstep_cap = 0;
+    int bar_extra = 0;                   // test hook: missing arrivals at the next launch's barriers
 };
 
 static int bfail(sim_batch_ctx *b, int code, const std::string &msg) {
@@ -1425,7 +1439,98 @@ static void batch_release(sim_batch_ctx *b) {
     b->graphs.clear();
     for (void *p : b->allocs) cudaFree(p);
     b->allocs.clear();
+    if (b->d_ckstep) cudaFree(b->d_ckstep);
+    b->d_ckstep = nullptr;
+    b->ckstep_cap = 0;
     for (size_t k = 0; k < b->m.size() && k < b->saved_streams.size(); ++k) b->m[k]->stream = b->saved_streams[k];
+}
+
+static size_t g_attr_bp[64];
+
+// Work items of the persistent batch executor: 32 links, 32 origin nodes or 32
+// transfer elements of one member each.  The executor is left off (with the
+// reason) when the device cannot run the cooperative launch.
+static int batch_persist_setup(sim_batch_ctx *b) {
+    const int n = (int)b->m.size();
+    std::vector<int2> iA, iB;
+    for (int k = 0; k < n; ++k) {
+        const sim_ctx *h = b->m[k];
+        for (int j0 = 0; j0 < h->L; j0 += 32) iA.push_back(make_int2(k, j0));
+        for (int n0 = 0; n0 < h->V; n0 += 32) iA.push_back(make_int2(k, n0 | kItemNode));
+        for (int i0 = 0; i0 < h->L + h->V; i0 += 32) iB.push_back(make_int2(k, i0));
+    }
+    b->nIA = (int)iA.size();
+    b->nIB = (int)iB.size();
+    int rc;
+    if ((rc = balloc(b, &b->d_itA, iA.size())) || (rc = balloc(b, &b->d_itB, iB.size())) ||
+        (rc = balloc(b, &b->d_bar, 1)) || (rc = balloc(b, &b->d_berr, 1)))
+        return rc;
+    BCU(cudaMemcpyAsync(b->d_itA, iA.data(), iA.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->d_itB, iB.data(), iB.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaStreamSynchronize(b->stream));
+    b->bp_ok = false;
+    if (n > kBMaxMembers) { b->bp_why = "more members than one launch holds"; return SIM_OK; }
+    int coop = 0, nsm = 0, occ = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->device);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
+    if (!coop) { b->bp_why = "no cooperative launch on this device"; return SIM_OK; }
+    b->bp_smem = b_dyn_bytes(n);
+    if (raise_smem_attr(k_batch_persist, g_attr_bp, b->device, b->bp_smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_persist, kBT, b->bp_smem) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        b->bp_why = "the persistent batch kernel does not fit on an SM";
+        return SIM_OK;
+    }
+    b->bp_grid = nsm;
+    b->bp_ok = true;
+    return SIM_OK;
+}
+
+static bool batch_use_persist(const sim_batch_ctx *b) { return b->bp_ok && b->executor != SIM_EXEC_STEP; }
+
+// One cooperative launch advancing every running member by up to n_steps steps.
+static int batch_launch_persist(sim_batch_ctx *b, int n_steps) {
+    const int n = (int)b->m.size();
+    std::vector<unsigned char> ck((size_t)n_steps, 0);
+    if (b->any_tape) {
+        for (int k = 0; k < n; ++k) {
+            const sim_ctx *h = b->m[k];
+            if (h->K <= 0 || b->hmode[k] != kModeRun) continue;
+            for (int s = 0; s < n_steps && h->t + s < b->hT[k]; ++s)
+                if ((h->t + s) % h->K == 0) ck[s] = 1;
+        }
+    }
+    if (b->ckstep_cap < n_steps) {
+        if (b->d_ckstep) cudaFree(b->d_ckstep);
+        b->d_ckstep = nullptr;
+        b->ckstep_cap = 0;
+        BCU(cudaMalloc(&b->d_ckstep, (size_t)n_steps));
+        b->ckstep_cap = n_steps;
+    }
+    BCU(cudaMemcpyAsync(b->d_ckstep, ck.data(), (size_t)n_steps, cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned), b->stream));
+    BCU(cudaMemsetAsync(b->d_berr, 0, sizeof(int), b->stream));
+    BArgs a{};
+    a.ds = b->d_ds;
+    a.ck = b->d_ck;
+    a.itA = b->d_itA;
+    a.itB = b->d_itB;
+    a.ckstep = b->d_ckstep;
+    a.nA = b->nIA;
+    a.nB = b->nIB;
+    a.tvec = b->d_t;
+    a.Tvec = b->d_T;
+    a.mode = b->d_mode;
+    a.n = n;
+    a.n_steps = n_steps;
+    a.bar = b->d_bar;
+    a.berr = b->d_berr;
+    a.bar_extra = b->bar_extra;
+    b->bar_extra = 0;
+    void *args[1] = {&a};
+    BCU(cudaLaunchCooperativeKernel((const void *)k_batch_persist, dim3(b->bp_grid), dim3(kBT), args, b->bp_smem,
+                                    b->stream));
+    return SIM_OK;
 }
 
 extern "C" int sim_batch_create(const sim_handle *members, int32_t n, sim_batch *out) {
@@ -1482,6 +1587,7 @@ extern "C" int sim_batch_create(const sim_handle *members, int32_t n, sim_batch 
     if (raise_smem_attr(k_batch_a, g_attr_ba, b->device, b->smem) != cudaSuccess ||
         cudaStreamSynchronize(b->stream) != cudaSuccess)
         return fin(bfail(b, SIM_ECUDA, "batch set-up"));
+    if ((rc = batch_persist_setup(b))) return fin(rc);
     *out = b;
     return SIM_OK;
 }
@@ -1526,7 +1632,11 @@ extern "C" int sim_batch_advance(sim_batch b, int32_t n_steps, int32_t *finished
     if (!b || n_steps < 0) return SIM_EINVAL;
     BCU(cudaSetDevice(b->device));
     const int n = (int)b->m.size();
-    if (n_steps > 0) {
+    if (n_steps > 0 && batch_use_persist(b)) {
+        const int rc = batch_launch_persist(b, n_steps);
+        if (rc) return rc;
+        BCU(cudaGetLastError());
+    } else if (n_steps > 0) {
         auto it = b->graphs.find(n_steps);
         if (it == b->graphs.end() && n_steps >= 8) {
             cudaGraph_t g;
@@ -1561,12 +1671,39 @@ extern "C" int sim_batch_advance(sim_batch b, int32_t n_steps, int32_t *finished
         h->bmode = mode[k];
         if (finished) finished[k] = mode[k] == kModeDone;
     }
+    if (n_steps > 0 && batch_use_persist(b)) {
+        int berr = 0;
+        BCU(cudaMemcpy(&berr, b->d_berr, sizeof(int), cudaMemcpyDeviceToHost));
+        if (berr) return bfail(b, SIM_ETIMEOUT, "persistent batch: a grid barrier timed out");
+    }
     for (int k = 0; k < n; ++k) {
         if (b->hT[k] == 0) continue;                 // never started in this batch
         const int rc = check_device_error(b->m[k]);
         if (rc) return bfail(b, rc, b->m[k]->err);
     }
     return SIM_OK;
+}
+
+extern "C" int sim_batch_set_executor(sim_batch b, int32_t executor) {
+    if (!b) return SIM_EINVAL;
+    if (executor != SIM_EXEC_AUTO && executor != SIM_EXEC_STEP && executor != SIM_EXEC_PERSISTENT)
+        return bfail(b, SIM_EINVAL, "unknown executor");
+    if (executor == SIM_EXEC_PERSISTENT && !b->bp_ok)
+        return bfail(b, SIM_EINVAL, "persistent batch executor unavailable: " + b->bp_why);
+    b->executor = executor;
+    return SIM_OK;
+}
+
+extern "C" int sim_batch_test_barrier_timeout(sim_batch b, int32_t missing) {
+    if (!b || missing < 0) return SIM_EINVAL;
+    if (!b->bp_ok) return bfail(b, SIM_EINVAL, "persistent batch executor unavailable: " + b->bp_why);
+    b->bar_extra = missing;
+    return SIM_OK;
+}
+
+extern "C" int32_t sim_batch_get_executor(sim_batch b) {
+    if (!b) return -1;
+    return batch_use_persist(b) ? SIM_EXEC_PERSISTENT : SIM_EXEC_STEP;
 }
 
 extern "C" int sim_batch_rollout(sim_batch b, int32_t T) {

@@ -115,8 +115,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ bool grid_sync(const DevSim &d, unsigned *bar, unsigned target, int t, int *stop) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
-        atomicAdd(bar, 1u);
+        // release arrival: covers this CTA's writes ordered before it by the
+        // block barrier; the acquire load that sees the target covers the rest
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(bar) : "memory");
         const unsigned long long t_start = global_ns();
         int ok = 1;
         for (unsigned it = 0;; ++it) {
@@ -130,7 +131,6 @@ __device__ __forceinline__ bool grid_sync(const DevSim &d, unsigned *bar, unsign
                 }
             }
         }
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         *stop = !ok;
     }
     __syncthreads();

@@ -334,12 +334,14 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
                 const unsigned seg = __match_any_sync(kFull, act ? li : -1);
                 const unsigned past = act && x >= __fmul_rn(S.g[li].x, 0.5f) ? 1u : 0u;
                 const unsigned sp = __reduce_add_sync(seg, past);
+                // exact 64-bit segment sum from two 32-bit reductions of
+                // 24-bit pieces (no carry is lost for positions below 2^31 m)
                 const long long xf = act ? pos_fx(x) : 0;
-                const unsigned slo = __reduce_add_sync(seg, (unsigned)(xf & 0xffffffffll));
-                const unsigned shi = __reduce_add_sync(seg, (unsigned)(xf >> 32));
+                const unsigned slo = __reduce_add_sync(seg, (unsigned)(xf & 0xffffffll));
+                const unsigned shi = __reduce_add_sync(seg, (unsigned)(xf >> 24));
                 if (act && lane == __ffs(seg) - 1) {
                     if (sp) atomicAdd(&S.past[li], (int)sp);
-                    atomicAdd(&S.psum[li], (unsigned long long)slo + ((unsigned long long)shi << 32));
+                    atomicAdd(&S.psum[li], (unsigned long long)slo + ((unsigned long long)shi << 24));
                 }
             }
         }
@@ -452,8 +454,9 @@ __device__ __forceinline__ void block_count(int v, int *dst, int *smem) {
     __syncthreads();
 }
 
-// Transfers of step t for link / origin node i (every thread of the block calls).
-__device__ __forceinline__ void step_b(const DevSim &d, int i, int t) {
+// Transfers of step t for link / origin node i; adds this element's origin
+// releases, arrivals, candidates and entries to c[0..3].
+__device__ __forceinline__ void step_b_core(const DevSim &d, int i, int t, int c4[4]) {
     const int p = t & 1;
     const unsigned long long *W = p ? d.W1 : d.W0;
     int released = 0, arrived = 0, entered = 0, cands = 0;
@@ -531,11 +534,21 @@ __device__ __forceinline__ void step_b(const DevSim &d, int i, int t) {
             if (w != 0ull && merge_vid(w) == c.x) { d.fifo_ptr[n] += 1; released = 1; }
         }
     }
+    c4[0] += released;
+    c4[1] += arrived;
+    c4[2] += cands;
+    c4[3] += entered;
+}
+
+// Transfers of step t for link / origin node i (every thread of the block calls).
+__device__ __forceinline__ void step_b(const DevSim &d, int i, int t) {
+    int c4[4] = {0, 0, 0, 0};
+    step_b_core(d, i, t, c4);
     __shared__ int smem[8];
-    block_count(released, &d.step_delta[4 * t + 0], smem);
-    block_count(arrived, &d.step_delta[4 * t + 1], smem);
-    block_count(cands, &d.step_delta[4 * t + 2], smem);
-    block_count(entered, &d.step_delta[4 * t + 3], smem);
+    block_count(c4[0], &d.step_delta[4 * t + 0], smem);
+    block_count(c4[1], &d.step_delta[4 * t + 1], smem);
+    block_count(c4[2], &d.step_delta[4 * t + 2], smem);
+    block_count(c4[3], &d.step_delta[4 * t + 3], smem);
 }
 
 
@@ -601,29 +614,32 @@ struct CkDev {
     longlong2 *lpos;
 };
 
+// checkpoint t / K of one member, by threads i0, i0 + stride, ...
+__device__ __forceinline__ void ckpt_member(const DevSim &d, const CkDev &c, int t, size_t i0, size_t stride) {
+    const size_t s = t / c.K;
+    const float *pc = (t & 1) ? d.pos1 : d.pos0;
+    for (size_t i = i0; i < (size_t)c.S; i += stride) {
+        c.pos[s * c.S + i] = pc[i];
+        c.saux[s * c.S + i] = d.saux[i];
+        c.sentry[s * c.S + i] = d.sentry[i];
+    }
+    for (size_t i = i0; i < (size_t)c.L; i += stride) {
+        c.lq[s * c.L + i] = d.lq[i];
+        c.lstat[s * c.L + i] = d.lstat[i];
+        c.vac[s * c.L + i] = d.vac[i];
+        c.lpos[s * c.L + i] = d.lpos[i];
+    }
+    for (size_t i = i0; i < (size_t)c.V; i += stride) c.fifo[s * c.V + i] = d.fifo_ptr[i];
+    for (size_t i = i0; i < (size_t)c.N; i += stride) c.vstate[s * c.N + i] = d.vstate[i];
+}
+
 __global__ void k_batch_ckpt(const DevSim *ds, const CkDev *cks, const int *tvec, const int *mode) {
     const int m = blockIdx.y;
     const CkDev c = cks[m];
     if (c.K <= 0 || mode[m] != kModeRun) return;
     const int t = tvec[m];
     if (t % c.K != 0) return;
-    const DevSim &d = ds[m];
-    const size_t s = t / c.K;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    const float *pc = (t & 1) ? d.pos1 : d.pos0;
-    for (size_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)c.S; i += stride) {
-        c.pos[s * c.S + i] = pc[i];
-        c.saux[s * c.S + i] = d.saux[i];
-        c.sentry[s * c.S + i] = d.sentry[i];
-    }
-    for (size_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)c.L; i += stride) {
-        c.lq[s * c.L + i] = d.lq[i];
-        c.lstat[s * c.L + i] = d.lstat[i];
-        c.vac[s * c.L + i] = d.vac[i];
-        c.lpos[s * c.L + i] = d.lpos[i];
-    }
-    for (size_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)c.V; i += stride) c.fifo[s * c.V + i] = d.fifo_ptr[i];
-    for (size_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)c.N; i += stride) c.vstate[s * c.N + i] = d.vstate[i];
+    ckpt_member(ds[m], c, t, blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
 }
 
 }  // namespace ts

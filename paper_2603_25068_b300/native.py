@@ -86,6 +86,9 @@ SIGNATURES = {
     "sim_batch_advance": (C.c_int, [P, C.c_int32, P]),
     "sim_batch_rollout": (C.c_int, [P, C.c_int32]),
     "sim_batch_destroy": (C.c_int, [P]),
+    "sim_batch_set_executor": (C.c_int, [P, C.c_int32]),
+    "sim_batch_get_executor": (C.c_int32, [P]),
+    "sim_batch_test_barrier_timeout": (C.c_int, [P, C.c_int32]),
     "sim_batch_last_error": (C.c_char_p, [P]),
     "sim_rollout_static": (C.c_int, [C.POINTER(sim_network), C.POINTER(sim_demand), C.POINTER(sim_params),
                                      C.POINTER(sim_options), C.c_int32, C.POINTER(sim_outputs)]),
