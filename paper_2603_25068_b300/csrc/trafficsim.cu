@@ -115,6 +115,9 @@ struct sim_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // reverse pass: the merge/choice Jacobian kernel runs on a second stream
+    cudaStream_t jstream = nullptr;
+    cudaEvent_t ev_z = nullptr, ev_g = nullptr;
     DevSim d{};
     // sizes
     int V = 0, L = 0, N = 0, F = 0, Z = 0, n_od = 0, S = 0;
@@ -676,6 +679,12 @@ static void release(sim_ctx *h) {
     h->allocs.clear();
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     h->stream = nullptr;
+    if (h->jstream) cudaStreamSynchronize(h->jstream);
+    if (h->ev_z) cudaEventDestroy(h->ev_z);
+    if (h->ev_g) cudaEventDestroy(h->ev_g);
+    if (h->jstream) cudaStreamDestroy(h->jstream);
+    h->jstream = nullptr;
+    h->ev_z = h->ev_g = nullptr;
 }
 
 extern "C" int sim_create(const sim_network *net, const sim_demand *dem, const sim_params *par,
@@ -1019,52 +1028,51 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     if (h->device < 0 || h->device >= 64) return fail(h, SIM_EINVAL, "device index");
     BwdPool &pool = g_bwd_pool[h->device];
     std::lock_guard<std::mutex> lock(pool.mu);
-    // carve the shared workspace
-    size_t need = 0;
-    auto room = [&](size_t n, size_t sz) { need += (std::max<size_t>(n, 1) * sz + 255) & ~(size_t)255; };
-    room((size_t)(K + 1) * S, sizeof(float)); room((size_t)(K + 1) * S, sizeof(int));
-    room((size_t)(K + 1) * L, sizeof(int4)); room((size_t)K * S, 1); room((size_t)K * L, sizeof(int4));
-    room((size_t)K * V, sizeof(int2)); room((size_t)K * L, sizeof(unsigned long long));
-    room(N, sizeof(double)); room((size_t)N * h->route_cap, sizeof(double));
-    for (int k = 0; k < 7; ++k) room(L, sizeof(double));
-    room(2 * (size_t)L, sizeof(double));                // second parity of the merge sums
-    room(1, sizeof(double)); room(std::max(h->n_od, 1), sizeof(double));
-    room((size_t)L + V, sizeof(double)); room((size_t)L + V, sizeof(double));
-    room((size_t)nb * L, sizeof(double)); room((size_t)(nb + 1) * L, sizeof(double));
-    room(N, sizeof(float)); room((size_t)5 * L + std::max(F, 1) + 1 + std::max(h->n_od, 1), sizeof(float));
+    // carve the shared workspace: one layout routine sizes it (from base 0)
+    // and then hands out the sub-arrays (from the buffer)
     const int n_gw = (L + kGwLinks - 1) / kGwLinks;
-    room((size_t)n_gw * std::max(F, 1), sizeof(double));
+    BwdDev b = h->b;
+    double *d_Cbar = nullptr, *d_Csuf = nullptr, *d_gw_part = nullptr;
+    float *d_dxT_w = nullptr, *d_gout = nullptr;
+    auto carve = [&](uintptr_t base) -> size_t {
+        uintptr_t wp = base;
+        auto take = [&](size_t n, size_t sz) {
+            void *p = (void *)wp;
+            wp += (std::max<size_t>(n, 1) * sz + 255) & ~(size_t)255;
+            return p;
+        };
+        b.tpos = (float *)take((size_t)(K + 1) * S, sizeof(float));
+        b.tvid = (int *)take((size_t)(K + 1) * S, sizeof(int));
+        b.tlq = (int4 *)take((size_t)(K + 1) * L, sizeof(int4));
+        b.ttag = (int8_t *)take((size_t)K * S, 1);
+        b.tcrec = (int4 *)take((size_t)K * L, sizeof(int4));
+        b.tnrec = (int2 *)take((size_t)K * V, sizeof(int2));
+        b.tW = (unsigned long long *)take((size_t)K * L, sizeof(unsigned long long));
+        b.xbar = (double *)take(N, sizeof(double));
+        b.eadj = (double *)take((size_t)N * h->route_cap, sizeof(double));
+        b.gu = (double *)take(L, sizeof(double)); b.gs = (double *)take(L, sizeof(double));
+        b.ga = (double *)take(L, sizeof(double)); b.gU = (double *)take(L, sizeof(double));
+        b.gG = (double *)take(L, sizeof(double)); b.Z = (double *)take(2 * (size_t)L, sizeof(double));
+        b.SA = (double *)take(2 * (size_t)L, sizeof(double));
+        b.gao = (double *)take(1, sizeof(double));
+        b.glam = (double *)take(std::max(h->n_od, 1), sizeof(double));
+        b.ebuf = (double *)take(2 * ((size_t)L + V), sizeof(double));
+        b.abuf = (double *)take(2 * ((size_t)L + V), sizeof(double));
+        d_Cbar = (double *)take((size_t)nb * L, sizeof(double));
+        d_Csuf = (double *)take((size_t)(nb + 1) * L, sizeof(double));
+        d_dxT_w = (float *)take(N, sizeof(float));
+        d_gout = (float *)take((size_t)5 * L + std::max(F, 1) + 1 + std::max(h->n_od, 1), sizeof(float));
+        d_gw_part = (double *)take((size_t)n_gw * std::max(F, 1), sizeof(double));
+        return (size_t)(wp - base);
+    };
+    const size_t need = carve(0);
     if (need > pool.cap) {
         if (pool.buf) { cudaDeviceSynchronize(); cudaFree(pool.buf); pool.buf = nullptr; pool.cap = 0; }
         cudaError_t e = cudaMalloc(&pool.buf, need);
         if (e != cudaSuccess) { pool.buf = nullptr; return fail(h, SIM_ENOMEM, "reverse-pass workspace: " + std::string(cudaGetErrorString(e))); }
         pool.cap = need;
     }
-    unsigned char *wp = (unsigned char *)pool.buf;
-    auto take = [&](size_t n, size_t sz) { void *p = wp; wp += (std::max<size_t>(n, 1) * sz + 255) & ~(size_t)255; return p; };
-    BwdDev b = h->b;
-    b.tpos = (float *)take((size_t)(K + 1) * S, sizeof(float));
-    b.tvid = (int *)take((size_t)(K + 1) * S, sizeof(int));
-    b.tlq = (int4 *)take((size_t)(K + 1) * L, sizeof(int4));
-    b.ttag = (int8_t *)take((size_t)K * S, 1);
-    b.tcrec = (int4 *)take((size_t)K * L, sizeof(int4));
-    b.tnrec = (int2 *)take((size_t)K * V, sizeof(int2));
-    b.tW = (unsigned long long *)take((size_t)K * L, sizeof(unsigned long long));
-    b.xbar = (double *)take(N, sizeof(double));
-    b.eadj = (double *)take((size_t)N * h->route_cap, sizeof(double));
-    b.gu = (double *)take(L, sizeof(double)); b.gs = (double *)take(L, sizeof(double));
-    b.ga = (double *)take(L, sizeof(double)); b.gU = (double *)take(L, sizeof(double));
-    b.gG = (double *)take(L, sizeof(double)); b.Z = (double *)take(2 * (size_t)L, sizeof(double));
-    b.SA = (double *)take(2 * (size_t)L, sizeof(double));
-    b.gao = (double *)take(1, sizeof(double));
-    b.glam = (double *)take(std::max(h->n_od, 1), sizeof(double));
-    b.ebuf = (double *)take((size_t)L + V, sizeof(double));
-    b.abuf = (double *)take((size_t)L + V, sizeof(double));
-    double *d_Cbar = (double *)take((size_t)nb * L, sizeof(double));
-    double *d_Csuf = (double *)take((size_t)(nb + 1) * L, sizeof(double));
-    float *d_dxT_w = (float *)take(N, sizeof(float));
-    float *d_gout = (float *)take((size_t)5 * L + std::max(F, 1) + 1 + std::max(h->n_od, 1), sizeof(float));
-    double *d_gw_part = (double *)take((size_t)n_gw * std::max(F, 1), sizeof(double));
+    carve((uintptr_t)pool.buf);
     CU(cudaMemcpyAsync(d_Cbar, cb.data(), cb.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CU(cudaMemcpyAsync(d_Csuf, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     b.Cbar = d_Cbar;
@@ -1089,6 +1097,12 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     const size_t smem_a = (size_t)h->stage_max * sizeof(float);
 
     const int gS = (std::max(S, L) + 255) / 256, gLV = (L + V + 255) / 256;
+    if (!h->jstream) {
+        CU(cudaStreamCreateWithFlags(&h->jstream, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&h->ev_z, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&h->ev_g, cudaEventDisableTiming));
+    }
+    CU(cudaEventRecord(h->ev_g, h->stream));              // nothing to wait for at the first step
     for (int sg = nseg - 1; sg >= 0; --sg) {
         const int t0 = sg * K, t1 = std::min(T, t0 + K);
         ckpt_copy(h, sg, t0 & 1, false);
@@ -1118,14 +1132,24 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         }
         dr.tape_W = nullptr;
         k_tape_pre<<<gS, 256, 0, h->stream>>>(dr, b, t1 - t0, t1 & 1);    // state at the end of the segment
+        // Per step: merge kernel, then car-following on the main stream; the
+        // Jacobian kernel of step t on the second stream after the merge kernel
+        // of step t, beside car-following of t and the merge kernel of t - 1.
+        // Car-following of t clears the merge sums that the Jacobian kernel of
+        // t + 1 reads, so it waits for that kernel (ev_g, recorded a step earlier).
         for (int t = t1 - 1; t >= t0; --t) {
             const int rec = t - t0;
             if ((t + 1) % obs == 0 || t + 1 == T)
                 k_bwd_obs<<<(L * 32 + 255) / 256, 256, 0, h->stream>>>(dr, b, rec + 1, t / obs);
             k_bwd_node_z<<<gLV, 256, 0, h->stream>>>(dr, b, t, rec, t / obs);
-            k_bwd_node_g<<<gLV, 256, 0, h->stream>>>(dr, b, t, rec);
+            CU(cudaEventRecord(h->ev_z, h->stream));
+            CU(cudaStreamWaitEvent(h->stream, h->ev_g, 0));
             k_bwd_cf<<<(L * 32 + kBwdCfThreads - 1) / kBwdCfThreads, kBwdCfThreads, 0, h->stream>>>(dr, b, rec, t);
+            CU(cudaStreamWaitEvent(h->jstream, h->ev_z, 0));
+            k_bwd_node_g<<<gLV, 256, 0, h->jstream>>>(dr, b, t, rec);
+            CU(cudaEventRecord(h->ev_g, h->jstream));
         }
+        CU(cudaStreamWaitEvent(h->stream, h->ev_g, 0));     // the tape is rewritten next
         CU(cudaGetLastError());
     }
     // parameter gradients

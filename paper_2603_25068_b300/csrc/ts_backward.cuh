@@ -53,7 +53,9 @@ struct BwdDev {
     double *glam;                // [n_od]
     double *Z, *SA;              // [2 L] per-target merge sums, by step parity (the
                                  // reverse car-following kernel clears the other parity)
-    double *ebuf, *abuf;         // [L + V] per-source merge weight and abar
+    double *ebuf, *abuf;         // [2 (L + V)] per-source merge weight and abar, by step
+                                 // parity (the Jacobian kernel of step t runs beside
+                                 // the merge kernel of step t - 1)
     const int *od;               // [N]
     const float *od_lambda;      // [n_od]
 };
@@ -67,14 +69,18 @@ __device__ __forceinline__ float merge_key_of(unsigned long long w) {
 // First index k in [k0, n) of vehicle v's route log whose entry (step, link)
 // satisfies pred, or -1.  Entries are read eight at a time with independent
 // 16-byte loads (rows are 64-byte aligned: the capacity is a multiple of 8).
+// A row holds cap entries, so each batch is loaded before the entry count is
+// known (the first batch's loads overlap that of the count); entries past the
+// count are ignored.
 template <class Pred>
 __device__ __forceinline__ int route_find(const BwdDev &b, int v, int k0, Pred pred) {
     const int n = b.route_len[v];
     const int4 *r = reinterpret_cast<const int4 *>(b.route_log + (size_t)v * b.cap);
-    for (int base = k0 & ~7; base < n; base += 8) {
+    for (int base = k0 & ~7; base < b.cap; base += 8) {
         int4 w[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) w[q] = base + 2 * q < n ? r[(base >> 1) + q] : make_int4(-1, -1, -1, -1);
+        for (int q = 0; q < 4; ++q) w[q] = r[(base >> 1) + q];
+        if (base >= n) break;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int ka = base + 2 * q, kb = ka + 1;
@@ -192,8 +198,9 @@ __global__ void k_bwd_node_z(DevSim d, BwdDev b, int t, int rec, int bin0) {
         Xold = b.xbar[v];
     }
     const double abar = (double)d.M * (Enew - Xold) - (double)c.x * Xold;
-    b.ebuf[i] = e;
-    b.abuf[i] = abar;
+    const size_t eo = (size_t)(t & 1) * (d.L + d.V) + i;
+    b.ebuf[eo] = e;
+    b.abuf[eo] = abar;
     const size_t zo = (size_t)(t & 1) * d.L + c.tgt;
     atomicAdd(&b.Z[zo], e);
     atomicAdd(&b.SA[zo], e * abar);
@@ -207,9 +214,10 @@ __global__ void k_bwd_node_g(DevSim d, BwdDev b, int t, int rec) {
     if (c.vid < 0 || c.tgt < 0) return;
     const size_t zo = (size_t)(t & 1) * d.L + c.tgt;
     const double Z = b.Z[zo];
-    const double pi = b.ebuf[i] / Z;
+    const size_t eo = (size_t)(t & 1) * (d.L + d.V) + i;
+    const double pi = b.ebuf[eo] / Z;
     const double S = b.SA[zo] / Z;
-    const double vbar = pi * (b.abuf[i] - S) * (double)b.inv_tau;   // adjoint of V'_i
+    const double vbar = pi * (b.abuf[eo] - S) * (double)b.inv_tau;   // adjoint of V'_i
     if (i < d.L) atomicAdd(&b.ga[i], vbar); else atomicAdd(b.gao, vbar);
     const double lbar = (double)c.alpha * vbar;                      // adjoint of l_i at the target
     if (lbar == 0.0) return;

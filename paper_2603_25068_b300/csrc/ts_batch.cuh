@@ -95,8 +95,49 @@ __device__ __forceinline__ bool bsync(const BArgs &a, unsigned target, int *stop
     return *stop == 0;
 }
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" :: "r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Element e of the concatenated queues of a link item: the lane of its link
+// (the last lane whose offset is <= e), its queue position and slot.
+struct BElem {
+    int li, k, lqy, slot;
+    float gx, gy, gz, gw;
+    bool act;
+};
+__device__ __forceinline__ BElem b_elem(int e, int total, int excl, int4 q, int4 st, float4 g) {
+    BElem r;
+    r.act = e < total;
+    int li = 0;
+#pragma unroll
+    for (int stp = 16; stp >= 1; stp >>= 1)
+        if (__shfl_sync(kFull, excl, li + stp) <= e) li += stp;
+    r.li = li;
+    r.k = e - __shfl_sync(kFull, excl, li);
+    const int lqx = __shfl_sync(kFull, q.x, li);
+    r.lqy = __shfl_sync(kFull, q.y, li);
+    const int lbase = __shfl_sync(kFull, st.x, li);
+    const int lcap = __shfl_sync(kFull, st.y, li);
+    r.gx = __shfl_sync(kFull, g.x, li);
+    r.gy = __shfl_sync(kFull, g.y, li);
+    r.gz = __shfl_sync(kFull, g.z, li);
+    r.gw = __shfl_sync(kFull, g.w, li);
+    int idx = lqx + r.k;
+    if (idx >= lcap) idx -= lcap;
+    r.slot = lbase + idx;
+    return r;
+}
+
 // Phase A, links [j0, j0 + 32) of member d; lane = link.  obs_only: the pass
-// that closes the last bin (observation outputs only).
+// that closes the last bin (observation outputs only).  A warp issues in
+// order and waits at the first use of a loaded value, so the loads go in three
+// rounds, each issued whole before anything waits on it: link data; leader,
+// choice slots, statistics (copied asynchronously into shared memory) and the
+// first 32 positions; destination features and the targets' flags, while the
+// Gumbel noise is drawn.
 __device__ __forceinline__ void bwarp_links(const DevSim &d, int j0, int t, bool obs_only, BWarpSmem &S) {
     const int lane = threadIdx.x & 31;
     const int nl = min(32, d.L - j0);
@@ -107,52 +148,23 @@ __device__ __forceinline__ void bwarp_links(const DevSim &d, int j0, int t, bool
     float *pn = p ? d.pos0 : d.pos1;
     const bool obs = obs_only || (t > 0 && t % d.obs_every == 0);
     __syncwarp();
-    // queue state, link data, credit, candidate
-    int4 q = make_int4(0, 0, 0, 0), st = make_int4(0, 0, 0, 0);
-    int flags = 0;
+    // round 1: queue state and link data
+    int4 q = make_int4(0, 0, 0, 0), st = make_int4(0, 0, 0, 0), nd = make_int4(0, 0, 0, 0);
+    float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    int flags = 0, eb = 0;
+    float alpha = 0.0f;
     if (valid) {
         q = d.lq[j];
         st = d.lst[j];
         flags = d.vac[j];
-    }
-    float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    int4 nd = make_int4(0, 0, 0, 0);
-    float alpha = 0.0f;
-    if (valid && (q.y > 0 || obs)) {     // an empty link off a bin end needs only its credit
         g = d.geo[j];
         nd = d.lnode[j];
         alpha = d.alpha[j];
-        S.stat[lane] = d.lstat[j];
-        S.ps[lane] = d.lpos[j];
+        eb = d.ebits[j];
     }
     const int credit = min(q.z + st.z, st.w);
     const bool cand = valid && !obs_only && q.y > 0 && (flags & kFlagArrive) && credit >= d.dn_fx;
     const int deg = nd.w - nd.z;
-    int2 lead = make_int2(-1, -1);
-    int ent = 0;
-    S.past[lane] = 0;
-    S.psum[lane] = 0ull;
-    float mkey = 0.0f;
-    if (cand) {                          // leader, its choice slots, utility + Gumbel keys
-        lead = d.saux[st.x + q.x];
-        ent = d.sentry[st.x + q.x];
-#pragma unroll
-        for (int k = 0; k < kMaxSlotsStaged; ++k)
-            if (k < deg) S.lo[lane][k] = d.loinfo[nd.z + k];
-        mkey = __fadd_rn(alpha, gumbel(d.key0, d.key1, lead.x, t, 1, 0));
-        if (nd.y != lead.y) {
-#pragma unroll
-            for (int k = 0; k < kMaxSlotsStaged; ++k) {
-                if (k < deg) {
-                    const float4 e = S.lo[lane][k];
-                    S.key[lane][k] = choice_key(d, e, lead.y, lead.x, t, k);
-                    S.vacm[lane][k] = d.vac[__float_as_int(e.w)] & kFlagVacant;
-                }
-            }
-        }
-    }
-    // car-following over the item's vehicles: element e of the concatenated
-    // queues -> lane of its link by a search over the lanes' offsets
     const int n = valid ? q.y : 0;
     int incl = n;
 #pragma unroll
@@ -162,53 +174,86 @@ __device__ __forceinline__ void bwarp_links(const DevSim &d, int j0, int t, bool
     }
     const int excl = incl - n;
     const int total = __shfl_sync(kFull, incl, 31);
+    // round 2: leader and choice slots of a candidate, bin statistics, the
+    // positions of the first 32 vehicles of the item
+    int2 lead = make_int2(-1, -1);
+    int ent = 0;
+    if (cand) {
+        lead = d.saux[st.x + q.x];
+        ent = d.sentry[st.x + q.x];
+#pragma unroll
+        for (int k = 0; k < kMaxSlotsStaged; ++k)
+            if (k < deg) cp_async16(&S.lo[lane][k], d.loinfo + nd.z + k);
+    }
+    if (valid && (n > 0 || obs)) {
+        cp_async16(&S.stat[lane], d.lstat + j);
+        cp_async16(&S.ps[lane], d.lpos + j);
+    }
+    BElem E = b_elem(lane, total, excl, q, st, g);
+    float x = E.act ? pc[E.slot] : 0.0f;
+    S.past[lane] = 0;
+    S.psum[lane] = 0ull;
+    cp_async_wait_all();
+    // round 3: utility + Gumbel keys of the candidate's slots
+    float mkey = 0.0f;
+    if (cand) {
+        const bool choose_here = nd.y != lead.y;
+        float df[kMaxSlotsStaged];
+        int vm[kMaxSlotsStaged];
+#pragma unroll
+        for (int k = 0; k < kMaxSlotsStaged; ++k) {
+            df[k] = 0.0f;
+            vm[k] = 0;
+            if (choose_here && k < deg) {
+                const float4 e = S.lo[lane][k];
+                df[k] = d.dest_feat[(size_t)lead.y * d.V + __float_as_int(e.z)];
+                vm[k] = d.vac[__float_as_int(e.w)];
+            }
+        }
+        mkey = __fadd_rn(alpha, gumbel(d.key0, d.key1, lead.x, t, 1, 0));
+        if (choose_here) {               // slots 0..3 are the four words of one Philox block
+            const uint4 o = gumbel_block(d.key0, d.key1, lead.x, t, 0, 0);
+#pragma unroll
+            for (int k = 0; k < kMaxSlotsStaged; ++k) {
+                if (k < deg) {
+                    const float gk = gumbel_of_word(k == 0 ? o.x : k == 1 ? o.y : k == 2 ? o.z : o.w);
+                    const float4 e = S.lo[lane][k];
+                    S.key[lane][k] = __fadd_rn(__fadd_rn(e.x, __fmul_rn(e.y, df[k])), gk);
+                    S.vacm[lane][k] = vm[k] & kFlagVacant;
+                }
+            }
+        }
+    }
+    // car-following over the item's vehicles (chunks of 32 of the concatenated
+    // queues; the vehicle ahead by shuffle, across chunks by carry)
     float carry = 0.0f;
     for (int base = 0; base < total; base += 32) {
-        const int e = base + lane;
-        const bool act = e < total;
-        int li = 0;
-#pragma unroll
-        for (int stp = 16; stp >= 1; stp >>= 1) {       // last lane whose offset is <= e
-            const int c = li + stp;
-            if (__shfl_sync(kFull, excl, c) <= e) li = c;
+        if (base > 0) {
+            E = b_elem(base + lane, total, excl, q, st, g);
+            x = E.act ? pc[E.slot] : 0.0f;
         }
-        const int k = e - __shfl_sync(kFull, excl, li);
-        const int lqx = __shfl_sync(kFull, q.x, li);
-        const int lqy = __shfl_sync(kFull, q.y, li);
-        const int lbase = __shfl_sync(kFull, st.x, li);
-        const int lcap = __shfl_sync(kFull, st.y, li);
-        const float gx = __shfl_sync(kFull, g.x, li);
-        const float gy = __shfl_sync(kFull, g.y, li);
-        const float gz = __shfl_sync(kFull, g.z, li);
-        const float gw = __shfl_sync(kFull, g.w, li);
-        float x = 0.0f;
-        int idx = 0;
-        if (act) {
-            idx = lqx + k;
-            if (idx >= lcap) idx -= lcap;
-            x = pc[lbase + idx];
-        }
-        float xp = __shfl_up_sync(kFull, x, 1);       // the vehicle ahead (same link when k > 0)
+        const int li = E.li, k = E.k;
+        float xp = __shfl_up_sync(kFull, x, 1);
         if (lane == 0) xp = carry;
         carry = __shfl_sync(kFull, x, 31);
-        if (act && !obs_only) {
+        if (E.act && !obs_only) {
             const float h = (k == 0) ? d.M : __fsub_rn(xp, x);
             int tag;
-            const float xn = newell(x, h, gx, gy, gz, gw, tag);
-            pn[lbase + idx] = xn;
+            const float xn = newell(x, h, E.gx, E.gy, E.gz, E.gw, tag);
+            pn[E.slot] = xn;
             if (k == 0) S.x4[li].x = xn;
             if (k == 1) S.x4[li].y = xn;
-            if (k == lqy - 2) S.x4[li].z = xn;
-            if (k == lqy - 1) S.x4[li].w = xn;
+            if (k == E.lqy - 2) S.x4[li].z = xn;
+            if (k == E.lqy - 1) S.x4[li].w = xn;
         }
         if (obs) {                       // warp-uniform: midpoint count and position sum per link
-            const unsigned seg = __match_any_sync(kFull, act ? li : -1);
-            const unsigned past = act && x >= __fmul_rn(gx, 0.5f) ? 1u : 0u;
+            const unsigned seg = __match_any_sync(kFull, E.act ? li : -1);
+            const unsigned past = E.act && x >= __fmul_rn(E.gx, 0.5f) ? 1u : 0u;
             const unsigned sp = __reduce_add_sync(seg, past);
-            const long long xf = act ? pos_fx(x) : 0;
+            const long long xf = E.act ? pos_fx(x) : 0;
             const unsigned slo = __reduce_add_sync(seg, (unsigned)(xf & 0xffffffll));
             const unsigned shi = __reduce_add_sync(seg, (unsigned)(xf >> 24));
-            if (act && lane == __ffs(seg) - 1) {
+            if (E.act && lane == __ffs(seg) - 1) {
                 S.past[li] += (int)sp;
                 S.psum[li] += (unsigned long long)slo + ((unsigned long long)shi << 24);
             }
@@ -219,7 +264,7 @@ __device__ __forceinline__ void bwarp_links(const DevSim &d, int j0, int t, bool
     if (!valid) return;
     if (n == 0 && !obs) {                // empty link: credit, and the static bits of an empty queue
         d.lq[j].z = credit;
-        d.crec[j] = make_int4(-1, kTgtNone, d.ebits[j], 0);
+        d.crec[j] = make_int4(-1, kTgtNone, eb, 0);
         return;
     }
     int4 stat = S.stat[lane];

@@ -57,12 +57,17 @@ __device__ __forceinline__ float log32(float x) {
 
 // Gumbel(0,1) for (vehicle, step, stream, slot): word slot&3 of the Philox block
 // slot>>2, mapped to U = ((w >> 9) + 1/2) 2^-23 (exact), g = -log(-log U).
-__device__ __forceinline__ float gumbel(uint32_t k0, uint32_t k1, int vid, int t, int stream, int slot) {
-    const uint4 o = philox4x32_10(make_uint4((uint32_t)vid, (uint32_t)t, (uint32_t)stream, (uint32_t)(slot >> 2)), k0, k1);
-    const int s = slot & 3;
-    const uint32_t w = s == 0 ? o.x : s == 1 ? o.y : s == 2 ? o.z : o.w;
+__device__ __forceinline__ float gumbel_of_word(uint32_t w) {
     const float u = __fmul_rn(__fadd_rn((float)(w >> 9), 0.5f), 0x1p-23f);
     return -log32(-log32(u));
+}
+__device__ __forceinline__ uint4 gumbel_block(uint32_t k0, uint32_t k1, int vid, int t, int stream, int blk) {
+    return philox4x32_10(make_uint4((uint32_t)vid, (uint32_t)t, (uint32_t)stream, (uint32_t)blk), k0, k1);
+}
+__device__ __forceinline__ float gumbel(uint32_t k0, uint32_t k1, int vid, int t, int stream, int slot) {
+    const uint4 o = gumbel_block(k0, k1, vid, t, stream, slot >> 2);
+    const int s = slot & 3;
+    return gumbel_of_word(s == 0 ? o.x : s == 1 ? o.y : s == 2 ? o.z : o.w);
 }
 
 // 64-bit merge word: order-preserving image of the float key in the high half,

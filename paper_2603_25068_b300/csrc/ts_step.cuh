@@ -468,6 +468,24 @@ __device__ __forceinline__ void step_b_core(const DevSim &d, int i, int t, int c
         const int4 c = d.crec[j];
         const unsigned long long win = W[j];
         if (d.tape_W) d.tape_W[j] = win;
+        // second round, issued before any of it is used: the target's merge
+        // word, the bin statistics a pop updates, the pushed vehicle's zone
+        const bool push = win != 0ull;
+        const int v = push ? merge_vid(win) : 0;
+        unsigned long long wt = 0ull;
+        int4 stat = make_int4(0, 0, 0, 0);
+        longlong2 ps = make_longlong2(0, 0);
+        int vz = 0;
+        if (c.y >= 0) wt = W[c.y];
+        if (c.x >= 0) {
+            stat = d.lstat[j];
+            ps = d.lpos[j];
+        }
+        int rl = 0;
+        if (push) {
+            vz = d.dest_zone[v];
+            if (d.route_log) rl = d.route_len[v];
+        }
         bool pop = false;
         cands = c.x >= 0;
         if (c.y == kTgtSink) {
@@ -475,12 +493,9 @@ __device__ __forceinline__ void step_b_core(const DevSim &d, int i, int t, int c
             d.vstate[c.x] = kVehArrived;
             arrived = 1;
         } else if (c.y >= 0) {
-            const unsigned long long w = W[c.y];
-            pop = (w != 0ull) && merge_vid(w) == c.x;
+            pop = (wt != 0ull) && merge_vid(wt) == c.x;
         }
         if (pop) {
-            int4 stat = d.lstat[j];
-            longlong2 ps = d.lpos[j];
             stat.y += t + 1 - (c.z >> 8);
             stat.z += 1;
             ps.y += pos_fx(__int_as_float(c.w));
@@ -491,22 +506,20 @@ __device__ __forceinline__ void step_b_core(const DevSim &d, int i, int t, int c
             q.z -= d.dn_fx;
             q.w += 1;
         }
-        const bool push = win != 0ull;
         if (push) {
-            const int v = merge_vid(win);
             if (q.y >= st.y) {
                 set_error(d, SIM_EOVERFLOW, j, t);
             } else {
                 int idx = q.x + q.y;
                 if (idx >= st.y) idx -= st.y;
                 pn[st.x + idx] = 0.0f;
-                d.saux[st.x + idx] = make_int2(v, d.dest_zone[v]);
+                d.saux[st.x + idx] = make_int2(v, vz);
                 d.sentry[st.x + idx] = t + 1;
                 q.y += 1;
                 d.vstate[v] = j;
                 entered = 1;
                 if (d.route_log) {                 // route log for the reverse pass
-                    const int r = d.route_len[v];
+                    const int r = rl;
                     if (r < d.route_cap) {
                         d.route_log[(size_t)v * d.route_cap + r] = make_int2(t, j);
                         d.route_len[v] = r + 1;
