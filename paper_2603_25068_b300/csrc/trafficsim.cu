@@ -1032,7 +1032,8 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     // and then hands out the sub-arrays (from the buffer)
     const int n_gw = (L + kGwLinks - 1) / kGwLinks;
     BwdDev b = h->b;
-    double *d_Cbar = nullptr, *d_Csuf = nullptr, *d_gw_part = nullptr;
+    float2 *d_Cbar = nullptr, *d_Csuf = nullptr;
+    double *d_gw_part = nullptr;
     float *d_dxT_w = nullptr, *d_gout = nullptr;
     auto carve = [&](uintptr_t base) -> size_t {
         uintptr_t wp = base;
@@ -1048,18 +1049,18 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         b.tcrec = (int4 *)take((size_t)K * L, sizeof(int4));
         b.tnrec = (int2 *)take((size_t)K * V, sizeof(int2));
         b.tW = (unsigned long long *)take((size_t)K * L, sizeof(unsigned long long));
-        b.xbar = (double *)take(N, sizeof(double));
-        b.eadj = (double *)take((size_t)N * h->route_cap, sizeof(double));
+        b.xbar = (float2 *)take(N, sizeof(float2));
+        b.eadj = (float2 *)take((size_t)N * h->route_cap, sizeof(float2));
         b.gu = (double *)take(L, sizeof(double)); b.gs = (double *)take(L, sizeof(double));
         b.ga = (double *)take(L, sizeof(double)); b.gU = (double *)take(L, sizeof(double));
         b.gG = (double *)take(L, sizeof(double)); b.Z = (double *)take(2 * (size_t)L, sizeof(double));
         b.SA = (double *)take(2 * (size_t)L, sizeof(double));
         b.gao = (double *)take(1, sizeof(double));
         b.glam = (double *)take(std::max(h->n_od, 1), sizeof(double));
-        b.ebuf = (double *)take(2 * ((size_t)L + V), sizeof(double));
-        b.abuf = (double *)take(2 * ((size_t)L + V), sizeof(double));
-        d_Cbar = (double *)take((size_t)nb * L, sizeof(double));
-        d_Csuf = (double *)take((size_t)(nb + 1) * L, sizeof(double));
+        b.ebuf = (float *)take(2 * ((size_t)L + V), sizeof(float));
+        b.abuf = (float2 *)take(2 * ((size_t)L + V), sizeof(float2));
+        d_Cbar = (float2 *)take((size_t)nb * L, sizeof(float2));
+        d_Csuf = (float2 *)take((size_t)(nb + 1) * L, sizeof(float2));
         d_dxT_w = (float *)take(N, sizeof(float));
         d_gout = (float *)take((size_t)5 * L + std::max(F, 1) + 1 + std::max(h->n_od, 1), sizeof(float));
         d_gw_part = (double *)take((size_t)n_gw * std::max(F, 1), sizeof(double));
@@ -1073,8 +1074,13 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         pool.cap = need;
     }
     carve((uintptr_t)pool.buf);
-    CU(cudaMemcpyAsync(d_Cbar, cb.data(), cb.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    CU(cudaMemcpyAsync(d_Csuf, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    // bin adjoints as double-float pairs (hi = nearest float, lo = nearest float of the rest)
+    std::vector<float2> cb2(cb.size()), cs2(cs.size());
+    auto split = [](double v) { const float hi = (float)v; return make_float2(hi, (float)(v - (double)hi)); };
+    for (size_t k = 0; k < cb.size(); ++k) cb2[k] = split(cb[k]);
+    for (size_t k = 0; k < cs.size(); ++k) cs2[k] = split(cs[k]);
+    CU(cudaMemcpyAsync(d_Cbar, cb2.data(), cb2.size() * sizeof(float2), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(d_Csuf, cs2.data(), cs2.size() * sizeof(float2), cudaMemcpyHostToDevice, h->stream));
     b.Cbar = d_Cbar;
     b.Csuf = d_Csuf;
     const float *dxT = nullptr;
@@ -1086,7 +1092,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     for (double *p : {b.gu, b.gs, b.ga, b.gU, b.gG}) CU(cudaMemsetAsync(p, 0, (size_t)L * sizeof(double), h->stream));
     CU(cudaMemsetAsync(b.gao, 0, sizeof(double), h->stream));
     CU(cudaMemsetAsync(b.glam, 0, (size_t)std::max(b.n_od, 1) * sizeof(double), h->stream));
-    CU(cudaMemsetAsync(b.eadj, 0, (size_t)N * h->route_cap * sizeof(double), h->stream));
+    CU(cudaMemsetAsync(b.eadj, 0, (size_t)N * h->route_cap * sizeof(float2), h->stream));
     CU(cudaMemsetAsync(b.Z, 0, 2 * (size_t)L * sizeof(double), h->stream));
     CU(cudaMemsetAsync(b.SA, 0, 2 * (size_t)L * sizeof(double), h->stream));
     k_bwd_init<<<(N + 255) / 256, 256, 0, h->stream>>>(h->d, b, dxT);
@@ -1144,7 +1150,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
             k_bwd_node_z<<<gLV, 256, 0, h->stream>>>(dr, b, t, rec, t / obs);
             CU(cudaEventRecord(h->ev_z, h->stream));
             CU(cudaStreamWaitEvent(h->stream, h->ev_g, 0));
-            k_bwd_cf<<<(L * 32 + kBwdCfThreads - 1) / kBwdCfThreads, kBwdCfThreads, 0, h->stream>>>(dr, b, rec, t);
+            k_bwd_cf<<<(L + kCfLinks - 1) / kCfLinks, kCfThreads, 0, h->stream>>>(dr, b, rec, t);
             CU(cudaStreamWaitEvent(h->jstream, h->ev_z, 0));
             k_bwd_node_g<<<gLV, 256, 0, h->jstream>>>(dr, b, t, rec);
             CU(cudaEventRecord(h->ev_g, h->jstream));

@@ -24,11 +24,53 @@
 //                 congested x' = x_leader - dn/kappa, stopped x' = x; the TG clip
 //                 passes the adjoint; the winner's old entry receives its new
 //                 entry's adjoint unchanged (grafting, SI-C).
-// Accumulators are double precision.
+// Precision.  FP64 arithmetic runs at a small fraction of the FP32 rate on this
+// part, so the kernels do none on the per-vehicle path.  Adjoints whose
+// differences cancel (xbar, eadj, abar, the merge sums SA / Z and the bin
+// adjoints Cbar) are double-float pairs, hi + lo with |lo| <= ulp(hi) / 2
+// (about 48 significant bits), computed with FP32 operations through the
+// error-free transformations TwoSum (Knuth), FastTwoSum (Dekker) and the
+// FMA-based TwoProduct.  Exponentials, softmax weights and per-link sums are
+// FP32.  The parameter accumulators are double, updated by atomics that
+// execute in L2; only those updates convert to double.
 #pragma once
 #include "ts_step.cuh"
 
 namespace ts {
+
+// ---- double-float arithmetic (value = x + y of a float2) ----
+__device__ __forceinline__ float2 ff_fast_two_sum(float a, float b) {      // |a| >= |b| or a == 0
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    float2 s = ff_two_sum(a.x, b.x);
+    const float2 t = ff_two_sum(a.y, b.y);
+    s = ff_fast_two_sum(s.x, __fadd_rn(s.y, t.x));
+    return ff_fast_two_sum(s.x, __fadd_rn(s.y, t.y));
+}
+__device__ __forceinline__ float2 ff_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 ff_sub(float2 a, float2 b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ float2 ff_mul_f(float2 a, float b) {
+    const float p = __fmul_rn(a.x, b);
+    const float e = __fmaf_rn(a.y, b, __fmaf_rn(a.x, b, -p));
+    return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ float2 ff_div(float2 a, float2 b) {
+    const float q1 = __fdiv_rn(a.x, b.x);
+    const float2 r = ff_sub(a, ff_mul_f(b, q1));
+    return ff_fast_two_sum(q1, __fdiv_rn(r.x, b.x));
+}
+__device__ __forceinline__ double ff_to_double(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ float2 ff_from_double(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
 
 struct BwdDev {
     int S, K, cap, n_od;
@@ -41,21 +83,21 @@ struct BwdDev {
     int4 *tcrec;                 // [K L]     link candidates
     int2 *tnrec;                 // [K V]     origin-queue candidates
     unsigned long long *tW;      // [K L]     merge words
-    // adjoints
-    double *xbar;                // [N]
-    double *eadj;                // [N cap]
+    // adjoints (float2 = double-float)
+    float2 *xbar;                // [N]
+    float2 *eadj;                // [N cap]
     const int2 *route_log;       // [N cap]
     const int *route_len;        // [N]
-    const double *Cbar;          // [n_bins L] adjoint of C_j at the end of each bin
-    const double *Csuf;          // [(n_bins + 1) L] suffix sums of Cbar
+    const float2 *Cbar;          // [n_bins L] adjoint of C_j at the end of each bin
+    const float2 *Csuf;          // [(n_bins + 1) L] suffix sums of Cbar
     double *gu, *gs, *ga, *gU, *gG;   // [L]
     double *gao;                 // [1]
     double *glam;                // [n_od]
     double *Z, *SA;              // [2 L] per-target merge sums, by step parity (the
                                  // reverse car-following kernel clears the other parity)
-    double *ebuf, *abuf;         // [2 (L + V)] per-source merge weight and abar, by step
-                                 // parity (the Jacobian kernel of step t runs beside
-                                 // the merge kernel of step t - 1)
+    float *ebuf;                 // [2 (L + V)] per-source merge weight, by step parity
+    float2 *abuf;                // [2 (L + V)] per-source abar (the Jacobian kernel of
+                                 // step t runs beside the merge kernel of step t - 1)
     const int *od;               // [N]
     const float *od_lambda;      // [n_od]
 };
@@ -92,9 +134,9 @@ __device__ __forceinline__ int route_find(const BwdDev &b, int v, int k0, Pred p
 }
 
 // adjoint right after vehicle v's first entry into link m at a step > t (0 if none)
-__device__ __forceinline__ double next_entry(const BwdDev &b, int v, int m, int t) {
+__device__ __forceinline__ float2 next_entry(const BwdDev &b, int v, int m, int t) {
     const int k = route_find(b, v, 0, [&](int s, int l) { return s > t && l == m; });
-    return k >= 0 ? b.eadj[(size_t)v * b.cap + k] : 0.0;
+    return k >= 0 ? b.eadj[(size_t)v * b.cap + k] : make_float2(0.0f, 0.0f);
 }
 
 __device__ __forceinline__ int entry_at(const BwdDev &b, int v, int t) {
@@ -116,30 +158,34 @@ __global__ void k_tape_pre(DevSim d, BwdDev b, int rec, int cur) {
 __global__ void k_bwd_init(DevSim d, BwdDev b, const float *dxT) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.N) return;
-    b.xbar[i] = (dxT && d.vstate[i] >= 0) ? (double)dxT[i] : 0.0;
+    b.xbar[i] = make_float2((dxT && d.vstate[i] >= 0) ? dxT[i] : 0.0f, 0.0f);
 }
 
-// (1) observation at time t + 1 = the state of tape record rec: one warp per link
+// (1) observation at time t + 1 = the state of tape record rec: one warp per link.
+// dC/dx = s sigma(z) (1 - sigma(z)), z = s (x - L / 2), in the form
+// s a / (1 + a)^2 with a = exp(-|z|) (symmetric in z, no cancellation).
 __global__ void k_bwd_obs(DevSim d, BwdDev b, int rec, int bin) {
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= d.L) return;
-    const double cb = b.Cbar[(size_t)bin * d.L + j];
-    if (cb == 0.0) return;
+    const float2 cb = b.Cbar[(size_t)bin * d.L + j];
+    if (cb.x == 0.0f) return;
     const int4 q = b.tlq[(size_t)rec * d.L + j];
     const int4 st = d.lst[j];
-    const double len = (double)d.geo[j].x, s5 = 5.0 / len, half = 0.5 * len;
+    const float len = d.geo[j].x, s5 = __fdiv_rn(5.0f, len), half = __fmul_rn(0.5f, len);
     for (int k = lane; k < q.y; k += 32) {
         int idx = q.x + k;
         if (idx >= st.y) idx -= st.y;
         const size_t o = (size_t)rec * b.S + st.x + idx;
         const int v = b.tvid[o];
-        const double x = (double)b.tpos[o];
-        const double sg = 1.0 / (1.0 + exp(-s5 * (x - half)));
-        b.xbar[v] += cb * s5 * sg * (1.0 - sg);
+        const float x = b.tpos[o];
+        const float a = expf(-fabsf(__fmul_rn(s5, __fsub_rn(x, half))));
+        const float a1 = __fadd_rn(1.0f, a);
+        const float w = __fdiv_rn(__fmul_rn(s5, a), __fmul_rn(a1, a1));
+        b.xbar[v] = ff_add(b.xbar[v], ff_mul_f(cb, w));
         if (x >= half) {
             const int k2 = b.od[v];
-            atomicAdd(&b.glam[k2], cb / (double)b.od_lambda[k2]);
+            atomicAdd(&b.glam[k2], (double)__fdiv_rn(cb.x, b.od_lambda[k2]));
         }
     }
 }
@@ -174,7 +220,7 @@ __global__ void k_bwd_node_z(DevSim d, BwdDev b, int t, int rec, int bin0) {
     const int v = c.vid;
     if (i < d.L && (c.won || c.tgt == kTgtSink)) {          // an exit from link i
         const int k2 = b.od[v];
-        atomicAdd(&b.glam[k2], b.Csuf[(size_t)bin0 * d.L + i] / (double)b.od_lambda[k2]);
+        atomicAdd(&b.glam[k2], (double)__fdiv_rn(b.Csuf[(size_t)bin0 * d.L + i].x, b.od_lambda[k2]));
     }
     int rw = -1;
     if (c.won) {                                             // adjoint right after this entry
@@ -182,13 +228,15 @@ __global__ void k_bwd_node_z(DevSim d, BwdDev b, int t, int rec, int bin0) {
         if (rw >= 0) b.eadj[(size_t)v * b.cap + rw] = b.xbar[v];
     }
     if (c.tgt < 0) return;
-    const double key = ((double)c.alpha + (double)gumbel(d.key0, d.key1, v, t, 1, 0)) * (double)b.inv_tau;
-    const double kmax = (double)merge_key_of(b.tW[(size_t)rec * d.L + c.tgt]) * (double)b.inv_tau;
-    const double e = exp(key - kmax);
-    double Enew, Xold;
+    // (alpha + g') is the merge key of the forward step; the largest key of the
+    // target is in its merge word
+    const float key = __fadd_rn(c.alpha, gumbel(d.key0, d.key1, v, t, 1, 0));
+    const float kmax = merge_key_of(b.tW[(size_t)rec * d.L + c.tgt]);
+    const float e = expf(__fmul_rn(__fsub_rn(key, kmax), b.inv_tau));
+    float2 Enew, Xold;
     if (c.won) {
         Enew = b.xbar[v];
-        Xold = 0.0;
+        Xold = make_float2(0.0f, 0.0f);
         if (i < d.L && rw >= 0) {                            // next re-entry into the source link
             const int k = route_find(b, v, rw + 1, [&](int, int l) { return l == i; });
             if (k >= 0) Xold = b.eadj[(size_t)v * b.cap + k];
@@ -197,13 +245,13 @@ __global__ void k_bwd_node_z(DevSim d, BwdDev b, int t, int rec, int bin0) {
         Enew = next_entry(b, v, c.tgt, t);
         Xold = b.xbar[v];
     }
-    const double abar = (double)d.M * (Enew - Xold) - (double)c.x * Xold;
+    const float2 abar = ff_sub(ff_mul_f(ff_sub(Enew, Xold), d.M), ff_mul_f(Xold, c.x));
     const size_t eo = (size_t)(t & 1) * (d.L + d.V) + i;
     b.ebuf[eo] = e;
     b.abuf[eo] = abar;
     const size_t zo = (size_t)(t & 1) * d.L + c.tgt;
-    atomicAdd(&b.Z[zo], e);
-    atomicAdd(&b.SA[zo], e * abar);
+    atomicAdd(&b.Z[zo], (double)e);
+    atomicAdd(&b.SA[zo], ff_to_double(ff_mul_f(abar, e)));
 }
 
 // (2b) merge and link-choice Jacobians of step t
@@ -213,14 +261,14 @@ __global__ void k_bwd_node_g(DevSim d, BwdDev b, int t, int rec) {
     const Cand c = load_cand(d, b, i, rec);
     if (c.vid < 0 || c.tgt < 0) return;
     const size_t zo = (size_t)(t & 1) * d.L + c.tgt;
-    const double Z = b.Z[zo];
+    const float2 Z = ff_from_double(b.Z[zo]);
+    const float2 S = ff_div(ff_from_double(b.SA[zo]), Z);            // softmax-weighted mean of abar
     const size_t eo = (size_t)(t & 1) * (d.L + d.V) + i;
-    const double pi = b.ebuf[eo] / Z;
-    const double S = b.SA[zo] / Z;
-    const double vbar = pi * (b.abuf[eo] - S) * (double)b.inv_tau;   // adjoint of V'_i
-    if (i < d.L) atomicAdd(&b.ga[i], vbar); else atomicAdd(b.gao, vbar);
-    const double lbar = (double)c.alpha * vbar;                      // adjoint of l_i at the target
-    if (lbar == 0.0) return;
+    const float pi = __fdiv_rn(b.ebuf[eo], Z.x);
+    const float vbar = __fmul_rn(__fmul_rn(pi, ff_sub(b.abuf[eo], S).x), b.inv_tau);   // adjoint of V'_i
+    if (i < d.L) atomicAdd(&b.ga[i], (double)vbar); else atomicAdd(b.gao, (double)vbar);
+    const float lbar = __fmul_rn(c.alpha, vbar);                     // adjoint of l_i at the target
+    if (lbar == 0.0f) return;
     // choice set of the candidate
     const int v = c.vid;
     const int zone = d.dest_zone[v];
@@ -235,163 +283,206 @@ __global__ void k_bwd_node_g(DevSim d, BwdDev b, int t, int rec) {
         info = d.noinfo + d.no_ptr[n];
         deg = d.no_ptr[n + 1] - d.no_ptr[n];
     }
-    // keys (V_k + g_k)/tau of the first kG slots held in registers (fully
-    // unrolled); slots past kG are recomputed where needed
+    // the forward step's choice keys V_k + g_k of the first kG slots held in
+    // registers (fully unrolled); slots past kG are recomputed where needed.
+    // Softmax weights exp((key_k - key_max) / tau).
     constexpr int kG = 8;
     auto keyk = [&](int k, int &m, float &df) {
         const float4 e = info[k];
         m = __float_as_int(e.w);
         df = d.dest_feat[(size_t)zone * d.V + __float_as_int(e.z)];
         const float util = __fadd_rn(e.x, __fmul_rn(e.y, df));
-        return ((double)util + (double)gumbel(d.key0, d.key1, v, t, 0, k)) * (double)b.inv_tau;
+        return __fadd_rn(util, gumbel(d.key0, d.key1, v, t, 0, k));
     };
-    double key[kG];
-    float dfs[kG];
+    const float itau = b.inv_tau;
+    float key[kG], dfs[kG];
     int ms[kG];
-    double kmax = -INFINITY;
+    float kmax = -INFINITY;
     int ks = 0;
 #pragma unroll
     for (int k = 0; k < kG; ++k) {
         if (k < deg) {
             key[k] = keyk(k, ms[k], dfs[k]);
-            kmax = fmax(kmax, key[k]);
+            kmax = fmaxf(kmax, key[k]);
             if (ms[k] == c.tgt) ks = k;
         }
     }
     for (int k = kG; k < deg; ++k) {
         int m;
         float df;
-        const double kk = keyk(k, m, df);
-        kmax = fmax(kmax, kk);
+        const float kk = keyk(k, m, df);
+        kmax = fmaxf(kmax, kk);
         if (m == c.tgt) ks = k;
     }
-    double zs = 0.0, eks = 0.0;
+    float zs = 0.0f, eks = 0.0f;
 #pragma unroll
     for (int k = 0; k < kG; ++k) {
         if (k < deg) {
-            key[k] = exp(key[k] - kmax);
-            zs += key[k];
+            key[k] = expf(__fmul_rn(__fsub_rn(key[k], kmax), itau));
+            zs = __fadd_rn(zs, key[k]);
             if (k == ks) eks = key[k];
         }
     }
     for (int k = kG; k < deg; ++k) {
         int m;
         float df;
-        const double ek = exp(keyk(k, m, df) - kmax);
-        zs += ek;
+        const float ek = expf(__fmul_rn(__fsub_rn(keyk(k, m, df), kmax), itau));
+        zs = __fadd_rn(zs, ek);
         if (k == ks) eks = ek;
     }
-    const double pks = eks / zs;
+    const float pks = __fdiv_rn(eks, zs);
+    const float lt = __fmul_rn(lbar, itau);
 #pragma unroll
     for (int k = 0; k < kG; ++k) {
         if (k < deg) {
-            const double pk = key[k] / zs;
-            const double Vbar = pk * ((k == ks ? 1.0 : 0.0) - pks) * lbar * (double)b.inv_tau;
-            atomicAdd(&b.gU[ms[k]], Vbar);
-            atomicAdd(&b.gG[ms[k]], Vbar * (double)dfs[k]);
+            const float pk = __fdiv_rn(key[k], zs);
+            const float Vbar = __fmul_rn(__fmul_rn(pk, __fsub_rn(k == ks ? 1.0f : 0.0f, pks)), lt);
+            atomicAdd(&b.gU[ms[k]], (double)Vbar);
+            atomicAdd(&b.gG[ms[k]], (double)__fmul_rn(Vbar, dfs[k]));
         }
     }
     for (int k = kG; k < deg; ++k) {
         int m;
         float df;
-        const double pk = exp(keyk(k, m, df) - kmax) / zs;
-        const double Vbar = pk * ((k == ks ? 1.0 : 0.0) - pks) * lbar * (double)b.inv_tau;
-        atomicAdd(&b.gU[m], Vbar);
-        atomicAdd(&b.gG[m], Vbar * (double)df);
+        const float pk = __fdiv_rn(expf(__fmul_rn(__fsub_rn(keyk(k, m, df), kmax), itau)), zs);
+        const float Vbar = __fmul_rn(__fmul_rn(pk, __fsub_rn(k == ks ? 1.0f : 0.0f, pks)), lt);
+        atomicAdd(&b.gU[m], (double)Vbar);
+        atomicAdd(&b.gG[m], (double)__fmul_rn(Vbar, df));
     }
 }
 
-// (3) car-following of step (t0 + rec): one warp per link; an iteration covers
-// kCfR rounds of 32 queue positions (leader first), issuing every tape and
-// adjoint load of them (and of the vehicle after them) before using any.
-// Vehicle k's adjoint at time t is its own adjoint at t + 1 unless its update
-// was congested (then x' depended on the leader only), plus its follower's
-// adjoint when the follower was congested (the follower's headway used x_k).
-// The follower's values come from the next lane, or for lane 31 from lane 0 of
-// the next round.  Every adjoint an iteration reads is read before any lane
-// writes, and a link's vehicles belong to its warp only.  Per-link parameter
-// sums: free -> u (x' = x + u dt), congested -> s.
-constexpr int kBwdCfThreads = 256;
-constexpr int kCfR = 2;
+// (3) car-following of step (t0 + rec): a block takes kCfLinks consecutive
+// links, and each of its threads kCfE consecutive positions of the links'
+// concatenated queues (leader first), so that every tape and adjoint load of a
+// pass is in flight at once.  Vehicle k's adjoint at time t is its own adjoint
+// at t + 1 unless its update was congested (then x' depended on the leader
+// only), plus its follower's adjoint when the follower was congested (the
+// follower's headway used x_k).  The follower's values come from the same
+// thread, from the next thread (shared memory) or, for the last position of a
+// pass, from a look-ahead load.  Each adjoint is read by one thread, which
+// then writes it.  The per-link parameter sums (free -> u: x' = x + u dt,
+// congested -> s) are reduced in a fixed order.  The block also clears its
+// links' per-target merge sums of the other step parity.
+constexpr int kCfThreads = 256;
+constexpr int kCfLinks = 32;
+constexpr int kCfE = 4;
+constexpr int kCfPass = kCfThreads * kCfE;
 
-__global__ void __launch_bounds__(kBwdCfThreads) k_bwd_cf(DevSim d, BwdDev b, int rec, int t) {
-    const int lane = threadIdx.x & 31;
-    const int j = (blockIdx.x * kBwdCfThreads + threadIdx.x) >> 5;
-    if (j >= d.L) return;
-    if (lane == 0) {                                        // merge sums of step t - 1 start from zero
-        const size_t zo = (size_t)((t + 1) & 1) * d.L + j;
-        b.Z[zo] = 0.0;
-        b.SA[zo] = 0.0;
+__global__ void __launch_bounds__(kCfThreads) k_bwd_cf(DevSim d, BwdDev b, int rec, int t) {
+    __shared__ int4 sq[kCfLinks];
+    __shared__ int sbase[kCfLinks], scap[kCfLinks], off[kCfLinks + 1];
+    __shared__ int ftag[kCfThreads];
+    __shared__ float2 fg[kCfThreads];
+    __shared__ float cu[kCfPass], cs[kCfPass];
+    __shared__ float lsu[kCfLinks], lss[kCfLinks];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int j0 = blockIdx.x * kCfLinks;
+    const int nl = min(kCfLinks, d.L - j0);
+    if (tid < kCfLinks) {                               // warp 0: queue states, exclusive scan
+        int n = 0;
+        if (tid < nl) {
+            const int j = j0 + tid;
+            const size_t zo = (size_t)((t + 1) & 1) * d.L + j;     // merge sums of step t - 1 start from zero
+            b.Z[zo] = 0.0;
+            b.SA[zo] = 0.0;
+            const int4 q = b.tlq[(size_t)rec * d.L + j];
+            const int4 st = d.lst[j];
+            sq[tid] = q;
+            sbase[tid] = st.x;
+            scap[tid] = st.y;
+            n = q.y;
+        }
+        int incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        off[tid] = incl - n;
+        if (tid == kCfLinks - 1) off[kCfLinks] = incl;
+        lsu[tid] = 0.0f;
+        lss[tid] = 0.0f;
     }
-    const int4 q = b.tlq[(size_t)rec * d.L + j];
-    const int4 st = d.lst[j];                               // issued with the queue state
-    const int n = q.y;
-    if (n == 0) return;
-    const double dt = (double)d.dt;
-    const size_t tb = (size_t)rec * b.S + st.x;
-    auto slot = [&](int k) {
-        int idx = q.x + k;
-        if (idx >= st.y) idx -= st.y;
-        return idx;
+    __syncthreads();
+    const int total = off[kCfLinks];
+    if (total == 0) return;
+    const float dt = d.dt;
+    const int *tvid = b.tvid + (size_t)rec * b.S;
+    const int8_t *ttag = b.ttag + (size_t)rec * b.S;
+    auto slot_of = [&](int li, int e) {
+        int idx = sq[li].x + (e - off[li]);
+        if (idx >= scap[li]) idx -= scap[li];
+        return sbase[li] + idx;
     };
-    double su = 0.0, ss = 0.0;
-    for (int k0 = 0; k0 < n; k0 += 32 * kCfR) {
-        int v[kCfR], tag[kCfR];
-        double g[kCfR];
+    for (int base = 0; base < total; base += kCfPass) {
+        const int e0 = base + tid * kCfE;
+        int v[kCfE], tag[kCfE], lk[kCfE];
+        float2 g[kCfE];
+        int li = e0 < total ? link_of(off, nl, e0) : 0;
 #pragma unroll
-        for (int r = 0; r < kCfR; ++r) {
-            const int k = k0 + 32 * r + lane;
-            v[r] = -1;
-            tag[r] = kTagStop;
-            if (k < n) {
-                const int idx = slot(k);
-                v[r] = b.tvid[tb + idx];
-                tag[r] = b.ttag[tb + idx];
+        for (int u = 0; u < kCfE; ++u) {
+            const int e = e0 + u;
+            v[u] = -1;
+            tag[u] = kTagStop;
+            lk[u] = 0;
+            if (e < total) {
+                li = link_advance(off, nl, li, e);
+                lk[u] = li;
+                const int s = slot_of(li, e);
+                v[u] = tvid[s];
+                tag[u] = ttag[s];
             }
         }
-        const int kx = k0 + 32 * kCfR;                      // the vehicle after this iteration
-        int vx = -1, tx = kTagStop;
-        if (lane == 0 && kx < n) {
-            const int idx = slot(kx);
-            vx = b.tvid[tb + idx];
-            tx = b.ttag[tb + idx];
+        int vx = -1, tx = kTagStop;                     // the position after this pass
+        const int ex = base + kCfPass;
+        if (tid == kCfThreads - 1 && ex < total) {
+            const int s = slot_of(link_of(off, nl, ex), ex);
+            vx = tvid[s];
+            tx = ttag[s];
         }
 #pragma unroll
-        for (int r = 0; r < kCfR; ++r) g[r] = v[r] >= 0 ? b.xbar[v[r]] : 0.0;
-        const double gx = vx >= 0 ? b.xbar[vx] : 0.0;
-        double pre[kCfR];
+        for (int u = 0; u < kCfE; ++u) g[u] = v[u] >= 0 ? b.xbar[v[u]] : make_float2(0.0f, 0.0f);
+        const float2 gx = vx >= 0 ? b.xbar[vx] : make_float2(0.0f, 0.0f);
+        ftag[tid] = tag[0];
+        fg[tid] = g[0];
+        __syncthreads();
+        const int ntag = tid + 1 < kCfThreads ? ftag[tid + 1] : tx;
+        const float2 ng = tid + 1 < kCfThreads ? fg[tid + 1] : gx;
 #pragma unroll
-        for (int r = 0; r < kCfR; ++r) {
-            int ftag = __shfl_down_sync(kFull, tag[r], 1);
-            double fg = __shfl_down_sync(kFull, g[r], 1);
-            const int ntag = __shfl_sync(kFull, r + 1 < kCfR ? tag[r + 1 < kCfR ? r + 1 : r] : tx, 0);
-            const double ng = __shfl_sync(kFull, r + 1 < kCfR ? g[r + 1 < kCfR ? r + 1 : r] : gx, 0);
-            if (lane == 31) {
-                ftag = ntag;
-                fg = ng;
+        for (int u = 0; u < kCfE; ++u) {
+            const int e = e0 + u;
+            if (e >= total) break;
+            const int ft = u + 1 < kCfE ? tag[u + 1 < kCfE ? u + 1 : u] : ntag;
+            const float2 fv = u + 1 < kCfE ? g[u + 1 < kCfE ? u + 1 : u] : ng;
+            const bool own = tag[u] != kTagCong, fol = e + 1 < off[lk[u] + 1] && ft == kTagCong;
+            const float2 pre = own ? (fol ? ff_add(g[u], fv) : g[u]) : (fol ? fv : make_float2(0.0f, 0.0f));
+            cu[e - base] = (tag[u] == kTagFree) ? __fmul_rn(g[u].x, dt) : 0.0f;
+            cs[e - base] = (tag[u] == kTagCong) ? -g[u].x : 0.0f;
+            if (v[u] >= 0) b.xbar[v[u]] = pre;
+        }
+        __syncthreads();
+        for (int l = warp; l < nl; l += kCfThreads / 32) {    // per-link sums of the pass, fixed order
+            const int a = max(off[l], base) - base, z = min(off[l + 1], base + kCfPass) - base;
+            float su = 0.0f, ss = 0.0f;
+            for (int k = a + lane; k < z; k += 32) {
+                su = __fadd_rn(su, cu[k]);
+                ss = __fadd_rn(ss, cs[k]);
             }
-            const int k = k0 + 32 * r + lane;
-            pre[r] = 0.0;
-            if (k < n) {
-                pre[r] = (tag[r] == kTagCong) ? 0.0 : g[r];
-                if (k + 1 < n && ftag == kTagCong) pre[r] += fg;
-                if (tag[r] == kTagFree) su += g[r] * dt;
-                if (tag[r] == kTagCong) ss -= g[r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                su += __shfl_xor_sync(kFull, su, o);
+                ss += __shfl_xor_sync(kFull, ss, o);
+            }
+            if (lane == 0) {
+                lsu[l] += su;
+                lss[l] += ss;
             }
         }
-        __syncwarp();                                       // every lane has read before any writes
-#pragma unroll
-        for (int r = 0; r < kCfR; ++r)
-            if (v[r] >= 0) b.xbar[v[r]] = pre[r];
+        __syncthreads();                                // before the next pass reuses the buffers
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        su += __shfl_xor_sync(kFull, su, o);
-        ss += __shfl_xor_sync(kFull, ss, o);
-    }
-    if (lane == 0) {
-        if (su != 0.0) b.gu[j] += su;
-        if (ss != 0.0) b.gs[j] += ss;
+    if (tid < nl) {
+        if (lsu[tid] != 0.0f) b.gu[j0 + tid] += (double)lsu[tid];
+        if (lss[tid] != 0.0f) b.gs[j0 + tid] += (double)lss[tid];
     }
 }
 
