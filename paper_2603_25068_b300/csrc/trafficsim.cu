@@ -1050,6 +1050,8 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         b.tnrec = (int2 *)take((size_t)K * V, sizeof(int2));
         b.tW = (unsigned long long *)take((size_t)K * L, sizeof(unsigned long long));
         b.xbar = (float2 *)take(N, sizeof(float2));
+        b.cursor = (int *)take(N, sizeof(int));
+        b.rdup = (unsigned char *)take(N, 1);
         b.eadj = (float2 *)take((size_t)N * h->route_cap, sizeof(float2));
         b.gu = (double *)take(L, sizeof(double)); b.gs = (double *)take(L, sizeof(double));
         b.ga = (double *)take(L, sizeof(double)); b.gU = (double *)take(L, sizeof(double));
@@ -1096,6 +1098,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     CU(cudaMemsetAsync(b.Z, 0, 2 * (size_t)L * sizeof(double), h->stream));
     CU(cudaMemsetAsync(b.SA, 0, 2 * (size_t)L * sizeof(double), h->stream));
     k_bwd_init<<<(N + 255) / 256, 256, 0, h->stream>>>(h->d, b, dxT);
+    k_route_scan<<<(int)(((size_t)N * 32 + 255) / 256), 256, 0, h->stream>>>(N, b);
     // recomputation: no route log, counters into a scratch array
     DevSim dr = h->d;
     dr.route_log = nullptr;

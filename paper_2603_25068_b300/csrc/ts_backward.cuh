@@ -88,6 +88,9 @@ struct BwdDev {
     float2 *eadj;                // [N cap]
     const int2 *route_log;       // [N cap]
     const int *route_len;        // [N]
+    int *cursor;                 // [N] index of each vehicle's latest entry at a step <= t
+                                 // (the reverse pass undoes entries from the last one)
+    unsigned char *rdup;         // [N] 1 if the vehicle's route enters some link twice
     const float2 *Cbar;          // [n_bins L] adjoint of C_j at the end of each bin
     const float2 *Csuf;          // [(n_bins + 1) L] suffix sums of Cbar
     double *gu, *gs, *ga, *gU, *gG;   // [L]
@@ -133,14 +136,31 @@ __device__ __forceinline__ int route_find(const BwdDev &b, int v, int k0, Pred p
     return -1;
 }
 
-// adjoint right after vehicle v's first entry into link m at a step > t (0 if none)
-__device__ __forceinline__ float2 next_entry(const BwdDev &b, int v, int m, int t) {
-    const int k = route_find(b, v, 0, [&](int s, int l) { return s > t && l == m; });
-    return k >= 0 ? b.eadj[(size_t)v * b.cap + k] : make_float2(0.0f, 0.0f);
-}
-
-__device__ __forceinline__ int entry_at(const BwdDev &b, int v, int t) {
-    return route_find(b, v, 0, [&](int s, int) { return s == t; });
+// Per vehicle (a warp each): the reverse pass's entry cursor starts at the last
+// entry, and whether the route enters some link twice (links compared within
+// 32-entry chunks by match, across chunks by shuffles).
+__global__ void k_route_scan(int N, BwdDev b) {
+    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (v >= N) return;
+    const int n = b.route_len[v];
+    const int2 *r = b.route_log + (size_t)v * b.cap;
+    bool dup = false;
+    for (int a = 0; a < n && !dup; a += 32) {
+        const int xa = a + lane < n ? r[a + lane].y : -1 - lane;          // padding never matches
+        const unsigned m = __match_any_sync(kFull, xa);
+        dup = __any_sync(kFull, xa >= 0 && __popc(m) > 1);
+        for (int c = a + 32; c < n && !dup; c += 32) {
+            const int xc = c + lane < n ? r[c + lane].y : -1000 - lane;
+            bool hit = false;
+#pragma unroll 8
+            for (int q = 0; q < 32; ++q) hit |= xa == __shfl_sync(kFull, xc, q);
+            dup = __any_sync(kFull, hit);
+        }
+    }
+    if (lane == 0) {
+        b.cursor[v] = n - 1;
+        b.rdup[v] = dup ? 1 : 0;
+    }
 }
 
 // copy the state at the start of step (t0 + rec) into the tape
@@ -223,8 +243,9 @@ __global__ void k_bwd_node_z(DevSim d, BwdDev b, int t, int rec, int bin0) {
         atomicAdd(&b.glam[k2], (double)__fdiv_rn(b.Csuf[(size_t)bin0 * d.L + i].x, b.od_lambda[k2]));
     }
     int rw = -1;
-    if (c.won) {                                             // adjoint right after this entry
-        rw = entry_at(b, v, t);
+    if (c.won) {                 // adjoint right after this entry: the latest one not yet undone
+        rw = b.cursor[v];
+        b.cursor[v] = rw - 1;
         if (rw >= 0) b.eadj[(size_t)v * b.cap + rw] = b.xbar[v];
     }
     if (c.tgt < 0) return;
@@ -237,12 +258,14 @@ __global__ void k_bwd_node_z(DevSim d, BwdDev b, int t, int rec, int bin0) {
     if (c.won) {
         Enew = b.xbar[v];
         Xold = make_float2(0.0f, 0.0f);
-        if (i < d.L && rw >= 0) {                            // next re-entry into the source link
+        if (i < d.L && rw >= 0 && b.rdup[v]) {               // next re-entry into the source link
             const int k = route_find(b, v, rw + 1, [&](int, int l) { return l == i; });
             if (k >= 0) Xold = b.eadj[(size_t)v * b.cap + k];
         }
-    } else {
-        Enew = next_entry(b, v, c.tgt, t);
+    } else {                     // first entry into the target after the current one
+        Enew = make_float2(0.0f, 0.0f);
+        const int k = route_find(b, v, b.cursor[v] + 1, [&](int s, int l) { return s > t && l == c.tgt; });
+        if (k >= 0) Enew = b.eadj[(size_t)v * b.cap + k];
         Xold = b.xbar[v];
     }
     const float2 abar = ff_sub(ff_mul_f(ff_sub(Enew, Xold), d.M), ff_mul_f(Xold, c.x));
