@@ -231,50 +231,63 @@ __device__ __forceinline__ Cand load_cand(const DevSim &d, const BwdDev &b, int 
     return c;
 }
 
-// (2a) merge candidates of step t: abar, softmax weight, per-target sums
+// (2a) merge candidates of step t: abar, softmax weight, per-target sums.  The
+// candidate's record first; then, in one round, the target's merge word and
+// everything that depends on the vehicle only.
 __global__ void k_bwd_node_z(DevSim d, BwdDev b, int t, int rec, int bin0) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.L + d.V) return;
-    const Cand c = load_cand(d, b, i, rec);
-    if (c.vid < 0) return;
-    const int v = c.vid;
-    if (i < d.L && (c.won || c.tgt == kTgtSink)) {          // an exit from link i
-        const int k2 = b.od[v];
-        atomicAdd(&b.glam[k2], (double)__fdiv_rn(b.Csuf[(size_t)bin0 * d.L + i].x, b.od_lambda[k2]));
+    int v, tgt;
+    float x, alpha;
+    if (i < d.L) {
+        const int4 r = b.tcrec[(size_t)rec * d.L + i];
+        v = r.x; tgt = r.y; x = __int_as_float(r.w); alpha = d.alpha[i];
+    } else {
+        const int2 r = b.tnrec[(size_t)rec * d.V + (i - d.L)];
+        v = r.x; tgt = r.y; x = 0.0f; alpha = d.alpha[d.L];
     }
-    int rw = -1;
-    if (c.won) {                 // adjoint right after this entry: the latest one not yet undone
-        rw = b.cursor[v];
-        b.cursor[v] = rw - 1;
-        if (rw >= 0) b.eadj[(size_t)v * b.cap + rw] = b.xbar[v];
+    if (v < 0) return;
+    const unsigned long long wt = tgt >= 0 ? b.tW[(size_t)rec * d.L + tgt] : 0ull;
+    const int cur = b.cursor[v];
+    const float2 xv = b.xbar[v];
+    const int dup = b.rdup[v];
+    const int k2 = b.od[v];
+    const float csuf = i < d.L ? b.Csuf[(size_t)bin0 * d.L + i].x : 0.0f;
+    const bool won = tgt >= 0 && wt != 0ull && merge_vid(wt) == v;
+    const bool exits = i < d.L && (won || tgt == kTgtSink);         // an exit from link i
+    const float lam = exits ? b.od_lambda[k2] : 1.0f;
+    if (won) {                   // adjoint right after this entry: the latest one not yet undone
+        b.cursor[v] = cur - 1;
+        if (cur >= 0) b.eadj[(size_t)v * b.cap + cur] = xv;
     }
-    if (c.tgt < 0) return;
-    // (alpha + g') is the merge key of the forward step; the largest key of the
-    // target is in its merge word
-    const float key = __fadd_rn(c.alpha, gumbel(d.key0, d.key1, v, t, 1, 0));
-    const float kmax = merge_key_of(b.tW[(size_t)rec * d.L + c.tgt]);
-    const float e = expf(__fmul_rn(__fsub_rn(key, kmax), b.inv_tau));
-    float2 Enew, Xold;
-    if (c.won) {
-        Enew = b.xbar[v];
-        Xold = make_float2(0.0f, 0.0f);
-        if (i < d.L && rw >= 0 && b.rdup[v]) {               // next re-entry into the source link
-            const int k = route_find(b, v, rw + 1, [&](int, int l) { return l == i; });
-            if (k >= 0) Xold = b.eadj[(size_t)v * b.cap + k];
+    if (tgt >= 0) {
+        // (alpha + g') is the merge key of the forward step; the largest key of
+        // the target is in its merge word
+        const float key = __fadd_rn(alpha, gumbel(d.key0, d.key1, v, t, 1, 0));
+        const float e = expf(__fmul_rn(__fsub_rn(key, merge_key_of(wt)), b.inv_tau));
+        float2 Enew, Xold;
+        if (won) {
+            Enew = xv;
+            Xold = make_float2(0.0f, 0.0f);
+            if (i < d.L && cur >= 0 && dup) {                    // next re-entry into the source link
+                const int k = route_find(b, v, cur + 1, [&](int, int l) { return l == i; });
+                if (k >= 0) Xold = b.eadj[(size_t)v * b.cap + k];
+            }
+        } else {                 // first entry into the target after the current one
+            Enew = make_float2(0.0f, 0.0f);
+            const int k = route_find(b, v, cur + 1, [&](int s, int l) { return s > t && l == tgt; });
+            if (k >= 0) Enew = b.eadj[(size_t)v * b.cap + k];
+            Xold = xv;
         }
-    } else {                     // first entry into the target after the current one
-        Enew = make_float2(0.0f, 0.0f);
-        const int k = route_find(b, v, b.cursor[v] + 1, [&](int s, int l) { return s > t && l == c.tgt; });
-        if (k >= 0) Enew = b.eadj[(size_t)v * b.cap + k];
-        Xold = b.xbar[v];
+        const float2 abar = ff_sub(ff_mul_f(ff_sub(Enew, Xold), d.M), ff_mul_f(Xold, x));
+        const size_t eo = (size_t)(t & 1) * (d.L + d.V) + i;
+        b.ebuf[eo] = e;
+        b.abuf[eo] = abar;
+        const size_t zo = (size_t)(t & 1) * d.L + tgt;
+        atomicAdd(&b.Z[zo], (double)e);
+        atomicAdd(&b.SA[zo], ff_to_double(ff_mul_f(abar, e)));
     }
-    const float2 abar = ff_sub(ff_mul_f(ff_sub(Enew, Xold), d.M), ff_mul_f(Xold, c.x));
-    const size_t eo = (size_t)(t & 1) * (d.L + d.V) + i;
-    b.ebuf[eo] = e;
-    b.abuf[eo] = abar;
-    const size_t zo = (size_t)(t & 1) * d.L + c.tgt;
-    atomicAdd(&b.Z[zo], (double)e);
-    atomicAdd(&b.SA[zo], ff_to_double(ff_mul_f(abar, e)));
+    if (exits) atomicAdd(&b.glam[k2], (double)__fdiv_rn(csuf, lam));
 }
 
 // (2b) merge and link-choice Jacobians of step t
@@ -387,8 +400,8 @@ __global__ void k_bwd_node_g(DevSim d, BwdDev b, int t, int rec) {
 // congested -> s) are reduced in a fixed order.  The block also clears its
 // links' per-target merge sums of the other step parity.
 constexpr int kCfThreads = 256;
-constexpr int kCfLinks = 32;
-constexpr int kCfE = 4;
+constexpr int kCfLinks = 64;
+constexpr int kCfE = 8;
 constexpr int kCfPass = kCfThreads * kCfE;
 
 __global__ void __launch_bounds__(kCfThreads) k_bwd_cf(DevSim d, BwdDev b, int rec, int t) {
@@ -401,8 +414,7 @@ __global__ void __launch_bounds__(kCfThreads) k_bwd_cf(DevSim d, BwdDev b, int r
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int j0 = blockIdx.x * kCfLinks;
     const int nl = min(kCfLinks, d.L - j0);
-    if (tid < kCfLinks) {                               // warp 0: queue states, exclusive scan
-        int n = 0;
+    if (tid < kCfLinks) {                               // queue states of the block's links
         if (tid < nl) {
             const int j = j0 + tid;
             const size_t zo = (size_t)((t + 1) & 1) * d.L + j;     // merge sums of step t - 1 start from zero
@@ -413,18 +425,23 @@ __global__ void __launch_bounds__(kCfThreads) k_bwd_cf(DevSim d, BwdDev b, int r
             sq[tid] = q;
             sbase[tid] = st.x;
             scap[tid] = st.y;
-            n = q.y;
         }
-        int incl = n;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-        }
-        off[tid] = incl - n;
-        if (tid == kCfLinks - 1) off[kCfLinks] = incl;
         lsu[tid] = 0.0f;
         lss[tid] = 0.0f;
+    }
+    __syncthreads();
+    if (tid < 32) {                                     // exclusive scan of the queue lengths (warp 0)
+        const int a = tid < nl ? sq[tid].y : 0, c = tid + 32 < nl ? sq[tid + 32].y : 0;
+        int ia = a, ic = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ya = __shfl_up_sync(kFull, ia, o), yc = __shfl_up_sync(kFull, ic, o);
+            if (lane >= o) { ia += ya; ic += yc; }
+        }
+        const int ta = __shfl_sync(kFull, ia, 31);
+        off[tid] = ia - a;
+        off[tid + 32] = ta + ic - c;
+        if (tid == 31) off[kCfLinks] = ta + ic;
     }
     __syncthreads();
     const int total = off[kCfLinks];
