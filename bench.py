@@ -371,7 +371,7 @@ def run_serving(args, dev, ws):
     sizes = (600, 1200, 2400) if args.small else (2000, 4500, 9000, 18000, 36000)
     n_range = (5000, 50000) if args.small else (50_000, 1_000_000)
     reqs = serve.make_request_stream(n=args.serve_requests, rate=4.0, seed=4, sizes=sizes, n_range=n_range)
-    eng = serve.Engine(device=dev.index, hbm_budget=150e9, chunk=60, ckpt_every=180)
+    eng = serve.Engine(device=dev.index, hbm_budget=150e9, chunk=240, ckpt_every=180)
     t0 = time.perf_counter()
     eng.run(reqs)
     makespan = max(r.finished for r in reqs)

@@ -280,6 +280,13 @@ SIM_API int sim_test_barrier_timeout(sim_handle h, int32_t missing);
  * Not for a handle that is a member of a live batch. */
 SIM_API int sim_set_stream(sim_handle h, void *stream);
 
+/* Device memory of simulators and batches comes from a stream-ordered memory
+ * pool per device, which keeps freed blocks mapped for the next simulator (as
+ * a caching allocator does).  This returns the device's unused cached blocks
+ * to the driver; memory of live simulators is unaffected.
+ * Errors: SIM_EINVAL (device index), SIM_ECUDA. */
+SIM_API int sim_release_cached_memory(int32_t device);
+
 /* Current time step and device bytes held by the handle. */
 SIM_API int32_t sim_time(sim_handle h);
 SIM_API size_t sim_device_bytes(sim_handle h);

@@ -198,12 +198,53 @@ static int fail(sim_ctx *h, int code, const std::string &msg) {
             return fail(h, SIM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+// Device memory of simulators and batches comes from one memory pool per
+// device, allocated and freed in stream order: releasing a simulator does not
+// wait for the whole device (as cudaFree does), and the next simulator reuses
+// the freed blocks without new mappings.  Like a caching allocator, the pool
+// keeps what it has mapped (up to the largest working set) until the process
+// ends or sim_release_cached_memory is called.
+static std::mutex g_mpool_mu;
+static cudaMemPool_t g_mpool[64];
+
+static cudaError_t pool_alloc(void **p, size_t bytes, int device, cudaStream_t s) {
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(g_mpool_mu);
+        if (!g_mpool[device]) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = device;
+            cudaError_t e = cudaMemPoolCreate(&g_mpool[device], &props);
+            if (e != cudaSuccess) { g_mpool[device] = nullptr; return e; }
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(g_mpool[device], cudaMemPoolAttrReleaseThreshold, &keep);
+            // never make an allocating stream wait for the work of the stream
+            // that freed a block (serving creates simulators beside a busy
+            // batch): reuse a block only once its free has completed
+            int no = 0;
+            cudaMemPoolSetAttribute(g_mpool[device], cudaMemPoolReuseAllowInternalDependencies, &no);
+        }
+        pool = g_mpool[device];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+extern "C" int sim_release_cached_memory(int32_t device) {
+    if (device < 0 || device >= 64) return SIM_EINVAL;
+    std::lock_guard<std::mutex> lock(g_mpool_mu);
+    if (g_mpool[device] && cudaMemPoolTrimTo(g_mpool[device], 0) != cudaSuccess) return SIM_ECUDA;
+    return SIM_OK;
+}
+
 template <class T>
 static int dalloc(sim_ctx *h, T **p, size_t n) {
     void *q = nullptr;
     size_t b = std::max<size_t>(n, 1) * sizeof(T);
-    cudaError_t e = cudaMalloc(&q, b);
-    if (e != cudaSuccess) return fail(h, SIM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    cudaError_t e = pool_alloc(&q, b, h->device, h->stream);
+    if (e != cudaSuccess) return fail(h, SIM_ENOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
     h->allocs.push_back(q);
     h->bytes += b;
     *p = (T *)q;
@@ -543,15 +584,31 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
     h->S = (int)S;
     h->lst_host = lst;
     // origin queues sorted by (origin, departure step, id)
+    // origin queues: vehicles ordered by (origin, departure step, id), as two
+    // stable counting sorts -- by departure step over the ids, then by origin
     std::vector<int> fifo(N), fifo_beg(V + 1, 0), fifo_dep(N), fifo_aux(2 * (size_t)N);
-    std::iota(fifo.begin(), fifo.end(), 0);
-    std::stable_sort(fifo.begin(), fifo.end(), [&](int a, int b) {
-        if (dem->origin[a] != dem->origin[b]) return dem->origin[a] < dem->origin[b];
-        if (dem->dep_step[a] != dem->dep_step[b]) return dem->dep_step[a] < dem->dep_step[b];
-        return a < b;
-    });
-    for (int i = 0; i < N; ++i) fifo_beg[dem->origin[i] + 1]++;
-    for (int n = 0; n < V; ++n) fifo_beg[n + 1] += fifo_beg[n];
+    {
+        int max_dep = 0;
+        for (int i = 0; i < N; ++i) max_dep = std::max(max_dep, dem->dep_step[i]);
+        std::vector<int> by_dep(N);
+        if (max_dep < (1 << 24)) {
+            std::vector<int> cnt((size_t)max_dep + 2, 0);
+            for (int i = 0; i < N; ++i) cnt[(size_t)dem->dep_step[i] + 1]++;
+            for (int s = 0; s <= max_dep; ++s) cnt[(size_t)s + 1] += cnt[s];
+            for (int i = 0; i < N; ++i) by_dep[cnt[dem->dep_step[i]]++] = i;
+        } else {                         // departure steps too far apart for counting
+            std::iota(by_dep.begin(), by_dep.end(), 0);
+            std::stable_sort(by_dep.begin(), by_dep.end(),
+                             [&](int a, int b) { return dem->dep_step[a] < dem->dep_step[b]; });
+        }
+        for (int i = 0; i < N; ++i) fifo_beg[dem->origin[i] + 1]++;
+        for (int n = 0; n < V; ++n) fifo_beg[n + 1] += fifo_beg[n];
+        std::vector<int> fill(fifo_beg.begin(), fifo_beg.end() - 1);
+        for (int k = 0; k < N; ++k) {
+            const int i = by_dep[k];
+            fifo[fill[dem->origin[i]]++] = i;
+        }
+    }
     for (int k = 0; k < N; ++k) {
         fifo_dep[k] = dem->dep_step[fifo[k]];
         fifo_aux[2 * k] = fifo[k];
@@ -675,8 +732,9 @@ static void release(sim_ctx *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.second);
     h->graphs.clear();
-    for (void *p : h->allocs) cudaFree(p);
+    for (void *p : h->allocs) cudaFreeAsync(p, h->stream);
     h->allocs.clear();
+    if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     h->stream = nullptr;
     if (h->jstream) cudaStreamSynchronize(h->jstream);
@@ -1445,8 +1503,8 @@ static int bfail(sim_batch_ctx *b, int code, const std::string &msg) {
 template <class T>
 static int balloc(sim_batch_ctx *b, T **p, size_t n) {
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
-    if (e != cudaSuccess) return bfail(b, SIM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    cudaError_t e = pool_alloc(&q, std::max<size_t>(n, 1) * sizeof(T), b->device, b->stream);
+    if (e != cudaSuccess) return bfail(b, SIM_ENOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
     b->allocs.push_back(q);
     *p = (T *)q;
     return SIM_OK;
@@ -1470,11 +1528,12 @@ static void batch_release(sim_batch_ctx *b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     for (auto &g : b->graphs) cudaGraphExecDestroy(g.second);
     b->graphs.clear();
-    for (void *p : b->allocs) cudaFree(p);
+    for (void *p : b->allocs) cudaFreeAsync(p, b->stream);
     b->allocs.clear();
-    if (b->d_ckstep) cudaFree(b->d_ckstep);
+    if (b->d_ckstep) cudaFreeAsync(b->d_ckstep, b->stream);
     b->d_ckstep = nullptr;
     b->ckstep_cap = 0;
+    if (b->stream) cudaStreamSynchronize(b->stream);
     for (size_t k = 0; k < b->m.size() && k < b->saved_streams.size(); ++k) b->m[k]->stream = b->saved_streams[k];
 }
 
@@ -1496,7 +1555,7 @@ static int batch_persist_setup(sim_batch_ctx *b) {
     b->nIB = (int)iB.size();
     int rc;
     if ((rc = balloc(b, &b->d_itA, iA.size())) || (rc = balloc(b, &b->d_itB, iB.size())) ||
-        (rc = balloc(b, &b->d_bar, 1)) || (rc = balloc(b, &b->d_berr, 1)))
+        (rc = balloc(b, &b->d_bar, 1)))
         return rc;
     BCU(cudaMemcpyAsync(b->d_itA, iA.data(), iA.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
     BCU(cudaMemcpyAsync(b->d_itB, iB.data(), iB.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
@@ -1521,6 +1580,51 @@ static int batch_persist_setup(sim_batch_ctx *b) {
 
 static bool batch_use_persist(const sim_batch_ctx *b) { return b->bp_ok && b->executor != SIM_EXEC_STEP; }
 
+// A lone running member advances on its own persistent executor (queues in
+// shared memory), which is faster for one member than the warp-item batch
+// kernel.  Both leave the state in the same format at a launch boundary, so
+// the executors can alternate between advances.  Returns -1 when the batch has
+// not exactly one running member (or it has no persistent executor).
+static int batch_solo_member(const sim_batch_ctx *b) {
+    int k1 = -1;
+    for (int k = 0; k < (int)b->m.size(); ++k) {
+        if (b->hmode[k] == kModeDone) continue;
+        if (k1 >= 0) return -1;
+        k1 = k;
+    }
+    return (k1 >= 0 && use_persist(b->m[k1])) ? k1 : -1;
+}
+
+static int batch_advance_solo(sim_batch_ctx *b, int k, int n_steps) {
+    sim_ctx *h = b->m[k];
+    const int T = b->hT[k];
+    int t = h->t, mode = b->hmode[k], left = n_steps;
+    if (mode == kModeRun) {
+        const int t_end = std::min(T, t + left);
+        while (t < t_end) {                      // segments between checkpoints
+            int t1 = t_end;
+            if (h->K > 0) {
+                if (t % h->K == 0) ckpt_copy(h, t / h->K, t & 1, true);
+                t1 = std::min(t_end, (t / h->K + 1) * h->K);
+            }
+            const bool fin = t1 == T && left > t1 - h->t;
+            if (enqueue_persist(h, t, t1, fin ? 1 : 0)) return bfail(b, SIM_ECUDA, h->err);
+            t = t1;
+        }
+        left -= t - h->t;
+        // at the horizon: the observation-only pass ran with the last segment
+        // if a step was left for it, else it is the member's next step
+        if (t == T) mode = left > 0 ? kModeDone : kModeFinal;
+    } else if (mode == kModeFinal) {
+        if (enqueue_persist(h, T, T, 1)) return bfail(b, SIM_ECUDA, h->err);
+        mode = kModeDone;
+    }
+    BCU(cudaMemcpyAsync(b->d_t + k, &t, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->d_mode + k, &mode, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaStreamSynchronize(b->stream));       // the host values above are stack variables
+    return SIM_OK;
+}
+
 // One cooperative launch advancing every running member by up to n_steps steps.
 static int batch_launch_persist(sim_batch_ctx *b, int n_steps) {
     const int n = (int)b->m.size();
@@ -1534,10 +1638,10 @@ static int batch_launch_persist(sim_batch_ctx *b, int n_steps) {
         }
     }
     if (b->ckstep_cap < n_steps) {
-        if (b->d_ckstep) cudaFree(b->d_ckstep);
+        if (b->d_ckstep) cudaFreeAsync(b->d_ckstep, b->stream);
         b->d_ckstep = nullptr;
         b->ckstep_cap = 0;
-        BCU(cudaMalloc(&b->d_ckstep, (size_t)n_steps));
+        BCU(pool_alloc((void **)&b->d_ckstep, (size_t)n_steps, b->device, b->stream));
         b->ckstep_cap = n_steps;
     }
     BCU(cudaMemcpyAsync(b->d_ckstep, ck.data(), (size_t)n_steps, cudaMemcpyHostToDevice, b->stream));
@@ -1596,9 +1700,13 @@ extern "C" int sim_batch_create(const sim_handle *members, int32_t n, sim_batch 
     b->nA = (int)bmA.size();
     b->nB = (int)bmB.size();
     if ((rc = balloc(b, &b->d_ds, n)) || (rc = balloc(b, &b->d_ck, n)) || (rc = balloc(b, &b->d_bmapA, b->nA)) ||
-        (rc = balloc(b, &b->d_bmapB, b->nB)) || (rc = balloc(b, &b->d_t, n)) || (rc = balloc(b, &b->d_T, n)) ||
-        (rc = balloc(b, &b->d_mode, n)))
+        (rc = balloc(b, &b->d_bmapB, b->nB)) || (rc = balloc(b, &b->d_t, 2 * (size_t)n + 1)) || (rc = balloc(b, &b->d_T, n)))
         return fin(rc);
+    // steps, modes and the barrier-timeout flag side by side: one read-back per advance
+    b->d_mode = b->d_t + n;
+    b->d_berr = b->d_t + 2 * n;
+    if (cudaMemsetAsync(b->d_berr, 0, sizeof(int), b->stream) != cudaSuccess)
+        return fin(bfail(b, SIM_ECUDA, "batch set-up"));
     // members already running in an earlier batch continue where they are
     std::vector<int> ht(n);
     b->hT.assign(n, 0);
@@ -1666,7 +1774,8 @@ extern "C" int sim_batch_advance(sim_batch b, int32_t n_steps, int32_t *finished
     BCU(cudaSetDevice(b->device));
     const int n = (int)b->m.size();
     if (n_steps > 0 && batch_use_persist(b)) {
-        const int rc = batch_launch_persist(b, n_steps);
+        const int solo = batch_solo_member(b);
+        const int rc = solo >= 0 ? batch_advance_solo(b, solo, n_steps) : batch_launch_persist(b, n_steps);
         if (rc) return rc;
         BCU(cudaGetLastError());
     } else if (n_steps > 0) {
@@ -1687,16 +1796,19 @@ extern "C" int sim_batch_advance(sim_batch b, int32_t n_steps, int32_t *finished
         else batch_enqueue_steps(b, n_steps);
         BCU(cudaGetLastError());
     }
-    std::vector<int> mode(n), tv(n);
-    BCU(cudaMemcpyAsync(mode.data(), b->d_mode, n * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
-    BCU(cudaMemcpyAsync(tv.data(), b->d_t, n * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    std::vector<int> tm(2 * (size_t)n + 1);
+    BCU(cudaMemcpyAsync(tm.data(), b->d_t, tm.size() * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     BCU(cudaStreamSynchronize(b->stream));
+    const int *tv = tm.data(), *mode = tm.data() + n;
+    if (tm[2 * (size_t)n]) return bfail(b, SIM_ETIMEOUT, "persistent batch: a grid barrier timed out");
+    std::vector<int> just_done;
     for (int k = 0; k < n; ++k) {
         sim_ctx *h = b->m[k];
         if (mode[k] == kModeDone && b->hmode[k] != kModeDone) {        // finished its horizon
             h->t = h->T;
             h->reset_done = true;
             h->tape_ready = h->K > 0;
+            just_done.push_back(k);
         } else if (mode[k] != kModeDone) {
             h->t = tv[k];
         }
@@ -1704,13 +1816,9 @@ extern "C" int sim_batch_advance(sim_batch b, int32_t n_steps, int32_t *finished
         h->bmode = mode[k];
         if (finished) finished[k] = mode[k] == kModeDone;
     }
-    if (n_steps > 0 && batch_use_persist(b)) {
-        int berr = 0;
-        BCU(cudaMemcpy(&berr, b->d_berr, sizeof(int), cudaMemcpyDeviceToHost));
-        if (berr) return bfail(b, SIM_ETIMEOUT, "persistent batch: a grid barrier timed out");
-    }
-    for (int k = 0; k < n; ++k) {
-        if (b->hT[k] == 0) continue;                 // never started in this batch
+    // device errors are sticky and a failing step skips its write, so a member's
+    // flag is read once, when it finishes its horizon
+    for (int k : just_done) {
         const int rc = check_device_error(b->m[k]);
         if (rc) return bfail(b, rc, b->m[k]->err);
     }

@@ -2,11 +2,14 @@
 
 Requests (nowcast rollouts, calibration-gradient rollouts, control-candidate
 rollouts) arrive over time.  The engine
-  * admits a request as soon as its device memory fits in the HBM budget
-    (sim_device_bytes of the created handle plus its reverse-pass needs),
-  * runs every admitted forward rollout in one batch: one launch per phase and
-    step for all of them (sim_batch_*), a new request joining at the next step
-    boundary, finished ones leaving it,
+  * admits a request as soon as an upper bound of its device memory fits in
+    the HBM budget (replaced by sim_device_bytes of the handle once created,
+    plus its reverse-pass needs),
+  * builds the simulator of an admitted request on a creation thread with a
+    stream of its own, so that host set-up and uploads overlap the running
+    batch instead of stalling it,
+  * runs every admitted forward rollout in one batch (sim_batch_*), a new
+    request joining at the next step boundary, finished ones leaving it,
   * runs the reverse pass of a finished gradient request on a worker thread with
     its own stream, so that it overlaps the batched forward work on the device,
   * records each request's latency from arrival to result.
@@ -79,9 +82,22 @@ def run_request_alone(req: Request, device: int = 0, ckpt_every: int = 180, rout
     return res
 
 
+def handle_bytes_bound(sc, ckpt_every: int, route_cap: int) -> float:
+    """Upper bound of sim_device_bytes for a scenario (admission before the
+    handle exists): slot arena, per-link and per-vehicle state, outputs, and
+    for a gradient request the checkpoints and the route log."""
+    slots = float(np.sum(np.floor(sc.length.astype(np.float64) * sc.kappa / sc.dn) + 2))
+    nb = -(-sc.T // sc.obs_every)
+    b = 32.0 * slots + (320.0 + 12.0 * nb) * sc.L + 48.0 * sc.N + 4.0 * sc.Z * sc.V + 16.0 * sc.V
+    if ckpt_every > 0:
+        b += (sc.T // ckpt_every + 1) * (16.0 * slots + 64.0 * sc.L + 4.0 * sc.V + 4.0 * sc.N)
+        b += (8.0 * (route_cap + 7) + 8.0) * sc.N
+    return b
+
+
 class Engine:
-    def __init__(self, device: int = 0, hbm_budget: float = 150e9, chunk: int = 60, ckpt_every: int = 180,
-                 route_cap: int = 256):
+    def __init__(self, device: int = 0, hbm_budget: float = 150e9, chunk: int = 240, ckpt_every: int = 180,
+                 route_cap: int = 256, creators: int = 2):
         import torch
         self.torch = torch
         self.device = device
@@ -95,12 +111,19 @@ class Engine:
         self.batch: Optional[Batch] = None
         self.batch_members: List[int] = []
         self.used = 0.0
-        self.bwd_q: "queue.Queue" = queue.Queue()
-        self.bwd_thread = threading.Thread(target=self._bwd_worker, daemon=True)
-        self.bwd_thread.start()
         self.lock = threading.Lock()
         self.worker_error = None
         self.t0 = None
+        self.bwd_q: "queue.Queue" = queue.Queue()
+        self.create_q: "queue.Queue" = queue.Queue()
+        self.ready_q: "queue.Queue" = queue.Queue()
+        self.bwd_thread = threading.Thread(target=self._bwd_worker, daemon=True)
+        self.create_threads = [threading.Thread(target=self._create_worker, args=(k,), daemon=True)
+                               for k in range(creators)]
+        self.create_streams = [torch.cuda.Stream(device=device) for _ in range(creators)]
+        self.bwd_thread.start()
+        for th in self.create_threads:
+            th.start()
 
     # -------------------------------------------------------------- helpers
     def now(self):
@@ -134,6 +157,33 @@ class Engine:
                 self.used -= nbytes
             req.finished = self.now()
 
+    def _create_worker(self, k: int):
+        torch = self.torch
+        try:                 # the thread's first simulator pays one-time set-up costs
+            from . import scenario as S
+            with torch.cuda.device(self.device):
+                Simulator(S.tiny_grid(n_vehicles=50, T=20), device=self.device, stream=self.create_streams[k]).close()
+        except Exception as e:
+            self.worker_error = e
+            return
+        while True:
+            item = self.create_q.get()
+            if item is None:
+                return
+            req, reserved = item
+            try:
+                with torch.cuda.device(self.device):
+                    sim = Simulator(req.scenario, device=self.device, stream=self.create_streams[k],
+                                    ckpt_every=self.ckpt_every if req.needs_grad else 0, route_cap=self.route_cap)
+                    sim.set_stream(self.stream)          # drains the creation stream
+                nbytes = float(sim.device_bytes()) + self._estimate_extra(req)
+                with self.lock:
+                    self.used += nbytes - reserved
+            except Exception as e:                      # reported by the main loop
+                self.worker_error = e
+                return
+            self.ready_q.put((req, sim, nbytes))
+
     def _rebuild(self, new=()):
         if self.batch is not None:
             self.batch.close()
@@ -145,25 +195,15 @@ class Engine:
                 self.batch.start(i, req.scenario.T)
 
     def _admit(self, req: Request) -> bool:
-        sc = req.scenario
-        extra = self._estimate_extra(req)
+        """Reserve an upper bound of the request's device memory and hand it to
+        the creation thread; False if it does not fit yet."""
+        reserved = handle_bytes_bound(req.scenario, self.ckpt_every if req.needs_grad else 0,
+                                      self.route_cap) + self._estimate_extra(req)
         with self.lock:
-            if self.used + extra >= self.budget:
+            if self.used + reserved > self.budget and (self.used > 0 or self.active):
                 return False
-        sim = Simulator(sc, device=self.device, stream=self.stream,
-                        ckpt_every=self.ckpt_every if req.needs_grad else 0, route_cap=self.route_cap)
-        nbytes = float(sim.device_bytes()) + extra
-        with self.lock:
-            if self.used + nbytes > self.budget and self.active:
-                ok = False
-            else:
-                self.used += nbytes
-                ok = True
-        if not ok:
-            sim.close()
-            return False
-        req.admitted = self.now()
-        self.active.append((req, sim, nbytes))
+            self.used += reserved
+        self.create_q.put((req, reserved))
         return True
 
     # -------------------------------------------------------------- main loop
@@ -177,18 +217,24 @@ class Engine:
         waiting: List[Request] = []
         with torch.cuda.device(self.device):
             while True:
-                if self.worker_error is not None or not self.bwd_thread.is_alive():
-                    raise RuntimeError(f"reverse-pass worker failed: {self.worker_error!r}")
+                if self.worker_error is not None or not self.bwd_thread.is_alive() \
+                        or not all(th.is_alive() for th in self.create_threads):
+                    raise RuntimeError(f"serving worker failed: {self.worker_error!r}")
                 if self.now() > max_seconds:
                     raise RuntimeError("serving run exceeded its time limit")
                 while k < len(pending) and pending[k].arrival <= self.now():
                     waiting.append(pending[k])
                     k += 1
+                waiting = [req for req in waiting if not self._admit(req)]
                 new = []
-                still = []
-                for req in waiting:
-                    (new if self._admit(req) else still).append(req)
-                waiting = still
+                while True:                              # simulators built by the creation thread
+                    try:
+                        req, sim, nbytes = self.ready_q.get_nowait()
+                    except queue.Empty:
+                        break
+                    req.admitted = self.now()
+                    self.active.append((req, sim, nbytes))
+                    new.append(req)
                 if new:
                     self._rebuild(new)
                 if not self.active:
@@ -215,7 +261,11 @@ class Engine:
                                 self.used -= nbytes
                             req.finished = self.now()
             self.bwd_q.put(None)
+            for _ in self.create_threads:
+                self.create_q.put(None)
             self.bwd_thread.join()
+            for th in self.create_threads:
+                th.join()
         return requests
 
 
