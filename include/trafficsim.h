@@ -280,6 +280,21 @@ SIM_API int sim_test_barrier_timeout(sim_handle h, int32_t missing);
  * Not for a handle that is a member of a live batch. */
 SIM_API int sim_set_stream(sim_handle h, void *stream);
 
+/* Segment recomputation of the reverse pass (sim_backward):
+ *   SIM_RECOMPUTE_OVERLAP (default)  segment s - 1 is recomputed by the
+ *       two-kernel executor on a low-priority stream while the reverse
+ *       kernels of segment s run on a high-priority one; two tape sets
+ *       (about 2 x (K + 1) x 9 bytes per queue slot);
+ *   SIM_RECOMPUTE_SERIAL  each segment is recomputed by one recording launch
+ *       of the persistent executor just before its reverse kernels; one tape
+ *       set (half the memory).
+ * Both give the same tape, so the same gradients (up to the order of the
+ * double-precision atomic additions).  SERIAL falls back to OVERLAP when the
+ * handle has no persistent executor.  Errors: SIM_EINVAL (unknown mode). */
+#define SIM_RECOMPUTE_OVERLAP 0
+#define SIM_RECOMPUTE_SERIAL  1
+SIM_API int sim_set_recompute(sim_handle h, int32_t mode);
+
 /* Device memory of simulators and batches comes from a stream-ordered memory
  * pool per device, which keeps freed blocks mapped for the next simulator (as
  * a caching allocator does).  This returns the device's unused cached blocks

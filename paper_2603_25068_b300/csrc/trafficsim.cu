@@ -118,6 +118,11 @@ struct sim_ctx {
     // reverse pass: the merge/choice Jacobian kernel runs on a second stream
     cudaStream_t jstream = nullptr;
     cudaEvent_t ev_z = nullptr, ev_g = nullptr;
+    // ... and the segment recomputation on a third stream, double-buffered tape;
+    // the reverse kernels themselves on a high-priority stream
+    cudaStream_t rstream = nullptr, vstream = nullptr;
+    int recompute = SIM_RECOMPUTE_OVERLAP;
+    cudaEvent_t ev_r[2] = {nullptr, nullptr}, ev_b[2] = {nullptr, nullptr};
     DevSim d{};
     // sizes
     int V = 0, L = 0, N = 0, F = 0, Z = 0, n_od = 0, S = 0;
@@ -448,7 +453,9 @@ static bool use_persist(const sim_ctx *h) { return h->persist_ok && h->executor 
 
 // steps [t0, t1) (+ the observation-only pass at t1) in one cooperative launch
 // of d (tape: the recording kernel, d's tape pointers the bases of record 0)
-static int enqueue_persist_d(sim_ctx *h, const DevSim &d, int t0, int t1, int final_obs, bool tape) {
+static int enqueue_persist_d(sim_ctx *h, const DevSim &d, int t0, int t1, int final_obs, bool tape,
+                             cudaStream_t st = nullptr) {
+    if (!st) st = h->stream;
     PArgs a = h->pa;
     a.t0 = t0;
     a.t1 = t1;
@@ -456,12 +463,12 @@ static int enqueue_persist_d(sim_ctx *h, const DevSim &d, int t0, int t1, int fi
     a.S = h->S;
     a.bar_extra = h->bar_extra;
     h->bar_extra = 0;
-    CU(cudaMemsetAsync(a.W3, 0, (size_t)3 * h->L * sizeof(unsigned long long), h->stream));
-    CU(cudaMemsetAsync(a.bar, 0, sizeof(unsigned), h->stream));
+    CU(cudaMemsetAsync(a.W3, 0, (size_t)3 * h->L * sizeof(unsigned long long), st));
+    CU(cudaMemsetAsync(a.bar, 0, sizeof(unsigned), st));
     DevSim dd = d;
     void *args[2] = {(void *)&dd, (void *)&a};
     CU(cudaLaunchCooperativeKernel(tape ? (const void *)k_persist_tape : (const void *)k_persist, dim3(h->G), dim3(kPT),
-                                   args, h->persist_smem, h->stream));
+                                   args, h->persist_smem, st));
     return SIM_OK;
 }
 static int enqueue_persist(sim_ctx *h, int t0, int t1, int final_obs) {
@@ -738,11 +745,16 @@ static void release(sim_ctx *h) {
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     h->stream = nullptr;
     if (h->jstream) cudaStreamSynchronize(h->jstream);
-    if (h->ev_z) cudaEventDestroy(h->ev_z);
-    if (h->ev_g) cudaEventDestroy(h->ev_g);
+    if (h->rstream) cudaStreamSynchronize(h->rstream);
+    for (cudaEvent_t e : {h->ev_z, h->ev_g, h->ev_r[0], h->ev_r[1], h->ev_b[0], h->ev_b[1]})
+        if (e) cudaEventDestroy(e);
+    if (h->vstream) cudaStreamSynchronize(h->vstream);
     if (h->jstream) cudaStreamDestroy(h->jstream);
-    h->jstream = nullptr;
+    if (h->rstream) cudaStreamDestroy(h->rstream);
+    if (h->vstream) cudaStreamDestroy(h->vstream);
+    h->jstream = h->rstream = h->vstream = nullptr;
     h->ev_z = h->ev_g = nullptr;
+    h->ev_r[0] = h->ev_r[1] = h->ev_b[0] = h->ev_b[1] = nullptr;
 }
 
 extern "C" int sim_create(const sim_network *net, const sim_demand *dem, const sim_params *par,
@@ -796,11 +808,12 @@ static int ensure_T(sim_ctx *h, int T) {
 }
 
 // checkpoint s <-> dynamic state at the start of step s K (positions in buffer cur)
-static void ckpt_copy(sim_ctx *h, int s, int cur, bool save) {
+static void ckpt_copy(sim_ctx *h, int s, int cur, bool save, cudaStream_t st = nullptr) {
     const size_t L = h->L, S = h->S, V = h->V, N = h->N;
+    if (!st) st = h->stream;
     auto cp = [&](void *state, void *ck, size_t bytes) {
-        if (save) cudaMemcpyAsync(ck, state, bytes, cudaMemcpyDeviceToDevice, h->stream);
-        else cudaMemcpyAsync(state, ck, bytes, cudaMemcpyDeviceToDevice, h->stream);
+        if (save) cudaMemcpyAsync(ck, state, bytes, cudaMemcpyDeviceToDevice, st);
+        else cudaMemcpyAsync(state, ck, bytes, cudaMemcpyDeviceToDevice, st);
     };
     DevSim &d = h->d;
     cp(d.lq, h->ck.lq + s * L, L * sizeof(int4));
@@ -1089,7 +1102,11 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     // carve the shared workspace: one layout routine sizes it (from base 0)
     // and then hands out the sub-arrays (from the buffer)
     const int n_gw = (L + kGwLinks - 1) / kGwLinks;
+    // recomputation beside the reverse pass (two tape sets), or before it in
+    // one persistent recording launch per segment (one tape set)
+    const bool overlap = h->recompute != SIM_RECOMPUTE_SERIAL || !use_persist(h);
     BwdDev b = h->b;
+    BwdDev bt[2] = {h->b, h->b};         // the tape sets (by segment parity when overlapping)
     float2 *d_Cbar = nullptr, *d_Csuf = nullptr;
     double *d_gw_part = nullptr;
     float *d_dxT_w = nullptr, *d_gout = nullptr;
@@ -1100,13 +1117,16 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
             wp += (std::max<size_t>(n, 1) * sz + 255) & ~(size_t)255;
             return p;
         };
-        b.tpos = (float *)take((size_t)(K + 1) * S, sizeof(float));
-        b.tvid = (int *)take((size_t)(K + 1) * S, sizeof(int));
-        b.tlq = (int4 *)take((size_t)(K + 1) * L, sizeof(int4));
-        b.ttag = (int8_t *)take((size_t)K * S, 1);
-        b.tcrec = (int4 *)take((size_t)K * L, sizeof(int4));
-        b.tnrec = (int2 *)take((size_t)K * V, sizeof(int2));
-        b.tW = (unsigned long long *)take((size_t)K * L, sizeof(unsigned long long));
+        for (int ts = 0; ts < (overlap ? 2 : 1); ++ts) {
+            BwdDev &q = bt[ts];
+            q.tpos = (float *)take((size_t)(K + 1) * S, sizeof(float));
+            q.tvid = (int *)take((size_t)(K + 1) * S, sizeof(int));
+            q.tlq = (int4 *)take((size_t)(K + 1) * L, sizeof(int4));
+            q.ttag = (int8_t *)take((size_t)K * S, 1);
+            q.tcrec = (int4 *)take((size_t)K * L, sizeof(int4));
+            q.tnrec = (int2 *)take((size_t)K * V, sizeof(int2));
+            q.tW = (unsigned long long *)take((size_t)K * L, sizeof(unsigned long long));
+        }
         b.xbar = (float2 *)take(N, sizeof(float2));
         b.cursor = (int *)take(N, sizeof(int));
         b.rdup = (unsigned char *)take(N, 1);
@@ -1165,40 +1185,85 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
 
     const int gS = (std::max(S, L) + 255) / 256, gLV = (L + V + 255) / 256;
     if (!h->jstream) {
-        CU(cudaStreamCreateWithFlags(&h->jstream, cudaStreamNonBlocking));
+        int lo = 0, hi = 0;
+        CU(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CU(cudaStreamCreateWithPriority(&h->vstream, cudaStreamNonBlocking, hi));
+        CU(cudaStreamCreateWithPriority(&h->jstream, cudaStreamNonBlocking, hi));
+        CU(cudaStreamCreateWithPriority(&h->rstream, cudaStreamNonBlocking, lo));
         CU(cudaEventCreateWithFlags(&h->ev_z, cudaEventDisableTiming));
         CU(cudaEventCreateWithFlags(&h->ev_g, cudaEventDisableTiming));
+        for (cudaEvent_t *e : {&h->ev_r[0], &h->ev_r[1], &h->ev_b[0], &h->ev_b[1]})
+            CU(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     }
-    CU(cudaEventRecord(h->ev_g, h->stream));              // nothing to wait for at the first step
-    for (int sg = nseg - 1; sg >= 0; --sg) {
-        const int t0 = sg * K, t1 = std::min(T, t0 + K);
-        ckpt_copy(h, sg, t0 & 1, false);
-        CU(cudaMemsetAsync((t0 & 1) ? h->d.W1 : h->d.W0, 0, (size_t)L * sizeof(unsigned long long), h->stream));
-        if (use_persist(h)) {                      // one recording launch for the segment
-            dr.tag_tape = b.ttag;
-            dr.tape_pos = b.tpos;
-            dr.tape_vid = b.tvid;
-            dr.tape_lq = b.tlq;
-            dr.tape_crec = b.tcrec;
-            dr.tape_nrec = b.tnrec;
-            dr.tape_W = b.tW;
-            TRY(enqueue_persist_d(h, dr, t0, t1, 0, true));
-        } else {
-            for (int t = t0; t < t1; ++t) {        // each step writes its own tape record
-                const size_t r = (size_t)(t - t0);
-                dr.tag_tape = b.ttag + r * S;
-                dr.tape_pos = b.tpos + r * S;
-                dr.tape_vid = b.tvid + r * S;
-                dr.tape_lq = b.tlq + r * L;
-                dr.tape_crec = b.tcrec + r * L;
-                dr.tape_nrec = b.tnrec + r * V;
-                dr.tape_W = b.tW + r * L;
-                k_step_a_tape<<<dr.nblk, kBlockA, smem_a, h->stream>>>(dr, t);
-                k_step_b<<<(L + V + 255) / 256, 256, 0, h->stream>>>(dr, t);
-            }
+    // Segments from the last.  The tape has two sets, by segment parity.  The
+    // recomputation of segment s - 1 (on the third stream, two-kernel executor,
+    // whose blocks share SMs with the reverse kernels) runs beside the reverse
+    // pass of segment s, which reads only its tape set and static data.  A set
+    // is rewritten only after the reverse pass that read it (ev_b); a reverse
+    // pass starts only once its set is recorded (ev_r).
+    auto with_set = [&](int ts) {
+        if (!overlap) ts = 0;
+        BwdDev q = b;
+        q.tpos = bt[ts].tpos; q.tvid = bt[ts].tvid; q.tlq = bt[ts].tlq; q.ttag = bt[ts].ttag;
+        q.tcrec = bt[ts].tcrec; q.tnrec = bt[ts].tnrec; q.tW = bt[ts].tW;
+        return q;
+    };
+    auto recompute = [&](int sg) -> int {
+        const int t0 = sg * K, t1 = std::min(T, t0 + K), ts = sg & 1;
+        const cudaStream_t rs = h->rstream;
+        const BwdDev q = with_set(ts);
+        CU(cudaStreamWaitEvent(rs, h->ev_b[ts], 0));
+        ckpt_copy(h, sg, t0 & 1, false, rs);
+        CU(cudaMemsetAsync((t0 & 1) ? h->d.W1 : h->d.W0, 0, (size_t)L * sizeof(unsigned long long), rs));
+        DevSim dq = dr;
+        for (int t = t0; t < t1; ++t) {            // each step writes its own tape record
+            const size_t r = (size_t)(t - t0);
+            dq.tag_tape = q.ttag + r * S;
+            dq.tape_pos = q.tpos + r * S;
+            dq.tape_vid = q.tvid + r * S;
+            dq.tape_lq = q.tlq + r * L;
+            dq.tape_crec = q.tcrec + r * L;
+            dq.tape_nrec = q.tnrec + r * V;
+            dq.tape_W = q.tW + r * L;
+            k_step_a_tape<<<dq.nblk, kBlockA, smem_a, rs>>>(dq, t);
+            k_step_b<<<(L + V + 255) / 256, 256, 0, rs>>>(dq, t);
         }
-        dr.tape_W = nullptr;
-        k_tape_pre<<<gS, 256, 0, h->stream>>>(dr, b, t1 - t0, t1 & 1);    // state at the end of the segment
+        dq.tape_W = nullptr;
+        k_tape_pre<<<gS, 256, 0, rs>>>(dq, q, t1 - t0, t1 & 1);        // state at the end of the segment
+        CU(cudaEventRecord(h->ev_r[ts], rs));
+        return SIM_OK;
+    };
+    // the initial adjoints are read before any recomputation changes the state
+    CU(cudaEventRecord(h->ev_b[0], h->stream));
+    CU(cudaEventRecord(h->ev_b[1], h->stream));
+    CU(cudaEventRecord(h->ev_g, h->stream));              // nothing to wait for at the first step
+    const cudaStream_t vs = h->vstream;                   // the reverse chain, high priority
+    CU(cudaStreamWaitEvent(vs, h->ev_g, 0));
+    // one recording launch of the persistent executor for segment sg, on the
+    // reverse chain's stream (serial mode)
+    auto recompute_serial = [&](int sg) -> int {
+        const int t0 = sg * K, t1 = std::min(T, t0 + K);
+        const BwdDev q = with_set(0);
+        ckpt_copy(h, sg, t0 & 1, false, vs);
+        CU(cudaMemsetAsync((t0 & 1) ? h->d.W1 : h->d.W0, 0, (size_t)L * sizeof(unsigned long long), vs));
+        DevSim dq = dr;
+        dq.tag_tape = q.ttag; dq.tape_pos = q.tpos; dq.tape_vid = q.tvid; dq.tape_lq = q.tlq;
+        dq.tape_crec = q.tcrec; dq.tape_nrec = q.tnrec; dq.tape_W = q.tW;
+        TRY(enqueue_persist_d(h, dq, t0, t1, 0, true, vs));
+        dq.tape_W = nullptr;
+        k_tape_pre<<<gS, 256, 0, vs>>>(dq, q, t1 - t0, t1 & 1);
+        return SIM_OK;
+    };
+    if (overlap) TRY(recompute(nseg - 1));
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int t0 = sg * K, t1 = std::min(T, t0 + K), ts = overlap ? (sg & 1) : 0;
+        if (overlap) {
+            if (sg > 0) TRY(recompute(sg - 1));
+            CU(cudaStreamWaitEvent(vs, h->ev_r[ts], 0));
+        } else {
+            TRY(recompute_serial(sg));
+        }
+        const BwdDev q = with_set(ts);
         // Per step: merge kernel, then car-following on the main stream; the
         // Jacobian kernel of step t on the second stream after the merge kernel
         // of step t, beside car-following of t and the merge kernel of t - 1.
@@ -1207,18 +1272,21 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         for (int t = t1 - 1; t >= t0; --t) {
             const int rec = t - t0;
             if ((t + 1) % obs == 0 || t + 1 == T)
-                k_bwd_obs<<<(L * 32 + 255) / 256, 256, 0, h->stream>>>(dr, b, rec + 1, t / obs);
-            k_bwd_node_z<<<gLV, 256, 0, h->stream>>>(dr, b, t, rec, t / obs);
-            CU(cudaEventRecord(h->ev_z, h->stream));
-            CU(cudaStreamWaitEvent(h->stream, h->ev_g, 0));
-            k_bwd_cf<<<(L + kCfLinks - 1) / kCfLinks, kCfThreads, 0, h->stream>>>(dr, b, rec, t);
+                k_bwd_obs<<<(L * 32 + 255) / 256, 256, 0, vs>>>(dr, q, rec + 1, t / obs);
+            k_bwd_node_z<<<gLV, 256, 0, vs>>>(dr, q, t, rec, t / obs);
+            CU(cudaEventRecord(h->ev_z, vs));
+            CU(cudaStreamWaitEvent(vs, h->ev_g, 0));
+            k_bwd_cf<<<(L + kCfLinks - 1) / kCfLinks, kCfThreads, 0, vs>>>(dr, q, rec, t);
             CU(cudaStreamWaitEvent(h->jstream, h->ev_z, 0));
-            k_bwd_node_g<<<gLV, 256, 0, h->jstream>>>(dr, b, t, rec);
+            k_bwd_node_g<<<gLV, 256, 0, h->jstream>>>(dr, q, t, rec);
             CU(cudaEventRecord(h->ev_g, h->jstream));
         }
-        CU(cudaStreamWaitEvent(h->stream, h->ev_g, 0));     // the tape is rewritten next
+        CU(cudaStreamWaitEvent(vs, h->ev_g, 0));
+        CU(cudaEventRecord(h->ev_b[ts], vs));              // this tape set may be rewritten
         CU(cudaGetLastError());
     }
+    CU(cudaEventRecord(h->ev_g, vs));
+    CU(cudaStreamWaitEvent(h->stream, h->ev_g, 0));       // the handle's stream resumes after the chain
     // parameter gradients
     float *go = d_gout;
     float *gu = go, *gk = go + L, *ga = go + 2 * L, *gbeta = go + 3 * L, *gc = go + 4 * L, *gw = go + 5 * L;
@@ -1432,6 +1500,13 @@ extern "C" int sim_test_barrier_timeout(sim_handle h, int32_t missing) {
     if (!h || missing < 0) return SIM_EINVAL;
     if (!h->persist_ok) return fail(h, SIM_EINVAL, "persistent executor unavailable: " + h->persist_why);
     h->bar_extra = missing;
+    return SIM_OK;
+}
+
+extern "C" int sim_set_recompute(sim_handle h, int32_t mode) {
+    if (!h) return SIM_EINVAL;
+    if (mode != SIM_RECOMPUTE_OVERLAP && mode != SIM_RECOMPUTE_SERIAL) return fail(h, SIM_EINVAL, "unknown recompute mode");
+    h->recompute = mode;
     return SIM_OK;
 }
 

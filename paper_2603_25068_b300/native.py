@@ -87,6 +87,7 @@ SIGNATURES = {
     "sim_batch_rollout": (C.c_int, [P, C.c_int32]),
     "sim_batch_destroy": (C.c_int, [P]),
     "sim_release_cached_memory": (C.c_int, [C.c_int32]),
+    "sim_set_recompute": (C.c_int, [P, C.c_int32]),
     "sim_batch_set_executor": (C.c_int, [P, C.c_int32]),
     "sim_batch_get_executor": (C.c_int32, [P]),
     "sim_batch_test_barrier_timeout": (C.c_int, [P, C.c_int32]),

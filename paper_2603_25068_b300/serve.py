@@ -135,7 +135,7 @@ class Engine:
             return 0.0
         sc = req.scenario
         slots = float(np.sum(np.floor(sc.length.astype(np.float64) * sc.kappa / sc.dn) + 2))
-        return 9.0 * (self.ckpt_every + 1) * slots + 16.0 * sc.N * self.route_cap
+        return 18.0 * (self.ckpt_every + 1) * slots + 16.0 * sc.N * self.route_cap    # two tape sets
 
     def _bwd_worker(self):
         torch = self.torch

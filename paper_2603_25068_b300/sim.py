@@ -104,6 +104,14 @@ class Simulator:
     def device_bytes(self):
         return self.lib.sim_device_bytes(self.h)
 
+    RECOMPUTE = {"overlap": 0, "serial": 1}
+
+    def set_recompute(self, name: str):
+        """Segment recomputation of the reverse pass: "overlap" (beside the
+        reverse kernels, two tape sets) or "serial" (one persistent recording
+        launch per segment, one tape set).  Gradients do not depend on it."""
+        self._check(self.lib.sim_set_recompute(self.h, self.RECOMPUTE[name]))
+
     EXECUTORS = {"auto": 0, "step": 1, "persistent": 2}
 
     def set_executor(self, name: str):

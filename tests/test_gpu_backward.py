@@ -24,9 +24,10 @@ def Simulator():
     return Simulator
 
 
-def compare(Simulator, sc, K, seed=0, with_xT=True, rtol=1e-4):
+def compare(Simulator, sc, K, seed=0, with_xT=True, rtol=1e-4, recompute="overlap"):
     rng = np.random.default_rng(seed)
     g = Simulator(sc, ckpt_every=K, route_cap=64)
+    g.set_recompute(recompute)
     out = g.rollout()
     nb = out["counts"].shape[0]
     ybar = rng.normal(size=(nb, sc.L)).astype(np.float32)
@@ -44,10 +45,11 @@ def compare(Simulator, sc, K, seed=0, with_xT=True, rtol=1e-4):
     return go
 
 
+@pytest.mark.parametrize("recompute", ["overlap", "serial"])
 @pytest.mark.parametrize("K", [300, 7])
-def test_backward_tiny_grid(Simulator, K):
+def test_backward_tiny_grid(Simulator, K, recompute):
     sc = S.tiny_grid(T=150).copy(obs_every=50)
-    compare(Simulator, sc, K)
+    compare(Simulator, sc, K, recompute=recompute)
 
 
 @pytest.mark.parametrize("seed", [1, 2, 7])
@@ -57,9 +59,10 @@ def test_backward_dense_small(Simulator, seed):
     assert np.count_nonzero(go["alpha"]) > 0 and np.count_nonzero(go["beta"]) > 0
 
 
-def test_backward_city_small(Simulator):
+@pytest.mark.parametrize("recompute", ["overlap", "serial"])
+def test_backward_city_small(Simulator, recompute):
     sc = S.city_small(T=240).copy(obs_every=60)
-    compare(Simulator, sc, 60, seed=5, with_xT=False)
+    compare(Simulator, sc, 60, seed=5, with_xT=False, recompute=recompute)
 
 
 def test_backward_tg_toy(Simulator):
