@@ -122,7 +122,7 @@ struct sim_ctx {
     // the reverse kernels themselves on a high-priority stream
     cudaStream_t rstream = nullptr, vstream = nullptr;
     int recompute = SIM_RECOMPUTE_OVERLAP;
-    cudaEvent_t ev_r[2] = {nullptr, nullptr}, ev_b[2] = {nullptr, nullptr};
+    cudaEvent_t ev_r[2] = {nullptr, nullptr}, ev_b[2] = {nullptr, nullptr}, ev_gr[2] = {nullptr, nullptr};
     DevSim d{};
     // sizes
     int V = 0, L = 0, N = 0, F = 0, Z = 0, n_od = 0, S = 0;
@@ -746,7 +746,7 @@ static void release(sim_ctx *h) {
     h->stream = nullptr;
     if (h->jstream) cudaStreamSynchronize(h->jstream);
     if (h->rstream) cudaStreamSynchronize(h->rstream);
-    for (cudaEvent_t e : {h->ev_z, h->ev_g, h->ev_r[0], h->ev_r[1], h->ev_b[0], h->ev_b[1]})
+    for (cudaEvent_t e : {h->ev_z, h->ev_g, h->ev_r[0], h->ev_r[1], h->ev_b[0], h->ev_b[1], h->ev_gr[0], h->ev_gr[1]})
         if (e) cudaEventDestroy(e);
     if (h->vstream) cudaStreamSynchronize(h->vstream);
     if (h->jstream) cudaStreamDestroy(h->jstream);
@@ -754,7 +754,7 @@ static void release(sim_ctx *h) {
     if (h->vstream) cudaStreamDestroy(h->vstream);
     h->jstream = h->rstream = h->vstream = nullptr;
     h->ev_z = h->ev_g = nullptr;
-    h->ev_r[0] = h->ev_r[1] = h->ev_b[0] = h->ev_b[1] = nullptr;
+    h->ev_r[0] = h->ev_r[1] = h->ev_b[0] = h->ev_b[1] = h->ev_gr[0] = h->ev_gr[1] = nullptr;
 }
 
 extern "C" int sim_create(const sim_network *net, const sim_demand *dem, const sim_params *par,
@@ -1133,8 +1133,8 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         b.eadj = (float2 *)take((size_t)N * h->route_cap, sizeof(float2));
         b.gu = (double *)take(L, sizeof(double)); b.gs = (double *)take(L, sizeof(double));
         b.ga = (double *)take(L, sizeof(double)); b.gU = (double *)take(L, sizeof(double));
-        b.gG = (double *)take(L, sizeof(double)); b.Z = (double *)take(2 * (size_t)L, sizeof(double));
-        b.SA = (double *)take(2 * (size_t)L, sizeof(double));
+        b.gG = (double *)take(L, sizeof(double)); b.Z = (double *)take(3 * (size_t)L, sizeof(double));
+        b.SA = (double *)take(3 * (size_t)L, sizeof(double));
         b.gao = (double *)take(1, sizeof(double));
         b.glam = (double *)take(std::max(h->n_od, 1), sizeof(double));
         b.ebuf = (float *)take(2 * ((size_t)L + V), sizeof(float));
@@ -1173,8 +1173,8 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     CU(cudaMemsetAsync(b.gao, 0, sizeof(double), h->stream));
     CU(cudaMemsetAsync(b.glam, 0, (size_t)std::max(b.n_od, 1) * sizeof(double), h->stream));
     CU(cudaMemsetAsync(b.eadj, 0, (size_t)N * h->route_cap * sizeof(float2), h->stream));
-    CU(cudaMemsetAsync(b.Z, 0, 2 * (size_t)L * sizeof(double), h->stream));
-    CU(cudaMemsetAsync(b.SA, 0, 2 * (size_t)L * sizeof(double), h->stream));
+    CU(cudaMemsetAsync(b.Z, 0, 3 * (size_t)L * sizeof(double), h->stream));
+    CU(cudaMemsetAsync(b.SA, 0, 3 * (size_t)L * sizeof(double), h->stream));
     k_bwd_init<<<(N + 255) / 256, 256, 0, h->stream>>>(h->d, b, dxT);
     k_route_scan<<<(int)(((size_t)N * 32 + 255) / 256), 256, 0, h->stream>>>(N, b);
     // recomputation: no route log, counters into a scratch array
@@ -1192,7 +1192,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         CU(cudaStreamCreateWithPriority(&h->rstream, cudaStreamNonBlocking, lo));
         CU(cudaEventCreateWithFlags(&h->ev_z, cudaEventDisableTiming));
         CU(cudaEventCreateWithFlags(&h->ev_g, cudaEventDisableTiming));
-        for (cudaEvent_t *e : {&h->ev_r[0], &h->ev_r[1], &h->ev_b[0], &h->ev_b[1]})
+        for (cudaEvent_t *e : {&h->ev_r[0], &h->ev_r[1], &h->ev_b[0], &h->ev_b[1], &h->ev_gr[0], &h->ev_gr[1]})
             CU(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     }
     // Segments from the last.  The tape has two sets, by segment parity.  The
@@ -1236,8 +1236,11 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     // the initial adjoints are read before any recomputation changes the state
     CU(cudaEventRecord(h->ev_b[0], h->stream));
     CU(cudaEventRecord(h->ev_b[1], h->stream));
-    CU(cudaEventRecord(h->ev_g, h->stream));              // nothing to wait for at the first step
+    CU(cudaEventRecord(h->ev_g, h->stream));              // nothing to wait for at the first steps
+    CU(cudaEventRecord(h->ev_gr[0], h->stream));
+    CU(cudaEventRecord(h->ev_gr[1], h->stream));
     const cudaStream_t vs = h->vstream;                   // the reverse chain, high priority
+    const int nlb = (L + kCfLinks - 1) / kCfLinks, npb = (V + nlb - 1) / nlb;
     CU(cudaStreamWaitEvent(vs, h->ev_g, 0));
     // one recording launch of the persistent executor for segment sg, on the
     // reverse chain's stream (serial mode)
@@ -1264,23 +1267,23 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
             TRY(recompute_serial(sg));
         }
         const BwdDev q = with_set(ts);
-        // Per step: merge kernel, then car-following on the main stream; the
-        // Jacobian kernel of step t on the second stream after the merge kernel
-        // of step t, beside car-following of t and the merge kernel of t - 1.
-        // Car-following of t clears the merge sums that the Jacobian kernel of
-        // t + 1 reads, so it waits for that kernel (ev_g, recorded a step earlier).
+        // Per step on the chain's stream: the merge adjoint and car-following in
+        // one launch; then the Jacobian kernel of the step on the second stream,
+        // beside the next steps.  The merge sums of step t live in buffer t mod
+        // 3 and step t clears buffer t + 2, which the Jacobian kernel of step
+        // t + 2 read: step t waits for it (ev_gr by step parity).
         for (int t = t1 - 1; t >= t0; --t) {
             const int rec = t - t0;
             if ((t + 1) % obs == 0 || t + 1 == T)
                 k_bwd_obs<<<(L * 32 + 255) / 256, 256, 0, vs>>>(dr, q, rec + 1, t / obs);
-            k_bwd_node_z<<<gLV, 256, 0, vs>>>(dr, q, t, rec, t / obs);
+            CU(cudaStreamWaitEvent(vs, h->ev_gr[t & 1], 0));
+            k_bwd_step<<<nlb, kBwdThreads, 0, vs>>>(dr, q, rec, t, t / obs, npb);
             CU(cudaEventRecord(h->ev_z, vs));
-            CU(cudaStreamWaitEvent(vs, h->ev_g, 0));
-            k_bwd_cf<<<(L + kCfLinks - 1) / kCfLinks, kCfThreads, 0, vs>>>(dr, q, rec, t);
             CU(cudaStreamWaitEvent(h->jstream, h->ev_z, 0));
             k_bwd_node_g<<<gLV, 256, 0, h->jstream>>>(dr, q, t, rec);
-            CU(cudaEventRecord(h->ev_g, h->jstream));
+            CU(cudaEventRecord(h->ev_gr[t & 1], h->jstream));
         }
+        CU(cudaEventRecord(h->ev_g, h->jstream));          // the segment's Jacobian kernels read its tape
         CU(cudaStreamWaitEvent(vs, h->ev_g, 0));
         CU(cudaEventRecord(h->ev_b[ts], vs));              // this tape set may be rewritten
         CU(cudaGetLastError());

@@ -96,8 +96,8 @@ struct BwdDev {
     double *gu, *gs, *ga, *gU, *gG;   // [L]
     double *gao;                 // [1]
     double *glam;                // [n_od]
-    double *Z, *SA;              // [2 L] per-target merge sums, by step parity (the
-                                 // reverse car-following kernel clears the other parity)
+    double *Z, *SA;              // [3 L] per-target merge sums of step t in buffer t mod 3
+                                 // (step t clears buffer t + 2, read two steps earlier)
     float *ebuf;                 // [2 (L + V)] per-source merge weight, by step parity
     float2 *abuf;                // [2 (L + V)] per-source abar (the Jacobian kernel of
                                  // step t runs beside the merge kernel of step t - 1)
@@ -231,45 +231,55 @@ __device__ __forceinline__ Cand load_cand(const DevSim &d, const BwdDev &b, int 
     return c;
 }
 
-// (2a) merge candidates of step t: abar, softmax weight, per-target sums.  The
-// candidate's record first; then, in one round, the target's merge word and
-// everything that depends on the vehicle only.
-__global__ void k_bwd_node_z(DevSim d, BwdDev b, int t, int rec, int bin0) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d.L + d.V) return;
-    int v, tgt;
-    float x, alpha;
+// (2a) merge candidate i of step t (link, or L + origin node): abar, merge-
+// softmax weight, per-target sums (buffer t mod 3), the winner's entry
+// adjoint and cursor, the demand weight of exits.  z_load issues the record,
+// then in one round the target's merge word and everything that depends on the
+// vehicle only (its adjoint at t + 1 among them); z_finish does the rest.
+struct ZLoad {
+    float2 xv;                   // the vehicle's adjoint at t + 1
+    unsigned long long wt;       // the target's merge word
+    int v, tgt, cur, dup, k2;
+    float x, alpha, csuf;
+};
+
+__device__ __forceinline__ bool z_load(const DevSim &d, const BwdDev &b, int i, int rec, int bin0, ZLoad &z) {
     if (i < d.L) {
         const int4 r = b.tcrec[(size_t)rec * d.L + i];
-        v = r.x; tgt = r.y; x = __int_as_float(r.w); alpha = d.alpha[i];
+        z.v = r.x; z.tgt = r.y; z.x = __int_as_float(r.w); z.alpha = d.alpha[i];
     } else {
         const int2 r = b.tnrec[(size_t)rec * d.V + (i - d.L)];
-        v = r.x; tgt = r.y; x = 0.0f; alpha = d.alpha[d.L];
+        z.v = r.x; z.tgt = r.y; z.x = 0.0f; z.alpha = d.alpha[d.L];
     }
-    if (v < 0) return;
-    const unsigned long long wt = tgt >= 0 ? b.tW[(size_t)rec * d.L + tgt] : 0ull;
-    const int cur = b.cursor[v];
-    const float2 xv = b.xbar[v];
-    const int dup = b.rdup[v];
-    const int k2 = b.od[v];
-    const float csuf = i < d.L ? b.Csuf[(size_t)bin0 * d.L + i].x : 0.0f;
-    const bool won = tgt >= 0 && wt != 0ull && merge_vid(wt) == v;
+    if (z.v < 0) return false;
+    z.wt = z.tgt >= 0 ? b.tW[(size_t)rec * d.L + z.tgt] : 0ull;
+    z.cur = b.cursor[z.v];
+    z.xv = b.xbar[z.v];
+    z.dup = b.rdup[z.v];
+    z.k2 = b.od[z.v];
+    z.csuf = i < d.L ? b.Csuf[(size_t)bin0 * d.L + i].x : 0.0f;
+    return true;
+}
+
+__device__ __forceinline__ void z_finish(const DevSim &d, const BwdDev &b, int i, int t, const ZLoad &z) {
+    const int v = z.v, tgt = z.tgt, cur = z.cur;
+    const bool won = tgt >= 0 && z.wt != 0ull && merge_vid(z.wt) == v;
     const bool exits = i < d.L && (won || tgt == kTgtSink);         // an exit from link i
-    const float lam = exits ? b.od_lambda[k2] : 1.0f;
+    const float lam = exits ? b.od_lambda[z.k2] : 1.0f;
     if (won) {                   // adjoint right after this entry: the latest one not yet undone
         b.cursor[v] = cur - 1;
-        if (cur >= 0) b.eadj[(size_t)v * b.cap + cur] = xv;
+        if (cur >= 0) b.eadj[(size_t)v * b.cap + cur] = z.xv;
     }
     if (tgt >= 0) {
         // (alpha + g') is the merge key of the forward step; the largest key of
         // the target is in its merge word
-        const float key = __fadd_rn(alpha, gumbel(d.key0, d.key1, v, t, 1, 0));
-        const float e = expf(__fmul_rn(__fsub_rn(key, merge_key_of(wt)), b.inv_tau));
+        const float key = __fadd_rn(z.alpha, gumbel(d.key0, d.key1, v, t, 1, 0));
+        const float e = expf(__fmul_rn(__fsub_rn(key, merge_key_of(z.wt)), b.inv_tau));
         float2 Enew, Xold;
         if (won) {
-            Enew = xv;
+            Enew = z.xv;
             Xold = make_float2(0.0f, 0.0f);
-            if (i < d.L && cur >= 0 && dup) {                    // next re-entry into the source link
+            if (i < d.L && cur >= 0 && z.dup) {                  // next re-entry into the source link
                 const int k = route_find(b, v, cur + 1, [&](int, int l) { return l == i; });
                 if (k >= 0) Xold = b.eadj[(size_t)v * b.cap + k];
             }
@@ -277,17 +287,17 @@ __global__ void k_bwd_node_z(DevSim d, BwdDev b, int t, int rec, int bin0) {
             Enew = make_float2(0.0f, 0.0f);
             const int k = route_find(b, v, cur + 1, [&](int s, int l) { return s > t && l == tgt; });
             if (k >= 0) Enew = b.eadj[(size_t)v * b.cap + k];
-            Xold = xv;
+            Xold = z.xv;
         }
-        const float2 abar = ff_sub(ff_mul_f(ff_sub(Enew, Xold), d.M), ff_mul_f(Xold, x));
+        const float2 abar = ff_sub(ff_mul_f(ff_sub(Enew, Xold), d.M), ff_mul_f(Xold, z.x));
         const size_t eo = (size_t)(t & 1) * (d.L + d.V) + i;
         b.ebuf[eo] = e;
         b.abuf[eo] = abar;
-        const size_t zo = (size_t)(t & 1) * d.L + tgt;
+        const size_t zo = (size_t)(t % 3) * d.L + tgt;
         atomicAdd(&b.Z[zo], (double)e);
         atomicAdd(&b.SA[zo], ff_to_double(ff_mul_f(abar, e)));
     }
-    if (exits) atomicAdd(&b.glam[k2], (double)__fdiv_rn(csuf, lam));
+    if (exits) atomicAdd(&b.glam[z.k2], (double)__fdiv_rn(z.csuf, lam));
 }
 
 // (2b) merge and link-choice Jacobians of step t
@@ -296,7 +306,7 @@ __global__ void k_bwd_node_g(DevSim d, BwdDev b, int t, int rec) {
     if (i >= d.L + d.V) return;
     const Cand c = load_cand(d, b, i, rec);
     if (c.vid < 0 || c.tgt < 0) return;
-    const size_t zo = (size_t)(t & 1) * d.L + c.tgt;
+    const size_t zo = (size_t)(t % 3) * d.L + c.tgt;
     const float2 Z = ff_from_double(b.Z[zo]);
     const float2 S = ff_div(ff_from_double(b.SA[zo]), Z);            // softmax-weighted mean of abar
     const size_t eo = (size_t)(t & 1) * (d.L + d.V) + i;
@@ -387,24 +397,37 @@ __global__ void k_bwd_node_g(DevSim d, BwdDev b, int t, int rec) {
     }
 }
 
-// (3) car-following of step (t0 + rec): a block takes kCfLinks consecutive
-// links, and each of its threads kCfE consecutive positions of the links'
-// concatenated queues (leader first), so that every tape and adjoint load of a
-// pass is in flight at once.  Vehicle k's adjoint at time t is its own adjoint
-// at t + 1 unless its update was congested (then x' depended on the leader
-// only), plus its follower's adjoint when the follower was congested (the
-// follower's headway used x_k).  The follower's values come from the same
-// thread, from the next thread (shared memory) or, for the last position of a
-// pass, from a look-ahead load.  Each adjoint is read by one thread, which
-// then writes it.  The per-link parameter sums (free -> u: x' = x + u dt,
-// congested -> s) are reduced in a fixed order.  The block also clears its
-// links' per-target merge sums of the other step parity.
-constexpr int kCfThreads = 256;
+// (2a + 3) merge adjoint and car-following of step (t0 + rec), one launch.
+// A block takes kCfLinks consecutive links and npb origin queues:
+//   * car-following warps: each thread takes kCfE consecutive positions of the
+//     links' concatenated queues (leader first), so that every tape and
+//     adjoint load of a pass is in flight at once.  Vehicle k's adjoint at
+//     time t is its own adjoint at t + 1 unless its update was congested (then
+//     x' depended on the leader only), plus its follower's adjoint when the
+//     follower was congested (the follower's headway used x_k).  The
+//     follower's values come from the same thread, from the next thread
+//     (shared memory) or, for the last position of a pass, from a look-ahead
+//     load.  The per-link parameter sums (free -> u: x' = x + u dt, congested
+//     -> s) are reduced in a fixed order.  These warps synchronise among
+//     themselves with a named barrier, and clear their links' merge sums of
+//     buffer t + 2.
+//   * merge warps: one thread per link candidate and per origin-queue
+//     candidate (z_load, z_finish).
+// A link's candidate is its leader, whose adjoint car-following overwrites, so
+// the two groups meet once, at a block barrier before the first write: by then
+// every candidate's adjoint at t + 1 has been read.  The merge warps then
+// finish their route-log chains while car-following computes and writes.
+constexpr int kCfWarps = 5, kZWarps = 3;
+constexpr int kCfThreads = 32 * kCfWarps;
+constexpr int kBwdThreads = 32 * (kCfWarps + kZWarps);
 constexpr int kCfLinks = 64;
+constexpr int kZNodeThreads = 32 * kZWarps - kCfLinks;
 constexpr int kCfE = 8;
 constexpr int kCfPass = kCfThreads * kCfE;
 
-__global__ void __launch_bounds__(kCfThreads) k_bwd_cf(DevSim d, BwdDev b, int rec, int t) {
+__device__ __forceinline__ void cf_bar() { asm volatile("bar.sync 1, %0;" :: "n"(kCfThreads) : "memory"); }
+
+__global__ void __launch_bounds__(kBwdThreads) k_bwd_step(DevSim d, BwdDev b, int rec, int t, int bin0, int npb) {
     __shared__ int4 sq[kCfLinks];
     __shared__ int sbase[kCfLinks], scap[kCfLinks], off[kCfLinks + 1];
     __shared__ int ftag[kCfThreads];
@@ -414,10 +437,26 @@ __global__ void __launch_bounds__(kCfThreads) k_bwd_cf(DevSim d, BwdDev b, int r
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int j0 = blockIdx.x * kCfLinks;
     const int nl = min(kCfLinks, d.L - j0);
+    if (tid >= kCfThreads) {                            // merge warps
+        const int zi = tid - kCfThreads;
+        ZLoad z;
+        const bool has = zi < nl && z_load(d, b, j0 + zi, rec, bin0, z);
+        if (has) asm volatile("" :: "f"(z.xv.x), "f"(z.xv.y));   // the adjoint is in before the barrier
+        __syncthreads();
+        if (has) z_finish(d, b, j0 + zi, t, z);
+        if (zi >= kCfLinks) {                           // origin queues (not touched by car-following)
+            const int n1 = min(d.V, (blockIdx.x + 1) * npb);
+            for (int n = blockIdx.x * npb + zi - kCfLinks; n < n1; n += kZNodeThreads) {
+                ZLoad zn;
+                if (z_load(d, b, d.L + n, rec, bin0, zn)) z_finish(d, b, d.L + n, t, zn);
+            }
+        }
+        return;
+    }
     if (tid < kCfLinks) {                               // queue states of the block's links
         if (tid < nl) {
             const int j = j0 + tid;
-            const size_t zo = (size_t)((t + 1) & 1) * d.L + j;     // merge sums of step t - 1 start from zero
+            const size_t zo = (size_t)((t + 2) % 3) * d.L + j;      // merge sums of step t - 1 start from zero
             b.Z[zo] = 0.0;
             b.SA[zo] = 0.0;
             const int4 q = b.tlq[(size_t)rec * d.L + j];
@@ -429,7 +468,7 @@ __global__ void __launch_bounds__(kCfThreads) k_bwd_cf(DevSim d, BwdDev b, int r
         lsu[tid] = 0.0f;
         lss[tid] = 0.0f;
     }
-    __syncthreads();
+    cf_bar();
     if (tid < 32) {                                     // exclusive scan of the queue lengths (warp 0)
         const int a = tid < nl ? sq[tid].y : 0, c = tid + 32 < nl ? sq[tid + 32].y : 0;
         int ia = a, ic = c;
@@ -443,9 +482,8 @@ __global__ void __launch_bounds__(kCfThreads) k_bwd_cf(DevSim d, BwdDev b, int r
         off[tid + 32] = ta + ic - c;
         if (tid == 31) off[kCfLinks] = ta + ic;
     }
-    __syncthreads();
+    cf_bar();
     const int total = off[kCfLinks];
-    if (total == 0) return;
     const float dt = d.dt;
     const int *tvid = b.tvid + (size_t)rec * b.S;
     const int8_t *ttag = b.ttag + (size_t)rec * b.S;
@@ -454,6 +492,7 @@ __global__ void __launch_bounds__(kCfThreads) k_bwd_cf(DevSim d, BwdDev b, int r
         if (idx >= scap[li]) idx -= scap[li];
         return sbase[li] + idx;
     };
+    bool met = false;                                   // the block barrier with the merge warps
     for (int base = 0; base < total; base += kCfPass) {
         const int e0 = base + tid * kCfE;
         int v[kCfE], tag[kCfE], lk[kCfE];
@@ -485,7 +524,12 @@ __global__ void __launch_bounds__(kCfThreads) k_bwd_cf(DevSim d, BwdDev b, int r
         const float2 gx = vx >= 0 ? b.xbar[vx] : make_float2(0.0f, 0.0f);
         ftag[tid] = tag[0];
         fg[tid] = g[0];
-        __syncthreads();
+        if (!met) {
+            __syncthreads();
+            met = true;
+        } else {
+            cf_bar();
+        }
         const int ntag = tid + 1 < kCfThreads ? ftag[tid + 1] : tx;
         const float2 ng = tid + 1 < kCfThreads ? fg[tid + 1] : gx;
 #pragma unroll
@@ -500,8 +544,8 @@ __global__ void __launch_bounds__(kCfThreads) k_bwd_cf(DevSim d, BwdDev b, int r
             cs[e - base] = (tag[u] == kTagCong) ? -g[u].x : 0.0f;
             if (v[u] >= 0) b.xbar[v[u]] = pre;
         }
-        __syncthreads();
-        for (int l = warp; l < nl; l += kCfThreads / 32) {    // per-link sums of the pass, fixed order
+        cf_bar();
+        for (int l = warp; l < nl; l += kCfWarps) {     // per-link sums of the pass, fixed order
             const int a = max(off[l], base) - base, z = min(off[l + 1], base + kCfPass) - base;
             float su = 0.0f, ss = 0.0f;
             for (int k = a + lane; k < z; k += 32) {
@@ -518,8 +562,9 @@ __global__ void __launch_bounds__(kCfThreads) k_bwd_cf(DevSim d, BwdDev b, int r
                 lss[l] += ss;
             }
         }
-        __syncthreads();                                // before the next pass reuses the buffers
+        cf_bar();                                       // before the next pass reuses the buffers
     }
+    if (!met) __syncthreads();                          // no vehicles: meet the merge warps anyway
     if (tid < nl) {
         if (lsu[tid] != 0.0f) b.gu[j0 + tid] += (double)lsu[tid];
         if (lss[tid] != 0.0f) b.gs[j0 + tid] += (double)lss[tid];
