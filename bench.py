@@ -285,6 +285,7 @@ def run_batched(args, dev, stream, flush, ws):
     against the same scenarios run one by one."""
     import torch
     from paper_2603_25068_b300 import scenario as S
+    from paper_2603_25068_b300 import native as nat
     from paper_2603_25068_b300.batch import Batch
     from paper_2603_25068_b300.sim import Simulator
     kw = dict(n_nodes=3000, n_links=9000, n_vehicles=250_000, n_origin_zones=20, n_dest_zones=32) if args.small else {}
@@ -309,6 +310,17 @@ def run_batched(args, dev, stream, flush, ws):
         b.rollout(T)
         torch.cuda.synchronize(dev)
         t1 = time.perf_counter()
+        # algorithmic bytes of the batched forward (the node-model bytes model of
+        # every member's steps, from its own counters), read before the reverse
+        # passes consume the runs
+        import ctypes as C
+        bytes_b = 0.0
+        for sc, sm in zip(scs, sims):
+            cnt = np.zeros(4 * T, np.int32)
+            nat.check(sm.lib.sim_step_counters(sm.h, cnt.ctypes.data_as(C.c_void_p)), sm.h)
+            n_on = sm.outputs()["n_on"][:T].astype(np.float64)
+            bytes_b += float(np.sum(kernel_a_bytes(sc, n_on, cnt.reshape(T, 4)[:, 2].astype(np.float64),
+                                                   avg_choice_degree(sc))))
         for sm, yb in zip(sims, ybars):
             sm.backward(yb)
         torch.cuda.synchronize(dev)
@@ -357,6 +369,11 @@ def run_batched(args, dev, stream, flush, ws):
             "serial_forward_plus_reverse": vs / res["serial_forward_plus_reverse_s"],
             "seconds": res,
             "executor": best,
+            "roofline": {"bound": "hbm", "kernel": f"{'k_batch_persist' if best == 'persistent' else 'k_batch_a + k_batch_b'} "
+                                                   "(whole batched forward, host wall clock)",
+                         "achieved": bytes_b / res["batched_forward_s"] / 1e9, "peak": load_peaks()[0], "unit": "GB/s",
+                         "frac": bytes_b / res["batched_forward_s"] / 1e9 / load_peaks()[0],
+                         "algorithmic_bytes": bytes_b},
             "autotune_ms_per_rollout": {k: round(v, 2) for k, v in tune_ms.items()},
             "other_executor_forward_s": other,
             "timing": "host wall clock, device synchronised; reverse passes run one scenario after another"}
