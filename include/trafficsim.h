@@ -297,9 +297,11 @@ SIM_API int sim_set_recompute(sim_handle h, int32_t mode);
 
 /* Device memory of simulators and batches comes from a stream-ordered memory
  * pool per device, which keeps freed blocks mapped for the next simulator (as
- * a caching allocator does).  This returns the device's unused cached blocks
- * to the driver; memory of live simulators is unaffected.
- * Errors: SIM_EINVAL (device index), SIM_ECUDA. */
+ * a caching allocator does); reverse-pass workspaces (one per sim_backward
+ * running at the same time on the device) stay for reuse too.  This frees the
+ * idle workspaces and returns the device's unused cached blocks to the
+ * driver; memory of live simulators is unaffected.  It synchronises the
+ * device.  Errors: SIM_EINVAL (device index), SIM_ECUDA. */
 SIM_API int sim_release_cached_memory(int32_t device);
 
 /* Current time step and device bytes held by the handle. */

@@ -182,12 +182,51 @@ struct sim_ctx {
 // shared by every handle of a device: sim_backward holds the device's lock for
 // the whole call, grows the workspace when a handle needs more and returns only
 // after its stream has drained.  It is released when the process exits.
-struct BwdPool {
-    std::mutex mu;
+// Reverse-pass workspaces of a device: a call takes a free one large enough
+// (growing or adding one if none is), so reverse passes of different
+// simulators can run at the same time; freed workspaces stay for reuse.
+struct BwdWs {
     void *buf = nullptr;
     size_t cap = 0;
+    bool busy = false;
+};
+struct BwdPool {
+    std::mutex mu;
+    std::vector<BwdWs *> ws;
 };
 static BwdPool g_bwd_pool[64];
+
+static BwdWs *bwd_take(int device, size_t need) {
+    BwdPool &pool = g_bwd_pool[device];
+    std::lock_guard<std::mutex> lock(pool.mu);
+    BwdWs *fit = nullptr, *any = nullptr;
+    for (BwdWs *w : pool.ws) {
+        if (w->busy) continue;
+        if (w->cap >= need && (!fit || w->cap < fit->cap)) fit = w;
+        if (!any || w->cap > any->cap) any = w;
+    }
+    BwdWs *w = fit ? fit : any;
+    if (!w) {
+        w = new BwdWs();
+        pool.ws.push_back(w);
+    }
+    w->busy = true;
+    return w;
+}
+
+// Gives the workspace back when the call ends, once the streams that may use
+// it have drained (an error can end the call with work in flight).
+struct BwdLease {
+    BwdPool *pool;
+    BwdWs *w;
+    std::vector<cudaStream_t> streams;
+    ~BwdLease() {
+        for (cudaStream_t s : streams)
+            if (s) cudaStreamSynchronize(s);
+        std::lock_guard<std::mutex> lock(pool->mu);
+        w->busy = false;
+    }
+};
 
 static std::string g_create_err;
 
@@ -239,6 +278,19 @@ static cudaError_t pool_alloc(void **p, size_t bytes, int device, cudaStream_t s
 
 extern "C" int sim_release_cached_memory(int32_t device) {
     if (device < 0 || device >= 64) return SIM_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return SIM_ECUDA;
+    {                                    // idle reverse-pass workspaces
+        BwdPool &pool = g_bwd_pool[device];
+        std::lock_guard<std::mutex> lock(pool.mu);
+        std::vector<BwdWs *> keep;
+        for (BwdWs *w : pool.ws) {
+            if (w->busy) { keep.push_back(w); continue; }
+            if (w->buf) cudaFreeAsync(w->buf, nullptr);
+            delete w;
+        }
+        pool.ws = keep;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) return SIM_ECUDA;
     std::lock_guard<std::mutex> lock(g_mpool_mu);
     if (g_mpool[device] && cudaMemPoolTrimTo(g_mpool[device], 0) != cudaSuccess) return SIM_ECUDA;
     return SIM_OK;
@@ -1097,10 +1149,8 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     for (int bb = nb - 1; bb >= 0; --bb)
         for (int j = 0; j < L; ++j) cs[(size_t)bb * L + j] = cs[(size_t)(bb + 1) * L + j] + cb[(size_t)bb * L + j];
     if (h->device < 0 || h->device >= 64) return fail(h, SIM_EINVAL, "device index");
-    BwdPool &pool = g_bwd_pool[h->device];
-    std::lock_guard<std::mutex> lock(pool.mu);
-    // carve the shared workspace: one layout routine sizes it (from base 0)
-    // and then hands out the sub-arrays (from the buffer)
+    // carve the workspace: one layout routine sizes it (from base 0) and then
+    // hands out the sub-arrays (from the buffer)
     const int n_gw = (L + kGwLinks - 1) / kGwLinks;
     // recomputation beside the reverse pass (two tape sets), or before it in
     // one persistent recording launch per segment (one tape set)
@@ -1147,13 +1197,28 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         return (size_t)(wp - base);
     };
     const size_t need = carve(0);
-    if (need > pool.cap) {
-        if (pool.buf) { cudaDeviceSynchronize(); cudaFree(pool.buf); pool.buf = nullptr; pool.cap = 0; }
-        cudaError_t e = cudaMalloc(&pool.buf, need);
-        if (e != cudaSuccess) { pool.buf = nullptr; return fail(h, SIM_ENOMEM, "reverse-pass workspace: " + std::string(cudaGetErrorString(e))); }
-        pool.cap = need;
+    if (!h->jstream) {                   // the reverse pass's streams and events
+        int lo = 0, hi = 0;
+        CU(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CU(cudaStreamCreateWithPriority(&h->vstream, cudaStreamNonBlocking, hi));
+        CU(cudaStreamCreateWithPriority(&h->jstream, cudaStreamNonBlocking, hi));
+        CU(cudaStreamCreateWithPriority(&h->rstream, cudaStreamNonBlocking, lo));
+        CU(cudaEventCreateWithFlags(&h->ev_z, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&h->ev_g, cudaEventDisableTiming));
+        for (cudaEvent_t *e : {&h->ev_r[0], &h->ev_r[1], &h->ev_b[0], &h->ev_b[1], &h->ev_gr[0], &h->ev_gr[1]})
+            CU(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     }
-    carve((uintptr_t)pool.buf);
+    BwdLease lease{&g_bwd_pool[h->device], bwd_take(h->device, need), {h->stream, h->vstream, h->jstream, h->rstream}};
+    BwdWs &ws = *lease.w;
+    if (need > ws.cap) {                 // grow (the previous user of this workspace has synchronised)
+        if (ws.buf) cudaFreeAsync(ws.buf, h->stream);
+        ws.buf = nullptr;
+        ws.cap = 0;
+        cudaError_t e = pool_alloc(&ws.buf, need, h->device, h->stream);
+        if (e != cudaSuccess) { ws.buf = nullptr; return fail(h, SIM_ENOMEM, "reverse-pass workspace: " + std::string(cudaGetErrorString(e))); }
+        ws.cap = need;
+    }
+    carve((uintptr_t)ws.buf);
     // bin adjoints as double-float pairs (hi = nearest float, lo = nearest float of the rest)
     std::vector<float2> cb2(cb.size()), cs2(cs.size());
     auto split = [](double v) { const float hi = (float)v; return make_float2(hi, (float)(v - (double)hi)); };
@@ -1184,17 +1249,6 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     const size_t smem_a = (size_t)h->stage_max * sizeof(float);
 
     const int gS = (std::max(S, L) + 255) / 256, gLV = (L + V + 255) / 256;
-    if (!h->jstream) {
-        int lo = 0, hi = 0;
-        CU(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-        CU(cudaStreamCreateWithPriority(&h->vstream, cudaStreamNonBlocking, hi));
-        CU(cudaStreamCreateWithPriority(&h->jstream, cudaStreamNonBlocking, hi));
-        CU(cudaStreamCreateWithPriority(&h->rstream, cudaStreamNonBlocking, lo));
-        CU(cudaEventCreateWithFlags(&h->ev_z, cudaEventDisableTiming));
-        CU(cudaEventCreateWithFlags(&h->ev_g, cudaEventDisableTiming));
-        for (cudaEvent_t *e : {&h->ev_r[0], &h->ev_r[1], &h->ev_b[0], &h->ev_b[1], &h->ev_gr[0], &h->ev_gr[1]})
-            CU(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
-    }
     // Segments from the last.  The tape has two sets, by segment parity.  The
     // recomputation of segment s - 1 (on the third stream, two-kernel executor,
     // whose blocks share SMs with the reverse kernels) runs beside the reverse

@@ -10,8 +10,9 @@ rollouts) arrive over time.  The engine
     batch instead of stalling it,
   * runs every admitted forward rollout in one batch (sim_batch_*), a new
     request joining at the next step boundary, finished ones leaving it,
-  * runs the reverse pass of a finished gradient request on a worker thread with
-    its own stream, so that it overlaps the batched forward work on the device,
+  * runs the reverse passes of finished gradient requests on worker threads,
+    each with its own stream, so that they overlap one another and the
+    batched forward work on the device,
   * records each request's latency from arrival to result.
 Each request's result is the one it would get alone: batching changes neither
 its random key nor its state.
@@ -97,7 +98,7 @@ def handle_bytes_bound(sc, ckpt_every: int, route_cap: int) -> float:
 
 class Engine:
     def __init__(self, device: int = 0, hbm_budget: float = 150e9, chunk: int = 240, ckpt_every: int = 180,
-                 route_cap: int = 256, creators: int = 2):
+                 route_cap: int = 256, creators: int = 2, reversers: int = 2):
         import torch
         self.torch = torch
         self.device = device
@@ -106,7 +107,7 @@ class Engine:
         self.ckpt_every = ckpt_every
         self.route_cap = route_cap
         self.stream = torch.cuda.Stream(device=device)
-        self.bwd_stream = torch.cuda.Stream(device=device)
+        self.bwd_streams = [torch.cuda.Stream(device=device) for _ in range(reversers)]
         self.active: List[tuple] = []          # (request, simulator, bytes)
         self.batch: Optional[Batch] = None
         self.batch_members: List[int] = []
@@ -117,12 +118,12 @@ class Engine:
         self.bwd_q: "queue.Queue" = queue.Queue()
         self.create_q: "queue.Queue" = queue.Queue()
         self.ready_q: "queue.Queue" = queue.Queue()
-        self.bwd_thread = threading.Thread(target=self._bwd_worker, daemon=True)
+        self.bwd_threads = [threading.Thread(target=self._bwd_worker, args=(k,), daemon=True)
+                            for k in range(reversers)]
         self.create_threads = [threading.Thread(target=self._create_worker, args=(k,), daemon=True)
                                for k in range(creators)]
         self.create_streams = [torch.cuda.Stream(device=device) for _ in range(creators)]
-        self.bwd_thread.start()
-        for th in self.create_threads:
+        for th in self.bwd_threads + self.create_threads:
             th.start()
 
     # -------------------------------------------------------------- helpers
@@ -137,7 +138,7 @@ class Engine:
         slots = float(np.sum(np.floor(sc.length.astype(np.float64) * sc.kappa / sc.dn) + 2))
         return 18.0 * (self.ckpt_every + 1) * slots + 16.0 * sc.N * self.route_cap    # two tape sets
 
-    def _bwd_worker(self):
+    def _bwd_worker(self, k: int):
         torch = self.torch
         while True:
             item = self.bwd_q.get()
@@ -146,6 +147,7 @@ class Engine:
             req, sim, nbytes = item
             try:
                 with torch.cuda.device(self.device):
+                    sim.set_stream(self.bwd_streams[k])     # out of the batch: a stream of this worker
                     out = sim.outputs()
                     g = sim.backward(loss_cotangent(req, out["counts"]))
                     req.result = dict(counts=out["counts"], speed=out["speed"], travel_time=out["travel_time"], grad=g)
@@ -217,8 +219,7 @@ class Engine:
         waiting: List[Request] = []
         with torch.cuda.device(self.device):
             while True:
-                if self.worker_error is not None or not self.bwd_thread.is_alive() \
-                        or not all(th.is_alive() for th in self.create_threads):
+                if self.worker_error is not None or not all(th.is_alive() for th in self.bwd_threads + self.create_threads):
                     raise RuntimeError(f"serving worker failed: {self.worker_error!r}")
                 if self.now() > max_seconds:
                     raise RuntimeError("serving run exceeded its time limit")
@@ -249,8 +250,6 @@ class Engine:
                     self._rebuild()
                     for req, sim, nbytes in done:
                         if req.needs_grad:
-                            # leave the batch's stream here, where nothing is being captured
-                            sim.set_stream(self.bwd_stream)
                             self.bwd_q.put((req, sim, nbytes))
                         else:
                             out = sim.outputs()
@@ -260,11 +259,11 @@ class Engine:
                             with self.lock:
                                 self.used -= nbytes
                             req.finished = self.now()
-            self.bwd_q.put(None)
+            for _ in self.bwd_threads:
+                self.bwd_q.put(None)
             for _ in self.create_threads:
                 self.create_q.put(None)
-            self.bwd_thread.join()
-            for th in self.create_threads:
+            for th in self.bwd_threads + self.create_threads:
                 th.join()
         return requests
 

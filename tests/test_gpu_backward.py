@@ -87,3 +87,38 @@ def test_backward_needs_a_recorded_rollout(Simulator):
     g.step(20)                                          # the step path records no tape
     with pytest.raises(SimError):
         g.backward(np.zeros((1, sc.L), np.float32))
+
+
+def test_concurrent_reverse_passes_equal_sequential(Simulator):
+    """Reverse passes of several simulators from several host threads (each
+    handle on its own stream, each call with its own workspace) give the
+    gradients of the same passes one after another, up to the order of the
+    double-precision atomic additions."""
+    import threading
+    import torch
+    scs = [S.random_small(seed=s, side=3, n_vehicles=150, T=80).copy(obs_every=20) for s in (11, 12, 13, 14)]
+    rng = np.random.default_rng(3)
+    sims = [Simulator(sc, ckpt_every=9, route_cap=64, stream=torch.cuda.Stream()) for sc in scs]
+    ybar = []
+    for s_ in sims:
+        out = s_.rollout()
+        ybar.append(rng.normal(size=out["counts"].shape).astype(np.float32))
+    seq = [s_.backward(y) for s_, y in zip(sims, ybar)]
+    for s_ in sims:
+        s_.rollout()
+    par = [None] * len(sims)
+
+    def run(k):
+        par[k] = sims[k].backward(ybar[k])
+    ths = [threading.Thread(target=run, args=(k,)) for k in range(len(sims))]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    for a, b in zip(seq, par):
+        assert b is not None
+        for k in a:
+            scale = max(1e-6, float(np.abs(a[k]).max()))
+            np.testing.assert_allclose(b[k], a[k], rtol=0, atol=1e-6 * scale, err_msg=k)
+    for s_ in sims:
+        s_.close()
