@@ -61,11 +61,7 @@ def parse():
     return ap.parse_args()
 
 
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+from paper_2603_25068_b300.replicas import dist_env, slowest, whole_job_rate  # noqa: E402
 
 
 def make_scenario(args):
@@ -260,11 +256,7 @@ def run_fwd_bwd(args, dev, stream, flush, ws):
             times.append(time.perf_counter() - t0)
             t_fwd.append(t1 - t0)
             t_bwd.append(time.perf_counter() - t1)
-    tot = sum(times)
-    if ws > 1:
-        t = torch.tensor([tot], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
+    tot = slowest(sum(times), dev)
     ms = 1000 * tot / args.steps
     return {"metric": "vehicle-steps/s (forward + reverse pass)", "value": ws * model.N * T / (ms / 1000),
             "unit": "vehicle-steps/s", "ms_per_iteration": ms, "x_real_time": T * model.dt / (ms / 1000),
@@ -467,13 +459,9 @@ def run_ours(args):
         if ws > 1:
             dist.barrier()
     ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = slowest(sum(ms), dev)
     ms_per = total_ms / args.steps
-    value = ws * N * T * args.steps / (total_ms / 1000.0)
+    value = whole_job_rate(N * T * args.steps, ws, total_ms / 1000.0)
     # our kernels per rollout: reset + (node model, transfer) per step + final
     # observation, or reset + one persistent launch
     launches_per_rollout = 2 * T + 2 if executor == "step" else 2
@@ -575,12 +563,8 @@ def run_ours(args):
             t0 = time.perf_counter()
             e2e_step()
             t_e2e.append(time.perf_counter() - t0)
-        tot = sum(t_e2e)
-        if ws > 1:
-            t = torch.tensor([tot], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        line["e2e"] = {"value": ws * N * T * args.steps / tot, "unit": "vehicle-steps/s",
+        tot = slowest(sum(t_e2e), dev)
+        line["e2e"] = {"value": whole_job_rate(N * T * args.steps, ws, tot), "unit": "vehicle-steps/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "ms_per_step": 1000 * tot / args.steps,
                        "note": "sim_set_params from pinned host arrays + sim_rollout into pinned host outputs"}
