@@ -97,3 +97,23 @@ def test_set_state_rejects_inconsistent_states(Simulator):
         g.set_state(st, sc.T + 1)                                   # outside the horizon
     g.set_state(st, 60)                                             # the state itself is accepted
     g.close()
+
+
+def test_release_cached_memory_and_recompute_mode_validation(Simulator):
+    """Cached pool memory can be returned to the driver between runs (live
+    simulators keep theirs); unknown recompute modes are refused."""
+    from paper_2603_25068_b300 import native as nat
+    sc = S.tiny_grid(T=60)
+    a = Simulator(sc)
+    ref = a.rollout(60)
+    lib = nat.lib()
+    nat.check(lib.sim_release_cached_memory(0), None)
+    assert lib.sim_release_cached_memory(-1) == nat.SIM_EINVAL
+    again = a.rollout(60)                          # the live simulator's memory is untouched
+    for k in ("counts", "speed", "travel_time"):
+        np.testing.assert_array_equal(again[k], ref[k])
+    assert lib.sim_set_recompute(a.h, 7) == nat.SIM_EINVAL
+    a.close()
+    b = Simulator(sc)                              # allocations after a release
+    np.testing.assert_array_equal(b.rollout(60)["counts"], ref["counts"])
+    b.close()
