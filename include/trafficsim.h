@@ -266,6 +266,22 @@ SIM_API int sim_set_executor(sim_handle h, int32_t executor);
  * -1 for a NULL handle. */
 SIM_API int32_t sim_get_executor(sim_handle h);
 
+/* Work partition of the persistent executor.  Each CTA owns a run of
+ * consecutive links; the runs are chosen so that the largest sum of link
+ * weights over a run is as small as the shared-memory limits allow.  By
+ * default a link weighs its queue capacity + 16 slots.  w (host, [L],
+ * finite, >= 0, not all 0) replaces that by a relative weight per link, e.g.
+ * the mean number of vehicles on the link measured in an earlier rollout plus
+ * a per-link constant, so that CTAs get equal work rather than equal capacity.
+ * NULL restores the default.  Results do not depend on the partition (they
+ * are bit-identical).  Call between runs, not while another call on h is in
+ * progress.  Errors: SIM_EINVAL (invalid weights; a weighting under which the
+ * queues no longer fit leaves the previous partition in place). */
+SIM_API int sim_set_partition_weights(sim_handle h, const float *w);
+/* Number of CTAs of the persistent executor (0 if it is unavailable, -1 on
+ * error); first_link (host, may be NULL) receives the G + 1 group bounds. */
+SIM_API int32_t sim_persist_groups(sim_handle h, int32_t *first_link);
+
 /* Test hook for the bounded waits of the persistent executor: the next
  * persistent launch of h waits at its grid barriers for `missing` arrivals
  * that never come, so every CTA gives up after its bounded wait (about 2 s),

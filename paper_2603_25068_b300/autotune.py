@@ -60,3 +60,33 @@ def tune_batch(batch, T: int = 120, reps: int = 1, executors=BATCH_EXECUTORS):
     best = min(times, key=times.get)
     batch.set_executor(best)
     return best, times
+
+
+def link_occupancy(sim, T=None, samples: int = 12):
+    """Mean number of vehicles on each link over a rollout of T steps, from
+    the exported state at ``samples`` evenly spaced steps."""
+    import numpy as np
+    T = sim.sc.T if T is None else T
+    sim.reset(T)
+    occ = np.zeros(sim.sc.L, np.float64)
+    every = max(1, T // samples)
+    n = 0
+    while sim.t + every <= T:
+        sim.step(every)
+        vl = sim.state(fields=("veh_link",))["veh_link"]
+        occ += np.bincount(vl[vl >= 0], minlength=sim.sc.L)
+        n += 1
+    return occ / max(n, 1)
+
+
+def balance_partition(sim, T=None, samples: int = 12, per_link: float = 1.0, occ=None):
+    """Partition the persistent executor's links by measured load: weight of a
+    link = its mean vehicle count over a rollout + ``per_link``.  Returns the
+    weights set (None if the simulator has no persistent executor)."""
+    if sim.persist_groups() is None:
+        return None
+    if occ is None:
+        occ = link_occupancy(sim, T, samples)
+    w = occ + float(per_link)
+    sim.set_partition_weights(w)
+    return w

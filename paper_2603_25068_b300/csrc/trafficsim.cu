@@ -174,6 +174,8 @@ struct sim_ctx {
     bool persist_ok = false;             // the network fits (groups, shared memory, co-residency)
     std::string persist_why;             // reason when it does not
     int G = 0;                           // CTAs (one per SM at most)
+    std::vector<long long> pw;           // partition weights (empty: queue capacity + 16)
+    int *d_grp = nullptr;                // group bounds, one slot per SM + 1
     size_t persist_smem = 0;
     PArgs pa{};
 };
@@ -378,8 +380,9 @@ static int build_blocks(sim_ctx *h) {
 
 // Groups of the persistent executor: consecutive links packed into at most one
 // group per SM, each within kPLinks links and the shared memory left for queue
-// slots, with the largest group weight (slots + 16 per link) made as small as
-// possible (binary search over the bound, greedy packing).
+// slots, with the largest group weight made as small as possible (binary search
+// over the bound, greedy packing).  A link weighs its queue capacity + 16 slots,
+// or the weight set by sim_set_partition_weights.
 static size_t g_attr_p[64], g_attr_pt[64];
 static int build_groups(sim_ctx *h) {
     h->persist_ok = false;
@@ -394,8 +397,11 @@ static int build_groups(sim_ctx *h) {
     for (int j = 0; j < L; ++j) {
         cap[j] = h->lst_host[4 * j + 1];
         lob[j] = 4 * cap[j] + 16 * (long long)h->lo_count[j];
-        wsum += cap[j] + 16;
-        wmax = std::max(wmax, cap[j] + 16);
+    }
+    auto weight = [&](int j) { return h->pw.empty() ? cap[j] + 16 : h->pw[j]; };
+    for (int j = 0; j < L; ++j) {
+        wsum += weight(j);
+        wmax = std::max(wmax, weight(j));
     }
     // the origin queues of a group are the nodes [g npg, (g + 1) npg)
     auto node_bytes = [&](int G) {
@@ -422,7 +428,7 @@ static int build_groups(sim_ctx *h) {
             long long w = 0, bytes = 0;
             if (out) out->clear();
             for (int j = 0; j < L; ++j) {
-                const long long wj = cap[j] + 16;
+                const long long wj = weight(j);
                 if (nl == 0 || nl == kPLinks || w + wj > bound || bytes + lob[j] > lbud) {
                     if (out) out->push_back(j);
                     ++groups;
@@ -482,14 +488,15 @@ static int build_groups(sim_ctx *h) {
         h->persist_why = "the CTAs cannot all be resident at once";
         return SIM_OK;
     }
-    int *d_grp = nullptr;
-    TRY(upload(h, &d_grp, grp.data(), grp.size()));
+    if (!h->d_grp) TRY(dalloc(h, &h->d_grp, (size_t)nsm + 1));
+    CU(cudaMemcpyAsync(h->d_grp, grp.data(), grp.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
     if (!h->pa.W3) {
         TRY(dalloc(h, &h->pa.W3, (size_t)3 * L));
         TRY(dalloc(h, &h->pa.crec2, (size_t)2 * L));
         TRY(dalloc(h, &h->pa.bar, 4));
     }
-    h->pa.grp_links = d_grp;
+    h->pa.grp_links = h->d_grp;
     h->pa.npg = npg;
     h->pa.packz = (h->N < (1 << 24) && h->Z <= 256) ? 1 : 0;
     h->G = G;
@@ -1551,6 +1558,41 @@ extern "C" int sim_set_executor(sim_handle h, int32_t executor) {
         return fail(h, SIM_EINVAL, "persistent executor unavailable: " + h->persist_why);
     h->executor = executor;
     return SIM_OK;
+}
+
+extern "C" int sim_set_partition_weights(sim_handle h, const float *w) {
+    if (!h) return SIM_EINVAL;
+    std::vector<long long> pw;
+    if (w) {
+        double m = 0.0;
+        for (int j = 0; j < h->L; ++j) {
+            if (!std::isfinite(w[j]) || w[j] < 0.0f) return fail(h, SIM_EINVAL, "partition weights must be finite and >= 0");
+            m = std::max(m, (double)w[j]);
+        }
+        if (!(m > 0.0)) return fail(h, SIM_EINVAL, "partition weights are all zero");
+        pw.resize(h->L);
+        for (int j = 0; j < h->L; ++j) pw[j] = 1 + std::llround((double)w[j] / m * (double)(1 << 20));
+    }
+    CU(cudaSetDevice(h->device));
+    CU(cudaStreamSynchronize(h->stream));       // launches in flight read the old bounds
+    const bool was_ok = h->persist_ok;
+    h->pw.swap(pw);
+    const int rc = build_groups(h);
+    if (rc == SIM_OK && (h->persist_ok || !was_ok)) return SIM_OK;
+    const std::string why = h->persist_why;
+    h->pw.swap(pw);                             // back to the previous weights
+    TRY(build_groups(h));
+    return rc ? rc : fail(h, SIM_EINVAL, "no persistent grouping with these weights: " + why);
+}
+
+extern "C" int32_t sim_persist_groups(sim_handle h, int32_t *first_link) {
+    if (!h) return -1;
+    if (!h->persist_ok) return 0;
+    if (first_link) {
+        if (cudaSetDevice(h->device) != cudaSuccess) return -1;
+        if (cudaMemcpy(first_link, h->d_grp, (size_t)(h->G + 1) * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    }
+    return h->G;
 }
 
 extern "C" int sim_test_barrier_timeout(sim_handle h, int32_t missing) {

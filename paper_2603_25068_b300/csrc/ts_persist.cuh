@@ -41,10 +41,11 @@ constexpr int kPT = 1024;                    // threads per CTA
 constexpr int kPLinks = 288;                 // links per CTA at most
 constexpr int kPNodes = 128;                 // origin queues per CTA at most
 constexpr int kPNodeTid = 512;               // thread of origin queue 0 in the per-entity phases
-constexpr int kPSlot = 4;                    // choice slots per candidate evaluated in parallel
-constexpr int kPCW = 16;                     // choice warps
+constexpr int kPSlot = 8;                    // choice slots per candidate evaluated in parallel
+constexpr int kPCW = 12;                     // choice warps
 constexpr int kPCFT = kPT - 32 * kPCW;       // car-following threads
 constexpr int kPPairs = (kPLinks + kPNodes) * (kPSlot + 1);
+static_assert(kPSlot + 1 <= 16, "a pair list entry holds the slot in 4 bits");
 
 struct PArgs {
     const int *grp_links;          // [G + 1] first link of each CTA's group
@@ -86,7 +87,7 @@ struct PSmem {
     float nmkey[kPNodes];
     float nkey[kPNodes][kPSlot];
     int ntv[kPNodes][kPSlot];
-    int plist[kPPairs];            // entity << 3 | (0 merge key, 1 + k choice slot k)
+    int plist[kPPairs];            // entity << 4 | (0 merge key, 1 + k choice slot k)
     int wsum[32];
     int cnt[4];                    // step counters: releases, arrivals, candidates, entries
     int npairs, ctot, stop;
@@ -443,7 +444,7 @@ __device__ __forceinline__ void p_scan(PSmem &S, const PCtx &c, int v, int nw) {
             if (S.ctot * q < nw) S.wl[q] = 0;
     }
     const int np = v >> 16;
-    for (int k = 0; k < np; ++k) S.plist[(ex >> 16) + k] = (tid << 3) | k;
+    for (int k = 0; k < np; ++k) S.plist[(ex >> 16) + k] = (tid << 4) | k;
     __syncthreads();
 }
 
@@ -471,7 +472,7 @@ __device__ __forceinline__ void p_pairs(const DevSim &d, const PArgs &a, PSmem &
             if (p >= np) continue;
             const int e = S.plist[p];
             pe[i] = e;
-            const int en = e >> 3, sl = e & 7;
+            const int en = e >> 4, sl = e & 15;
             const bool isl = en < kPNodeTid;
             const int4 who = isl ? S.ld[en] : S.nh[en - kPNodeTid];
             vid[i] = who.x;
@@ -495,13 +496,13 @@ __device__ __forceinline__ void p_pairs(const DevSim &d, const PArgs &a, PSmem &
 #pragma unroll
             for (int i = 0; i < kPP; ++i) {
                 wt[i] = 0ull;
-                if (pe[i] >= 0 && (pe[i] & 7) != 0 && cy[i] >= 0) wt[i] = __ldcg(Wp + cy[i]);
+                if (pe[i] >= 0 && (pe[i] & 15) != 0 && cy[i] >= 0) wt[i] = __ldcg(Wp + cy[i]);
             }
         }
 #pragma unroll
         for (int i = 0; i < kPP; ++i) {
             if (pe[i] < 0) continue;
-            const int en = pe[i] >> 3, sl = pe[i] & 7;
+            const int en = pe[i] >> 4, sl = pe[i] & 15;
             const bool isl = en < kPNodeTid;
             const int ni = en - kPNodeTid;
             if (sl == 0) {

@@ -81,6 +81,8 @@ SIGNATURES = {
     "sim_set_executor": (C.c_int, [P, C.c_int32]),
     "sim_get_executor": (C.c_int32, [P]),
     "sim_test_barrier_timeout": (C.c_int, [P, C.c_int32]),
+    "sim_set_partition_weights": (C.c_int, [P, P]),
+    "sim_persist_groups": (C.c_int32, [P, P]),
     "sim_batch_create": (C.c_int, [C.POINTER(P), C.c_int32, C.POINTER(P)]),
     "sim_batch_start": (C.c_int, [P, C.c_int32, C.c_int32]),
     "sim_batch_advance": (C.c_int, [P, C.c_int32, P]),

@@ -450,6 +450,25 @@ def custom(tail, head, length, origin, dest_node, dep_step, u=10.0, kappa=0.2, a
                     seed=seed, obs_every=T)
 
 
+def hub(n_spokes: int = 11, n_vehicles: int = 400, T: int = 400, seed: int = 0) -> Scenario:
+    """Star network whose centre has n_spokes out-links (a choice set wider
+    than the slots a persistent CTA evaluates in parallel) and whose spokes are
+    joined in a ring; vehicles travel between random spokes.  Heterogeneous
+    lengths, beta and alpha make the choices and merges uneven."""
+    rng = np.random.default_rng(seed)
+    K = n_spokes
+    tail, head = [], []
+    for i in range(1, K + 1):
+        tail += [0, i, i]
+        head += [i, 0, i % K + 1]
+    L = len(tail)
+    o = rng.integers(1, K + 1, size=n_vehicles)
+    dest = (o - 1 + rng.integers(1, K, size=n_vehicles)) % K + 1
+    return custom(tail, head, length=rng.uniform(30.0, 90.0, size=L), origin=o, dest_node=dest,
+                  dep_step=rng.integers(0, T // 2, size=n_vehicles), beta=rng.uniform(0.0, 2.0, size=L),
+                  alpha=rng.uniform(0.5, 4.0, size=L), q=0.6, T=T, seed=seed, name="hub").copy(obs_every=60)
+
+
 def calibration(n_sensors: int = 2000, T: int = 1800, seed_truth: int = 2, **kw):
     """Calibration-gradient workload: the city network and 30-minute rollouts
     with 5-minute counts on n_sensors links; observations come from a hidden

@@ -104,6 +104,31 @@ class Simulator:
     def device_bytes(self):
         return self.lib.sim_device_bytes(self.h)
 
+    def set_partition_weights(self, w=None):
+        """Per-link weights of the persistent executor's work partition (host
+        array of L, relative; None restores queue capacity + 16).  Results are
+        unchanged; only which CTA owns which links moves."""
+        if w is None:
+            self._check(self.lib.sim_set_partition_weights(self.h, None))
+            return
+        w = np.ascontiguousarray(np.asarray(w, np.float32))
+        if w.shape != (self.sc.L,):
+            raise ValueError(f"partition weights need shape ({self.sc.L},), got {w.shape}")
+        self._check(self.lib.sim_set_partition_weights(self.h, _p(w)))
+
+    def persist_groups(self):
+        """First link of each CTA's group (G + 1 bounds), or None when the
+        persistent executor is unavailable."""
+        G = self.lib.sim_persist_groups(self.h, None)
+        if G < 0:
+            self._check(-1)
+        if G == 0:
+            return None
+        b = np.zeros(G + 1, np.int32)
+        if self.lib.sim_persist_groups(self.h, _p(b)) != G:
+            raise RuntimeError("sim_persist_groups failed")
+        return b
+
     RECOMPUTE = {"overlap": 0, "serial": 1}
 
     def set_recompute(self, name: str):
@@ -196,14 +221,17 @@ class Simulator:
                                           None if xb is None else C.c_void_p(xb.data_ptr()), 1, C.byref(o)))
         return g
 
-    def state(self):
+    def state(self, fields=None):
+        """Exported state as host arrays; ``fields`` (names) limits the copy."""
         sc = self.sc
         d = dict(veh_link=np.zeros(sc.N, np.int32), veh_pos=np.zeros(sc.N, np.float64),
                  veh_rank=np.zeros(sc.N, np.int32), veh_entry=np.zeros(sc.N, np.int32),
                  link_credit=np.zeros(sc.L, np.int64), link_exits=np.zeros(sc.L, np.int64),
                  fifo_off=np.zeros(sc.V, np.int32))
-        v = nat.sim_state_view(*(_p(d[k]) for k in ("veh_link", "veh_pos", "veh_rank", "veh_entry",
-                                                     "link_credit", "link_exits", "fifo_off")))
+        if fields is not None:
+            d = {k: d[k] for k in fields}
+        v = nat.sim_state_view(*(_p(d.get(k)) for k in ("veh_link", "veh_pos", "veh_rank", "veh_entry",
+                                                        "link_credit", "link_exits", "fifo_off")))
         self._check(self.lib.sim_get_state(self.h, C.byref(v)))
         return d
 

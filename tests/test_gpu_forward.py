@@ -71,6 +71,14 @@ def test_lockstep_dense_small(Simulator, seed):
     lockstep(Simulator, sc.copy(obs_every=40), 150)
 
 
+def test_lockstep_wide_choice_set(Simulator):
+    # the hub has 11 out-links: slots beyond those evaluated in parallel by the
+    # persistent executor's choice warps are evaluated at the decision
+    sc = S.hub()
+    assert np.bincount(sc.tail).max() == 11
+    lockstep(Simulator, sc, sc.T)
+
+
 @pytest.mark.parametrize("stage", [256, 2048])
 def test_lockstep_long_queues(Simulator, stage):
     # queues longer than a block's thread count, links larger than the stage

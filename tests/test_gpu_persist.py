@@ -58,6 +58,7 @@ SCENARIOS = {
     "dense_small": lambda: S.random_small(seed=2, side=3, n_vehicles=150, T=150).copy(obs_every=40),
     "city_small": lambda: S.city_small(),
     "line": lambda: S.line_network(n_links=2, length=1500.0, u=13.9, kappa=0.2, q=0.5, N=700, T=900).copy(obs_every=70),
+    "hub": lambda: S.hub(),          # an 11-way choice set: wider than the parallel slots
 }
 
 
@@ -206,4 +207,36 @@ def test_bounded_barrier_wait_reports_timeout_and_recovers(Simulator):
     out = g.rollout(sc.T)                      # reset by the rollout: a normal run again
     for k in OUT_KEYS:
         np.testing.assert_array_equal(out[k], ref["out"][k], err_msg=k)
+    g.close()
+
+
+def test_partition_weights_leave_results_unchanged(Simulator):
+    # which CTA owns which links must not change any result: equal-capacity
+    # groups, random weights and one heavy link give bit-identical runs
+    from paper_2603_25068_b300.native import SimError
+    sc = S.city_small()
+    base = run(Simulator, sc, sc.T, "persistent")
+    g = Simulator(sc)
+    b0 = g.persist_groups()
+    assert b0[0] == 0 and b0[-1] == sc.L and np.all(np.diff(b0) >= 0)
+    rng = np.random.default_rng(4)
+    w_heavy = np.ones(sc.L)
+    w_heavy[sc.L // 2] = 500.0
+    seen = {tuple(b0)}
+    for w in (rng.uniform(0.0, 10.0, sc.L), rng.lognormal(0.0, 2.0, sc.L), w_heavy):
+        g.set_partition_weights(w)
+        b = g.persist_groups()
+        assert b[0] == 0 and b[-1] == sc.L and np.all(np.diff(b) >= 0)
+        seen.add(tuple(b))
+        out = g.rollout(sc.T)
+        res = dict(out=out, state=g.state(), rec=g.records())
+        assert_same(base, res)
+    assert len(seen) > 1, "the weights never moved a group bound"
+    for bad in (np.full(sc.L, -1.0), np.zeros(sc.L), np.full(sc.L, np.nan)):
+        with pytest.raises(SimError):
+            g.set_partition_weights(bad)
+    with pytest.raises(ValueError):
+        g.set_partition_weights(np.ones(sc.L + 1))
+    g.set_partition_weights(None)
+    np.testing.assert_array_equal(g.persist_groups(), b0)
     g.close()
