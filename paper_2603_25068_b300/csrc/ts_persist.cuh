@@ -73,6 +73,8 @@ struct PSmem {
     int flags[kPLinks];            // vacancy / arrival for the coming step
     int lbase[kPLinks + 1];        // first ring slot of each link in shared memory (static)
     int wl[32 + 1];                // first link of each car-following warp
+    int wr[32 + 1];                // and its first round of 32 vehicles in that link
+    float wah[32 + 1];             // time-t position of the vehicle ahead of a warp starting at round > 0
     int past[kPLinks];
     float mkey[kPLinks];
     float alpha[kPLinks];
@@ -401,8 +403,11 @@ __device__ __forceinline__ int p_candidate(const DevSim &d, PSmem &S, const PCtx
 }
 
 // Block scan of every thread's (choice pairs << 16 | car-following cost): the
-// compact pair list and the first link of each of the nw car-following warps
-// (contiguous runs of links with equal shares of the total cost).
+// compact pair list and the start of each of the nw car-following warps.  The
+// cost of a link is 1 + its rounds of 32 vehicles; warp q starts at cost unit
+// floor(q tot / nw), so a long queue is split between warps at a round
+// boundary.  A warp that starts inside a link gets the time-t position of the
+// vehicle ahead of its first one, read here before any warp writes.
 __device__ __forceinline__ void p_scan(PSmem &S, const PCtx &c, int v, int nw) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     int s = v;
@@ -430,18 +435,30 @@ __device__ __forceinline__ void p_scan(PSmem &S, const PCtx &c, int v, int nw) {
     __syncthreads();
     const int ex = s - v + S.wsum[w];
     if (tid < c.nl) {
-        // car-following warp q starts at the first link whose cost prefix
-        // reaches q tot / nw: link tid + 1 for the targets in (ex, ex + cost]
-        // q with e0 < floor(tot q / nw) <= e1: q in [ceil((e0 + 1) nw / tot), ((e1 + 1) nw - 1) / tot]
+        // link tid holds the cost units [e0, e1): e0 its setup, e0 + 1 + r its
+        // round r; the warps q in [1, nw) with e0 <= floor(q tot / nw) < e1
+        // are q in [ceil(e0 nw / tot), ceil(e1 nw / tot) - 1]
         const int tot = S.ctot, e0 = ex & 0xffff, e1 = e0 + (v & 0xffff);
-        const int qa = max(1, ((e0 + 1) * nw + tot - 1) / tot), qb = min(nw - 1, ((e1 + 1) * nw - 1) / tot);
-        for (int q = qa; q <= qb; ++q) S.wl[q] = tid + 1;
+        const int qa = max(1, (e0 * nw + tot - 1) / tot), qb = min(nw - 1, (e1 * nw + tot - 1) / tot - 1);
+        for (int q = qa; q <= qb; ++q) {
+            const int r = max(0, (q * tot) / nw - e0 - 1);
+            S.wl[q] = tid;
+            S.wr[q] = r;
+            if (r > 0) {
+                const int lb = S.lbase[tid], cap = S.lbase[tid + 1] - lb;
+                int idx = S.q[tid].x + 32 * r - 1;
+                if (idx >= cap) idx -= cap;
+                S.wah[q] = c.P[lb + idx];
+            }
+        }
     }
-    if (tid == 0) {                         // targets 0 start at link 0 (covers nl = 0)
+    if (tid == 0) {
         S.wl[0] = 0;
+        S.wr[0] = 0;
         S.wl[nw] = c.nl;
-        for (int q = 1; q < nw; ++q)
-            if (S.ctot * q < nw) S.wl[q] = 0;
+        S.wr[nw] = 0;
+        if (c.nl == 0)
+            for (int q = 1; q < nw; ++q) S.wl[q] = 0, S.wr[q] = 0;
     }
     const int np = v >> 16;
     for (int k = 0; k < np; ++k) S.plist[(ex >> 16) + k] = (tid << 4) | k;
@@ -536,84 +553,64 @@ __device__ __forceinline__ void p_pairs(const DevSim &d, const PArgs &a, PSmem &
 }
 
 // Newell car-following of every queued vehicle of the CTA, in shared memory,
-// by warps 0 .. nw - 1: warp w owns a contiguous run of links with an equal
-// share of the total cost (1 + rounds of 32 vehicles per link); for a
-// link, lane l updates queue positions l, l + 32, ... (leader first), taking
-// the time-t position of the vehicle ahead from lane l - 1 by a shuffle (from
-// the previous round of 32 for lane 0) before any lane writes.  No barrier is
-// needed: a link's slots are touched by its warp only.  At bin ends the warp
-// also sums the link's vehicles past the midpoint and their positions.
+// by warps 0 .. nw - 1: warp w owns the rounds of 32 queue positions from
+// (S.wl[w], S.wr[w]) up to the start of warp w + 1 (an equal share of the
+// total cost, 1 + rounds per link).  Within a round lane l updates queue
+// position 32 r + l (leader first), taking the time-t position of the vehicle
+// ahead from lane l - 1 by a shuffle, from the previous round for lane 0 (or,
+// at the warp's first round inside a link, from the scan's copy) before any
+// lane writes.  No barrier is needed: a slot is touched by one warp only.  At
+// bin ends the warps also sum the link's vehicles past the midpoint and their
+// positions (shared-memory atomics: a link may be split between warps).
 constexpr int kPCFW = kPCFT / 32;
-
-constexpr int kPLG = 1;          // links a car-following warp updates at once
 
 template <bool kTape>
 __device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int r, bool obs,
                                             bool obs_only) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float M = d.M;
-    const int l0 = S.wl[w], l1 = S.wl[w + 1];
-    for (int lg = l0; lg < l1; lg += kPLG) {
-        int n[kPLG], qh[kPLG], cap[kPLG];
-        unsigned R[kPLG];
-        float4 g[kPLG];
-        float ahead[kPLG];
-        int rounds = 0;
-#pragma unroll
-        for (int j = 0; j < kPLG; ++j) {
-            const int li = lg + j;
-            n[j] = 0;
-            ahead[j] = M;
-            if (li < l1) {
-                const int2 qv = *reinterpret_cast<const int2 *>(&S.q[li]);     // head, length
-                n[j] = qv.y;
-                qh[j] = qv.x;
-                const int lb = S.lbase[li];
-                cap[j] = S.lbase[li + 1] - lb;
-                R[j] = (unsigned)lb;
-                g[j] = S.g[li];
-                rounds = max(rounds, (qv.y + 31) >> 5);
-            }
+    const int l0 = S.wl[w], r0 = S.wr[w], l1 = S.wl[w + 1], r1 = S.wr[w + 1];
+    const int lend = r1 > 0 ? l1 + 1 : l1;
+    for (int li = l0; li < lend; ++li) {
+        const int2 qv = *reinterpret_cast<const int2 *>(&S.q[li]);     // head, length
+        const int lb = S.lbase[li], cap = S.lbase[li + 1] - lb;
+        const float4 g = S.g[li];
+        int kb = 0, ke = qv.y;
+        float ahead = M;
+        if (li == l0 && r0 > 0) {
+            kb = 32 * r0;
+            ahead = S.wah[w];
         }
-        for (int k0 = 0; k0 < rounds * 32; k0 += 32) {
+        if (li == l1) ke = min(ke, 32 * r1);
+        for (int k0 = kb; k0 < ke; k0 += 32) {
             const int k = k0 + lane;
-            float x[kPLG];
-            int idx[kPLG];
+            const bool act = k < ke;
+            int idx = qv.x + k;
+            if (idx >= cap) idx -= cap;
+            const float x = act ? c.P[lb + idx] : 0.0f;
+            const float up = __shfl_up_sync(kFull, x, 1);
+            const float last = __shfl_sync(kFull, x, 31);
+            if (obs) {                      // bin end: vehicles past the midpoint, position sum (time t)
+                const int pj = warp_sum(act && x >= __fmul_rn(g.x, 0.5f) ? 1 : 0);
+                long long sj = act ? pos_fx(x) : 0;
 #pragma unroll
-            for (int j = 0; j < kPLG; ++j) {
-                idx[j] = qh[j] + k;
-                if (idx[j] >= cap[j]) idx[j] -= cap[j];
-                x[j] = k < n[j] ? c.P[R[j] + idx[j]] : 0.0f;
-            }
-#pragma unroll
-            for (int j = 0; j < kPLG; ++j) {
-                const float up = __shfl_up_sync(kFull, x[j], 1);
-                const float last = __shfl_sync(kFull, x[j], 31);
-                if (obs && k0 < n[j]) {     // bin end: vehicles past the midpoint, position sum (time t)
-                    const bool act = k < n[j];
-                    const int pj = warp_sum(act && x[j] >= __fmul_rn(g[j].x, 0.5f) ? 1 : 0);
-                    long long sj = act ? pos_fx(x[j]) : 0;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(kFull, sj, o);
-                    if (lane == 0) {
-                        S.past[lg + j] += pj;
-                        S.psum[lg + j] += (unsigned long long)sj;
-                    }
+                for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(kFull, sj, o);
+                if (lane == 0) {
+                    atomicAdd(&S.past[li], pj);
+                    atomicAdd(&S.psum[li], (unsigned long long)sj);
                 }
-                if (k < n[j]) {
-                    if (!obs_only) {
-                        const float h = k == 0 ? M : __fsub_rn(lane == 0 ? ahead[j] : up, x[j]);
-                        int tag;
-                        c.P[R[j] + idx[j]] = newell(x[j], h, g[j].x, g[j].y, g[j].z, g[j].w, tag);
-                        if (kTape) {                // tape: time-t position and branch tag of the slot
-                            const size_t o = (size_t)r * a.S + c.base0 + R[j] + idx[j];
-                            d.tape_pos[o] = x[j];
-                            d.tag_tape[o] = (int8_t)tag;
-                        }
-                    }
-                }
-                ahead[j] = last;
             }
+            if (act && !obs_only) {
+                const float h = k == 0 ? M : __fsub_rn(lane == 0 ? ahead : up, x);
+                int tag;
+                c.P[lb + idx] = newell(x, h, g.x, g.y, g.z, g.w, tag);
+                if (kTape) {                // tape: time-t position and branch tag of the slot
+                    const size_t o = (size_t)r * a.S + c.base0 + lb + idx;
+                    d.tape_pos[o] = x;
+                    d.tag_tape[o] = (int8_t)tag;
+                }
+            }
+            ahead = last;
         }
     }
 }
