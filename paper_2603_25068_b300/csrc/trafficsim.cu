@@ -1248,7 +1248,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     CU(cudaMemsetAsync(b.Z, 0, 3 * (size_t)L * sizeof(double), h->stream));
     CU(cudaMemsetAsync(b.SA, 0, 3 * (size_t)L * sizeof(double), h->stream));
     k_bwd_init<<<(N + 255) / 256, 256, 0, h->stream>>>(h->d, b, dxT);
-    k_route_scan<<<(int)(((size_t)N * 32 + 255) / 256), 256, 0, h->stream>>>(N, b);
+    k_route_scan<<<(int)(((size_t)N * 32 + 255) / 256), 256, 0, h->stream>>>(h->d, N, b);
     // recomputation: no route log, counters into a scratch array
     DevSim dr = h->d;
     dr.route_log = nullptr;

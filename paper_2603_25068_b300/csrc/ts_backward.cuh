@@ -90,7 +90,8 @@ struct BwdDev {
     const int *route_len;        // [N]
     int *cursor;                 // [N] index of each vehicle's latest entry at a step <= t
                                  // (the reverse pass undoes entries from the last one)
-    unsigned char *rdup;         // [N] 1 if the vehicle's route enters some link twice
+    unsigned char *rdup;         // [N] bit 0: the vehicle's route enters some link twice; bit 1: some
+                                 // node is the head of two of its links (implied by bit 0)
     const float2 *Cbar;          // [n_bins L] adjoint of C_j at the end of each bin
     const float2 *Csuf;          // [(n_bins + 1) L] suffix sums of Cbar
     double *gu, *gs, *ga, *gU, *gG;   // [L]
@@ -137,29 +138,40 @@ __device__ __forceinline__ int route_find(const BwdDev &b, int v, int k0, Pred p
 }
 
 // Per vehicle (a warp each): the reverse pass's entry cursor starts at the last
-// entry, and whether the route enters some link twice (links compared within
-// 32-entry chunks by match, across chunks by shuffles).
-__global__ void k_route_scan(int N, BwdDev b) {
+// entry; whether the route enters some link twice, and whether some node is the
+// head of two of its links (values compared within 32-entry chunks by match,
+// across chunks by shuffles).  A link entered twice has its head twice, so the
+// search ends at the first repeated link.
+__global__ void k_route_scan(DevSim d, int N, BwdDev b) {
     const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (v >= N) return;
     const int n = b.route_len[v];
     const int2 *r = b.route_log + (size_t)v * b.cap;
-    bool dup = false;
+    bool dup = false, hdup = false;
     for (int a = 0; a < n && !dup; a += 32) {
-        const int xa = a + lane < n ? r[a + lane].y : -1 - lane;          // padding never matches
-        const unsigned m = __match_any_sync(kFull, xa);
-        dup = __any_sync(kFull, xa >= 0 && __popc(m) > 1);
+        const int la = a + lane < n ? r[a + lane].y : -1;
+        const int xa = la >= 0 ? la : -1 - lane;                          // padding never matches
+        const int ha = la >= 0 ? d.lnode[la].x : -1 - lane;
+        const unsigned mx = __match_any_sync(kFull, xa), mh = __match_any_sync(kFull, ha);   // every lane
+        dup = __any_sync(kFull, xa >= 0 && __popc(mx) > 1);
+        hdup = hdup || __any_sync(kFull, ha >= 0 && __popc(mh) > 1);
         for (int c = a + 32; c < n && !dup; c += 32) {
-            const int xc = c + lane < n ? r[c + lane].y : -1000 - lane;
-            bool hit = false;
+            const int lc = c + lane < n ? r[c + lane].y : -1;
+            const int xc = lc >= 0 ? lc : -1000 - lane;
+            const int hc = lc >= 0 ? d.lnode[lc].x : -1000 - lane;
+            bool hit = false, hhit = false;
 #pragma unroll 8
-            for (int q = 0; q < 32; ++q) hit |= xa == __shfl_sync(kFull, xc, q);
+            for (int q = 0; q < 32; ++q) {
+                hit |= xa == __shfl_sync(kFull, xc, q);
+                hhit |= ha == __shfl_sync(kFull, hc, q);
+            }
             dup = __any_sync(kFull, hit);
+            hdup = hdup || __any_sync(kFull, hhit);
         }
     }
     if (lane == 0) {
         b.cursor[v] = n - 1;
-        b.rdup[v] = dup ? 1 : 0;
+        b.rdup[v] = (dup ? 1 : 0) | ((dup || hdup) ? 2 : 0);
     }
 }
 
@@ -279,13 +291,23 @@ __device__ __forceinline__ void z_finish(const DevSim &d, const BwdDev &b, int i
         if (won) {
             Enew = z.xv;
             Xold = make_float2(0.0f, 0.0f);
-            if (i < d.L && cur >= 0 && z.dup) {                  // next re-entry into the source link
+            if (i < d.L && cur >= 0 && (z.dup & 1)) {            // next re-entry into the source link
                 const int k = route_find(b, v, cur + 1, [&](int, int l) { return l == i; });
                 if (k >= 0) Xold = b.eadj[(size_t)v * b.cap + k];
             }
         } else {                 // first entry into the target after the current one
             Enew = make_float2(0.0f, 0.0f);
-            const int k = route_find(b, v, cur + 1, [&](int s, int l) { return s > t && l == tgt; });
+            int k = -1;
+            if (i < d.L && !(z.dup & 2)) {
+                // the target starts at the head of link i (entry cur); an entry into it
+                // past cur + 1 would make that node the head of a second link of the route
+                if (cur + 1 < b.route_len[v]) {
+                    const int2 e = b.route_log[(size_t)v * b.cap + cur + 1];
+                    if (e.x > t && e.y == tgt) k = cur + 1;
+                }
+            } else {
+                k = route_find(b, v, cur + 1, [&](int s, int l) { return s > t && l == tgt; });
+            }
             if (k >= 0) Enew = b.eadj[(size_t)v * b.cap + k];
             Xold = z.xv;
         }

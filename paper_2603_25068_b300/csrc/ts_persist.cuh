@@ -703,18 +703,58 @@ __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem 
 }
 
 // tape: vehicle of every occupied slot at the start of step t (record r), by
-// threads [tfirst, tfirst + nt) (the choice warps, once their pairs are done)
-__device__ __forceinline__ void p_tape_vid(const DevSim &d, const PArgs &a, const PSmem &S, const PCtx &c, int r,
-                                           int tfirst, int nt) {
-    const int w = (threadIdx.x - tfirst) >> 5, nw = nt >> 5, lane = threadIdx.x & 31;
-    for (int li = w; li < c.nl; li += nw) {
-        const int2 qv = *reinterpret_cast<const int2 *>(&S.q[li]);
-        const int lb = S.lbase[li], cap = S.lbase[li + 1] - lb;
-        for (int k = lane; k < qv.y; k += 32) {
-            int idx = qv.x + k;
-            if (idx >= cap) idx -= cap;
-            const int gs = c.base0 + lb + idx;
-            d.tape_vid[(size_t)r * a.S + gs] = d.saux[gs].x;
+// every warp once the choice and car-following work of the step is done (the
+// decisions that follow do not depend on it).  A warp takes kTVL consecutive
+// links at a time and issues the loads of their first 32 queue positions before
+// any store, so that the L2 round trips overlap.
+constexpr int kTVL = 4;
+
+__device__ __forceinline__ void p_tape_vid(const DevSim &d, const PArgs &a, const PSmem &S, const PCtx &c, int r) {
+    const int w = threadIdx.x >> 5, nw = kPT / 32, lane = threadIdx.x & 31;
+    int *tv = d.tape_vid + (size_t)r * a.S;
+    for (int l0 = w * kTVL; l0 < c.nl; l0 += nw * kTVL) {
+        int gs[kTVL], v[kTVL];
+#pragma unroll
+        for (int j = 0; j < kTVL; ++j) {
+            const int li = l0 + j;
+            gs[j] = -1;
+            if (li < c.nl) {
+                const int2 qv = *reinterpret_cast<const int2 *>(&S.q[li]);
+                if (lane < qv.y) {
+                    const int lb = S.lbase[li], cap = S.lbase[li + 1] - lb;
+                    int idx = qv.x + lane;
+                    if (idx >= cap) idx -= cap;
+                    gs[j] = c.base0 + lb + idx;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kTVL; ++j) v[j] = gs[j] >= 0 ? __ldcg(&d.saux[gs[j]].x) : 0;
+#pragma unroll
+        for (int j = 0; j < kTVL; ++j)
+            if (gs[j] >= 0) tv[gs[j]] = v[j];
+        for (int j = 0; j < kTVL; ++j) {            // queue positions 32, 64, ... of long queues, kTVL rounds at once
+            const int li = l0 + j;
+            if (li >= c.nl) break;
+            const int2 qv = *reinterpret_cast<const int2 *>(&S.q[li]);
+            const int lb = S.lbase[li], cap = S.lbase[li + 1] - lb;
+            for (int k0 = 32; k0 < qv.y; k0 += 32 * kTVL) {
+#pragma unroll
+                for (int m = 0; m < kTVL; ++m) {
+                    const int k = k0 + 32 * m + lane;
+                    gs[m] = -1;
+                    if (k < qv.y) {
+                        int idx = qv.x + k;
+                        if (idx >= cap) idx -= cap;
+                        gs[m] = c.base0 + lb + idx;
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < kTVL; ++m) v[m] = gs[m] >= 0 ? __ldcg(&d.saux[gs[m]].x) : 0;
+#pragma unroll
+                for (int m = 0; m < kTVL; ++m)
+                    if (gs[m] >= 0) tv[gs[m]] = v[m];
+            }
         }
     }
 }
@@ -826,11 +866,11 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         const unsigned long long *Wp = a.W3 + (size_t)((t + 2) % 3) * d.L;     // words of step t-1
         if (tid >= kPCFT) {
             p_pairs(d, a, S, c, t, first, Cp, Wp, kPCFT, kPT - kPCFT);
-            if (kTape) p_tape_vid(d, a, S, c, t - a.t0, kPCFT, kPT - kPCFT);
         } else {
             p_carfollow<kTape>(d, a, S, c, t - a.t0, obs, false);
         }
         __syncthreads();
+        if (kTape) p_tape_vid(d, a, S, c, t - a.t0);
         if (tid < 4) S.cnt[tid] = 0;
         p_decide<kTape>(d, a, S, c, t, first, obs, false, Cp, Wp);
         p_refill(S, c, pd);
