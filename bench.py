@@ -243,6 +243,10 @@ def run_fwd_bwd(args, dev, stream, flush, ws):
     sim = Simulator(model, device=dev.index, stream=stream, ckpt_every=60, route_cap=256)
     nb = sim.n_bins(T)
     sens = model.sensors
+    from paper_2603_25068_b300.autotune import tune_recompute
+    ybar0 = np.zeros((nb, model.L), np.float32)
+    ybar0[:, sens] = 1e-3
+    recompute, recompute_ms = tune_recompute(sim, ybar0, T)
     times, t_fwd, t_bwd = [], [], []
     for k in range(args.warmup + args.steps):
         flush.fill_(float(k))
@@ -269,6 +273,7 @@ def run_fwd_bwd(args, dev, stream, flush, ws):
             "timing": "host wall clock per iteration (rollout with host outputs, host loss, sim_backward to host), "
                       "L2 flushed before each",
             "forward_ms": 1000 * float(np.mean(t_fwd)), "reverse_ms": 1000 * float(np.mean(t_bwd)),
+            "recompute": recompute, "recompute_autotune_ms": {k: round(v, 2) for k, v in recompute_ms.items()},
             "grad_norm_w": float(np.linalg.norm(g["w"])), "grad_norm_lambda": float(np.linalg.norm(g["od_lambda"]))}
 
 

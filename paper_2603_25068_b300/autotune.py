@@ -90,3 +90,28 @@ def balance_partition(sim, T=None, samples: int = 12, per_link: float = 1.0, occ
     w = occ + float(per_link)
     sim.set_partition_weights(w)
     return w
+
+
+RECOMPUTE_MODES = ("overlap", "serial")
+
+
+def tune_recompute(sim, ybar, T=None, modes=RECOMPUTE_MODES):
+    """Segment recomputation of the reverse pass: times one reverse pass of a
+    fresh rollout per mode (after one untimed pass) and keeps the faster.
+    Gradients do not depend on the mode.  Returns (best, {mode: ms})."""
+    import time
+    import torch
+    sim.rollout(T)
+    sim.backward(ybar)                               # workspaces and streams exist before timing
+    times = {}
+    for m in modes:
+        sim.set_recompute(m)
+        sim.rollout(T)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.backward(ybar)
+        torch.cuda.synchronize()
+        times[m] = 1e3 * (time.perf_counter() - t0)
+    best = min(times, key=times.get)
+    sim.set_recompute(best)
+    return best, times

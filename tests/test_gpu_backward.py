@@ -122,3 +122,25 @@ def test_concurrent_reverse_passes_equal_sequential(Simulator):
             np.testing.assert_allclose(b[k], a[k], rtol=0, atol=1e-6 * scale, err_msg=k)
     for s_ in sims:
         s_.close()
+
+
+def test_tune_recompute_keeps_a_mode_and_the_gradient(Simulator):
+    # the recompute-mode autotuner times both modes and keeps one; the
+    # gradient after tuning is the gradient of either mode
+    from paper_2603_25068_b300.autotune import RECOMPUTE_MODES, tune_recompute
+    sc = S.city_small()
+    g = Simulator(sc, ckpt_every=30, route_cap=64)
+    out = g.rollout()
+    ybar = np.random.default_rng(5).normal(size=out["counts"].shape).astype(np.float32)
+    g.set_recompute("overlap")
+    g.rollout()
+    ref = g.backward(ybar)
+    best, times = tune_recompute(g, ybar)
+    assert best in RECOMPUTE_MODES and set(times) == set(RECOMPUTE_MODES)
+    assert all(v > 0 for v in times.values())
+    g.rollout()
+    got = g.backward(ybar)
+    for k in ref:
+        scale = np.max(np.abs(ref[k])) + 1e-30
+        assert np.max(np.abs(got[k].astype(np.float64) - ref[k])) <= 1e-6 * scale, k
+    g.close()
