@@ -54,6 +54,7 @@ def parse():
                     help="forward executor of the timed rollouts")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other forward executor")
     ap.add_argument("--no-fwd-bwd", action="store_true", help="skip the calibration-gradient leg")
+    ap.add_argument("--no-platoons", action="store_true", help="skip the platoon (dn = 30) leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-scenario leg")
     ap.add_argument("--batch-n", type=int, default=64)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
@@ -225,6 +226,41 @@ def ncu_traffic(kernel, workload_key, launch_units):
 
 
 # ------------------------------------------------------------------ fwd + bwd
+def run_platoons(args, dev, stream, flush, ws):
+    """Platoon form of the forward rollout (Methods: dt = tau dn, tau = 1 s):
+    the city network's 1,000,000 vehicles as 33,334 agents of 30 vehicles, one
+    hour in 120 steps of 30 s, departures over the first 30 minutes."""
+    import torch
+    from paper_2603_25068_b300 import scenario as S
+    from paper_2603_25068_b300.sim import Simulator
+    dn = 30
+    sc = S.with_platoons(S.city(n_vehicles=1_000_000 // dn), dn)
+    sim = Simulator(sc, device=dev.index, stream=stream)
+    out = sim.rollout(device=True)
+    for _ in range(max(args.warmup, 3)):
+        sim.rollout(device=True, out=out)
+    reps = max(args.steps, 20)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    torch.cuda.synchronize(dev)
+    for k in range(reps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        sim.rollout(device=True, out=out)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = slowest(sum(a.elapsed_time(b) for a, b in ev) / 1000.0, dev) * 1000.0 / reps
+    n_arr = int(sim.outputs()["n_arrived"][-1]) if hasattr(sim, "outputs") else None
+    sim.close()
+    horizon_s = sc.T * sc.dt
+    return {"workload": f"city network, {sc.N * dn:,} vehicles as {sc.N:,} platoons of {dn}, "
+                        f"{sc.T} steps of {sc.dt:g} s (one hour)",
+            "ms_per_rollout": ms, "x_real_time": horizon_s / (ms / 1000.0),
+            "agent_steps_per_s": ws * sc.N * sc.T / (ms / 1000.0),
+            "vehicle_seconds_per_s": ws * sc.N * dn * horizon_s / (ms / 1000.0),
+            "executor": "persistent", "arrived_platoons": n_arr,
+            "timing": "CUDA events on the simulator's stream, L2 flushed before each rollout"}
+
+
 def run_fwd_bwd(args, dev, stream, flush, ws):
     """Calibration-gradient workload: 1,800-step rollout of the city network with
     the reverse pass (checkpoints every 60 steps) of the squared error of
@@ -580,6 +616,8 @@ def run_ours(args):
 
     if not args.no_fwd_bwd:
         line["fwd_bwd"] = run_fwd_bwd(args, dev, stream, flush, ws)
+    if not args.no_platoons:
+        line["platoons"] = run_platoons(args, dev, stream, flush, ws)
     if not args.no_batched:
         line["batched"] = run_batched(args, dev, stream, flush, ws)
     if not args.no_serve:

@@ -388,6 +388,22 @@ def line_network(n_links: int = 3, length: float = 100.0, u: float = 10.0,
                     od_lambda=_f32([float(N)]), T=T, tau=tau, seed=seed, obs_every=T)
 
 
+def with_platoons(sc: Scenario, dn: float, tau_s: float = 1.0) -> Scenario:
+    """The same scenario with agents that are platoons of dn vehicles (Methods:
+    step length dt = tau_s dn, jam spacing dn / kappa, a transfer needs dn of
+    outflow credit).  Times keep their length in seconds: the outflow capacity in
+    vehicles per second (so the credit per step becomes q dt), the departure
+    times, the horizon and the observation bins.  The agents are those of sc;
+    for the same number of vehicles draw sc with N / dn of them."""
+    dt = float(tau_s) * float(dn)
+    r = sc.dt / dt
+    q = sc.q_fx.astype(np.float64) / 65536.0 / sc.dt
+    return sc.copy(dn=float(dn), dt=dt, q_fx=_capacity_fx(q, dt),
+                   dep_step=_i32(np.floor(sc.dep_step.astype(np.float64) * r)),
+                   T=max(1, int(np.ceil(sc.T * r))),
+                   obs_every=max(1, int(round(sc.obs_every * r))))
+
+
 def random_small(seed: int = 0, side: int = 3, n_vehicles: int = 40, T: int = 80,
                  tau: float = 0.5, length_range=(20.0, 60.0)) -> Scenario:
     """Small grid with heterogeneous links and parameters, dense enough that

@@ -65,6 +65,13 @@ def test_backward_city_small(Simulator, recompute):
     compare(Simulator, sc, 60, seed=5, with_xT=False, recompute=recompute)
 
 
+@pytest.mark.parametrize("recompute", ["overlap", "serial"])
+def test_backward_platoons(Simulator, recompute):
+    # agents of 5 vehicles (step 5 s); gradients against the oracle's reverse mode
+    sc = S.with_platoons(S.random_small(seed=2, side=3, n_vehicles=150, T=750), 5.0)
+    compare(Simulator, sc, 20, recompute=recompute)
+
+
 def test_backward_tg_toy(Simulator):
     sc = S.tg_toy(2.0, 1.0)
     g = Simulator(sc, ckpt_every=4, route_cap=8)

@@ -71,6 +71,14 @@ def test_lockstep_dense_small(Simulator, seed):
     lockstep(Simulator, sc.copy(obs_every=40), 150)
 
 
+@pytest.mark.parametrize("dn", [5.0, 30.0])
+def test_lockstep_platoons(Simulator, dn):
+    # agents of dn vehicles: step dn seconds, jam spacing dn / kappa, a transfer
+    # takes dn of outflow credit
+    sc = S.with_platoons(S.random_small(seed=2, side=3, n_vehicles=150, T=int(150 * dn)), dn)
+    lockstep(Simulator, sc, sc.T)
+
+
 def test_lockstep_wide_choice_set(Simulator):
     # the hub has 11 out-links: slots beyond those evaluated in parallel by the
     # persistent executor's choice warps are evaluated at the decision

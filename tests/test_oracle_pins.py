@@ -155,6 +155,30 @@ def test_invariants_dense_small(prec):
     _per_step_invariants(sc, prec)
 
 
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_invariants_platoons(prec):
+    # agents of 5 vehicles (step 5 s, jam spacing 5 / kappa, credit 5 per transfer)
+    sc = S.with_platoons(S.random_small(seed=3, side=3, n_vehicles=120, T=600), 5.0)
+    _per_step_invariants(sc, prec)
+
+
+@pytest.mark.parametrize("dn", [1, 5, 30])
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_platoon_discharge_rate_is_capacity(prec, dn):
+    """Platoons of dn vehicles with a step of dn seconds (Methods: dt = tau dn,
+    tau = 1 s): the credit grows by q dt per step and a transfer takes dn of it,
+    so a saturated link still discharges q = 0.5 vehicles per second."""
+    N = 300
+    sc = S.with_platoons(S.line_network(n_links=2, length=300.0, u=13.9, kappa=0.2, q=0.5, N=N, T=10), dn)
+    T = int(np.ceil(N * dn / 0.5 / sc.dt)) + int(np.ceil(120.0 / sc.dt)) + 10     # + the free-flow trip
+    out = OracleSim(sc.copy(T=T, obs_every=T), prec).rollout()
+    arr = out["n_arrived"]
+    assert arr[-1] == N
+    i0, i1 = np.searchsorted(arr, 0.2 * N), np.searchsorted(arr, 0.8 * N)
+    rate = (arr[i1] - arr[i0]) * dn / ((i1 - i0) * sc.dt)
+    assert abs(rate - 0.5) < 0.01, rate
+
+
 # ---------------------------------------------------------------- choice model
 def _star(beta, n_veh, tau=0.5, seed=0):
     k = len(beta)
