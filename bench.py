@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other forward executor")
     ap.add_argument("--no-fwd-bwd", action="store_true", help="skip the calibration-gradient leg")
     ap.add_argument("--no-platoons", action="store_true", help="skip the platoon (dn = 30) leg")
+    ap.add_argument("--no-calib-loop", action="store_true", help="skip the calibration-loop leg")
+    ap.add_argument("--calib-iters", type=int, default=10)
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-scenario leg")
     ap.add_argument("--batch-n", type=int, default=64)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
@@ -259,6 +261,32 @@ def run_platoons(args, dev, stream, flush, ws):
             "vehicle_seconds_per_s": ws * sc.N * dn * horizon_s / (ms / 1000.0),
             "executor": "persistent", "arrived_platoons": n_arr,
             "timing": "CUDA events on the simulator's stream, L2 flushed before each rollout"}
+
+
+def run_calibration_loop(args, dev, stream, ws):
+    """The calibration loop (Methods, Optimization) on the calibration-gradient
+    workload: AdamW on the 10,240 demand and 16 route-choice parameters,
+    a fixed number of iterations (the early stop is not reached)."""
+    import torch
+    from paper_2603_25068_b300 import scenario as S
+    from paper_2603_25068_b300.optimize import calibrate
+    from paper_2603_25068_b300.sim import Simulator
+    model, truth = S.calibration()
+    sens = model.sensors
+    y_obs = Simulator(truth, device=dev.index, stream=stream).rollout()["counts"][:, sens]
+    sim = Simulator(model, device=dev.index, stream=stream, ckpt_every=60, route_cap=256)
+    calibrate(sim, y_obs, sens, max_iter=1)                     # workspaces, graphs
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    res = calibrate(sim, y_obs, sens, max_iter=args.calib_iters, patience=10 ** 6)
+    torch.cuda.synchronize(dev)
+    sec = slowest(time.perf_counter() - t0, dev)
+    sim.close()
+    return {"workload": f"calibration gradient workload ({model.N:,} vehicles, {model.T} steps), AdamW lr 0.1 "
+                        f"wd 1e-5 on {model.n_od} demand + {model.F} route-choice parameters",
+            "iterations": res["iterations"], "seconds": sec, "s_per_iteration": sec / res["iterations"],
+            "loss_first": res["losses"][0], "loss_best": res["best_loss"], "best_iter": res["best_iter"],
+            "timing": "host wall clock, device synchronised (forward, loss, reverse pass, update)"}
 
 
 def run_fwd_bwd(args, dev, stream, flush, ws):
@@ -618,6 +646,8 @@ def run_ours(args):
         line["fwd_bwd"] = run_fwd_bwd(args, dev, stream, flush, ws)
     if not args.no_platoons:
         line["platoons"] = run_platoons(args, dev, stream, flush, ws)
+    if not args.no_calib_loop:
+        line["calibration_loop"] = run_calibration_loop(args, dev, stream, ws)
     if not args.no_batched:
         line["batched"] = run_batched(args, dev, stream, flush, ws)
     if not args.no_serve:

@@ -291,6 +291,13 @@ SIM_API int32_t sim_persist_groups(sim_handle h, int32_t *first_link);
  * Errors: SIM_EINVAL (missing < 0, or no persistent executor for h). */
 SIM_API int sim_test_barrier_timeout(sim_handle h, int32_t missing);
 
+/* The stream the handle's work is enqueued on (a cudaStream_t: the caller's
+ * options.stream, or the one the handle created), NULL for a NULL handle.
+ * Device outputs are complete once this stream has reached the point where
+ * the call returned; callers on other streams order themselves after it with
+ * an event. */
+SIM_API void *sim_get_stream(sim_handle h);
+
 /* Move the handle's work to another stream of its device (the old stream is
  * drained first; a stream the handle created is destroyed).  NULL: only drain.
  * Not for a handle that is a member of a live batch. */

@@ -18,19 +18,31 @@ PARAMS = ("u", "kappa", "alpha", "beta", "cost", "w", "alpha_origin", "od_lambda
 
 
 class RolloutCounts(torch.autograd.Function):
+    # The simulator enqueues on its own stream: it waits for torch's current
+    # stream before it reads or writes tensors torch produced or allocated, and
+    # torch's stream waits for it before the outputs are used.
     @staticmethod
     def forward(ctx, sim, T, u, kappa, alpha, beta, cost, w, alpha_origin, od_lambda):
         host = lambda x: x.detach().to("cpu", torch.float32).numpy()
         sim.set_params(u=host(u), kappa=host(kappa), alpha=host(alpha), beta=host(beta), cost=host(cost),
                        w=host(w), alpha_origin=float(alpha_origin.detach().reshape(-1)[0]))
+        cur, s = torch.cuda.current_stream(torch.device("cuda", sim.device)), sim.torch_stream()
+        s.wait_stream(cur)
         out = sim.rollout(T, device=True)
+        cur.wait_stream(s)
         ctx.sim = sim
         ctx.od_dtype = od_lambda.dtype
         return out["counts"].to(torch.float32)
 
     @staticmethod
     def backward(ctx, g_counts):
-        g = ctx.sim.backward_device(g_counts)
+        sim = ctx.sim
+        dev = torch.device("cuda", sim.device)
+        yb = g_counts.to(device=dev, dtype=torch.float32).contiguous()      # before the wait: made on torch's stream
+        cur, s = torch.cuda.current_stream(dev), sim.torch_stream()
+        s.wait_stream(cur)
+        g = sim.backward_device(yb)
+        cur.wait_stream(s)
         return (None, None, g["u"], g["kappa"], g["alpha"], g["beta"], g["cost"], g["w"],
                 g["alpha_origin"].reshape(()), g["od_lambda"])
 

@@ -1615,6 +1615,7 @@ extern "C" int32_t sim_get_executor(sim_handle h) {
 }
 
 extern "C" int32_t sim_time(sim_handle h) { return h ? h->t : -1; }
+extern "C" void *sim_get_stream(sim_handle h) { return h ? (void *)h->stream : nullptr; }
 extern "C" size_t sim_device_bytes(sim_handle h) { return h ? h->bytes : 0; }
 
 extern "C" int sim_destroy(sim_handle h) {

@@ -78,6 +78,7 @@ SIGNATURES = {
     "sim_set_state": (C.c_int, [P, C.POINTER(sim_state_view), C.c_int32]),
     "sim_set_stage": (C.c_int, [P, C.c_int32]),
     "sim_set_stream": (C.c_int, [P, P]),
+    "sim_get_stream": (C.c_void_p, [P]),
     "sim_set_executor": (C.c_int, [P, C.c_int32]),
     "sim_get_executor": (C.c_int32, [P]),
     "sim_test_barrier_timeout": (C.c_int, [P, C.c_int32]),

@@ -101,6 +101,15 @@ class Simulator:
         self._check(self.lib.sim_set_stream(self.h, stream))
         self.stream_ptr = stream
 
+    def torch_stream(self):
+        """The handle's stream as a torch stream (for ordering torch work
+        before or after the simulator's device work)."""
+        import torch
+        ptr = self.lib.sim_get_stream(self.h)
+        if not ptr:
+            return torch.cuda.default_stream(self.device)
+        return torch.cuda.ExternalStream(ptr, device=torch.device("cuda", self.device))
+
     def device_bytes(self):
         return self.lib.sim_device_bytes(self.h)
 
