@@ -41,13 +41,17 @@ def initial_params(sim):
 
 
 def run(sim, loss_fn, names, params=None, max_iter=200, patience=PATIENCE, lr=LR, weight_decay=WEIGHT_DECAY,
-        project=None, T=None):
+        project=None, T=None, transform=None):
     """The loop for the parameters in `names`.  loss_fn(counts) -> scalar
     tensor, counts [n_bins, L] float32 on the device.  project(params), if
     given, restores bounds after each update (in place, no gradient).
+    transform(params), if given, maps the trained tensors to the simulator's
+    parameters (differentiably) before each rollout.
     Returns a dict: best_loss, best_iter, iterations, losses (per iteration),
-    params (host copies of the trained tensors at the best iteration)."""
+    params (host copies of the named simulator parameters at the best
+    iteration) and last_params (the same after the last update)."""
     p = initial_params(sim) if params is None else params
+    tf = transform if transform is not None else (lambda x: x)
     train = [p[k] for k in names]
     for t in train:
         t.requires_grad_(True)
@@ -55,23 +59,25 @@ def run(sim, loss_fn, names, params=None, max_iter=200, patience=PATIENCE, lr=LR
     best, best_iter, best_params, losses = float("inf"), -1, None, []
     for it in range(max_iter):
         opt.zero_grad(set_to_none=True)
-        counts = rollout_counts(sim, p["u"], p["kappa"], p["alpha"], p["beta"], p["cost"], p["w"],
-                                p["alpha_origin"], p["od_lambda"], T=T)
+        q = tf(p)
+        counts = rollout_counts(sim, q["u"], q["kappa"], q["alpha"], q["beta"], q["cost"], q["w"],
+                                q["alpha_origin"], q["od_lambda"], T=T)
         loss = loss_fn(counts)
         loss.backward()
         lv = float(loss.detach())
         losses.append(lv)
         if lv < best:
             best, best_iter = lv, it
-            best_params = {k: p[k].detach().cpu().numpy().copy() for k in names}
+            best_params = {k: q[k].detach().cpu().numpy().copy() for k in names}
         if it - best_iter >= patience:
             break
         opt.step()
         if project is not None:
             with torch.no_grad():
                 project(p)
+    last = tf(p)
     return {"best_loss": best, "best_iter": best_iter, "iterations": len(losses), "losses": losses,
-            "params": best_params}
+            "params": best_params, "last_params": {k: last[k].detach().cpu().numpy().copy() for k in names}}
 
 
 def calibrate(sim, observed, sensors, names=("w", "od_lambda"), lambda_min=1e-3, **kw):
@@ -109,3 +115,51 @@ def control(sim, target, goal_fraction=0.5, baseline=None, names=("cost",), cost
     res = run(sim, loss_fn, names, project=project, **kw)
     res.update(goal=goal, baseline=baseline)
     return res
+
+
+def range_simulator(model, ranges, **sim_kw):
+    """A simulator for calibrating within `ranges`: its queue rings are sized
+    for the largest jam density of the range (the ring capacity is fixed when
+    the simulator is created), and it starts at the model's parameters."""
+    from .sim import Simulator
+    sized = model
+    if "kappa" in ranges:
+        sized = model.copy(kappa=np.full(model.L, max(float(ranges["kappa"][1]), float(np.max(model.kappa))),
+                                         np.float32))
+    sim = Simulator(sized, **sim_kw)
+    sim.sc = model
+    sim.set_params()
+    return sim
+
+
+def calibrate_ranges(sim, observed, sensors, ranges, **kw):
+    """Calibration of per-link parameters within given ranges ({name: (lo,
+    hi)}, e.g. the paper's u, kappa, beta, alpha ranges).  The optimiser works
+    on z = (theta - lo) / (hi - lo), kept in [0, 1], so that the learning rate
+    is a fraction of each range (a step of 0.1 moves a tenth of it); it starts
+    from the simulator's current parameters.  The result's params are the
+    simulator parameters theta."""
+    p = initial_params(sim)
+    lo = {k: float(r[0]) for k, r in ranges.items()}
+    span = {k: float(r[1]) - float(r[0]) for k, r in ranges.items()}
+    for k in ranges:
+        p[k] = ((p[k] - lo[k]) / span[k]).clamp(0.0, 1.0)
+
+    def transform(x):
+        y = dict(x)
+        for k in ranges:
+            y[k] = lo[k] + span[k] * x[k]
+        return y
+
+    def project(x):
+        for k in ranges:
+            x[k].clamp_(0.0, 1.0)
+
+    dev = torch.device("cuda", sim.device)
+    obs = torch.as_tensor(np.asarray(observed), dtype=torch.float32, device=dev)
+    sens = torch.as_tensor(np.asarray(sensors), dtype=torch.long, device=dev)
+
+    def loss_fn(counts):
+        return ((counts[:, sens] - obs) ** 2).mean()
+
+    return run(sim, loss_fn, tuple(ranges), params=p, project=project, transform=transform, **kw)

@@ -485,6 +485,52 @@ def hub(n_spokes: int = 11, n_vehicles: int = 400, T: int = 400, seed: int = 0) 
                   alpha=rng.uniform(0.5, 4.0, size=L), q=0.6, T=T, seed=seed, name="hub").copy(obs_every=60)
 
 
+PAPER_RANGES = {"u": (13.9, 22.2), "kappa": (0.18, 0.22), "beta": (0.0, 5.0), "alpha": (0.01, 5.0)}
+
+
+def paper_mode(seed: int = 0, n_nodes: int = 48, n_links: int = 100, n_vehicles: int = 20_000,
+               T: int = 1800, dep_window: float = 1800.0, coverage: float = 0.8, q: float = 1.5,
+               w_dest: float = 6.0):
+    """Paper-mode calibration problem shaped like the paper's Sioux Falls runs
+    (Methods, experimental setting): a planar network of n_nodes / n_links,
+    utility beta / c with c = 1 plus one fixed destination term (w_dest times
+    minus the free-flow minutes to the destination; with no destination term
+    the choice does not steer vehicles home and the network jams), vehicles
+    spread evenly over the nodes as origins with random destinations,
+    departures uniform over dep_window seconds.  The truth draws u, kappa,
+    beta, alpha per link uniformly from the paper's ranges; the model starts
+    at the range means.  Sensors: a `coverage` fraction of the links.
+    Returns (model, truth), both with `sensors` set."""
+    rng = np.random.default_rng(seed)
+    pts, und = _planar_graph(rng, n_nodes, n_links // 2)
+    tail = _i32(np.concatenate([und[:, 0], und[:, 1]]))
+    head = _i32(np.concatenate([und[:, 1], und[:, 0]]))
+    L = len(tail)
+    length = _f32(np.clip(rng.lognormal(np.log(1500.0), 0.5, size=L), 200.0, 8000.0))   # km-scale links
+    origin = _i32(np.arange(n_vehicles) % n_nodes)
+    dest = _i32((origin + rng.integers(1, n_nodes, size=n_vehicles)) % n_nodes)
+    dep = _i32(np.sort(rng.integers(0, max(1, int(dep_window)), size=n_vehicles)))
+    truth_p = {k: _f32(rng.uniform(lo, hi, size=L)) for k, (lo, hi) in PAPER_RANGES.items()}
+    mean_p = {k: _f32(np.full(L, 0.5 * (lo + hi))) for k, (lo, hi) in PAPER_RANGES.items()}
+    sensors = _i32(np.sort(rng.choice(L, size=int(round(coverage * L)), replace=False)))
+
+    def make(p, name):
+        sc = custom(tail, head, length=length, origin=origin, dest_node=dest, dep_step=dep, u=p["u"],
+                    kappa=p["kappa"], alpha=p["alpha"], beta=p["beta"], cost=1.0, q=q, T=T, seed=seed,
+                    phi=np.zeros((L, 1), np.float32), psi=np.ones((L, 1), np.float32), w=_f32([w_dest]),
+                    name=name)
+        return sc.copy(obs_every=300, sensors=sensors, coords=pts)
+
+    return make(mean_p, "paper_mode"), make(truth_p, "paper_mode_truth")
+
+
+def noisy_counts(counts, rng, rel=0.1):
+    """Observed counts: simulated counts with multiplicative Gaussian noise of
+    relative size `rel` (10 % in the paper), rounded and kept >= 0."""
+    c = np.asarray(counts, np.float64)
+    return np.maximum(0.0, np.rint(c * (1.0 + rel * rng.standard_normal(c.shape))))
+
+
 def calibration(n_sensors: int = 2000, T: int = 1800, seed_truth: int = 2, **kw):
     """Calibration-gradient workload: the city network and 30-minute rollouts
     with 5-minute counts on n_sensors links; observations come from a hidden
