@@ -275,8 +275,9 @@ SIM_API int32_t sim_get_executor(sim_handle h);
  * a per-link constant, so that CTAs get equal work rather than equal capacity.
  * NULL restores the default.  Results do not depend on the partition (they
  * are bit-identical).  Call between runs, not while another call on h is in
- * progress.  Errors: SIM_EINVAL (invalid weights; a weighting under which the
- * queues no longer fit leaves the previous partition in place). */
+ * progress.  The paper has no counterpart (its step is not partitioned).
+ * Errors: SIM_EINVAL (invalid weights; a weighting under which the queues no
+ * longer fit leaves the previous partition in place). */
 SIM_API int sim_set_partition_weights(sim_handle h, const float *w);
 /* Number of CTAs of the persistent executor (0 if it is unavailable, -1 on
  * error); first_link (host, may be NULL) receives the G + 1 group bounds. */
@@ -295,7 +296,7 @@ SIM_API int sim_test_barrier_timeout(sim_handle h, int32_t missing);
  * options.stream, or the one the handle created), NULL for a NULL handle.
  * Device outputs are complete once this stream has reached the point where
  * the call returned; callers on other streams order themselves after it with
- * an event. */
+ * an event.  The paper has no counterpart. */
 SIM_API void *sim_get_stream(sim_handle h);
 
 /* Move the handle's work to another stream of its device (the old stream is
