@@ -1,0 +1,60 @@
+"""The reverse pass's gradient against the expected loss it stands for.
+
+The simulation draws Gumbel noise, so the loss of one run is piecewise
+constant in the parameters; its expectation over the noise is smooth.  Along
+the descent direction d of the surrogate gradient (averaged over seeds), a
+central finite difference of the mean loss over the same seeds (common random
+numbers) must fall as the surrogate predicts (Methods, Optimization: the
+gradient steers the calibration).  Oracle only (fp64), a small paper-mode
+problem."""
+import numpy as np
+import pytest
+
+from oracle.optim import calibration_loss
+from oracle.oracle import OracleSim
+from paper_2603_25068_b300 import scenario as S
+
+K = 24                       # seeds
+
+
+@pytest.fixture(scope="module")
+def problem():
+    model, truth = S.paper_mode(n_vehicles=4000, T=600, dep_window=600)
+    obs = S.noisy_counts(OracleSim(truth, "fp64").rollout()["counts"][:, model.sensors], np.random.default_rng(1))
+    return model, obs
+
+
+def _loss(sc, obs, grad):
+    o = OracleSim(sc, "fp64", keep_history=grad)
+    L, yb = calibration_loss(o.rollout()["counts"], obs, sc.sensors)
+    return L, (o.backward(yb) if grad else None)
+
+
+def _check(problem, name):
+    model, obs = problem
+    gbar = np.mean([_loss(model.copy(seed=100 + s), obs, True)[1][name] for s in range(K)], axis=0)
+    d = -gbar / np.abs(gbar).max()
+    lo, hi = S.PAPER_RANGES[name]
+    eps = 0.02 * (hi - lo)
+    p = getattr(model, name).astype(np.float64)
+    fd = np.array([(_loss(model.copy(seed=100 + s, **{name: (p + eps * d).astype(np.float32)}), obs, False)[0]
+                    - _loss(model.copy(seed=100 + s, **{name: (p - eps * d).astype(np.float32)}), obs, False)[0])
+                   / (2 * eps) for s in range(K)])
+    pred = float(gbar @ d)
+    return pred, fd.mean(), fd.std() / np.sqrt(K)
+
+
+@pytest.mark.parametrize("name", ["u", "kappa"])
+def test_surrogate_gradient_descends_the_expected_loss(problem, name):
+    pred, fd, se = _check(problem, name)
+    assert pred < 0
+    assert fd < -2.0 * se, (name, pred, fd, se)        # the loss falls along the surrogate's descent direction
+
+
+@pytest.mark.xfail(strict=True, reason="the merge-priority gradient of the straight-through surrogate is "
+                                       "dominated by its M-scaled sentinel term and does not descend the "
+                                       "expected loss on this problem (measured: +4.3 +- 1.1 along its "
+                                       "descent direction)")
+def test_merge_priority_gradient_descends_the_expected_loss(problem):
+    pred, fd, se = _check(problem, "alpha")
+    assert fd < -2.0 * se, (pred, fd, se)
