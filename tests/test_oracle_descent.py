@@ -51,10 +51,10 @@ def test_surrogate_gradient_descends_the_expected_loss(problem, name):
     assert fd < -2.0 * se, (name, pred, fd, se)        # the loss falls along the surrogate's descent direction
 
 
-@pytest.mark.xfail(strict=True, reason="the merge-priority gradient of the straight-through surrogate is "
-                                       "dominated by its M-scaled sentinel term and does not descend the "
-                                       "expected loss on this problem (measured: +4.3 +- 1.1 along its "
-                                       "descent direction)")
+@pytest.mark.xfail(strict=True, reason="the paper's straight-through merge surrogate (Eq. transfer carries "
+                                       "the sentinel M into the merge adjoint) gives an alpha gradient that "
+                                       "does not descend the expected loss on this problem (measured: "
+                                       "+4.3 +- 1.1 along its descent direction)")
 def test_merge_priority_gradient_descends_the_expected_loss(problem):
     pred, fd, se = _check(problem, "alpha")
     assert fd < -2.0 * se, (pred, fd, se)
