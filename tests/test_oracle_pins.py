@@ -68,6 +68,21 @@ def test_lone_vehicle_link_time(prec, length, u):
     np.testing.assert_allclose(tt[:3], k, rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("dn", [5.0, 30.0])
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_lone_platoon_link_time(prec, dn):
+    """A lone platoon of dn vehicles (Methods: dt = tau dn, tau = 1 s) moves
+    u dt per step: it is at each link's end after k = ceil((L - eps)/(u dt))
+    steps, and its link time is k dt seconds."""
+    length, u = 1000.0, 13.9
+    sc = S.with_platoons(S.line_network(n_links=3, length=length, u=u, N=1, T=2000), dn)
+    out = OracleSim(sc, prec).rollout()
+    k = math.ceil((np.float32(length) - 0.01) / (np.float32(u) * np.float32(sc.dt)))
+    arr = np.nonzero(out["n_arrived"])[0][0]
+    assert arr == 1 + 3 * k
+    np.testing.assert_allclose(out["travel_time"][0][:3], k * sc.dt, rtol=1e-6)
+
+
 @pytest.mark.parametrize("dt", [1.0, 0.1, 0.02])
 def test_lone_vehicle_small_dt_limit(dt):
     """With dt = tau dn, tau = 1 (Methods), the link time of a lone vehicle
