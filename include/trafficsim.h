@@ -393,25 +393,33 @@ SIM_API const char *sim_batch_last_error(sim_batch b);
 
 /* Forward rollout that allocates nothing -- the same computation and outputs as
  * sim_create + sim_rollout + sim_destroy, for callers that may not allocate
- * device memory: code running while a stream is captured into a CUDA graph,
- * plug-ins whose host process owns every device allocation, real-time loops.
- * The paper has no counterpart of this entry point.
+ * device memory: plug-ins inside a host application whose memory manager owns
+ * every device allocation (it may refuse, or fail to account for, a cudaMalloc
+ * made behind its back), and real-time loops, where cudaMalloc / cudaFree can
+ * block the host thread and synchronise the device.  The paper has no
+ * counterpart of this entry point.
  *   Scratch: one file-scope device array of 16 MiB (every GPU that loads the
  *   library holds it until the process exits) plus fixed static host buffers.
  *   Limits: V <= 4096 nodes, L <= 8192 links, N <= 65536 vehicles, T <= 8192
  *   steps, all choice sets together <= 65536 entries, and every array of the
- *   run inside the 16 MiB; beyond them the call returns SIM_EOVERFLOW.
- *   Inputs: host arrays as for sim_create.  Outputs: as sim_rollout (device or
- *   host per out->on_device; the n_* counters only into host memory).
+ *   run inside the 16 MiB; beyond them the call returns SIM_EOVERFLOW before
+ *   any device work.
+ *   Inputs: host arrays as for sim_create (phi, psi and w may be NULL only when
+ *   F = 0; the demand arrays only when N = 0).  Outputs: as sim_rollout
+ *   (device or host per out->on_device; the n_* counters only into host
+ *   memory: with on_device set they must be NULL).
  *   Work runs on options->stream (NULL = the default stream) of
  *   options->device; the call returns after the stream has drained.
  *   The first call on a device looks up the device address of the scratch
- *   array (cudaGetSymbolAddress); make that first call before any stream
- *   capture.  Every call re-initialises the whole scratch, and all calls share
- *   it: calls that overlap on the GPU (other streams, other host threads) race.
- *   Returns SIM_OK, SIM_EINVAL (bad argument), SIM_EOVERFLOW (a limit above,
- *   or a link queue overflowed on the device) or SIM_ECUDA; no error text is
- *   kept for this call. */
+ *   array (cudaGetSymbolAddress) before any work is enqueued.  Every call
+ *   re-initialises the whole scratch (nothing of an earlier call is read).
+ *   The static host buffers are guarded by one mutex, so calls from several
+ *   host threads run one after another.  The device array is shared too: a
+ *   call whose work still runs on the GPU when another call starts (on another
+ *   stream, or issued by code that does not wait for it) races with it.
+ *   Returns SIM_OK, SIM_EINVAL (bad or NULL argument), SIM_EOVERFLOW (a limit
+ *   above, or a link queue overflowed on the device) or SIM_ECUDA; no error
+ *   text is kept for this call. */
 SIM_API int sim_rollout_static(const sim_network *net, const sim_demand *dem, const sim_params *par,
                                const sim_options *opt, int32_t T, sim_outputs *out);
 

@@ -80,6 +80,12 @@ def _lib(precision: str):
             lib.or_philox4x32_10.argtypes = [P, P, P]
             lib.or_backward.argtypes = [P, P, P, C.c_int] + [P] * 8
             lib.or_positions.argtypes = [P, P]
+            lib.or_position_margins.argtypes = [P, P, P]
+            lib.or_import_state.argtypes = [P, C.c_int32] + [P] * 7
+            lib.or_choice_weights.restype = C.c_int32
+            lib.or_choice_weights.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.c_double, P, P]
+            lib.or_merge_weights.restype = C.c_int32
+            lib.or_merge_weights.argtypes = [P, C.c_int32, C.c_int32, C.c_double, P, P, P]
             lib.or_log32.restype = C.c_float
             lib.or_log32.argtypes = [C.c_float]
             _loaded[precision] = lib
@@ -187,14 +193,55 @@ class OracleSim:
         return d
 
     def records(self):
+        """Decisions of the last step, with the margins that flag near-ties:
+        top-2 key gaps of each link / origin-node choice and of each merge, and
+        the distances of each link's leader from the arrival line
+        (arr_margin) and of its rearmost vehicle from the jam spacing
+        (vac_margin), all after car-following."""
         sc = self.sc
         d = dict(link_cand=np.zeros(sc.L, np.int32), link_target=np.zeros(sc.L, np.int32),
                  node_cand=np.zeros(sc.V, np.int32), node_target=np.zeros(sc.V, np.int32),
                  link_in=np.zeros(sc.L, np.int32), link_margin=np.zeros(sc.L),
-                 node_margin=np.zeros(sc.V), merge_margin=np.zeros(sc.L))
+                 node_margin=np.zeros(sc.V), merge_margin=np.zeros(sc.L),
+                 arr_margin=np.zeros(sc.L), vac_margin=np.zeros(sc.L))
         self.lib.or_records(self.h, *(_p(d[k]) for k in ("link_cand", "link_target", "node_cand", "node_target",
                                                          "link_in", "link_margin", "node_margin", "merge_margin")))
+        self.lib.or_position_margins(self.h, _p(d["arr_margin"]), _p(d["vac_margin"]))
         return d
+
+    def set_state(self, state: dict, t: int):
+        """Continue from a given state at step t (the layout of state(); a run
+        without history).  The observation bin containing t restarts at t."""
+        a = dict(veh_link=np.ascontiguousarray(state["veh_link"], np.int32),
+                 veh_pos=np.ascontiguousarray(state["veh_pos"], np.float64),
+                 veh_rank=np.ascontiguousarray(state["veh_rank"], np.int32),
+                 veh_entry=np.ascontiguousarray(state["veh_entry"], np.int32),
+                 link_credit=np.ascontiguousarray(state["link_credit"], np.int64),
+                 link_exits=np.ascontiguousarray(state["link_exits"], np.int64),
+                 fifo_off=np.ascontiguousarray(state["fifo_off"], np.int32))
+        self._check(self.lib.or_import_state(self.h, int(t), *(_p(a[k]) for k in (
+            "veh_link", "veh_pos", "veh_rank", "veh_entry", "link_credit", "link_exits", "fifo_off"))))
+
+    def choice_weights(self, t, tau, link=-1, node=-1):
+        """Relaxed link-choice weights softmax((V + g)/tau) of the candidate at
+        source link ``link`` (or origin node ``node``) at step t of the recorded
+        rollout, and the slot the forward chose; None when it made no choice."""
+        pi = np.zeros(64)
+        slot = np.zeros(1, np.int32)
+        n = self.lib.or_choice_weights(self.h, int(t), int(link), int(node), float(tau), _p(pi), _p(slot))
+        if n < 0:
+            raise RuntimeError("oracle: choice weights need a recorded rollout")
+        return None if n == 0 else (pi[:n].copy(), int(slot[0]))
+
+    def merge_weights(self, t, m, tau):
+        """Relaxed merge weights softmax((alpha_src + g')/tau) of the valid
+        candidates of link m at step t, with their vehicle ids and win flags."""
+        cap = self.sc.L + self.sc.V
+        w, vid, won = np.zeros(cap), np.zeros(cap, np.int32), np.zeros(cap, np.int32)
+        n = self.lib.or_merge_weights(self.h, int(t), int(m), float(tau), _p(w), _p(vid), _p(won))
+        if n < 0:
+            raise RuntimeError("oracle: merge weights need a recorded rollout")
+        return w[:n].copy(), vid[:n].copy(), won[:n].astype(bool)
 
     def backward(self, ybar, xbarT=None, no_tg=False):
         """Reverse mode of the last rollout (needs keep_history=True).  ybar:

@@ -206,6 +206,7 @@ typedef struct {
     /* last step records */
     int32_t *rec_link_cand, *rec_link_target, *rec_node_cand, *rec_node_target, *rec_link_in;
     double *rec_link_margin, *rec_node_margin, *rec_merge_margin;
+    double *rec_arr_margin, *rec_vac_margin;
     /* history (for the backward) */
     int keep_hist;
     or_hist *hist;
@@ -385,6 +386,8 @@ or_sim *or_create(const or_scenario *sc, int keep_hist)
     o->rec_link_margin = (double *)xcalloc(L, sizeof(double));
     o->rec_node_margin = (double *)xcalloc(V, sizeof(double));
     o->rec_merge_margin = (double *)xcalloc(L, sizeof(double));
+    o->rec_arr_margin = (double *)xcalloc(L, sizeof(double));
+    o->rec_vac_margin = (double *)xcalloc(L, sizeof(double));
     o->mem_cnt = (int32_t *)xcalloc(L + 1, sizeof(int32_t));
     o->mem_ptr = (int32_t *)xcalloc(L + 1, sizeof(int32_t));
     o->mem_list = (int32_t *)xcalloc(N, sizeof(int32_t));
@@ -546,10 +549,17 @@ int or_step(or_sim *o)
     char *vacant = (char *)xcalloc(L, 1);
     for (int j = 0; j < L; ++j) {
         int b = o->mem_ptr[j], e = o->mem_ptr[j + 1];
+        o->rec_vac_margin[j] = INFINITY;
+        o->rec_arr_margin[j] = INFINITY;
         if (b == e) { vacant[j] = 1; continue; }
         real xm = o->vx[o->mem_list[b]];
         for (int k = b; k < e; ++k) xm = rmin(xm, o->vx[o->mem_list[k]]);
         vacant[j] = xm > o->s[j];
+        /* distances of the two position comparisons of this step from their
+         * thresholds (near-tie flags): rearmost vehicle vs the jam spacing, leader
+         * vs the arrival line */
+        o->rec_vac_margin[j] = (double)xm - (double)o->s[j];
+        o->rec_arr_margin[j] = (double)o->vx[o->mem_list[b]] - ((double)o->len[j] - (double)sc->eps_arr);
     }
     /* candidates: arrived leaders with credit, and the heads of origin queues */
     int max_c = L + V;
@@ -747,6 +757,74 @@ void or_records(const or_sim *o, int32_t *link_cand, int32_t *link_target, int32
     if (merge_margin) memcpy(merge_margin, o->rec_merge_margin, (size_t)L * sizeof(double));
 }
 
+/* Position margins of the last step, for flagging near-ties of the two position
+ * comparisons of the node model: arr_margin[j] = x_lead - (L_j - eps_arr) of
+ * link j's leader after f (Alg. S2 arrival test), vac_margin[j] = x_min - 1/kappa
+ * dn of its rearmost vehicle after f (vacancy test); INFINITY for empty links. */
+void or_position_margins(const or_sim *o, double *arr_margin, double *vac_margin)
+{
+    int L = o->sc.L;
+    if (arr_margin) memcpy(arr_margin, o->rec_arr_margin, (size_t)L * sizeof(double));
+    if (vac_margin) memcpy(vac_margin, o->rec_vac_margin, (size_t)L * sizeof(double));
+}
+
+/* Replace the state by a given one at step t of the current horizon (the layout
+ * of or_export_state; positions are rounded to the working precision), so that
+ * a lockstep comparison can continue from another simulator's state.  The
+ * observation bin containing t restarts at t: its counts, speeds and travel
+ * times cover [t, bin end).  Forward-only runs (no history).  Returns 0 or -1
+ * (state inconsistent: a field out of range, ranks that are not the order of
+ * the positions, waiting vehicles that do not match the origin queues). */
+int or_import_state(or_sim *o, int32_t t, const int32_t *veh_link, const double *veh_pos,
+                    const int32_t *veh_rank, const int32_t *veh_entry, const int64_t *link_credit,
+                    const int64_t *link_exits, const int32_t *fifo_off)
+{
+    const int N = o->sc.N, L = o->sc.L, V = o->sc.V;
+    if (o->keep_hist) { fail(o, "state import is for runs without history", t, 0); return -1; }
+    if (t < 0 || t > o->T) { fail(o, "import step outside the horizon", t, o->T); return -1; }
+    int64_t queued = 0;
+    for (int n = 0; n < V; ++n) {
+        int len = o->fifo_end[n] - o->fifo_beg[n];
+        if (fifo_off[n] < 0 || fifo_off[n] > len) { fail(o, "origin queue offset out of range", n, fifo_off[n]); return -1; }
+        o->fifo_ptr[n] = o->fifo_beg[n] + fifo_off[n];
+        queued += len - fifo_off[n];
+    }
+    o->cnt_wait = o->cnt_on = o->cnt_arr = 0;
+    for (int i = 0; i < N; ++i) {
+        int j = veh_link[i];
+        if (j < VEH_ARRIVED || j >= L) { fail(o, "vehicle link out of range", i, j); return -1; }
+        o->vlink[i] = j;
+        if (j == VEH_WAITING) { o->cnt_wait++; o->vx[i] = 0; continue; }
+        if (j == VEH_ARRIVED) { o->cnt_arr++; o->vx[i] = 0; continue; }
+        if (!(veh_pos[i] >= 0.0 && veh_pos[i] <= (double)o->length[j])) { fail(o, "position outside its link", i, j); return -1; }
+        o->cnt_on++;
+        o->vx[i] = (real)veh_pos[i];
+        o->ventry[i] = veh_entry[i];
+        o->vseq[i] = veh_entry[i];
+    }
+    if (queued != o->cnt_wait) { fail(o, "waiting vehicles do not match the origin queues", (int)queued, (int)o->cnt_wait); return -1; }
+    for (int n = 0; n < V; ++n)
+        for (int p = o->fifo_ptr[n]; p < o->fifo_end[n]; ++p)
+            if (o->vlink[o->fifo_list[p]] != VEH_WAITING) { fail(o, "queued vehicle not waiting", n, o->fifo_list[p]); return -1; }
+    build_members(o);
+    for (int j = 0; j < L; ++j) {
+        int64_t past = 0;
+        for (int k = o->mem_ptr[j]; k < o->mem_ptr[j + 1]; ++k) {
+            int i = o->mem_list[k];
+            if (veh_rank[i] != k - o->mem_ptr[j]) { fail(o, "ranks are not the order of the positions", i, j); return -1; }
+            if (o->vx[i] >= o->half_len[j]) past++;
+        }
+        o->credit[j] = link_credit[j];
+        o->exits[j] = link_exits[j];
+        o->C_prev[j] = link_exits[j] + past;
+        o->acc_dx[j] = 0; o->acc_n[j] = 0; o->tt_sum[j] = 0; o->tt_cnt[j] = 0;
+    }
+    o->t = t;
+    o->n_wait[t] = o->cnt_wait; o->n_on[t] = o->cnt_on; o->n_arr[t] = o->cnt_arr;
+    o->failed = 0;
+    return 0;
+}
+
 /* Route log of one vehicle: steps and links of its entries, in order. */
 int32_t or_route(const or_sim *o, int32_t i, int32_t *steps, int32_t *links, int32_t cap)
 {
@@ -772,6 +850,7 @@ void or_destroy(or_sim *o)
     free(o->out_counts); free(o->out_speed); free(o->out_tt); free(o->n_wait); free(o->n_on); free(o->n_arr);
     free(o->rec_link_cand); free(o->rec_link_target); free(o->rec_node_cand); free(o->rec_node_target);
     free(o->rec_link_in); free(o->rec_link_margin); free(o->rec_node_margin); free(o->rec_merge_margin);
+    free(o->rec_arr_margin); free(o->rec_vac_margin);
     free(o->mem_cnt); free(o->mem_ptr); free(o->mem_list); free(o->xnew); free(o->tagbuf);
     for (int i = 0; i < o->sc.N; ++i) { free(o->route_t[i]); free(o->route_m[i]); }
     free(o->route_len); free(o->route_cap); free(o->route_t); free(o->route_m);
@@ -813,6 +892,100 @@ static double next_entry_adj(const or_sim *o, double **eadj, int i, int m, int t
     for (int r = 0; r < o->route_len[i]; ++r)
         if (o->route_t[i][r] > t && o->route_m[i][r] == m) return eadj[i][r];
     return 0.0;
+}
+
+/* Relaxed link-choice weights of candidate c at step t: pi = softmax((V + g)/tau)
+ * over its choice set (SI-B Eqs. softmax and gumbel), the weights whose
+ * straight-through one-hot the forward takes (Eq. straigththrough).  Writes deg
+ * weights to pk and the choice set to *set_out; returns deg. */
+static int choice_weights(const or_sim *o, const or_cand *c, int t, double tau, double *pk,
+                          const int32_t **set_out)
+{
+    const or_scenario *sc = &o->sc;
+    const int i = c->vid, z = o->dest_zone[i];
+    const int32_t *set; int deg;
+    if (c->src_link >= 0) { set = o->lo_idx + o->lo_ptr[c->src_link]; deg = o->lo_ptr[c->src_link + 1] - o->lo_ptr[c->src_link]; }
+    else { set = o->no_idx + o->no_ptr[c->src_node]; deg = o->no_ptr[c->src_node + 1] - o->no_ptr[c->src_node]; }
+    double pmax = -INFINITY, ps = 0.0;
+    for (int q = 0; q < deg; ++q) {
+        pk[q] = ((double)utility(o, set[q], z) + (double)gumbel(sc->seed, sc->scenario_id, i, t, 0, q)) / tau;
+        if (pk[q] > pmax) pmax = pk[q];
+    }
+    for (int q = 0; q < deg; ++q) { pk[q] = exp(pk[q] - pmax); ps += pk[q]; }
+    for (int q = 0; q < deg; ++q) pk[q] /= ps;
+    if (set_out) *set_out = set;
+    return deg;
+}
+
+/* Relaxed merge weights of a target link at step t: pi' = softmax((alpha_src +
+ * g')/tau) over its valid candidates (SI-B "Merge choice"), given as the nm
+ * candidate indices idx (in candidate order).  Writes the weights to w. */
+static void merge_weights(const or_sim *o, const or_cand *cand, const int *idx, int nm, int t, double tau,
+                          double *w)
+{
+    const or_scenario *sc = &o->sc;
+    double kmax = -INFINITY, zs = 0.0;
+    for (int k = 0; k < nm; ++k) {
+        const or_cand *c = &cand[idx[k]];
+        const double al = c->src_link >= 0 ? (double)o->alpha[c->src_link] : (double)sc->alpha_origin;
+        w[k] = (al + (double)gumbel(sc->seed, sc->scenario_id, c->vid, t, 1, 0)) / tau;
+        if (w[k] > kmax) kmax = w[k];
+    }
+    for (int k = 0; k < nm; ++k) { w[k] = exp(w[k] - kmax); zs += w[k]; }
+    for (int k = 0; k < nm; ++k) w[k] /= zs;
+}
+
+/* Valid candidates of every target link, in candidate order: those of link m
+ * are idx[ptr[m] .. ptr[m + 1]).  ptr has L + 1 entries, idx nc. */
+static void merge_lists(const or_sim *o, const or_cand *cand, int nc, int *ptr, int *idx)
+{
+    const int L = o->sc.L;
+    memset(ptr, 0, (size_t)(L + 1) * sizeof(int));
+    for (int ci = 0; ci < nc; ++ci)
+        if (cand[ci].target >= 0 && cand[ci].valid) ptr[cand[ci].target + 1]++;
+    for (int m = 0; m < L; ++m) ptr[m + 1] += ptr[m];
+    int *fill = (int *)xcalloc(L, sizeof(int));
+    for (int ci = 0; ci < nc; ++ci)
+        if (cand[ci].target >= 0 && cand[ci].valid) { int m = cand[ci].target; idx[ptr[m] + fill[m]++] = ci; }
+    free(fill);
+}
+
+/* The relaxed weights of a recorded rollout (history needed) at temperature tau,
+ * exported to pin them: the link-choice weights of the candidate at source link
+ * src_link (or origin node src_node when src_link < 0) at step t, with the
+ * forward's chosen slot in *slot; returns the choice-set size, 0 when that
+ * source had no choosing candidate at t, -1 without history. */
+int32_t or_choice_weights(const or_sim *o, int32_t t, int32_t src_link, int32_t src_node, double tau,
+                          double *pi, int32_t *slot)
+{
+    if (!o->keep_hist || !o->hist || t < 0 || t >= o->t) return -1;
+    const or_hist *H = &o->hist[t];
+    for (int ci = 0; ci < H->n_cand; ++ci) {
+        const or_cand *c = &H->cand[ci];
+        if (src_link >= 0 ? c->src_link != src_link : (c->src_link >= 0 || c->src_node != src_node)) continue;
+        if (c->slot < 0) return 0;                           /* left to the sink: no choice */
+        if (slot) *slot = c->slot;
+        return choice_weights(o, c, t, tau, pi, NULL);
+    }
+    return 0;
+}
+
+/* The merge weights of target link m at step t at temperature tau, with each
+ * candidate's vehicle id and whether it won; returns their number (0 without
+ * valid candidates, -1 without history).  vid / won need room for L + V. */
+int32_t or_merge_weights(const or_sim *o, int32_t t, int32_t m, double tau, double *w, int32_t *vid,
+                         int32_t *won)
+{
+    if (!o->keep_hist || !o->hist || t < 0 || t >= o->t) return -1;
+    const or_hist *H = &o->hist[t];
+    int *ptr = (int *)xcalloc(o->sc.L + 1, sizeof(int));
+    int *idx = (int *)xcalloc(H->n_cand, sizeof(int));
+    merge_lists(o, H->cand, H->n_cand, ptr, idx);
+    const int nm = ptr[m + 1] - ptr[m];
+    merge_weights(o, H->cand, idx + ptr[m], nm, t, tau, w);
+    for (int k = 0; k < nm; ++k) { vid[k] = H->cand[idx[ptr[m] + k]].vid; won[k] = H->cand[idx[ptr[m] + k]].won; }
+    free(ptr); free(idx);
+    return nm;
 }
 
 int or_backward(or_sim *o, const double *ybar, const double *xbarT, int no_tg,
@@ -882,23 +1055,24 @@ int or_backward(or_sim *o, const double *ybar, const double *xbarT, int no_tg,
             const int b0 = t / sc->obs_every;      /* bins whose end is >= t + 1 */
             glam[o->od[c->vid]] += Csuf[(size_t)b0 * L + c->src_link] / (double)o->od_lambda[o->od[c->vid]];
         }
+        double *wm = (double *)xcalloc(nc ? nc : 1, sizeof(double));
+        double *abar = (double *)xcalloc(nc ? nc : 1, sizeof(double));
+        int *mptr = (int *)xcalloc(L + 1, sizeof(int));
+        int *midx = (int *)xcalloc(nc ? nc : 1, sizeof(int));
+        merge_lists(o, cand, nc, mptr, midx);
+        int maxdeg = 1;
+        for (int n = 0; n < V; ++n) if (o->no_ptr[n + 1] - o->no_ptr[n] > maxdeg) maxdeg = o->no_ptr[n + 1] - o->no_ptr[n];
+        double *pk = (double *)xcalloc(maxdeg, sizeof(double));
         for (int m = 0; m < L; ++m) {
-            /* valid candidates of target m */
-            int nm = 0;
-            for (int ci = 0; ci < nc; ++ci) if (cand[ci].target == m && cand[ci].valid) nm++;
+            /* merge softmax over the valid candidates of target m */
+            const int nm = mptr[m + 1] - mptr[m];
             if (nm == 0) continue;
-            double *key = (double *)xcalloc(nm, sizeof(double));
-            double *abar = (double *)xcalloc(nm, sizeof(double));
-            int *idx = (int *)xcalloc(nm, sizeof(int));
-            int k = 0;
-            double kmax = -INFINITY;
-            for (int ci = 0; ci < nc; ++ci) {
-                or_cand *c = &cand[ci];
-                if (c->target != m || !c->valid) continue;
+            const int *idx = midx + mptr[m];
+            merge_weights(o, cand, idx, nm, t, tau, wm);
+            double S = 0.0;
+            for (int k = 0; k < nm; ++k) {
+                or_cand *c = &cand[idx[k]];
                 const int i = c->vid;
-                const double al = c->src_link >= 0 ? (double)o->alpha[c->src_link] : (double)sc->alpha_origin;
-                key[k] = (al + (double)gumbel(sc->seed, sc->scenario_id, i, t, 1, 0)) / tau;
-                if (key[k] > kmax) kmax = key[k];
                 double Enew, Xold;
                 if (c->won) {
                     int rw = -1;
@@ -913,42 +1087,27 @@ int or_backward(or_sim *o, const double *ybar, const double *xbarT, int no_tg,
                     Xold = xbar[i];
                 }
                 abar[k] = M * (Enew - Xold) - (double)c->x * Xold;
-                idx[k] = ci;
-                k++;
+                S += wm[k] * abar[k];
             }
-            double zs = 0.0;
-            for (k = 0; k < nm; ++k) { key[k] = exp(key[k] - kmax); zs += key[k]; }
-            double S = 0.0;
-            for (k = 0; k < nm; ++k) { key[k] /= zs; S += key[k] * abar[k]; }
-            for (k = 0; k < nm; ++k) {
+            for (int k = 0; k < nm; ++k) {
                 or_cand *c = &cand[idx[k]];
-                const double vbar = key[k] * (abar[k] - S) / tau;         /* adjoint of V'_i = p_i */
+                const double vbar = wm[k] * (abar[k] - S) / tau;          /* adjoint of V'_i = p_i */
                 const double al = c->src_link >= 0 ? (double)o->alpha[c->src_link] : (double)sc->alpha_origin;
                 if (c->src_link >= 0) ga[c->src_link] += vbar; else gao += vbar;
                 const double lbar = al * vbar;                            /* adjoint of l_i at m */
                 /* link choice of this candidate: pi = softmax((V + g)/tau) over its choice set */
-                const int i = c->vid, z = o->dest_zone[i];
-                const int32_t *set; int deg;
-                if (c->src_link >= 0) { set = o->lo_idx + o->lo_ptr[c->src_link]; deg = o->lo_ptr[c->src_link + 1] - o->lo_ptr[c->src_link]; }
-                else { set = o->no_idx + o->no_ptr[c->src_node]; deg = o->no_ptr[c->src_node + 1] - o->no_ptr[c->src_node]; }
-                double *pk = (double *)xcalloc(deg, sizeof(double));
-                double pmax = -INFINITY, ps = 0.0;
-                for (int q = 0; q < deg; ++q) {
-                    pk[q] = ((double)utility(o, set[q], z) + (double)gumbel(sc->seed, sc->scenario_id, i, t, 0, q)) / tau;
-                    if (pk[q] > pmax) pmax = pk[q];
-                }
-                for (int q = 0; q < deg; ++q) { pk[q] = exp(pk[q] - pmax); ps += pk[q]; }
-                for (int q = 0; q < deg; ++q) pk[q] /= ps;
+                const int z = o->dest_zone[c->vid];
+                const int32_t *set;
+                const int deg = choice_weights(o, c, t, tau, pk, &set);
                 for (int q = 0; q < deg; ++q) {
                     const double Vbar = pk[q] * ((q == c->slot ? 1.0 : 0.0) - pk[c->slot]) * lbar / tau;
                     const int mq = set[q];
                     gU[mq] += Vbar;
                     gG[mq] += Vbar * (double)o->dest_feat[(size_t)z * V + o->head[mq]];
                 }
-                free(pk);
             }
-            free(key); free(abar); free(idx);
         }
+        free(wm); free(abar); free(mptr); free(midx); free(pk);
         /* grafting: a winner's old entry gets its new entry's adjoint (xbar[i]
          * carries over unchanged); without TG the old entry gets nothing */
         if (no_tg)

@@ -536,6 +536,8 @@ static int enqueue_persist(sim_ctx *h, int t0, int t1, int final_obs) {
 
 static int upload_params(sim_ctx *h, const sim_params *par) {
     const int L = h->L, F = h->F;
+    if (!par->u || !par->kappa || !par->alpha || !par->beta || !par->cost || (F > 0 && !par->w))
+        return fail(h, SIM_EINVAL, "null parameter array");
     for (int j = 0; j < L; ++j) {
         if (!(par->u[j] > 0.0f) || !std::isfinite(par->u[j])) return fail(h, SIM_EINVAL, "u must be positive");
         if (!(par->kappa[j] > 0.0f) || !std::isfinite(par->kappa[j])) return fail(h, SIM_EINVAL, "kappa must be positive");
@@ -576,6 +578,11 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
     if (!net || !dem || !par || !opt) return fail(h, SIM_EINVAL, "null argument");
     const int V = net->V, L = net->L, N = dem->N, F = net->F, Z = net->Z;
     if (V <= 0 || L <= 0 || N < 0 || F < 0 || Z <= 0) return fail(h, SIM_EINVAL, "bad sizes");
+    if (!net->tail || !net->head || !net->length || !net->q_fx || !net->node_zone || !net->dest_feat ||
+        (F > 0 && (!net->phi || !net->psi)) || !par->u)
+        return fail(h, SIM_EINVAL, "null network array");
+    if (N > 0 && (!dem->origin || !dem->dest_zone || !dem->dep_step))
+        return fail(h, SIM_EINVAL, "null demand array");
     if (!(opt->dt > 0) || !(opt->dn > 0) || opt->obs_every <= 0 || !(opt->tau_gumbel > 0))
         return fail(h, SIM_EINVAL, "bad options");
     for (int j = 0; j < L; ++j)
@@ -776,6 +783,8 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
         d.route_cap = h->route_cap;
         b.route_log = d.route_log;
         b.route_len = d.route_len;
+        if ((N > 0 && !dem->od) || (dem->n_od > 0 && !dem->od_lambda))
+            return fail(h, SIM_EINVAL, "null od / od_lambda array");
         TRY(upload(h, &h->d_od, dem->od, N));
         TRY(upload(h, &h->d_od_lambda, dem->od_lambda, std::max(dem->n_od, 1)));
         for (int k = 0; k < dem->n_od; ++k)
@@ -2044,13 +2053,15 @@ extern "C" const char *sim_batch_last_error(sim_batch b) { return b ? b->err.c_s
 // ============================================================================
 // Allocation-free forward rollout.
 //
-// For callers that may not allocate device memory: code that runs while a CUDA
-// stream is being captured into a graph (cudaMalloc is not capturable), plug-ins
-// embedded in a host process whose memory manager owns every device allocation,
-// and real-time loops where an allocation could stall.  All simulator state of
-// the call lives in one file-scope device array of fixed size that every GPU
-// loading this library holds until the process exits; host-side set-up uses
-// fixed-size static host buffers.  The paper has no counterpart of this.
+// For callers that may not allocate device memory: plug-ins embedded in a host
+// process whose memory manager owns every device allocation (and may refuse or
+// account for any cudaMalloc made behind its back), and real-time loops, where
+// cudaMalloc / cudaFree can block the host and synchronise the device.  All
+// simulator state of the call lives in one file-scope device array of fixed
+// size that every GPU loading this library holds until the process exits;
+// host-side set-up uses fixed-size static host buffers, which one mutex guards
+// (calls from several host threads run one after another, whatever their
+// devices).  The paper has no counterpart of this.
 // ============================================================================
 
 namespace {
@@ -2066,7 +2077,9 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 // device address of g_static_scratch, looked up once per device
 static void *g_static_addr[kStaticMaxDevices];
 
-// host-side set-up buffers (no dynamic allocation)
+// host-side set-up buffers (no dynamic allocation), shared by every device and
+// guarded by g_static_mutex from the first write to the last read
+static std::mutex g_static_mutex;
 static int hs_no_ptr[kStaticMaxV + 1], hs_no_idx[kStaticMaxL], hs_lo_idx[kStaticMaxChoice];
 static int hs_lnode[4 * kStaticMaxL], hs_lst[4 * kStaticMaxL], hs_blk[kStaticMaxL + 1];
 static int hs_fifo[kStaticMaxN], hs_fifo_beg[kStaticMaxV + 1], hs_fifo_dep[kStaticMaxN];
@@ -2095,6 +2108,15 @@ extern "C" int sim_rollout_static(const sim_network *net, const sim_demand *dem,
     if (!net || !dem || !par || !opt || !out) return SIM_EINVAL;
     const int V = net->V, L = net->L, N = dem->N, F = net->F, Z = net->Z;
     if (V <= 0 || L <= 0 || N < 0 || F < 0 || Z <= 0 || T < 1) return SIM_EINVAL;
+    // every array the run reads must be given (the feature arrays only when F > 0,
+    // the demand arrays only when N > 0)
+    if (!net->tail || !net->head || !net->length || !net->q_fx || !net->node_zone || !net->dest_feat ||
+        !par->u || !par->kappa || !par->alpha || !par->beta || !par->cost)
+        return SIM_EINVAL;
+    if (F > 0 && (!net->phi || !net->psi || !par->w)) return SIM_EINVAL;
+    if (N > 0 && (!dem->origin || !dem->dest_zone || !dem->dep_step)) return SIM_EINVAL;
+    // the step counters are summed on the host: device outputs cannot take them
+    if (out->on_device && (out->n_waiting || out->n_on || out->n_arrived)) return SIM_EINVAL;
     if (V > kStaticMaxV || L > kStaticMaxL || N > kStaticMaxN || T > kStaticMaxT) return SIM_EOVERFLOW;
     if (!(opt->dt > 0) || !(opt->dn > 0) || opt->obs_every <= 0 || !(opt->tau_gumbel > 0)) return SIM_EINVAL;
     if (opt->device < 0 || opt->device >= kStaticMaxDevices) return SIM_EINVAL;
@@ -2111,6 +2133,7 @@ extern "C" int sim_rollout_static(const sim_network *net, const sim_demand *dem,
             dem->dep_step[i] < 0)
             return SIM_EINVAL;
     // ---- host set-up (same derived structures as sim_create) ----
+    std::lock_guard<std::mutex> lock(g_static_mutex);
     for (int n = 0; n <= V; ++n) hs_no_ptr[n] = 0;
     for (int j = 0; j < L; ++j) hs_no_ptr[net->tail[j] + 1]++;
     for (int n = 0; n < V; ++n) hs_no_ptr[n + 1] += hs_no_ptr[n];
@@ -2294,7 +2317,6 @@ extern "C" int sim_rollout_static(const sim_network *net, const sim_demand *dem,
     int err[4] = {0, 0, 0, 0};
     if (cudaMemcpyAsync(err, d.err, sizeof err, cudaMemcpyDeviceToHost, s) != cudaSuccess) return SIM_ECUDA;
     if (out->n_waiting || out->n_on || out->n_arrived) {
-        if (out->on_device) return SIM_EINVAL;      // counters are produced on the host
         if (cudaMemcpyAsync(hs_counters, d.step_delta, (size_t)4 * T * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return SIM_ECUDA;
     }

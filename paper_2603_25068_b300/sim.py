@@ -270,11 +270,10 @@ class Simulator:
         return d
 
 
-def rollout_static(sc, T: Optional[int] = None, device: int = 0, stream=None):
-    """Forward rollout through sim_rollout_static, the entry point that allocates
-    no device memory (for callers that may not allocate: graph capture, hosts
-    that own all device memory, real-time loops).  Host outputs."""
-    lib = nat.lib()
+def static_arguments(sc, T: int, device: int = 0, stream=None):
+    """The ctypes structures sim_rollout_static takes for scenario ``sc``
+    (host arrays), with the list of arrays that must stay alive while they
+    are in use: (net, dem, par, opt, keep)."""
     keep = []
 
     def a(x, dt):
@@ -282,7 +281,6 @@ def rollout_static(sc, T: Optional[int] = None, device: int = 0, stream=None):
         keep.append(x)
         return _p(x)
 
-    T = sc.T if T is None else T
     net = nat.sim_network(V=sc.V, L=sc.L, tail=a(sc.tail, np.int32), head=a(sc.head, np.int32),
                           length=a(sc.length, np.float32), q_fx=a(sc.q_fx, np.int32), F=sc.F,
                           phi=a(sc.phi, np.float32), psi=a(sc.psi, np.float32), Z=sc.Z,
@@ -298,6 +296,17 @@ def rollout_static(sc, T: Optional[int] = None, device: int = 0, stream=None):
     opt = nat.sim_options(dt=sc.dt, dn=sc.dn, tau_gumbel=sc.tau, M=sc.M, eps_arr=sc.eps_arr,
                           eps_tag=sc.eps_tag, seed=sc.seed, scenario_id=sc.scenario_id,
                           obs_every=sc.obs_every, ckpt_every=0, route_cap=0, device=device, stream=stream)
+    return net, dem, par, opt, keep
+
+
+def rollout_static(sc, T: Optional[int] = None, device: int = 0, stream=None):
+    """Forward rollout through sim_rollout_static, the entry point that allocates
+    no device memory (for callers that may not allocate: plug-ins whose host
+    application owns every device allocation, real-time loops that must not
+    block in cudaMalloc).  Host outputs."""
+    lib = nat.lib()
+    T = sc.T if T is None else T
+    net, dem, par, opt, keep = static_arguments(sc, T, device, stream)
     nb = lib.sim_n_bins(T, sc.obs_every)
     res = dict(counts=np.zeros((nb, sc.L), np.int32), speed=np.zeros((nb, sc.L), np.float32),
                travel_time=np.zeros((nb, sc.L), np.float32), n_waiting=np.zeros(T + 1, np.int64),

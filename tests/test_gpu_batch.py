@@ -1,11 +1,30 @@
 """Batched execution: every member of a batch gives bitwise the same outputs and
 state as when it runs alone, whatever its size, horizon or start step, with
 either batch executor (one cooperative launch per advance, or one launch per
-phase and step)."""
+phase and step).  The batch kernels carry their own node-model and transfer
+code, so each member is also compared with the oracle directly: state and
+counts bitwise against its float build, speeds and travel times to 1e-4 and
+1e-6 relative, gradients against its reverse mode (gradcheck.py)."""
 import numpy as np
 import pytest
 
+from gradcheck import compare_grads
+from oracle.oracle import OracleSim
 from paper_2603_25068_b300 import scenario as S
+
+
+def _oracle_equal(sc, T, out, st):
+    o = OracleSim(sc, "fp32")
+    ref = o.rollout(T)
+    np.testing.assert_array_equal(out["counts"], ref["counts"], err_msg=sc.name)
+    for k in ("n_waiting", "n_on", "n_arrived"):
+        if k in out:
+            np.testing.assert_array_equal(out[k], ref[k][:T + 1], err_msg=k)
+    np.testing.assert_allclose(out["travel_time"], ref["travel_time"], rtol=1e-6, atol=0)
+    np.testing.assert_allclose(out["speed"], ref["speed"], rtol=1e-4, atol=1e-5)
+    ost = o.state()
+    for k in ("veh_link", "veh_rank", "link_credit", "link_exits", "fifo_off", "veh_pos"):
+        np.testing.assert_array_equal(st[k], ost[k], err_msg=f"{sc.name} {k}")
 
 pytestmark = pytest.mark.gpu
 
@@ -77,6 +96,7 @@ def test_continuous_batching_staggered_members_equal_solo(executor):
         ref, rst = _solo(sc, T)
         _same(o, ref)
         _same(st, rst)
+        _oracle_equal(sc, T, o, st)
 
 
 @pytest.mark.parametrize("executor", EXECUTORS)
@@ -96,6 +116,9 @@ def test_batched_member_reverse_pass_equals_solo(executor):
         gs = solo.backward(y)
         for k in g:
             np.testing.assert_array_equal(g[k], gs[k], err_msg=k)
+        o = OracleSim(sc, "fp32", keep_history=True)
+        o.rollout()
+        compare_grads(g, o.backward(y.astype(np.float64)))
 
 
 @pytest.mark.parametrize("executor", EXECUTORS)

@@ -11,14 +11,22 @@ persistent executor exactly as the benchmark runs it.
   size: conservation at every step, counts equal to link exits plus vehicles
   past the midpoint, positions inside their links, FIFO order and jam spacing
   in every queue, occupancy within capacity.
-* The reverse pass at full size (1,800 steps, checkpoints every 60) is checked
+* The reverse pass at full size is compared with the oracle's reverse mode
+  over the first 300 steps (checkpoints every 60, five 1-minute bins of the
+  2,000 sensor links of the calibration workload): every gradient family
+  within 1e-5 of its largest entry and 1e-4 relative on entries above 1 % of
+  it.
+* The reverse pass over the whole 1,800-step calibration horizon is checked
   for linearity in the loss cotangent and for repeatability (its double
   accumulators take atomic additions in a run-dependent order, so two calls
   agree to rounding, not bit for bit).
 """
+import json
+
 import numpy as np
 import pytest
 
+from gradcheck import compare_grads
 from oracle.oracle import OracleSim
 from paper_2603_25068_b300 import scenario as S
 
@@ -123,3 +131,27 @@ def test_full_size_gradient_is_linear_and_deterministic(Simulator):
         assert np.max(np.abs(g12[k] - lin)) <= 1e-4 * scale, k
     assert np.linalg.norm(g1["od_lambda"]) > 0 and np.linalg.norm(g1["w"]) > 0
     g.close()
+
+
+def test_full_size_reverse_pass_equals_oracle_first_300_steps(Simulator):
+    model, _ = S.calibration()
+    sc = model.copy(T=300, obs_every=60)
+    g = Simulator(sc, ckpt_every=60, route_cap=256)
+    out = g.rollout(sc.T)
+    nb = out["counts"].shape[0]
+    rng = np.random.default_rng(9)
+    ybar = np.zeros((nb, sc.L), np.float32)
+    ybar[:, sc.sensors] = rng.normal(size=(nb, len(sc.sensors))).astype(np.float32)
+    gg = g.backward(ybar)
+    g.close()
+    o = OracleSim(sc, "fp32", keep_history=True)
+    ref = o.rollout(sc.T)
+    np.testing.assert_array_equal(out["counts"], ref["counts"])
+    assert (o.state()["veh_link"] >= 0).sum() > 50_000
+    go = o.backward(ybar.astype(np.float64))
+    del o
+    stats = compare_grads(gg, go, ("u", "kappa", "alpha", "alpha_origin", "beta", "cost", "w", "od_lambda"))
+    print("full-size reverse pass vs oracle (max |diff|/max |g|, max rel. err. on entries >= 1 %, count):",
+          json.dumps(stats))
+    for k in ("u", "kappa", "alpha", "w", "od_lambda"):
+        assert np.count_nonzero(go[k]) > 0, k

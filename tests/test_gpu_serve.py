@@ -1,9 +1,14 @@
 """Serving with continuous batching: requests of different kinds, networks and
 sizes arrive while others run; each result equals the result of the same request
 processed alone (forward outputs bitwise; gradients up to the order of double
-additions in the reverse pass)."""
+additions in the reverse pass), and the result of the oracle: counts bitwise
+against its float build, speeds and travel times to 1e-4 / 1e-6 relative,
+gradients against its reverse mode (gradcheck.py)."""
 import numpy as np
 import pytest
+
+from gradcheck import compare_grads
+from oracle.oracle import OracleSim
 
 pytestmark = pytest.mark.gpu
 
@@ -29,6 +34,16 @@ def test_served_results_equal_results_alone():
             for k, g in alone["grad"].items():
                 scale = max(1e-6, float(np.abs(g).max()))
                 np.testing.assert_allclose(r.result["grad"][k], g, rtol=0, atol=1e-5 * scale, err_msg=f"{r.kind} {k}")
+        # against the oracle
+        sc = r.scenario
+        o = OracleSim(sc, "fp32", keep_history=r.needs_grad)
+        ref = o.rollout(sc.T)
+        np.testing.assert_array_equal(r.result["counts"], ref["counts"], err_msg=r.kind)
+        np.testing.assert_allclose(r.result["travel_time"], ref["travel_time"], rtol=1e-6, atol=0)
+        np.testing.assert_allclose(r.result["speed"], ref["speed"], rtol=1e-4, atol=1e-5)
+        if r.needs_grad:
+            yb = serve.loss_cotangent(r, ref["counts"]).astype(np.float64)
+            compare_grads(r.result["grad"], o.backward(yb))
 
 
 def test_admission_respects_the_budget():

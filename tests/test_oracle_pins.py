@@ -279,3 +279,139 @@ def test_brute_force_fork_and_merge():
     assert abs(sum(exact.values()) - 1) < 1e-12
     chi2 = ((ob - e) ** 2 / e).sum()
     assert stats.chi2.sf(chi2, 3) > 1e-3, (ob, e)
+
+
+# ---------------------------------------------------------------- link speeds (P25 reading)
+def _lone_vehicle_bin_speeds(length, u, dt, eps, n_links, n_bins, obs_every):
+    """Closed form of the bin speeds of one vehicle crossing a chain of equal
+    links in free flow: on each link it makes k = ceil((L - eps)/(u dt))
+    car-following steps, the s-th moving it to min(s u dt, L) (the TG clip),
+    and leaves in the k-th; it departs at step 0 and is on link l during steps
+    1 + l k .. (l + 1) k.  Speed of a link in a bin = distance travelled on it
+    in the bin / (vehicle-steps on it in the bin x dt)."""
+    udt = u * dt
+    k = math.ceil((length - eps) / udt)
+    dist = np.zeros((n_bins, 2 * n_links))
+    steps = np.zeros((n_bins, 2 * n_links))
+    for l in range(n_links):
+        for s in range(1, k + 1):
+            t = 1 + l * k + (s - 1)
+            b = t // obs_every
+            if b < n_bins:
+                dist[b, l] += min(s * udt, length) - min((s - 1) * udt, length)
+                steps[b, l] += 1
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(steps > 0, dist / (steps * dt), 0.0), k
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("length,u,obs_every", [(200.0, 13.9, 5), (200.0, 13.9, 7), (237.0, 8.3, 11),
+                                                (100.0, 10.0, 200)])
+def test_lone_vehicle_bin_speed(prec, length, u, obs_every):
+    """Mean link speed of a bin (reading P25: distance over vehicle-time on the
+    link in the bin) for a lone vehicle: u in bins of unclipped free flow, the
+    clipped last metres over one step where it reaches the end, 0 on empty
+    links, in every bin in closed form."""
+    T = 200
+    sc = S.line_network(n_links=3, length=length, u=u, N=1, T=T).copy(obs_every=obs_every)
+    out = OracleSim(sc, prec).rollout()
+    nb = out["speed"].shape[0]
+    exp, k = _lone_vehicle_bin_speeds(float(np.float32(length)), float(np.float32(u)), 1.0, 0.01, 3, nb,
+                                      obs_every)
+    np.testing.assert_allclose(out["speed"], exp, rtol=1e-5, atol=1e-9)
+    if obs_every >= 3 * k + 1:       # one bin holds the whole trip: distance L per link over k steps
+        np.testing.assert_allclose(out["speed"][0][:3], min(k * np.float32(u), np.float32(length)) / k, rtol=1e-6)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_speed_counts_waiting_vehicle_steps(prec):
+    """A vehicle held at the end of a link by the outflow credit keeps counting
+    vehicle-steps at zero displacement (P25 denominator), and its link time
+    counts the wait (travel time = exit step + 1 - entry step).  Link 1 of a
+    chain lets 1 veh out per 65536 / q_fx steps: vehicle 0 (departing at 0)
+    leaves it at step 2k, vehicle 1 (departing at 50) arrives at step 50 + 2k
+    and waits until the credit refills at step 2k + ceil(65536 / q_fx)."""
+    length, u = 200.0, 13.9
+    sc = S.line_network(n_links=3, length=length, u=u, N=2, dep=[0, 50], T=400).copy(obs_every=400)
+    q = sc.q_fx.copy()
+    q[1] = 655                                    # 0.01 veh/s
+    sc = sc.copy(q_fx=q)
+    out = OracleSim(sc, prec).rollout()
+    k = math.ceil((np.float32(length) - 0.01) / np.float32(u))
+    d = min(k * float(np.float32(u)), float(np.float32(length)))
+    s2 = max(50 + 2 * k, 2 * k + math.ceil(65536 / 655))        # vehicle 1's exit step from link 1
+    steps1 = k + (s2 - (51 + k) + 1)                             # vehicle-steps on link 1
+    np.testing.assert_allclose(out["speed"][0][1], 2 * d / steps1, rtol=1e-6)
+    np.testing.assert_allclose(out["speed"][0][0], d / k, rtol=1e-6)
+    np.testing.assert_allclose(out["travel_time"][0][1], (k + (s2 + 1 - (51 + k))) / 2, rtol=1e-12)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_standing_queue_has_zero_speed(prec):
+    """Ten vehicles queue on link 1 of a chain whose exit passes one vehicle per
+    101 steps (q_fx = 655).  Exits happen at steps 2k + 101 m; in a bin with no
+    exit every queued vehicle stands (headway exactly the jam spacing, Eq.
+    newell_model second term 0), so the link's bin speed is 0, while the bin's
+    vehicle-steps are not."""
+    length, u = 200.0, 13.9
+    sc = S.line_network(n_links=3, length=length, u=u, N=10, T=400).copy(obs_every=50)
+    q = sc.q_fx.copy()
+    q[1] = 655
+    out = OracleSim(sc.copy(q_fx=q), prec).rollout()
+    k = math.ceil((np.float32(length) - 0.01) / np.float32(u))
+    exits = [2 * k + 101 * m for m in range(5)]
+    assert exits[3] < 350 and exits[4] >= 400 and k == 15
+    assert out["speed"][7][1] == 0.0 and out["travel_time"][7][1] == 0.0      # steps 350-399
+    o = OracleSim(sc.copy(q_fx=q), prec)
+    o.reset(400)
+    o.step(375)
+    assert (o.state()["veh_link"] == 1).sum() == 6                           # the queue is there
+
+
+# ------------------------------------------------- relaxed weights as the temperature goes to 0
+def test_relaxed_choice_weights_tend_to_the_forward_one_hot():
+    """The Gumbel-softmax weights softmax((V + g)/tau) whose straight-through
+    one-hot the forward takes (SI-B Eqs. gumbel, straigththrough) tend to the
+    one-hot of the chosen link as tau -> 0: argmax pi is the forward's choice,
+    1 - pi_chosen <= (deg - 1) exp(-gap / tau) with gap the top-2 key gap, pi
+    sharpens monotonically, and log(pi_a / pi_b) scales exactly as 1/tau.  The
+    merge weights over (alpha_src + g')/tau tend to the winner the same way."""
+    sc = S.tiny_grid(T=120)
+    o = OracleSim(sc, "fp64", keep_history=True)
+    o.reset(sc.T)
+    taus = [1.0, 0.1, 0.01, 0.001]
+    n_choice = n_merge = 0
+    for t in range(sc.T):
+        o.step(1)
+        r = o.records()
+        for j in range(sc.L):
+            if r["link_cand"][j] < 0 or r["link_target"][j] == -2:
+                continue
+            gap = r["link_margin"][j]
+            prev = 0.0
+            for tau in taus:
+                pi, slot = o.choice_weights(t, tau, link=j)
+                assert abs(pi.sum() - 1) < 1e-12
+                if gap > 0:
+                    assert int(np.argmax(pi)) == slot
+                    assert 1 - pi[slot] <= (len(pi) - 1) * math.exp(-gap / tau) * (1 + 1e-9) + 1e-15
+                assert pi[slot] >= prev - 1e-15
+                prev = pi[slot]
+            pi1, slot = o.choice_weights(t, 1.0, link=j)
+            pi2, _ = o.choice_weights(t, 0.5, link=j)
+            ok = (pi1 > 1e-150) & (pi2 > 1e-150)
+            np.testing.assert_allclose(np.log(pi2[ok] / pi2[slot]), 2 * np.log(pi1[ok] / pi1[slot]),
+                                       rtol=1e-9, atol=1e-9)
+            n_choice += 1
+        for m in range(sc.L):
+            if r["link_in"][m] < 0:
+                continue
+            gap = r["merge_margin"][m]
+            for tau in taus:
+                w, vid, won = o.merge_weights(t, m, tau)
+                assert won.sum() == 1 and vid[won][0] == r["link_in"][m]
+                if np.isfinite(gap) and gap > 0:
+                    assert int(np.argmax(w)) == int(np.nonzero(won)[0][0])
+                    assert 1 - w[won][0] <= (len(w) - 1) * math.exp(-gap / tau) * (1 + 1e-9) + 1e-15
+            n_merge += 1
+    assert n_choice > 200 and n_merge > 200

@@ -2,12 +2,13 @@
 ordinary one (sim_create + sim_rollout).
 
 sim_rollout_static exists for callers that may not allocate device memory:
-code that runs while a stream is being captured into a CUDA graph, plug-ins
-whose host process owns every device allocation, and real-time loops.  It keeps
-all state in one fixed device array shared by every call, so two calls in a
-row must each re-initialise it and give the same outputs as the ordinary path.
-This file is collected last so that a run stopping at the first failure has
-already run every other test.
+plug-ins inside a host application whose memory manager owns every device
+allocation, and real-time loops where cudaMalloc / cudaFree could block the
+host and synchronise the device.  It keeps all state in one fixed device array
+shared by every call, so two calls in a row must each re-initialise it, give
+the same outputs as the ordinary path, and leave the device's free memory as
+it was.  This file is collected last so that a run stopping at the first
+failure has already run every other test.
 """
 import numpy as np
 import pytest
@@ -31,11 +32,20 @@ def test_static_rollout_matches_ordinary_rollout_twice(make):
     assert torch.cuda.is_available()
     from paper_2603_25068_b300.sim import Simulator, rollout_static
     sc = make()
-    ref = Simulator(sc).rollout()
+    g = Simulator(sc)
+    ref = g.rollout()
+    g.close()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(0)[0]
     first = rollout_static(sc)
+    free1 = torch.cuda.mem_get_info(0)[0]
     second = rollout_static(sc)
+    free2 = torch.cuda.mem_get_info(0)[0]
     _outputs_match(first, ref, sc.T)
     _outputs_match(second, ref, sc.T)
+    # nothing is allocated: the device's free memory is unchanged by either call
+    # (the scratch array is part of the loaded module, present before the first)
+    assert free1 == free0 and free2 == free0, (free0, free1, free2)
 
 
 def test_static_rollout_rejects_sizes_beyond_its_limit():
