@@ -14,18 +14,27 @@
 //     candidates, low half ~(vehicle << 8 | zone) when the sizes allow, so that
 //     the target learns the entrant's zone with the word), three buffers
 //     indexed by step mod 3, and
-//   * each link's record of the step (candidate, target, next-step vacancy /
-//     arrival bits for the four (pop, push) outcomes), two buffers by parity,
-// from which any CTA derives the vacancy of any link for the next step without
-// waiting for the link's owner to apply its transfers.  One grid-wide barrier
-// per step therefore suffices.  Epoch t of a CTA:
+//   * the vacancy of each link at each step, published by the link's owner
+//     (two buffers by step parity).
+// A candidate is valid when its chosen link is vacant (SI-B: a link accepts
+// an entrant only if its rearmost vehicle has left the jam spacing), and every
+// candidate of one target shares that target's vacancy.  So the validity test
+// is taken where the merge is resolved, one step later: every candidate
+// takes part in the atomicMax of its chosen link; in the transfers of step t
+// the owner of a link admits the word's winner only if the link was vacant at
+// t, and the owner of a candidate pops it only if it won and its target was
+// vacant (read with the word, in the same round of loads).  Merges, winners
+// and transfers are exactly those of the per-step definition, while the choice
+// phase loads nothing but the destination features.  One grid-wide barrier per
+// step therefore suffices.  Epoch t of a CTA:
 //   T   transfers of step t-1 for its links and origin queues (one round of
-//       merge-word loads), then credit and candidates of step t;
+//       merge-word and vacancy loads), publication of its links' vacancy at t,
+//       then credit and candidates of step t;
 //   S   one block scan of the choice work -> a compact list of (candidate,
 //       choice slot) pairs;
-//   C|F choice warps evaluate the pairs (utility + Gumbel keys, vacancy of the
-//       slot's link) while the other warps run the Newell update of every
-//       queued vehicle in shared memory, one warp per link at a time;
+//   C|F choice warps evaluate the pairs (utility + Gumbel key of each slot,
+//       the merge key) while the other warps run the Newell update of every
+//       queued vehicle in shared memory, in equal runs of vehicles;
 //   P   argmax, merge atomicMax, next-step bits, records; barrier.
 //
 // Every floating-point operation is the one of the two-kernel path (same device
@@ -42,7 +51,10 @@ constexpr int kPLinks = 288;                 // links per CTA at most
 constexpr int kPNodes = 128;                 // origin queues per CTA at most
 constexpr int kPNodeTid = 512;               // thread of origin queue 0 in the per-entity phases
 constexpr int kPSlot = 8;                    // choice slots per candidate evaluated in parallel
-constexpr int kPCW = 12;                     // choice warps
+#ifndef TS_PERSIST_CHOICE_WARPS
+#define TS_PERSIST_CHOICE_WARPS 8
+#endif
+constexpr int kPCW = TS_PERSIST_CHOICE_WARPS; // choice warps (the rest update car-following)
 constexpr int kPCFT = kPT - 32 * kPCW;       // car-following threads
 constexpr int kPPairs = (kPLinks + kPNodes) * (kPSlot + 1);
 static_assert(kPSlot + 1 <= 16, "a pair list entry holds the slot in 4 bits");
@@ -52,7 +64,7 @@ struct PArgs {
     int npg;                       // origin queues per CTA
     int packz;                     // merge words carry the entrant's zone
     unsigned long long *W3;        // [3 L] merge words by step mod 3
-    int4 *crec2;                   // [2 L] link records by step parity
+    int *vacp;                     // [2 L] vacancy of each link at step t, index t & 1, written by its owner
     unsigned *bar;                 // grid barrier counter (zero at launch)
     int t0, t1;                    // steps [t0, t1)
     int final_obs;                 // close the last bin at t1 (observation-only pass)
@@ -72,15 +84,13 @@ struct PSmem {
     int2 le[kPLinks];              // entry steps at queue positions 0 and 1
     int flags[kPLinks];            // vacancy / arrival for the coming step
     int lbase[kPLinks + 1];        // first ring slot of each link in shared memory (static)
-    int wl[32 + 1];                // first link of each car-following warp
-    int wr[32 + 1];                // and its first round of 32 vehicles in that link
-    float wah[32 + 1];             // time-t position of the vehicle ahead of a warp starting at round > 0
+    int voff[kPLinks + 1];         // first vehicle of each link in the CTA's queue order (step t)
     int past[kPLinks];
     float mkey[kPLinks];
     float alpha[kPLinks];
     unsigned long long psum[kPLinks];
     float key[kPLinks][kPSlot];
-    int tv[kPLinks][kPSlot];       // target << 1 | vacant
+    int tv[kPLinks][kPSlot];       // link of choice slot k
     int4 nq[kPNodes];              // next vehicle, end of queue, first staged out-link entry, out-degree
     int4 nh[kPNodes];              // (vehicle, zone) at queue positions 0 and 1
     int2 ndep[kPNodes];            // departure steps at queue positions 0 and 1
@@ -88,7 +98,7 @@ struct PSmem {
     int nzone[kPNodes];
     float nmkey[kPNodes];
     float nkey[kPNodes][kPSlot];
-    int ntv[kPNodes][kPSlot];
+    int ntv[kPNodes][kPSlot];      // link of choice slot k
     int plist[kPPairs];            // entity << 4 | (0 merge key, 1 + k choice slot k)
     int wsum[32];
     int cnt[4];                    // step counters: releases, arrivals, candidates, entries
@@ -151,48 +161,27 @@ __device__ __forceinline__ int p_vid(unsigned long long w, int packz) {
     return packz ? (int)((~(uint32_t)(w & 0xffffffffull)) >> 8) : merge_vid(w);
 }
 
-// Vacancy / arrival flags of link m for step t, from its record of step t-1
-// and the merge words of step t-1 (what its owner will apply).
-__device__ __forceinline__ int derived_flags(const int4 *Cp, const unsigned long long *Wp, int m, int packz) {
-    const int4 c = __ldcg(Cp + m);
-    const unsigned long long wm = __ldcg(Wp + m);
-    bool pop = c.y == kTgtSink;
-    if (c.y >= 0) {
-        const unsigned long long w = __ldcg(Wp + c.y);
-        pop = w != 0ull && p_vid(w, packz) == c.x;
-    }
-    const int o = (pop ? 1 : 0) | (wm != 0ull ? 2 : 0);
-    return ((c.z >> o) & 1) | (((c.z >> (4 + o)) & 1) << 1);
-}
-
-__device__ __forceinline__ int vacant_of(const DevSim &d, bool first, const int4 *Cp, const unsigned long long *Wp,
-                                         int m, int packz) {
-    return (first ? __ldcg(d.vac + m) : derived_flags(Cp, Wp, m, packz)) & kFlagVacant;
-}
-
 // argmax of the staged keys (ties to the lowest slot); slots past the stage
-// are evaluated inline.  Returns the target or kTgtBlocked.
-__device__ __forceinline__ int p_choose(const DevSim &d, bool first, const int4 *Cp, const unsigned long long *Wp,
-                                        int packz, const float *key, const int *tv, const float4 *info, int deg,
+// are evaluated inline.  Returns the chosen link (its vacancy is taken at the
+// transfers).
+__device__ __forceinline__ int p_choose(const DevSim &d, const float *key, const int *tv, const float4 *info, int deg,
                                         int zone, int vid, int t) {
     float bk = -INFINITY;
-    int bm = -1, bv = 0;
+    int bm = -1;
     for (int k = 0; k < deg; ++k) {
         float kk;
-        int m, vm;
+        int m;
         if (k < kPSlot) {
             kk = key[k];
-            m = tv[k] >> 1;
-            vm = tv[k] & 1;
+            m = tv[k];
         } else {
             const float4 e = info[k];
             kk = choice_key(d, e, zone, vid, t, k);
             m = __float_as_int(e.w);
-            vm = vacant_of(d, first, Cp, Wp, m, packz);
         }
-        if (bm < 0 || kk > bk) { bk = kk; bm = m; bv = vm; }
+        if (bm < 0 || kk > bk) { bk = kk; bm = m; }
     }
-    return bv ? bm : kTgtBlocked;
+    return bm;
 }
 
 // A refill of the second cached queue position, loaded in phase T and stored
@@ -223,24 +212,36 @@ struct PCtx {
 };
 
 // Transfers of step tb for this thread's link or origin queue (SI-B Eq.
-// transfer): pop the leader that won its merge or left to its destination, push
-// the merge winner at x = 0, flags of step tb + 1.  Counters accumulate.
+// transfer): pop the leader that won its merge into a vacant link or left to its
+// destination, push the merge winner at x = 0 if the link was vacant at tb,
+// flags of step tb + 1 and their publication.  The record of step tb gets its
+// final target (kTgtBlocked when the chosen link was not vacant).  Counters
+// accumulate.
 template <bool kTape>
 __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int tb, PPend &pd,
                                         int *cnt) {
     const int tid = threadIdx.x;
     const unsigned long long *Wb = a.W3 + (size_t)(tb % 3) * d.L;
+    const int *Vb = a.vacp + (size_t)(tb & 1) * d.L;           // vacancy of every link at tb
+    int *Vn = a.vacp + (size_t)((tb + 1) & 1) * d.L;           // this CTA's links at tb + 1
     if (tid < c.nl) {
         const int li = tid, j = c.j0 + li;
         int4 q = S.q[li];
         const int4 st = S.st[li];
-        const int4 cr = S.cr[li];
-        const unsigned long long win = __ldcg(Wb + j);
+        int4 cr = S.cr[li];
+        const unsigned long long w0 = __ldcg(Wb + j);
+        unsigned long long wt = 0ull;
+        int vt = 0;
+        if (cr.y >= 0) {
+            wt = __ldcg(Wb + cr.y);
+            vt = __ldcg(Vb + cr.y);
+        }
+        // the candidates of a link that was not vacant at tb could not enter it:
+        // its word names no entrant
+        const unsigned long long win = (S.flags[li] & kFlagVacant) ? w0 : 0ull;
         if (kTape)                  // the tape keeps merge words in the standard format (~vehicle low half)
             d.tape_W[(size_t)(tb - a.t0) * d.L + j] =
                 win ? ((win & 0xffffffff00000000ull) | (unsigned long long)(~(uint32_t)p_vid(win, a.packz))) : 0ull;
-        unsigned long long wt = 0ull;
-        if (cr.y >= 0) wt = __ldcg(Wb + cr.y);
         bool pop = false;
         cnt[2] += cr.x >= 0;
         if (cr.y == kTgtSink) {
@@ -248,8 +249,11 @@ __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &
             d.vstate[cr.x] = kVehArrived;
             cnt[1] += 1;
         } else if (cr.y >= 0) {
-            pop = wt != 0ull && p_vid(wt, a.packz) == cr.x;
+            if (vt) pop = wt != 0ull && p_vid(wt, a.packz) == cr.x;
+            else cr.y = kTgtBlocked;
         }
+        if (kTape) d.tape_crec[(size_t)(tb - a.t0) * d.L + j] = cr;
+        S.cr[li] = cr;
         int4 ld = S.ld[li];
         int2 le = S.le[li];
         if (pop) {
@@ -307,11 +311,13 @@ __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &
         S.ld[li] = ld;
         S.le[li] = le;
         const int o = (pop ? 1 : 0) | (push ? 2 : 0);
-        S.flags[li] = ((cr.z >> o) & 1) | (((cr.z >> (4 + o)) & 1) << 1);
+        const int fl = ((cr.z >> o) & 1) | (((cr.z >> (4 + o)) & 1) << 1);
+        S.flags[li] = fl;
+        Vn[j] = fl & kFlagVacant;                            // read by the transfers of step tb + 1
         a.W3[(size_t)((tb + 2) % 3) * d.L + j] = 0ull;      // words of step tb + 2 start from zero
     } else if (tid >= kPNodeTid && tid < kPNodeTid + c.nn) {
         const int ni = tid - kPNodeTid;
-        const int2 cr = S.nrec[ni];
+        int2 cr = S.nrec[ni];
         cnt[2] += cr.x >= 0;
         bool rel = false;
         if (cr.y == kTgtSink) {
@@ -320,8 +326,11 @@ __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &
             cnt[1] += 1;
         } else if (cr.y >= 0) {
             const unsigned long long w = __ldcg(Wb + cr.y);
-            rel = w != 0ull && p_vid(w, a.packz) == cr.x;
+            if (__ldcg(Vb + cr.y)) rel = w != 0ull && p_vid(w, a.packz) == cr.x;
+            else cr.y = kTgtBlocked;
         }
+        if (kTape) d.tape_nrec[(size_t)(tb - a.t0) * d.V + c.n0 + ni] = cr;
+        S.nrec[ni] = cr;
         if (rel) {
             cnt[0] += 1;
             int4 nq = S.nq[ni];
@@ -370,7 +379,7 @@ __device__ __forceinline__ void p_count(PSmem &S, const int *cnt) {
 
 // Step t of this thread's link or origin queue up to the choice: credit,
 // candidate.  Returns (choice pairs (merge key + choice slots) << 16) | the
-// link's car-following cost (1 + rounds of 32 vehicles).
+// link's number of queued vehicles.
 template <bool kTape>
 __device__ __forceinline__ int p_candidate(const DevSim &d, PSmem &S, const PCtx &c, int t, int r, bool obs_only) {
     const int tid = threadIdx.x;
@@ -379,7 +388,7 @@ __device__ __forceinline__ int p_candidate(const DevSim &d, PSmem &S, const PCtx
         S.past[li] = 0;
         S.psum[li] = 0ull;
         const int4 q = S.q[li];
-        const int cost = 1 + ((q.y + 31) >> 5);           // car-following rounds of the link (+1)
+        const int cost = q.y;                              // vehicles to update
         if (obs_only) return cost;
         if (kTape) d.tape_lq[(size_t)r * d.L + c.j0 + li] = q;
         const int4 st = S.st[li];
@@ -402,13 +411,11 @@ __device__ __forceinline__ int p_candidate(const DevSim &d, PSmem &S, const PCtx
     return 0;
 }
 
-// Block scan of every thread's (choice pairs << 16 | car-following cost): the
-// compact pair list and the start of each of the nw car-following warps.  The
-// cost of a link is 1 + its rounds of 32 vehicles; warp q starts at cost unit
-// floor(q tot / nw), so a long queue is split between warps at a round
-// boundary.  A warp that starts inside a link gets the time-t position of the
-// vehicle ahead of its first one, read here before any warp writes.
-__device__ __forceinline__ void p_scan(PSmem &S, const PCtx &c, int v, int nw) {
+// Block scan of every thread's (choice pairs << 16 | queued vehicles): the
+// compact pair list and the first vehicle of each link in the CTA's queue
+// order (the queues of its links one after another, leader first), from which
+// the car-following threads take equal runs of vehicles.
+__device__ __forceinline__ void p_scan(PSmem &S, const PCtx &c, int v) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     int s = v;
 #pragma unroll
@@ -429,197 +436,139 @@ __device__ __forceinline__ void p_scan(PSmem &S, const PCtx &c, int v, int nw) {
         S.wsum[lane] = r - x;
         if (lane == 31) {
             S.npairs = r >> 16;
-            S.ctot = r & 0xffff;
+            S.voff[c.nl] = r & 0xffff;
         }
     }
     __syncthreads();
     const int ex = s - v + S.wsum[w];
-    if (tid < c.nl) {
-        // link tid holds the cost units [e0, e1): e0 its setup, e0 + 1 + r its
-        // round r; the warps q in [1, nw) with e0 <= floor(q tot / nw) < e1
-        // are q in [ceil(e0 nw / tot), ceil(e1 nw / tot) - 1]
-        const int tot = S.ctot, e0 = ex & 0xffff, e1 = e0 + (v & 0xffff);
-        const int qa = max(1, (e0 * nw + tot - 1) / tot), qb = min(nw - 1, (e1 * nw + tot - 1) / tot - 1);
-        for (int q = qa; q <= qb; ++q) {
-            const int r = max(0, (q * tot) / nw - e0 - 1);
-            S.wl[q] = tid;
-            S.wr[q] = r;
-            if (r > 0) {
-                const int lb = S.lbase[tid], cap = S.lbase[tid + 1] - lb;
-                int idx = S.q[tid].x + 32 * r - 1;
-                if (idx >= cap) idx -= cap;
-                S.wah[q] = c.P[lb + idx];
-            }
-        }
-    }
-    if (tid == 0) {
-        S.wl[0] = 0;
-        S.wr[0] = 0;
-        S.wl[nw] = c.nl;
-        S.wr[nw] = 0;
-        if (c.nl == 0)
-            for (int q = 1; q < nw; ++q) S.wl[q] = 0, S.wr[q] = 0;
-    }
+    if (tid < c.nl) S.voff[tid] = ex & 0xffff;
     const int np = v >> 16;
     for (int k = 0; k < np; ++k) S.plist[(ex >> 16) + k] = (tid << 4) | k;
     __syncthreads();
 }
 
-// The (candidate, slot) pairs of the choice warps, kPP at a time per thread:
-// slot 0 is the candidate's merge key alpha + g', slot 1 + k the utility +
-// Gumbel key of choice slot k and the vacancy of its link.  All global loads of
-// the kPP pairs (destination feature, the slot link's record and merge word,
-// then its candidate's target word) are issued before any is consumed, and the
-// Gumbel draws are computed while they are in flight.
-constexpr int kPP = 1;
-
-__device__ __forceinline__ void p_pairs(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int t, bool first,
-                                        const int4 *Cp, const unsigned long long *Wp, int tfirst, int CT) {
-    const int ct = threadIdx.x - tfirst;
+// The (candidate, slot) pairs of the choice warps: slot 0 is the candidate's
+// merge key alpha + g', slot 1 + k the utility + Gumbel key of choice slot k.
+// The only global load is the destination feature of the slot's link, issued
+// before the Gumbel draw is computed.
+__device__ __forceinline__ void p_pairs(const DevSim &d, PSmem &S, const PCtx &c, int t, int tfirst, int CT) {
     const int np = S.npairs;
-    for (int base = ct; base < np; base += CT * kPP) {
-        int pe[kPP], vid[kPP], m[kPP], cx[kPP], cy[kPP], cz[kPP];
-        float ux[kPP], uy[kPP], df[kPP];
-        bool push[kPP];
-        unsigned long long wt[kPP];
-#pragma unroll
-        for (int i = 0; i < kPP; ++i) {
-            const int p = base + i * CT;
-            pe[i] = -1;
-            if (p >= np) continue;
-            const int e = S.plist[p];
-            pe[i] = e;
-            const int en = e >> 4, sl = e & 15;
-            const bool isl = en < kPNodeTid;
-            const int4 who = isl ? S.ld[en] : S.nh[en - kPNodeTid];
-            vid[i] = who.x;
-            if (sl == 0) continue;
-            const float4 info = isl ? c.LO[S.nd[en].z + sl - 1] : c.NO[S.nq[en - kPNodeTid].z + sl - 1];
-            ux[i] = info.x;
-            uy[i] = info.y;
-            m[i] = __float_as_int(info.w);
-            df[i] = d.dest_feat[(size_t)who.y * d.V + __float_as_int(info.z)];
-            if (first) {
-                cz[i] = __ldcg(d.vac + m[i]);
-            } else {
-                const int4 cc = __ldcg(Cp + m[i]);
-                cx[i] = cc.x;
-                cy[i] = cc.y;
-                cz[i] = cc.z;
-                push[i] = __ldcg(Wp + m[i]) != 0ull;
-            }
+    for (int p = threadIdx.x - tfirst; p < np; p += CT) {
+        const int e = S.plist[p];
+        const int en = e >> 4, sl = e & 15;
+        const bool isl = en < kPNodeTid;
+        const int ni = en - kPNodeTid;
+        const int4 who = isl ? S.ld[en] : S.nh[ni];
+        if (sl == 0) {
+            const float g = gumbel(d.key0, d.key1, who.x, t, 1, 0);
+            const float al = isl ? S.alpha[en] : d.alpha[d.L];
+            if (isl) S.mkey[en] = __fadd_rn(al, g);
+            else S.nmkey[ni] = __fadd_rn(al, g);
+            continue;
         }
-        if (!first) {
-#pragma unroll
-            for (int i = 0; i < kPP; ++i) {
-                wt[i] = 0ull;
-                if (pe[i] >= 0 && (pe[i] & 15) != 0 && cy[i] >= 0) wt[i] = __ldcg(Wp + cy[i]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < kPP; ++i) {
-            if (pe[i] < 0) continue;
-            const int en = pe[i] >> 4, sl = pe[i] & 15;
-            const bool isl = en < kPNodeTid;
-            const int ni = en - kPNodeTid;
-            if (sl == 0) {
-                const float g = gumbel(d.key0, d.key1, vid[i], t, 1, 0);
-                const float al = isl ? S.alpha[en] : d.alpha[d.L];
-                if (isl) S.mkey[en] = __fadd_rn(al, g);
-                else S.nmkey[ni] = __fadd_rn(al, g);
-                continue;
-            }
-            const int k = sl - 1;
-            const float g = gumbel(d.key0, d.key1, vid[i], t, 0, k);
-            const float key = __fadd_rn(__fadd_rn(ux[i], __fmul_rn(uy[i], df[i])), g);
-            int vac;
-            if (first) {
-                vac = cz[i] & kFlagVacant;
-            } else {
-                bool pop = cy[i] == kTgtSink;
-                if (cy[i] >= 0) pop = wt[i] != 0ull && p_vid(wt[i], a.packz) == cx[i];
-                const int o = (pop ? 1 : 0) | (push[i] ? 2 : 0);
-                vac = (cz[i] >> o) & 1;
-            }
-            if (isl) {
-                S.key[en][k] = key;
-                S.tv[en][k] = (m[i] << 1) | vac;
-            } else {
-                S.nkey[ni][k] = key;
-                S.ntv[ni][k] = (m[i] << 1) | vac;
-            }
+        const int k = sl - 1;
+        const float4 info = isl ? c.LO[S.nd[en].z + k] : c.NO[S.nq[ni].z + k];
+        const float df = d.dest_feat[(size_t)who.y * d.V + __float_as_int(info.z)];
+        const float g = gumbel(d.key0, d.key1, who.x, t, 0, k);
+        const float key = __fadd_rn(__fadd_rn(info.x, __fmul_rn(info.y, df)), g);
+        if (isl) {
+            S.key[en][k] = key;
+            S.tv[en][k] = __float_as_int(info.w);
+        } else {
+            S.nkey[ni][k] = key;
+            S.ntv[ni][k] = __float_as_int(info.w);
         }
     }
 }
 
 // Newell car-following of every queued vehicle of the CTA, in shared memory,
-// by warps 0 .. nw - 1: warp w owns the rounds of 32 queue positions from
-// (S.wl[w], S.wr[w]) up to the start of warp w + 1 (an equal share of the
-// total cost, 1 + rounds per link).  Within a round lane l updates queue
-// position 32 r + l (leader first), taking the time-t position of the vehicle
-// ahead from lane l - 1 by a shuffle, from the previous round for lane 0 (or,
-// at the warp's first round inside a link, from the scan's copy) before any
-// lane writes.  No barrier is needed: a slot is touched by one warp only.  At
-// bin ends the warps also sum the link's vehicles past the midpoint and their
-// positions (shared-memory atomics: a link may be split between warps).
-constexpr int kPCFW = kPCFT / 32;
-
+// by the kPCFT car-following threads.  The CTA's vehicles, taken in queue
+// order link after link (leader first), are cut into kPCFT equal runs; thread
+// c updates run c one vehicle after another, walking from link to link.  The
+// headway of a vehicle uses the time-t position of the one ahead: within a run
+// the thread keeps it from the previous iteration; for the first vehicle of a
+// run that is not a leader it is read before a barrier of the car-following
+// threads, after which they write.  A slot is written by one thread only.  At
+// bin ends the threads also sum each link's vehicles past the midpoint and
+// their positions (shared-memory atomics: a link may span several runs).
 template <bool kTape>
 __device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int r, bool obs,
                                             bool obs_only) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int ct = threadIdx.x;
     const float M = d.M;
-    const int l0 = S.wl[w], r0 = S.wr[w], l1 = S.wl[w + 1], r1 = S.wr[w + 1];
-    const int lend = r1 > 0 ? l1 + 1 : l1;
-    for (int li = l0; li < lend; ++li) {
-        const int2 qv = *reinterpret_cast<const int2 *>(&S.q[li]);     // head, length
-        const int lb = S.lbase[li], cap = S.lbase[li + 1] - lb;
-        const float4 g = S.g[li];
-        int kb = 0, ke = qv.y;
-        float ahead = M;
-        if (li == l0 && r0 > 0) {
-            kb = 32 * r0;
-            ahead = S.wah[w];
+    const int nv = S.voff[c.nl];
+    const int v0 = (int)(((long long)ct * nv) / kPCFT), v1 = (int)(((long long)(ct + 1) * nv) / kPCFT);
+    int li = 0, k = 0, idx = 0, n = 0, lb = 0, cap = 0;
+    float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float ahead = M;
+    if (v0 < v1) {
+        // the link holding vehicle v0: the last li with voff[li] <= v0 (empty
+        // links before it share its offset; those after it start beyond v0)
+        int lo = 0, hi = c.nl - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (S.voff[mid] <= v0) lo = mid; else hi = mid - 1;
         }
-        if (li == l1) ke = min(ke, 32 * r1);
-        for (int k0 = kb; k0 < ke; k0 += 32) {
-            const int k = k0 + lane;
-            const bool act = k < ke;
-            int idx = qv.x + k;
-            if (idx >= cap) idx -= cap;
-            const float x = act ? c.P[lb + idx] : 0.0f;
-            const float up = __shfl_up_sync(kFull, x, 1);
-            const float last = __shfl_sync(kFull, x, 31);
-            if (obs) {                      // bin end: vehicles past the midpoint, position sum (time t)
-                const int pj = warp_sum(act && x >= __fmul_rn(g.x, 0.5f) ? 1 : 0);
-                long long sj = act ? pos_fx(x) : 0;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(kFull, sj, o);
-                if (lane == 0) {
-                    atomicAdd(&S.past[li], pj);
-                    atomicAdd(&S.psum[li], (unsigned long long)sj);
-                }
+        li = lo;
+        k = v0 - S.voff[li];
+        const int2 qv = *reinterpret_cast<const int2 *>(&S.q[li]);
+        n = qv.y;
+        lb = S.lbase[li];
+        cap = S.lbase[li + 1] - lb;
+        g = S.g[li];
+        idx = qv.x + k;
+        if (idx >= cap) idx -= cap;
+        if (k > 0) ahead = c.P[lb + (idx == 0 ? cap - 1 : idx - 1)];
+    }
+    asm volatile("bar.sync 1, %0;" :: "n"(kPCFT) : "memory");      // every run has read its vehicle ahead
+    int past = 0;
+    long long psum = 0;
+    for (int v = v0; v < v1; ++v) {
+        if (k == n) {                       // the run continues with the leader of the next occupied link
+            if (obs) {
+                atomicAdd(&S.past[li], past);
+                atomicAdd(&S.psum[li], (unsigned long long)psum);
+                past = 0;
+                psum = 0;
             }
-            if (act && !obs_only) {
-                const float h = k == 0 ? M : __fsub_rn(lane == 0 ? ahead : up, x);
-                int tag;
-                c.P[lb + idx] = newell(x, h, g.x, g.y, g.z, g.w, tag);
-                if (kTape) {                // tape: time-t position and branch tag of the slot
-                    const size_t o = (size_t)r * a.S + c.base0 + lb + idx;
-                    d.tape_pos[o] = x;
-                    d.tag_tape[o] = (int8_t)tag;
-                }
-            }
-            ahead = last;
+            do { ++li; } while (S.voff[li + 1] == S.voff[li]);
+            const int2 qv = *reinterpret_cast<const int2 *>(&S.q[li]);
+            n = qv.y;
+            lb = S.lbase[li];
+            cap = S.lbase[li + 1] - lb;
+            g = S.g[li];
+            idx = qv.x;
+            k = 0;
         }
+        const float x = c.P[lb + idx];
+        if (obs) {                          // bin end: vehicles past the midpoint, position sum (time t)
+            past += x >= __fmul_rn(g.x, 0.5f) ? 1 : 0;
+            psum += pos_fx(x);
+        }
+        if (!obs_only) {
+            const float h = k == 0 ? M : __fsub_rn(ahead, x);
+            int tag;
+            c.P[lb + idx] = newell(x, h, g.x, g.y, g.z, g.w, tag);
+            if (kTape) {                    // tape: time-t position and branch tag of the slot
+                const size_t o = (size_t)r * a.S + c.base0 + lb + idx;
+                d.tape_pos[o] = x;
+                d.tag_tape[o] = (int8_t)tag;
+            }
+        }
+        ahead = x;
+        ++k;
+        if (++idx == cap) idx = 0;
+    }
+    if (obs && v0 < v1) {
+        atomicAdd(&S.past[li], past);
+        atomicAdd(&S.psum[li], (unsigned long long)psum);
     }
 }
 
 // Observation at bin ends, choice, merge, next-step bits and records of this
 // thread's link or origin queue.
-template <bool kTape>
-__device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int t, bool first,
-                                         bool obs, bool obs_only, const int4 *Cp, const unsigned long long *Wp) {
+__device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int t, bool obs,
+                                         bool obs_only) {
     const int tid = threadIdx.x;
     unsigned long long *Wt = a.W3 + (size_t)(t % 3) * d.L;
     const float M = d.M;
@@ -652,8 +601,8 @@ __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem 
             if (nd.y == ld.y) {
                 tgt = kTgtSink;
             } else {
-                tgt = p_choose(d, first, Cp, Wp, a.packz, S.key[li], S.tv[li], c.LO + nd.z, nd.w, ld.y, ld.x, t);
-                if (tgt >= 0) atomicMax(Wt + tgt, p_word(S.mkey[li], ld.x, ld.y, a.packz));
+                tgt = p_choose(d, S.key[li], S.tv[li], c.LO + nd.z, nd.w, ld.y, ld.x, t);
+                atomicMax(Wt + tgt, p_word(S.mkey[li], ld.x, ld.y, a.packz));
             }
         }
         const float4 g = S.g[li];
@@ -677,28 +626,22 @@ __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem 
         bits |= (n >= 2 && arrives_after(x1, g, M, d.eps_arr)) << 5;
         bits |= arrives_after(n >= 1 ? x0 : 0.0f, g, M, d.eps_arr) << 6;
         bits |= arrives_after(n >= 2 ? x1 : 0.0f, g, M, d.eps_arr) << 7;
-        const int4 rec = make_int4(c0.x, c0.x >= 0 ? tgt : kTgtNone, (c0.z << 8) | bits, __float_as_int(x0));
-        S.cr[li] = rec;
-        a.crec2[(size_t)(t & 1) * d.L + j] = rec;
-        if (kTape) d.tape_crec[(size_t)(t - a.t0) * d.L + j] = rec;
+        // the record of step t; the transfers of step t set its final target
+        S.cr[li] = make_int4(c0.x, c0.x >= 0 ? tgt : kTgtNone, (c0.z << 8) | bits, __float_as_int(x0));
     } else if (!obs_only && tid >= kPNodeTid && tid < kPNodeTid + c.nn) {
         const int ni = tid - kPNodeTid;
         const int2 r = S.nrec[ni];
-        if (r.x < 0) {
-            if (kTape) d.tape_nrec[(size_t)(t - a.t0) * d.V + c.n0 + ni] = r;
-            return;
-        }
+        if (r.x < 0) return;
         const int4 nh = S.nh[ni];
         int tgt;
         if (S.nzone[ni] == nh.y) {
             tgt = kTgtSink;
         } else {
             const int4 nq = S.nq[ni];
-            tgt = p_choose(d, first, Cp, Wp, a.packz, S.nkey[ni], S.ntv[ni], c.NO + nq.z, nq.w, nh.y, nh.x, t);
-            if (tgt >= 0) atomicMax(Wt + tgt, p_word(S.nmkey[ni], nh.x, nh.y, a.packz));
+            tgt = p_choose(d, S.nkey[ni], S.ntv[ni], c.NO + nq.z, nq.w, nh.y, nh.x, t);
+            atomicMax(Wt + tgt, p_word(S.nmkey[ni], nh.x, nh.y, a.packz));
         }
         S.nrec[ni] = make_int2(r.x, tgt);
-        if (kTape) d.tape_nrec[(size_t)(t - a.t0) * d.V + c.n0 + ni] = make_int2(r.x, tgt);
     }
 }
 
@@ -797,6 +740,7 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         S.nd[li] = make_int4(nd.x, nd.y, nd.z - c.lo0, nd.w - nd.z);
         S.stat[li] = d.lstat[j];
         S.flags[li] = d.vac[j];
+        a.vacp[(size_t)(a.t0 & 1) * d.L + j] = d.vac[j] & kFlagVacant;   // read by the transfers of step t0
         S.cr[li] = d.crec[j];
         S.alpha[li] = d.alpha[j];
         int4 ld = make_int4(-1, -1, -1, -1);
@@ -857,22 +801,20 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         if (!first) p_apply<kTape>(d, a, S, c, t - 1, pd, cnt);
         const int v = p_candidate<kTape>(d, S, c, t, t - a.t0, false);   // reads what this thread's p_apply wrote
         if (!first) p_count(S, cnt);
-        p_scan(S, c, v, kPCFW);
+        p_scan(S, c, v);
         if (!first && tid < 4) {
             const int x = S.cnt[tid];
             if (x) atomicAdd(&d.step_delta[4 * (t - 1) + tid], x);
         }
-        const int4 *Cp = a.crec2 + (size_t)((t + 1) & 1) * d.L;                 // records of step t-1
-        const unsigned long long *Wp = a.W3 + (size_t)((t + 2) % 3) * d.L;     // words of step t-1
         if (tid >= kPCFT) {
-            p_pairs(d, a, S, c, t, first, Cp, Wp, kPCFT, kPT - kPCFT);
+            p_pairs(d, S, c, t, kPCFT, kPT - kPCFT);
         } else {
             p_carfollow<kTape>(d, a, S, c, t - a.t0, obs, false);
         }
         __syncthreads();
         if (kTape) p_tape_vid(d, a, S, c, t - a.t0);
         if (tid < 4) S.cnt[tid] = 0;
-        p_decide<kTape>(d, a, S, c, t, first, obs, false, Cp, Wp);
+        p_decide(d, a, S, c, t, obs, false);
         p_refill(S, c, pd);
         ++epoch;
         if (!grid_sync(d, a.bar, epoch * gridDim.x + (unsigned)a.bar_extra, t, &S.stop)) return;
@@ -889,10 +831,10 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
     if (a.final_obs) {
         __syncthreads();
         const int v = p_candidate<false>(d, S, c, a.t1, 0, true);
-        p_scan(S, c, v, kPCFW);
+        p_scan(S, c, v);
         if (tid < kPCFT) p_carfollow<false>(d, a, S, c, 0, true, true);
         __syncthreads();
-        p_decide<false>(d, a, S, c, a.t1, false, true, true, nullptr, nullptr);
+        p_decide(d, a, S, c, a.t1, true, true);
     }
     __syncthreads();
     // ---------------- write the group's state back ----------------
@@ -909,8 +851,8 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         d.lstat[j] = S.stat[li];
         d.vac[j] = S.flags[li];
         d.crec[j] = S.cr[li];
-        if (a.t1 > a.t0) {
-            const unsigned long long w = __ldcg(Wl + j);
+        if (a.t1 > a.t0) {          // a word on a link that was not vacant names no entrant
+            const unsigned long long w = a.vacp[(size_t)((a.t1 - 1) & 1) * d.L + j] ? __ldcg(Wl + j) : 0ull;
             Wlast[j] = w ? ((w & 0xffffffff00000000ull) | (unsigned long long)(~(uint32_t)p_vid(w, a.packz))) : 0ull;
         }
         Wnext[j] = 0ull;
