@@ -51,12 +51,8 @@ constexpr int kPLinks = 288;                 // links per CTA at most
 constexpr int kPNodes = 128;                 // origin queues per CTA at most
 constexpr int kPNodeTid = 512;               // thread of origin queue 0 in the per-entity phases
 constexpr int kPSlot = 8;                    // choice slots per candidate evaluated in parallel
-#ifndef TS_PERSIST_CHOICE_WARPS
-#define TS_PERSIST_CHOICE_WARPS 8
-#endif
-constexpr int kPCW = TS_PERSIST_CHOICE_WARPS; // choice warps (the rest update car-following)
-constexpr int kPCFT = kPT - 32 * kPCW;       // car-following threads
-constexpr int kPPairs = (kPLinks + kPNodes) * (kPSlot + 1);
+constexpr int kPEnt = kPLinks + kPNodes;     // entities: links, then origin queues (index kPLinks + node)
+constexpr int kPPairs = kPEnt * (kPSlot + 1);
 static_assert(kPSlot + 1 <= 16, "a pair list entry holds the slot in 4 bits");
 
 struct PArgs {
@@ -85,20 +81,20 @@ struct PSmem {
     int flags[kPLinks];            // vacancy / arrival for the coming step
     int lbase[kPLinks + 1];        // first ring slot of each link in shared memory (static)
     int voff[kPLinks + 1];         // first vehicle of each link in the CTA's queue order (step t)
-    int past[kPLinks];
-    float mkey[kPLinks];
+    int past[kPLinks];             // bin end: vehicles past the midpoint (time t), summed over the step
+    float xt[kPLinks];             // position of the rearmost vehicle after the step's car-following
+    float4 bx[kPLinks];            // positions after the step's car-following at queue positions 0, 1, n-1, n-2
+    float mkey[kPEnt];              // merge key alpha + g' of each entity's candidate
     float alpha[kPLinks];
     unsigned long long psum[kPLinks];
-    float key[kPLinks][kPSlot];
-    int tv[kPLinks][kPSlot];       // link of choice slot k
+    float key[kPSlot][kPEnt];      // key of choice slot k of each entity's candidate (slot-major: no bank conflicts)
+    int tv[kPSlot][kPEnt];         // link of choice slot k
+    longlong2 lpos[kPLinks];       // position sums of the open bin: at its start, of its leavers (2^-16 m)
     int4 nq[kPNodes];              // next vehicle, end of queue, first staged out-link entry, out-degree
     int4 nh[kPNodes];              // (vehicle, zone) at queue positions 0 and 1
     int2 ndep[kPNodes];            // departure steps at queue positions 0 and 1
     int2 nrec[kPNodes];            // (candidate, target) of the step
     int nzone[kPNodes];
-    float nmkey[kPNodes];
-    float nkey[kPNodes][kPSlot];
-    int ntv[kPNodes][kPSlot];      // link of choice slot k
     int plist[kPPairs];            // entity << 4 | (0 merge key, 1 + k choice slot k)
     int wsum[32];
     int cnt[4];                    // step counters: releases, arrivals, candidates, entries
@@ -116,6 +112,10 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+// merge reduction with no value returned: the thread does not wait for it
+__device__ __forceinline__ void red_max_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -123,14 +123,19 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Grid-wide barrier number `target / gridDim.x` (counter never reset inside a
-// launch).  Bounded: gives up after ~2 s or 2^22 polls, or as soon as another
-// CTA has recorded a timeout; returns false then (every thread of the CTA).
-__device__ __forceinline__ bool grid_sync(const DevSim &d, unsigned *bar, unsigned target, int t, int *stop) {
+// launch), in two halves so that a CTA can work between its arrival and the
+// wait: grid_arrive (block barrier, then one release arrival) and grid_wait.
+// Bounded: gives up after ~2 s or 2^22 polls, or as soon as another CTA has
+// recorded a timeout; returns false then (every thread of the CTA).
+__device__ __forceinline__ void grid_arrive(unsigned *bar) {
+    __syncthreads();
+    // release arrival: covers this CTA's writes ordered before it by the block
+    // barrier; the acquire load that sees the target covers the rest
+    if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(bar) : "memory");
+}
+__device__ __forceinline__ bool grid_wait(const DevSim &d, unsigned *bar, unsigned target, int t, int *stop) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        // release arrival: covers this CTA's writes ordered before it by the
-        // block barrier; the acquire load that sees the target covers the rest
-        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(bar) : "memory");
         const unsigned long long t_start = global_ns();
         int ok = 1;
         for (unsigned it = 0;; ++it) {
@@ -149,6 +154,10 @@ __device__ __forceinline__ bool grid_sync(const DevSim &d, unsigned *bar, unsign
     __syncthreads();
     return *stop == 0;
 }
+__device__ __forceinline__ bool grid_sync(const DevSim &d, unsigned *bar, unsigned target, int t, int *stop) {
+    grid_arrive(bar);
+    return grid_wait(d, bar, target, t, stop);
+}
 
 // merge words: the key in the high half; ~(vehicle << 8 | zone) or ~vehicle in
 // the low half (the largest key wins, equal keys go to the lowest vehicle)
@@ -164,22 +173,22 @@ __device__ __forceinline__ int p_vid(unsigned long long w, int packz) {
 // argmax of the staged keys (ties to the lowest slot); slots past the stage
 // are evaluated inline.  Returns the chosen link (its vacancy is taken at the
 // transfers).
-__device__ __forceinline__ int p_choose(const DevSim &d, const float *key, const int *tv, const float4 *info, int deg,
+__device__ __forceinline__ int p_choose(const DevSim &d, const PSmem &S, int ei, const float4 *info, int deg,
                                         int zone, int vid, int t) {
     float bk = -INFINITY;
     int bm = -1;
-    for (int k = 0; k < deg; ++k) {
-        float kk;
-        int m;
-        if (k < kPSlot) {
-            kk = key[k];
-            m = tv[k];
-        } else {
-            const float4 e = info[k];
-            kk = choice_key(d, e, zone, vid, t, k);
-            m = __float_as_int(e.w);
+#pragma unroll
+    for (int k = 0; k < kPSlot; ++k) {
+        if (k < deg) {
+            const float kk = S.key[k][ei];
+            const int m = S.tv[k][ei];
+            if (bm < 0 || kk > bk) { bk = kk; bm = m; }
         }
-        if (bm < 0 || kk > bk) { bk = kk; bm = m; }
+    }
+    for (int k = kPSlot; k < deg; ++k) {
+        const float4 e = info[k];
+        const float kk = choice_key(d, e, zone, vid, t, k);
+        if (kk > bk) { bk = kk; bm = __float_as_int(e.w); }
     }
     return bm;
 }
@@ -211,6 +220,69 @@ struct PCtx {
     int lo0, no0;                  // first staged entry (global index)
 };
 
+// Car-following of step t (SI-A) for the vehicles of link li whose update the
+// transfers of step t - 1 decide: the old leader if it stays (headway M), the
+// second vehicle (the leader if the first one leaves) and the entrant at x = 0
+// (behind the old rearmost vehicle, whose time-t position p_decide kept in
+// S.xt).  q0 is the queue before the transfers; the other vehicles were
+// updated during the grid barrier before (p_carfollow with kmin = 2).  The
+// updates of both outcomes are computed first (p_ends_pre, while the loads of
+// the merge words are in flight), then the outcome picks (p_ends_post).  At
+// bin ends the time-t positions join the link's sums.
+struct PEnds {
+    float x0, x1, y0, y1m, y1f, yem, yet;
+    int tags;                      // 2 bits each: y0, y1m, y1f, yem, yet
+};
+
+__device__ __forceinline__ PEnds p_ends_pre(const DevSim &d, const PSmem &S, const PCtx &c, int li, int4 q0) {
+    const float M = d.M;
+    const float4 g = S.g[li];
+    const int4 st = S.st[li];
+    const int lb = st.x - c.base0, cap = st.y, n = q0.y;
+    const int i1 = q0.x + 1 >= cap ? q0.x + 1 - cap : q0.x + 1;
+    PEnds e;
+    e.x0 = n >= 1 ? c.P[lb + q0.x] : 0.0f;
+    e.x1 = n >= 2 ? c.P[lb + i1] : 0.0f;
+    int t0, t1, t2, t3, t4;
+    e.y0 = newell(e.x0, M, g.x, g.y, g.z, g.w, t0);
+    e.y1m = newell(e.x1, M, g.x, g.y, g.z, g.w, t1);
+    e.y1f = newell(e.x1, __fsub_rn(e.x0, e.x1), g.x, g.y, g.z, g.w, t2);
+    e.yem = newell(0.0f, M, g.x, g.y, g.z, g.w, t3);
+    e.yet = newell(0.0f, __fsub_rn(S.xt[li], 0.0f), g.x, g.y, g.z, g.w, t4);
+    e.tags = t0 | (t1 << 2) | (t2 << 4) | (t3 << 6) | (t4 << 8);
+    return e;
+}
+
+template <bool kTape>
+__device__ __forceinline__ void p_ends_post(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int li,
+                                            int4 q0, const PEnds &e, bool pop, bool push, int t, bool obs) {
+    const int4 st = S.st[li];
+    const int lb = st.x - c.base0, cap = st.y, n = q0.y;
+    const int i0 = q0.x, i1 = q0.x + 1 >= cap ? q0.x + 1 - cap : q0.x + 1;
+    int ie = q0.x + n;
+    if (ie >= cap) ie -= cap;
+    const bool up0 = n >= 1 && !pop, up1 = n >= 2;
+    const bool lead_e = n == 0 || (pop && n == 1);          // the entrant is alone on the link
+    if (obs) {
+        const float half = __fmul_rn(S.g[li].x, 0.5f);
+        int past = 0;
+        long long ps = 0;
+        if (up0) { past += e.x0 >= half ? 1 : 0; ps += pos_fx(e.x0); }
+        if (up1) { past += e.x1 >= half ? 1 : 0; ps += pos_fx(e.x1); }
+        S.past[li] += past;                                   // the entrant at 0 adds nothing
+        S.psum[li] += (unsigned long long)ps;
+    }
+    if (up0) c.P[lb + i0] = e.y0;
+    if (up1) c.P[lb + i1] = pop ? e.y1m : e.y1f;
+    if (push) c.P[lb + ie] = lead_e ? e.yem : e.yet;
+    if (kTape) {                    // tape: time-t position and branch tag of the slot
+        const size_t o = (size_t)(t - a.t0) * a.S + c.base0 + lb;
+        if (up0) { d.tape_pos[o + i0] = e.x0; d.tag_tape[o + i0] = (int8_t)(e.tags & 3); }
+        if (up1) { d.tape_pos[o + i1] = e.x1; d.tag_tape[o + i1] = (int8_t)((e.tags >> (pop ? 2 : 4)) & 3); }
+        if (push) { d.tape_pos[o + ie] = 0.0f; d.tag_tape[o + ie] = (int8_t)((e.tags >> (lead_e ? 6 : 8)) & 3); }
+    }
+}
+
 // Transfers of step tb for this thread's link or origin queue (SI-B Eq.
 // transfer): pop the leader that won its merge into a vacant link or left to its
 // destination, push the merge winner at x = 0 if the link was vacant at tb,
@@ -219,7 +291,7 @@ struct PCtx {
 // accumulate.
 template <bool kTape>
 __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int tb, PPend &pd,
-                                        int *cnt) {
+                                        int *cnt, bool cf, bool obs) {
     const int tid = threadIdx.x;
     const unsigned long long *Wb = a.W3 + (size_t)(tb % 3) * d.L;
     const int *Vb = a.vacp + (size_t)(tb & 1) * d.L;           // vacancy of every link at tb
@@ -236,6 +308,8 @@ __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &
             wt = __ldcg(Wb + cr.y);
             vt = __ldcg(Vb + cr.y);
         }
+        PEnds ends;
+        if (cf) ends = p_ends_pre(d, S, c, li, q);            // while the loads are in flight
         // the candidates of a link that was not vacant at tb could not enter it:
         // its word names no entrant
         const unsigned long long win = (S.flags[li] & kFlagVacant) ? w0 : 0ull;
@@ -254,6 +328,7 @@ __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &
         }
         if (kTape) d.tape_crec[(size_t)(tb - a.t0) * d.L + j] = cr;
         S.cr[li] = cr;
+        const int4 q0 = q;                                   // the queue before the transfers
         int4 ld = S.ld[li];
         int2 le = S.le[li];
         if (pop) {
@@ -261,9 +336,7 @@ __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &
             stat.y += tb + 1 - (cr.z >> 8);
             stat.z += 1;
             S.stat[li] = stat;
-            longlong2 ps = d.lpos[j];
-            ps.y += pos_fx(__int_as_float(cr.w));
-            d.lpos[j] = ps;
+            S.lpos[li].y += pos_fx(__int_as_float(cr.w));
             q.x = (q.x + 1 == st.y) ? 0 : q.x + 1;
             q.y -= 1;
             q.z -= d.dn_fx;
@@ -279,11 +352,12 @@ __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &
                 pd.on = 1;
             }
         }
-        const bool push = win != 0ull;
+        bool push = win != 0ull;
         if (push) {
             const int v = p_vid(win, a.packz);
             if (q.y >= st.y) {
                 set_error(d, SIM_EOVERFLOW, j, tb);
+                push = false;
             } else {
                 const int z = a.packz ? (int)((~(uint32_t)(win & 0xffffffffull)) & 0xffu) : d.dest_zone[v];
                 int idx = q.x + q.y;
@@ -307,6 +381,7 @@ __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &
                 }
             }
         }
+        if (cf) p_ends_post<kTape>(d, a, S, c, li, q0, ends, pop, push, tb + 1, obs);
         S.q[li] = q;
         S.ld[li] = ld;
         S.le[li] = le;
@@ -372,7 +447,7 @@ __device__ __forceinline__ void p_refill(PSmem &S, const PCtx &c, const PPend &p
 __device__ __forceinline__ void p_count(PSmem &S, const int *cnt) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const int v = warp_sum(cnt[k]);
+        const int v = (int)__reduce_add_sync(kFull, (unsigned)cnt[k]);
         if ((threadIdx.x & 31) == 0 && v) atomicAdd(&S.cnt[k], v);
     }
 }
@@ -385,8 +460,6 @@ __device__ __forceinline__ int p_candidate(const DevSim &d, PSmem &S, const PCtx
     const int tid = threadIdx.x;
     if (tid < c.nl) {
         const int li = tid;
-        S.past[li] = 0;
-        S.psum[li] = 0ull;
         const int4 q = S.q[li];
         const int cost = q.y;                              // vehicles to update
         if (obs_only) return cost;
@@ -447,57 +520,59 @@ __device__ __forceinline__ void p_scan(PSmem &S, const PCtx &c, int v) {
     __syncthreads();
 }
 
-// The (candidate, slot) pairs of the choice warps: slot 0 is the candidate's
-// merge key alpha + g', slot 1 + k the utility + Gumbel key of choice slot k.
-// The only global load is the destination feature of the slot's link, issued
-// before the Gumbel draw is computed.
-__device__ __forceinline__ void p_pairs(const DevSim &d, PSmem &S, const PCtx &c, int t, int tfirst, int CT) {
+// The (candidate, slot) pairs, one per thread at a time: slot 0 is the
+// candidate's merge key alpha + g' (Gumbel word of stream 1, block 0), slot
+// 1 + k the utility + Gumbel key of choice slot k (stream 0, word k of the
+// candidate's blocks).  Both kinds run one code path (one Philox block, one
+// Gumbel transform), so a warp holding both does not serialise them; the only
+// global load is the destination feature of a slot's link, issued before the
+// Gumbel draw is computed.
+__device__ __forceinline__ void p_pairs(const DevSim &d, PSmem &S, const PCtx &c, int t) {
     const int np = S.npairs;
-    for (int p = threadIdx.x - tfirst; p < np; p += CT) {
+    for (int p = threadIdx.x; p < np; p += kPT) {
         const int e = S.plist[p];
         const int en = e >> 4, sl = e & 15;
         const bool isl = en < kPNodeTid;
         const int ni = en - kPNodeTid;
+        const int ei = isl ? en : kPLinks + ni;
         const int4 who = isl ? S.ld[en] : S.nh[ni];
-        if (sl == 0) {
-            const float g = gumbel(d.key0, d.key1, who.x, t, 1, 0);
-            const float al = isl ? S.alpha[en] : d.alpha[d.L];
-            if (isl) S.mkey[en] = __fadd_rn(al, g);
-            else S.nmkey[ni] = __fadd_rn(al, g);
-            continue;
-        }
         const int k = sl - 1;
-        const float4 info = isl ? c.LO[S.nd[en].z + k] : c.NO[S.nq[ni].z + k];
-        const float df = d.dest_feat[(size_t)who.y * d.V + __float_as_int(info.z)];
-        const float g = gumbel(d.key0, d.key1, who.x, t, 0, k);
-        const float key = __fadd_rn(__fadd_rn(info.x, __fmul_rn(info.y, df)), g);
-        if (isl) {
-            S.key[en][k] = key;
-            S.tv[en][k] = __float_as_int(info.w);
+        float4 info = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        float df = 0.0f;
+        if (sl > 0) {
+            info = isl ? c.LO[S.nd[en].z + k] : c.NO[S.nq[ni].z + k];
+            df = d.dest_feat[(size_t)who.y * d.V + __float_as_int(info.z)];
+        }
+        const float g = gumbel(d.key0, d.key1, who.x, t, sl == 0 ? 1 : 0, sl == 0 ? 0 : k);
+        if (sl == 0) {
+            S.mkey[ei] = __fadd_rn(isl ? S.alpha[en] : d.alpha[d.L], g);
         } else {
-            S.nkey[ni][k] = key;
-            S.ntv[ni][k] = __float_as_int(info.w);
+            S.key[k][ei] = __fadd_rn(__fadd_rn(info.x, __fmul_rn(info.y, df)), g);
+            S.tv[k][ei] = __float_as_int(info.w);
         }
     }
 }
 
-// Newell car-following of every queued vehicle of the CTA, in shared memory,
-// by the kPCFT car-following threads.  The CTA's vehicles, taken in queue
-// order link after link (leader first), are cut into kPCFT equal runs; thread
-// c updates run c one vehicle after another, walking from link to link.  The
-// headway of a vehicle uses the time-t position of the one ahead: within a run
-// the thread keeps it from the previous iteration; for the first vehicle of a
-// run that is not a leader it is read before a barrier of the car-following
-// threads, after which they write.  A slot is written by one thread only.  At
-// bin ends the threads also sum each link's vehicles past the midpoint and
-// their positions (shared-memory atomics: a link may span several runs).
+// Newell car-following of the queued vehicles of the CTA, in shared memory, by
+// threads 0 .. NT - 1.  The CTA's vehicles, taken in queue order link after
+// link (leader first), are cut into NT equal runs; thread c updates run c one
+// vehicle after another, walking from link to link.  The headway of a vehicle
+// uses the time-t position of the one ahead: within a run the thread keeps it
+// from the previous iteration; for the first vehicle of a run that is not a
+// leader it is read before a barrier of the NT threads, after which they
+// write.  A slot is written by one thread only.  Queue positions below kmin
+// are read but not updated (kmin = 2: the vehicles whose update the coming
+// transfers decide, see p_cf_ends).  At bin ends the threads also sum each
+// link's vehicles past the midpoint and their positions over the updated
+// vehicles (shared-memory atomics: a link may span several runs).
 template <bool kTape>
 __device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int r, bool obs,
-                                            bool obs_only) {
+                                            bool obs_only, int kmin) {
+    constexpr int NT = kPT;
     const int ct = threadIdx.x;
     const float M = d.M;
     const int nv = S.voff[c.nl];
-    const int v0 = (int)(((long long)ct * nv) / kPCFT), v1 = (int)(((long long)(ct + 1) * nv) / kPCFT);
+    const int v0 = (int)(((long long)ct * nv) / NT), v1 = (int)(((long long)(ct + 1) * nv) / NT);
     int li = 0, k = 0, idx = 0, n = 0, lb = 0, cap = 0;
     float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float ahead = M;
@@ -520,7 +595,7 @@ __device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSm
         if (idx >= cap) idx -= cap;
         if (k > 0) ahead = c.P[lb + (idx == 0 ? cap - 1 : idx - 1)];
     }
-    asm volatile("bar.sync 1, %0;" :: "n"(kPCFT) : "memory");      // every run has read its vehicle ahead
+    asm volatile("bar.sync 1, %0;" :: "n"(NT) : "memory");         // every run has read its vehicle ahead
     int past = 0;
     long long psum = 0;
     for (int v = v0; v < v1; ++v) {
@@ -541,11 +616,11 @@ __device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSm
             k = 0;
         }
         const float x = c.P[lb + idx];
-        if (obs) {                          // bin end: vehicles past the midpoint, position sum (time t)
+        if (obs && k >= kmin) {             // bin end: vehicles past the midpoint, position sum (time t)
             past += x >= __fmul_rn(g.x, 0.5f) ? 1 : 0;
             psum += pos_fx(x);
         }
-        if (!obs_only) {
+        if (!obs_only && k >= kmin) {
             const float h = k == 0 ? M : __fsub_rn(ahead, x);
             int tag;
             c.P[lb + idx] = newell(x, h, g.x, g.y, g.z, g.w, tag);
@@ -582,13 +657,13 @@ __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem 
             const size_t o = (size_t)bin * d.L + j;
             const int C = q.w + S.past[li];
             d.out_counts[o] = C - stat.w;
-            const longlong2 ps = d.lpos[j];
+            const longlong2 ps = S.lpos[li];
             const long long pnow = (long long)S.psum[li];
             const long long dist = pnow - ps.x + ps.y;
             d.out_speed[o] = stat.x ? (float)((double)dist / (double)kPosScale / ((double)stat.x * (double)d.dt)) : 0.0f;
             d.out_tt[o] = stat.z ? (float)((double)stat.y * (double)d.dt / (double)stat.z) : 0.0f;
             stat = make_int4(0, 0, 0, C);
-            d.lpos[j] = make_longlong2(pnow, 0);
+            S.lpos[li] = make_longlong2(pnow, 0);
             if (obs_only) { S.stat[li] = stat; return; }
         }
         stat.x += n;
@@ -601,8 +676,8 @@ __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem 
             if (nd.y == ld.y) {
                 tgt = kTgtSink;
             } else {
-                tgt = p_choose(d, S.key[li], S.tv[li], c.LO + nd.z, nd.w, ld.y, ld.x, t);
-                atomicMax(Wt + tgt, p_word(S.mkey[li], ld.x, ld.y, a.packz));
+                tgt = p_choose(d, S, li, c.LO + nd.z, nd.w, ld.y, ld.x, t);
+                red_max_u64(Wt + tgt, p_word(S.mkey[li], ld.x, ld.y, a.packz));
             }
         }
         const float4 g = S.g[li];
@@ -616,18 +691,14 @@ __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem 
         const float x0 = n >= 1 ? at(0) : 0.0f;
         const float x1 = n >= 2 ? at(1) : 0.0f;
         const float xt = n >= 1 ? at(n - 1) : 0.0f;
+        S.xt[li] = xt;                      // ahead of the next entrant (p_cf_ends)
+        S.past[li] = 0;                     // the sums of the next step start from zero
+        S.psum[li] = 0ull;
         const float xpt = n >= 2 ? at(n - 2) : 0.0f;
-        int bits = 0;
-        bits |= (n == 0 || vacant_after(xt, n >= 2 ? __fsub_rn(xpt, xt) : M, g)) << 0;
-        bits |= (n <= 1 || vacant_after(xt, n >= 3 ? __fsub_rn(xpt, xt) : M, g)) << 1;
-        bits |= vacant_after(0.0f, n >= 1 ? xt : M, g) << 2;
-        bits |= vacant_after(0.0f, n >= 2 ? xt : M, g) << 3;
-        bits |= (n >= 1 && arrives_after(x0, g, M, d.eps_arr)) << 4;
-        bits |= (n >= 2 && arrives_after(x1, g, M, d.eps_arr)) << 5;
-        bits |= arrives_after(n >= 1 ? x0 : 0.0f, g, M, d.eps_arr) << 6;
-        bits |= arrives_after(n >= 2 ? x1 : 0.0f, g, M, d.eps_arr) << 7;
-        // the record of step t; the transfers of step t set its final target
-        S.cr[li] = make_int4(c0.x, c0.x >= 0 ? tgt : kTgtNone, (c0.z << 8) | bits, __float_as_int(x0));
+        S.bx[li] = make_float4(x0, x1, xt, xpt);              // for p_bits
+        // the record of step t (p_bits adds the next-step bits, the transfers of
+        // step t set its final target)
+        S.cr[li] = make_int4(c0.x, c0.x >= 0 ? tgt : kTgtNone, c0.z << 8, __float_as_int(x0));
     } else if (!obs_only && tid >= kPNodeTid && tid < kPNodeTid + c.nn) {
         const int ni = tid - kPNodeTid;
         const int2 r = S.nrec[ni];
@@ -638,11 +709,36 @@ __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem 
             tgt = kTgtSink;
         } else {
             const int4 nq = S.nq[ni];
-            tgt = p_choose(d, S.nkey[ni], S.ntv[ni], c.NO + nq.z, nq.w, nh.y, nh.x, t);
-            atomicMax(Wt + tgt, p_word(S.nmkey[ni], nh.x, nh.y, a.packz));
+            tgt = p_choose(d, S, kPLinks + ni, c.NO + nq.z, nq.w, nh.y, nh.x, t);
+            red_max_u64(Wt + tgt, p_word(S.mkey[kPLinks + ni], nh.x, nh.y, a.packz));
         }
         S.nrec[ni] = make_int2(r.x, tgt);
     }
+}
+
+// Next-step vacancy and arrival bits of this thread's link for the four (pop,
+// push) outcomes of the coming transfers, from the positions after the step's
+// car-following that p_decide kept: a vehicle entering at 0 finds the link
+// vacant after the next car-following (rearmost vehicle beyond the jam spacing,
+// SI-B) / the leader reaches the arrival line (Alg. S2).  Run while the CTA
+// waits at the grid barrier: only the transfers of the next step read them.
+__device__ __forceinline__ void p_bits(const DevSim &d, PSmem &S, const PCtx &c) {
+    const int li = threadIdx.x;
+    if (li >= c.nl) return;
+    const float M = d.M;
+    const int n = S.q[li].y;
+    const float4 x = S.bx[li];              // x0, x1, xt (rearmost), xpt (ahead of it)
+    const float4 g = S.g[li];
+    int bits = 0;
+    bits |= (n == 0 || vacant_after(x.z, n >= 2 ? __fsub_rn(x.w, x.z) : M, g)) << 0;
+    bits |= (n <= 1 || vacant_after(x.z, n >= 3 ? __fsub_rn(x.w, x.z) : M, g)) << 1;
+    bits |= vacant_after(0.0f, n >= 1 ? x.z : M, g) << 2;
+    bits |= vacant_after(0.0f, n >= 2 ? x.z : M, g) << 3;
+    bits |= (n >= 1 && arrives_after(x.x, g, M, d.eps_arr)) << 4;
+    bits |= (n >= 2 && arrives_after(x.y, g, M, d.eps_arr)) << 5;
+    bits |= arrives_after(n >= 1 ? x.x : 0.0f, g, M, d.eps_arr) << 6;
+    bits |= arrives_after(n >= 2 ? x.y : 0.0f, g, M, d.eps_arr) << 7;
+    S.cr[li].z |= bits;
 }
 
 // tape: vehicle of every occupied slot at the start of step t (record r), by
@@ -739,6 +835,9 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         S.g[li] = d.geo[j];
         S.nd[li] = make_int4(nd.x, nd.y, nd.z - c.lo0, nd.w - nd.z);
         S.stat[li] = d.lstat[j];
+        S.past[li] = 0;
+        S.psum[li] = 0ull;
+        S.lpos[li] = d.lpos[j];
         S.flags[li] = d.vac[j];
         a.vacp[(size_t)(a.t0 & 1) * d.L + j] = d.vac[j] & kFlagVacant;   // read by the transfers of step t0
         S.cr[li] = d.crec[j];
@@ -792,13 +891,20 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
     }
     __syncthreads();
     // ---------------- steps ----------------
+    // Step t: its car-following runs in two parts.  The vehicles at queue
+    // positions >= 2 of the queues as step t - 1 leaves them do not depend on
+    // the transfers of t - 1 (their vehicle ahead stays), so they are updated
+    // while the CTA waits at the grid barrier of step t - 1; the first two and
+    // the entrant follow in the transfers (p_cf_ends).  The first step of the
+    // launch, with no transfers pending, updates every vehicle before its
+    // choices.
     unsigned epoch = 0;
     for (int t = a.t0; t < a.t1; ++t) {
         const bool first = t == a.t0;
         const bool obs = t > 0 && t % d.obs_every == 0;
         PPend pd{};
         int cnt[4] = {0, 0, 0, 0};
-        if (!first) p_apply<kTape>(d, a, S, c, t - 1, pd, cnt);
+        if (!first) p_apply<kTape>(d, a, S, c, t - 1, pd, cnt, true, obs);
         const int v = p_candidate<kTape>(d, S, c, t, t - a.t0, false);   // reads what this thread's p_apply wrote
         if (!first) p_count(S, cnt);
         p_scan(S, c, v);
@@ -806,23 +912,29 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
             const int x = S.cnt[tid];
             if (x) atomicAdd(&d.step_delta[4 * (t - 1) + tid], x);
         }
-        if (tid >= kPCFT) {
-            p_pairs(d, S, c, t, kPCFT, kPT - kPCFT);
-        } else {
-            p_carfollow<kTape>(d, a, S, c, t - a.t0, obs, false);
+        if (first) {
+            p_carfollow<kTape>(d, a, S, c, t - a.t0, obs, false, 0);
+            __syncthreads();
         }
+        p_pairs(d, S, c, t);
         __syncthreads();
         if (kTape) p_tape_vid(d, a, S, c, t - a.t0);
         if (tid < 4) S.cnt[tid] = 0;
         p_decide(d, a, S, c, t, obs, false);
         p_refill(S, c, pd);
         ++epoch;
-        if (!grid_sync(d, a.bar, epoch * gridDim.x + (unsigned)a.bar_extra, t, &S.stop)) return;
+        grid_arrive(a.bar);
+        p_bits(d, S, c);
+        if (t + 1 < a.t1) {
+            const bool obs1 = (t + 1) % d.obs_every == 0;
+            p_carfollow<kTape>(d, a, S, c, t + 1 - a.t0, obs1, false, 2);
+        }
+        if (!grid_wait(d, a.bar, epoch * gridDim.x + (unsigned)a.bar_extra, t, &S.stop)) return;
     }
     if (a.t1 > a.t0) {
         PPend pd{};
         int cnt[4] = {0, 0, 0, 0};
-        p_apply<kTape>(d, a, S, c, a.t1 - 1, pd, cnt);
+        p_apply<kTape>(d, a, S, c, a.t1 - 1, pd, cnt, false, false);
         p_count(S, cnt);
         p_refill(S, c, pd);
         __syncthreads();
@@ -832,7 +944,7 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         __syncthreads();
         const int v = p_candidate<false>(d, S, c, a.t1, 0, true);
         p_scan(S, c, v);
-        if (tid < kPCFT) p_carfollow<false>(d, a, S, c, 0, true, true);
+        p_carfollow<false>(d, a, S, c, 0, true, true, 0);
         __syncthreads();
         p_decide(d, a, S, c, a.t1, true, true);
     }
@@ -849,6 +961,7 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         const int j = c.j0 + li;
         d.lq[j] = S.q[li];
         d.lstat[j] = S.stat[li];
+        d.lpos[j] = S.lpos[li];
         d.vac[j] = S.flags[li];
         d.crec[j] = S.cr[li];
         if (a.t1 > a.t0) {          // a word on a link that was not vacant names no entrant
