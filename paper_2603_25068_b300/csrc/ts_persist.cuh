@@ -225,7 +225,7 @@ struct PCtx {
 // second vehicle (the leader if the first one leaves) and the entrant at x = 0
 // (behind the old rearmost vehicle, whose time-t position p_decide kept in
 // S.xt).  q0 is the queue before the transfers; the other vehicles were
-// updated during the grid barrier before (p_carfollow with kmin = 2).  The
+// updated during the grid barrier before (p_carfollow with kMin = 2).  The
 // updates of both outcomes are computed first (p_ends_pre, while the loads of
 // the merge words are in flight), then the outcome picks (p_ends_post).  At
 // bin ends the time-t positions join the link's sums.
@@ -560,19 +560,18 @@ __device__ __forceinline__ void p_pairs(const DevSim &d, PSmem &S, const PCtx &c
 // uses the time-t position of the one ahead: within a run the thread keeps it
 // from the previous iteration; for the first vehicle of a run that is not a
 // leader it is read before a barrier of the NT threads, after which they
-// write.  A slot is written by one thread only.  Queue positions below kmin
-// are read but not updated (kmin = 2: the vehicles whose update the coming
-// transfers decide, see p_cf_ends).  At bin ends the threads also sum each
+// write.  A slot is written by one thread only.  Queue positions below kMin
+// are read but not updated (kMin = 2: the vehicles whose update the coming
+// transfers decide, see p_ends_pre).  At bin ends the threads also sum each
 // link's vehicles past the midpoint and their positions over the updated
 // vehicles (shared-memory atomics: a link may span several runs).
-template <bool kTape>
-__device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int r, bool obs,
-                                            bool obs_only, int kmin) {
+template <bool kTape, bool kObsOnly, int kMin>
+__device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int r, bool obs) {
     constexpr int NT = kPT;
     const int ct = threadIdx.x;
     const float M = d.M;
-    const int nv = S.voff[c.nl];
-    const int v0 = (int)(((long long)ct * nv) / NT), v1 = (int)(((long long)(ct + 1) * nv) / NT);
+    const int nv = S.voff[c.nl];                             // < 2^16: ct nv fits in 32 bits
+    const int v0 = (ct * nv) / NT, v1 = ((ct + 1) * nv) / NT;
     int li = 0, k = 0, idx = 0, n = 0, lb = 0, cap = 0;
     float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float ahead = M;
@@ -616,11 +615,11 @@ __device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSm
             k = 0;
         }
         const float x = c.P[lb + idx];
-        if (obs && k >= kmin) {             // bin end: vehicles past the midpoint, position sum (time t)
+        if (obs && k >= kMin) {             // bin end: vehicles past the midpoint, position sum (time t)
             past += x >= __fmul_rn(g.x, 0.5f) ? 1 : 0;
             psum += pos_fx(x);
         }
-        if (!obs_only && k >= kmin) {
+        if (!kObsOnly && k >= kMin) {
             const float h = k == 0 ? M : __fsub_rn(ahead, x);
             int tag;
             c.P[lb + idx] = newell(x, h, g.x, g.y, g.z, g.w, tag);
@@ -691,7 +690,7 @@ __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem 
         const float x0 = n >= 1 ? at(0) : 0.0f;
         const float x1 = n >= 2 ? at(1) : 0.0f;
         const float xt = n >= 1 ? at(n - 1) : 0.0f;
-        S.xt[li] = xt;                      // ahead of the next entrant (p_cf_ends)
+        S.xt[li] = xt;                      // ahead of the next entrant (p_ends_pre)
         S.past[li] = 0;                     // the sums of the next step start from zero
         S.psum[li] = 0ull;
         const float xpt = n >= 2 ? at(n - 2) : 0.0f;
@@ -895,7 +894,7 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
     // positions >= 2 of the queues as step t - 1 leaves them do not depend on
     // the transfers of t - 1 (their vehicle ahead stays), so they are updated
     // while the CTA waits at the grid barrier of step t - 1; the first two and
-    // the entrant follow in the transfers (p_cf_ends).  The first step of the
+    // the entrant follow in the transfers (p_ends_pre, p_ends_post).  The first step of the
     // launch, with no transfers pending, updates every vehicle before its
     // choices.
     unsigned epoch = 0;
@@ -913,7 +912,7 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
             if (x) atomicAdd(&d.step_delta[4 * (t - 1) + tid], x);
         }
         if (first) {
-            p_carfollow<kTape>(d, a, S, c, t - a.t0, obs, false, 0);
+            p_carfollow<kTape, false, 0>(d, a, S, c, t - a.t0, obs);
             __syncthreads();
         }
         p_pairs(d, S, c, t);
@@ -927,7 +926,7 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         p_bits(d, S, c);
         if (t + 1 < a.t1) {
             const bool obs1 = (t + 1) % d.obs_every == 0;
-            p_carfollow<kTape>(d, a, S, c, t + 1 - a.t0, obs1, false, 2);
+            p_carfollow<kTape, false, 2>(d, a, S, c, t + 1 - a.t0, obs1);
         }
         if (!grid_wait(d, a.bar, epoch * gridDim.x + (unsigned)a.bar_extra, t, &S.stop)) return;
     }
@@ -944,7 +943,7 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         __syncthreads();
         const int v = p_candidate<false>(d, S, c, a.t1, 0, true);
         p_scan(S, c, v);
-        p_carfollow<false>(d, a, S, c, 0, true, true, 0);
+        p_carfollow<false, true, 0>(d, a, S, c, 0, true);
         __syncthreads();
         p_decide(d, a, S, c, a.t1, true, true);
     }
