@@ -174,6 +174,20 @@ SIM_API int sim_create(const sim_network *net, const sim_demand *dem, const sim_
  * Takes effect at the next reset / rollout. */
 SIM_API int sim_set_params(sim_handle h, const sim_params *par);
 
+/* As sim_set_params, with the arrays (u, kappa, alpha, beta, cost [L], w [F])
+ * and the origin queues' merge priority (*alpha_origin, one float; the struct's
+ * alpha_origin field is not read) in memory of the handle's device, e.g.
+ * tensors of a training loop.  The copies and the derivation of the per-link
+ * quantities are enqueued on the handle's stream without a host
+ * synchronisation: the arrays must hold their values until the stream reaches
+ * the call (order the producer's stream before it with an event) and may
+ * change after.  Validation (the rules of sim_set_params) runs on the device;
+ * an invalid parameter is reported as SIM_EINVAL by the next call that reads
+ * the handle's device errors (a rollout into host outputs, sim_step,
+ * sim_backward), until parameters are set again.  The paper has no
+ * counterpart.  Errors: SIM_EINVAL (NULL arrays), SIM_ECUDA. */
+SIM_API int sim_set_params_device(sim_handle h, const sim_params *par, const float *alpha_origin);
+
 /* Reset to t = 0 for a rollout of horizon T (every vehicle waiting, links empty,
  * full outflow credit).  Errors: SIM_EINVAL (T < 1). */
 SIM_API int sim_reset(sim_handle h, int32_t T);

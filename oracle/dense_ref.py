@@ -196,9 +196,6 @@ def run(sc, T=None, ybar=None, xbarT=None, tape=None, params=None):
         lp = onehot + pi - sg(pi)
         vac_t = torch.tensor(vacant.astype(np.float64))
         l = arrived[:, None] * (vac_t[None, :] * lp)
-        alpha_src = torch.zeros(N, dtype=dt64)
-        for i in range(N):
-            alpha_src = alpha_src + 0.0
         src_alpha = []
         for i in range(N):
             j = int(vlink[i])

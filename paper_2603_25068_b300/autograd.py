@@ -23,11 +23,20 @@ class RolloutCounts(torch.autograd.Function):
     # torch's stream waits for it before the outputs are used.
     @staticmethod
     def forward(ctx, sim, T, u, kappa, alpha, beta, cost, w, alpha_origin, od_lambda):
-        host = lambda x: x.detach().to("cpu", torch.float32).numpy()
-        sim.set_params(u=host(u), kappa=host(kappa), alpha=host(alpha), beta=host(beta), cost=host(cost),
-                       w=host(w), alpha_origin=float(alpha_origin.detach().reshape(-1)[0]))
-        cur, s = torch.cuda.current_stream(torch.device("cuda", sim.device)), sim.torch_stream()
-        s.wait_stream(cur)
+        dev = torch.device("cuda", sim.device)
+        params = (u, kappa, alpha, beta, cost, w, alpha_origin)
+        cur, s = torch.cuda.current_stream(dev), sim.torch_stream()
+        if all(x.device == dev for x in params):
+            # device tensors: copied on the simulator's stream, no host round trip
+            prep = lambda x: x.detach().to(torch.float32).contiguous().reshape(-1)
+            dp = [prep(x) for x in params]                       # made on torch's stream
+            s.wait_stream(cur)
+            sim.set_params_device(*dp)
+        else:
+            host = lambda x: x.detach().to("cpu", torch.float32).numpy()
+            sim.set_params(u=host(u), kappa=host(kappa), alpha=host(alpha), beta=host(beta), cost=host(cost),
+                           w=host(w), alpha_origin=float(alpha_origin.detach().reshape(-1)[0]))
+            s.wait_stream(cur)
         out = sim.rollout(T, device=True)
         cur.wait_stream(s)
         ctx.sim = sim

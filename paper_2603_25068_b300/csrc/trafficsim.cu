@@ -53,6 +53,24 @@ __global__ void k_params(DevSim d, const float *len, const float *u, const float
     const_cast<float4 *>(d.tinfo)[j] = make_float4(a, g, __int_as_float(head[j]), __fmul_rn(L, 0.5f));
 }
 
+// The validity test of upload_params on parameters that live on the device:
+// u, kappa, cost positive and finite, u dt below 2000 m, alpha, beta, w and the
+// origin queues' merge priority finite; *perr becomes nonzero otherwise.
+__global__ void k_check_params(const float *u, const float *kappa, const float *alpha, const float *beta,
+                               const float *cost, const float *w, const float *alpha_origin, int L, int F, float dt,
+                               int *perr) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (i < L) {
+        bad = !(u[i] > 0.0f) || !isfinite(u[i]) || !((double)u[i] * dt < 2000.0) || !(kappa[i] > 0.0f) ||
+              !isfinite(kappa[i]) || !(cost[i] > 0.0f) || !isfinite(cost[i]) || !isfinite(alpha[i]) ||
+              !isfinite(beta[i]);
+    }
+    if (i < F) bad = bad || !isfinite(w[i]);
+    if (i == 0) bad = bad || !isfinite(*alpha_origin);
+    if (bad) atomicOr(perr, 1);
+}
+
 __global__ void k_reset(DevSim d, const int *fifo_beg) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < d.L) {
@@ -146,6 +164,7 @@ struct sim_ctx {
     // run state
     int t = 0, T = 0, n_bins = 0;
     bool reset_done = false;
+    int *d_perr = nullptr;               // set by k_check_params when device parameters are invalid
     int cap_T = 0;                       // capacity of the per-T output buffers
     std::map<int, cudaGraphExec_t> graphs;
     std::string err;
@@ -560,6 +579,7 @@ static int upload_params(sim_ctx *h, const sim_params *par) {
     CU(cudaMemcpyAsync(h->d_beta, par->beta, L * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     CU(cudaMemcpyAsync(h->d_cost, par->cost, L * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     if (F) CU(cudaMemcpyAsync(h->d_w, par->w, F * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    if (h->d_perr) CU(cudaMemsetAsync(h->d_perr, 0, sizeof(int), h->stream));
     k_params<<<(L + 255) / 256, 256, 0, h->stream>>>(h->d, h->d_len, h->d_u, h->d_kappa, h->d_beta, h->d_cost,
                                                      h->d_phi, h->d_psi, h->d_w, h->d_head, h->opt.dn,
                                                      h->opt.eps_tag);
@@ -760,6 +780,8 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
     TRY(dalloc(h, &d.lstat, L));
     TRY(dalloc(h, &d.lpos, L));
     TRY(dalloc(h, &d.err, 4));
+    TRY(dalloc(h, &h->d_perr, 1));
+    CU(cudaMemsetAsync(h->d_perr, 0, sizeof(int), h->stream));
     CU(cudaMemsetAsync(d.err, 0, 4 * sizeof(int), h->stream));
     CU(cudaMemsetAsync(d.pos0, 0, (size_t)S * sizeof(float), h->stream));
     CU(cudaMemsetAsync(d.pos1, 0, (size_t)S * sizeof(float), h->stream));
@@ -847,6 +869,35 @@ extern "C" int sim_set_params(sim_handle h, const sim_params *par) {
     return upload_params(h, par);
 }
 
+extern "C" int sim_set_params_device(sim_handle h, const sim_params *par, const float *alpha_origin) {
+    if (!h || !par || !alpha_origin) return SIM_EINVAL;
+    const int L = h->L, F = h->F;
+    if (!par->u || !par->kappa || !par->alpha || !par->beta || !par->cost || (F > 0 && !par->w))
+        return fail(h, SIM_EINVAL, "null parameter array");
+    CU(cudaSetDevice(h->device));
+    cudaStream_t s = h->stream;
+    CU(cudaMemsetAsync(h->d_perr, 0, sizeof(int), s));
+    const int nc = std::max(std::max(L, F), 1);
+    k_check_params<<<(nc + 255) / 256, 256, 0, s>>>(par->u, par->kappa, par->alpha, par->beta, par->cost,
+                                                   F > 0 ? par->w : par->u, alpha_origin, L, F, h->opt.dt,
+                                                   h->d_perr);
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    CU(cudaMemcpyAsync(h->d_u, par->u, L * sizeof(float), k, s));
+    CU(cudaMemcpyAsync(h->d_kappa, par->kappa, L * sizeof(float), k, s));
+    CU(cudaMemcpyAsync(const_cast<float *>(h->d.alpha), par->alpha, L * sizeof(float), k, s));
+    CU(cudaMemcpyAsync(const_cast<float *>(h->d.alpha) + L, alpha_origin, sizeof(float), k, s));
+    CU(cudaMemcpyAsync(h->d_beta, par->beta, L * sizeof(float), k, s));
+    CU(cudaMemcpyAsync(h->d_cost, par->cost, L * sizeof(float), k, s));
+    if (F) CU(cudaMemcpyAsync(h->d_w, par->w, F * sizeof(float), k, s));
+    k_params<<<(L + 255) / 256, 256, 0, s>>>(h->d, h->d_len, h->d_u, h->d_kappa, h->d_beta, h->d_cost, h->d_phi,
+                                             h->d_psi, h->d_w, h->d_head, h->opt.dn, h->opt.eps_tag);
+    const int ne = std::max(h->n_lo, h->n_no);
+    k_choice_info<<<(ne + 255) / 256, 256, 0, s>>>(h->d, h->d_lo_idx, h->n_lo, h->d_no_idx, h->n_no);
+    CU(cudaGetLastError());
+    h->reset_done = false;
+    return SIM_OK;
+}
+
 // per-horizon buffers: outputs and step counters
 static int ensure_T(sim_ctx *h, int T) {
     if (T <= h->cap_T) return SIM_OK;
@@ -921,9 +972,11 @@ static void enqueue_step(sim_ctx *h, int t) {
 static void enqueue_obs_final(sim_ctx *h, int T) { enqueue_a(h, T, 1); }
 
 static int check_device_error(sim_ctx *h) {
-    int e[4];
+    int e[4], perr = 0;
     CU(cudaMemcpyAsync(e, h->d.err, sizeof e, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(&perr, h->d_perr, sizeof perr, cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
+    if (perr) return fail(h, SIM_EINVAL, "invalid parameter (checked on the device by sim_set_params_device)");
     if (e[0] == SIM_EOVERFLOW) {
         char b[128];
         snprintf(b, sizeof b, "queue of link %d overflowed at step %d", e[1], e[2]);

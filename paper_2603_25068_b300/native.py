@@ -66,6 +66,7 @@ SIGNATURES = {
     "sim_create": (C.c_int, [C.POINTER(sim_network), C.POINTER(sim_demand), C.POINTER(sim_params),
                              C.POINTER(sim_options), C.POINTER(P)]),
     "sim_set_params": (C.c_int, [P, C.POINTER(sim_params)]),
+    "sim_set_params_device": (C.c_int, [P, C.POINTER(sim_params), P]),
     "sim_reset": (C.c_int, [P, C.c_int32]),
     "sim_step": (C.c_int, [P, C.c_int32]),
     "sim_rollout": (C.c_int, [P, C.c_int32, C.POINTER(sim_outputs)]),

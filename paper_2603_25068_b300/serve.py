@@ -2,9 +2,11 @@
 
 Requests (nowcast rollouts, calibration-gradient rollouts, control-candidate
 rollouts) arrive over time.  The engine
-  * admits a request as soon as an upper bound of its device memory fits in
-    the HBM budget (replaced by sim_device_bytes of the handle once created,
-    plus its reverse-pass needs),
+  * admits waiting requests shortest remaining work first (vehicle-steps,
+    three times for a gradient request), each as soon as an upper bound of its
+    device memory fits in the HBM budget (replaced by sim_device_bytes of the
+    handle once created, plus its reverse-pass needs) and fewer than
+    max_in_flight requests are admitted and unfinished (None: memory only),
   * builds the simulator of an admitted request on a creation thread with a
     stream of its own, so that host set-up and uploads overlap the running
     batch instead of stalling it,
@@ -98,11 +100,17 @@ def handle_bytes_bound(sc, ckpt_every: int, route_cap: int) -> float:
 
 class Engine:
     def __init__(self, device: int = 0, hbm_budget: float = 150e9, chunk: int = 240, ckpt_every: int = 180,
-                 route_cap: int = 256, creators: int = 2, reversers: int = 2):
+                 route_cap: int = 256, creators: int = 2, reversers: int = 2, max_in_flight: Optional[int] = None,
+                 order: str = "srw"):
         import torch
         self.torch = torch
         self.device = device
         self.budget = hbm_budget
+        if order not in ("srw", "fifo"):
+            raise ValueError("order must be 'srw' (shortest remaining work) or 'fifo'")
+        self.max_in_flight = max_in_flight
+        self.order = order
+        self.in_flight = 0
         self.chunk = chunk
         self.ckpt_every = ckpt_every
         self.route_cap = route_cap
@@ -157,6 +165,7 @@ class Engine:
                 return
             with self.lock:
                 self.used -= nbytes
+                self.in_flight -= 1
             req.finished = self.now()
 
     def _create_worker(self, k: int):
@@ -202,9 +211,12 @@ class Engine:
         reserved = handle_bytes_bound(req.scenario, self.ckpt_every if req.needs_grad else 0,
                                       self.route_cap) + self._estimate_extra(req)
         with self.lock:
+            if self.max_in_flight is not None and self.in_flight >= self.max_in_flight:
+                return False
             if self.used + reserved > self.budget and (self.used > 0 or self.active):
                 return False
             self.used += reserved
+            self.in_flight += 1
         self.create_q.put((req, reserved))
         return True
 
@@ -226,6 +238,8 @@ class Engine:
                 while k < len(pending) and pending[k].arrival <= self.now():
                     waiting.append(pending[k])
                     k += 1
+                if self.order == "srw":
+                    waiting.sort(key=request_work)
                 waiting = [req for req in waiting if not self._admit(req)]
                 new = []
                 while True:                              # simulators built by the creation thread
@@ -258,6 +272,7 @@ class Engine:
                             sim.close()
                             with self.lock:
                                 self.used -= nbytes
+                                self.in_flight -= 1
                             req.finished = self.now()
             for _ in self.bwd_threads:
                 self.bwd_q.put(None)
@@ -266,6 +281,13 @@ class Engine:
             for th in self.bwd_threads + self.create_threads:
                 th.join()
         return requests
+
+
+def request_work(req: Request) -> float:
+    """Work of a request for shortest-remaining-work admission: its
+    vehicle-steps, three times for a gradient request (forward, segment
+    recomputation and reverse step)."""
+    return float(req.vehicle_steps) * (3.0 if req.needs_grad else 1.0)
 
 
 def latency_stats(reqs: List[Request]) -> dict:

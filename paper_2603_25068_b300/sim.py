@@ -79,6 +79,23 @@ class Simulator:
         self._check(self.lib.sim_set_params(self.h, C.byref(par)))
         self._keep = []
 
+    def set_params_device(self, u, kappa, alpha, beta, cost, w, alpha_origin):
+        """Replace the parameters from torch CUDA tensors on the simulator's
+        device (float32; alpha_origin a one-element tensor) without a host
+        round trip: the copies are enqueued on the simulator's stream, which the
+        caller orders after the tensors' producer.  The tensors must stay alive
+        until that stream has passed this call."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        ts = [t.detach() for t in (u, kappa, alpha, beta, cost, w, alpha_origin)]
+        for t, n in zip(ts, (self.sc.L,) * 5 + (self.sc.F, 1)):
+            if t.device != dev or t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != n:
+                raise ValueError("device parameters: contiguous float32 tensors of the simulator's device "
+                                 "with one entry per link (w: per feature, alpha_origin: one)")
+        par = nat.sim_params(*(C.c_void_p(t.data_ptr()) for t in ts[:6]), alpha_origin=0.0)
+        self._check(self.lib.sim_set_params_device(self.h, C.byref(par), C.c_void_p(ts[6].data_ptr())))
+        self._dev_params = ts          # alive until the next call replaces them
+
     # ------------------------------------------------------------------ running
     def n_bins(self, T=None):
         return self.lib.sim_n_bins(self.sc.T if T is None else T, self.sc.obs_every)

@@ -67,3 +67,40 @@ def test_calibration_loop_runs_on_device():
             lam.clamp_(min=1e-3)
         losses.append(float(loss))
     assert all(np.isfinite(losses))
+
+
+def test_device_parameters_equal_host_parameters_and_are_validated():
+    """sim_set_params_device (parameters in device memory, no host round trip)
+    gives the rollout of sim_set_params with the same values; an invalid
+    device parameter is reported by the next synchronous call."""
+    import torch
+    from paper_2603_25068_b300.native import SimError, SIM_EINVAL
+    from paper_2603_25068_b300.sim import Simulator
+    dev = torch.device("cuda", 0)
+    sc = S.random_small(seed=3, side=3, n_vehicles=160, T=90).copy(obs_every=30)
+    rng = np.random.default_rng(4)
+    new = dict(u=(sc.u * rng.uniform(0.8, 1.2, sc.L)).astype(np.float32),
+               kappa=(sc.kappa * rng.uniform(0.9, 1.0, sc.L)).astype(np.float32),
+               alpha=rng.uniform(0.5, 4.0, sc.L).astype(np.float32), beta=rng.uniform(0, 2, sc.L).astype(np.float32),
+               cost=rng.uniform(0.5, 2.0, sc.L).astype(np.float32), w=(sc.w + 0.3).astype(np.float32))
+    host = Simulator(sc)
+    host.set_params(alpha_origin=1.7, **new)
+    ref = host.rollout()
+    devsim = Simulator(sc)
+    t = {k: torch.tensor(v, device=dev) for k, v in new.items()}
+    devsim.set_params_device(t["u"], t["kappa"], t["alpha"], t["beta"], t["cost"], t["w"],
+                             torch.tensor([1.7], device=dev))
+    got = devsim.rollout()
+    for k in ("counts", "speed", "travel_time", "n_arrived"):
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
+    bad = t["u"].clone()
+    bad[3] = -1.0
+    devsim.set_params_device(bad, t["kappa"], t["alpha"], t["beta"], t["cost"], t["w"], torch.tensor([1.7], device=dev))
+    with pytest.raises(SimError) as e:
+        devsim.rollout()
+    assert e.value.code == SIM_EINVAL
+    devsim.set_params_device(t["u"], t["kappa"], t["alpha"], t["beta"], t["cost"], t["w"],
+                             torch.tensor([1.7], device=dev))
+    np.testing.assert_array_equal(devsim.rollout()["counts"], ref["counts"])
+    host.close()
+    devsim.close()

@@ -52,7 +52,7 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes", "1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
            os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0",
-           "--small", "--cpu-budget", "1"]
+           "--small"]
     env = dict(os.environ, OMP_NUM_THREADS="1")
     res = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert res.returncode == 0, res.stderr[-2000:]
@@ -61,3 +61,7 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+    # the same workload description as the GPU arm's line, and the window it times
+    assert line["config"]["step"].startswith("one ") and line["config"]["vehicles"] == 250_000
+    assert "steps 0-299" in line["cpu_baseline"]["sample"]
+    assert 0 < line["cpu_baseline"]["active_value"] < line["value"]
