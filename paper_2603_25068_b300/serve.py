@@ -6,7 +6,11 @@ rollouts) arrive over time.  The engine
     three times for a gradient request), each as soon as an upper bound of its
     device memory fits in the HBM budget (replaced by sim_device_bytes of the
     handle once created, plus its reverse-pass needs) and fewer than
-    max_in_flight requests are admitted and unfinished (None: memory only),
+    max_in_flight + prefetch requests are admitted and unfinished (None:
+    memory only); at most max_in_flight of them run at once, the others'
+    simulators are built ahead so that host set-up overlaps the GPU work,
+  * runs a request that is alone (max_in_flight 1, or nothing else running or
+    ready) as one rollout of its own simulator, without a batch,
   * builds the simulator of an admitted request on a creation thread with a
     stream of its own, so that host set-up and uploads overlap the running
     batch instead of stalling it,
@@ -101,7 +105,7 @@ def handle_bytes_bound(sc, ckpt_every: int, route_cap: int) -> float:
 class Engine:
     def __init__(self, device: int = 0, hbm_budget: float = 150e9, chunk: int = 240, ckpt_every: int = 180,
                  route_cap: int = 256, creators: int = 2, reversers: int = 2, max_in_flight: Optional[int] = None,
-                 order: str = "srw"):
+                 order: str = "srw", prefetch: int = 2):
         import torch
         self.torch = torch
         self.device = device
@@ -109,8 +113,10 @@ class Engine:
         if order not in ("srw", "fifo"):
             raise ValueError("order must be 'srw' (shortest remaining work) or 'fifo'")
         self.max_in_flight = max_in_flight
+        self.prefetch = prefetch
         self.order = order
-        self.in_flight = 0
+        self.in_flight = 0                      # admitted and not finished (creating, ready, running, reversing)
+        self.ready: List[tuple] = []            # built simulators waiting to run: (request, simulator, bytes)
         self.chunk = chunk
         self.ckpt_every = ckpt_every
         self.route_cap = route_cap
@@ -211,7 +217,7 @@ class Engine:
         reserved = handle_bytes_bound(req.scenario, self.ckpt_every if req.needs_grad else 0,
                                       self.route_cap) + self._estimate_extra(req)
         with self.lock:
-            if self.max_in_flight is not None and self.in_flight >= self.max_in_flight:
+            if self.max_in_flight is not None and self.in_flight >= self.max_in_flight + self.prefetch:
                 return False
             if self.used + reserved > self.budget and (self.used > 0 or self.active):
                 return False
@@ -219,6 +225,24 @@ class Engine:
             self.in_flight += 1
         self.create_q.put((req, reserved))
         return True
+
+    def _finish_forward(self, req, sim, nbytes):
+        if req.needs_grad:
+            self.bwd_q.put((req, sim, nbytes))
+            return
+        out = sim.outputs()
+        req.result = dict(counts=out["counts"], speed=out["speed"], travel_time=out["travel_time"])
+        sim.close()
+        with self.lock:
+            self.used -= nbytes
+            self.in_flight -= 1
+        req.finished = self.now()
+
+    def _run_alone(self, req, sim, nbytes):
+        """A request with nothing beside it: one rollout of its own simulator
+        (a single persistent launch), as serial execution runs it."""
+        sim.rollout(req.scenario.T)
+        self._finish_forward(req, sim, nbytes)
 
     # -------------------------------------------------------------- main loop
     def run(self, requests: List[Request], poll: float = 0.0005, max_seconds: float = 3600.0):
@@ -241,15 +265,22 @@ class Engine:
                 if self.order == "srw":
                     waiting.sort(key=request_work)
                 waiting = [req for req in waiting if not self._admit(req)]
-                new = []
                 while True:                              # simulators built by the creation thread
                     try:
-                        req, sim, nbytes = self.ready_q.get_nowait()
+                        self.ready.append(self.ready_q.get_nowait())
                     except queue.Empty:
                         break
+                if self.order == "srw":
+                    self.ready.sort(key=lambda a: request_work(a[0]))
+                new = []
+                while self.ready and (self.max_in_flight is None or len(self.active) < self.max_in_flight):
+                    req, sim, nbytes = self.ready.pop(0)
                     req.admitted = self.now()
                     self.active.append((req, sim, nbytes))
                     new.append(req)
+                if len(new) == 1 and len(self.active) == 1 and (self.max_in_flight == 1 or not self.ready):
+                    self._run_alone(*self.active.pop())
+                    continue
                 if new:
                     self._rebuild(new)
                 if not self.active:
@@ -262,18 +293,8 @@ class Engine:
                     done = [self.active[i] for i in np.nonzero(fin)[0]]
                     self.active = [a for i, a in enumerate(self.active) if not fin[i]]
                     self._rebuild()
-                    for req, sim, nbytes in done:
-                        if req.needs_grad:
-                            self.bwd_q.put((req, sim, nbytes))
-                        else:
-                            out = sim.outputs()
-                            req.result = dict(counts=out["counts"], speed=out["speed"],
-                                              travel_time=out["travel_time"])
-                            sim.close()
-                            with self.lock:
-                                self.used -= nbytes
-                                self.in_flight -= 1
-                            req.finished = self.now()
+                    for item in done:
+                        self._finish_forward(*item)
             for _ in self.bwd_threads:
                 self.bwd_q.put(None)
             for _ in self.create_threads:
