@@ -132,63 +132,79 @@ def run(sc, T=None, ybar=None, xbarT=None, tape=None, params=None):
     trace = []
     for t in range(T):
         # ---------------- f: car-following (SI-A) ----------------
-        rows, cols, vals = [], [], []
-        for j in range(L):
-            on = np.nonzero(vlink == j)[0]
-            if len(on) == 0:
-                continue
-            xv = X[on, j].detach().numpy()
-            order = dec(on[np.lexsort((seq[on], -xv))])      # argsort(-x), ties by entry
-            xs = X[order, j]
-            h = torch.cat([torch.tensor([M], dtype=dt64), xs[:-1] - xs[1:]])
-            d = h - s[j]
+        # every link at once (Alg. S1 maps one link's update over all links):
+        # the agents on links in order of (link, -x, entry), i.e. per link
+        # argsort(-x) with ties by entry (recorded; a replay takes the record)
+        on = np.nonzero(vlink >= 0)[0]
+        if len(on):
+            if tape.replaying():
+                order = dec(None)
+            else:
+                xo = X[on, vlink[on]].detach().numpy()
+                order = dec(on[np.lexsort((seq[on], -xo, vlink[on]))])
+            lk = vlink[order]
+            tl = torch.tensor(lk)
+            first = torch.tensor(np.r_[True, lk[1:] != lk[:-1]])           # the link's leader
+            xs = X[torch.tensor(order), tl]
+            h = torch.where(first, torch.full_like(xs, M), torch.cat([xs[:1], xs[:-1]]) - xs)
+            d = h - s[tl]
             dd = d.detach()
-            tag = dec(torch.where(dd <= dtag[j], STOP, torch.where(dd >= udt[j].detach() - dtag[j], FREE, CONG)))
+            tag = dec(torch.where(dd <= dtag[tl], STOP, torch.where(dd >= udt[tl].detach() - dtag[tl], FREE, CONG)))
             # value min(u dt, max(d, 0)); derivative of the tagged branch
-            path = torch.where(tag == FREE, udt[j] + 0 * d, torch.where(tag == CONG, d, 0 * d))
-            val = sg(torch.minimum(udt[j], torch.clamp(d, min=0.0)))
+            path = torch.where(tag == FREE, udt[tl] + 0 * d, torch.where(tag == CONG, d, 0 * d))
+            val = sg(torch.minimum(udt[tl], torch.clamp(d, min=0.0)))
             dx = val + (path - sg(path))
             xp = xs + dx
-            xlim = length[j] + xp - sg(xp)
+            xlim = length[tl] + xp - sg(xp)
             clipped = dec((xp.detach() > xlim.detach()))
             xn = torch.where(clipped, xlim, xp)
-            rows.append(torch.tensor(order)); cols.append(torch.full((len(order),), j)); vals.append(xn)
-        if rows:
-            X = X.index_put((torch.cat(rows), torch.cat(cols)), torch.cat(vals))
+            X = X.index_put((torch.tensor(order), tl), xn)
         # ---------------- g: node model (SI-B) ----------------
         credit = np.minimum(credit + sc.q_fx.astype(np.int64), cap)
-        Xd = X.detach()
-        vacant = np.ones(L, bool)
-        for j in range(L):
-            on = np.nonzero(vlink == j)[0]
-            if len(on):
-                vacant[j] = float(Xd[on, j].min()) > float(s[j].detach())
-        vacant = dec(vacant)
-        cands = []          # (agent, source column, set, is_link)
-        for j in range(L):
-            on = np.nonzero(vlink == j)[0]
-            arr = [i for i in on if float(Xd[i, j]) >= float(length[j]) - eps_arr]
-            assert len(arr) <= 1
-            if arr and credit[j] >= dn_fx:
-                cands.append((arr[0], j, link_set[j], True))
-        for n in range(V):
-            if fptr[n] < len(fifo[n]) and int(sc.dep_step[fifo[n][fptr[n]]]) <= t:
-                cands.append((fifo[n][fptr[n]], L + n, out_links[n], False))
-        cands = dec(cands)
+        def vacancy():                      # rearmost position beyond the jam spacing, or empty
+            Xd = X.detach().numpy()
+            vac = np.ones(L, bool)
+            for j in range(L):
+                on = np.nonzero(vlink == j)[0]
+                if len(on):
+                    vac[j] = float(Xd[on, j].min()) > float(s[j].detach())
+            return vac
+
+        def candidates():                   # arrived leaders with credit, heads of origin queues
+            Xd = X.detach().numpy()
+            out = []                        # (agent, source column, set, is_link)
+            for j in range(L):
+                on = np.nonzero(vlink == j)[0]
+                arr = [i for i in on if Xd[i, j] >= float(length[j]) - eps_arr]
+                assert len(arr) <= 1
+                if arr and credit[j] >= dn_fx:
+                    out.append((arr[0], j, link_set[j], True))
+            for n in range(V):
+                if fptr[n] < len(fifo[n]) and int(sc.dep_step[fifo[n][fptr[n]]]) <= t:
+                    out.append((fifo[n][fptr[n]], L + n, out_links[n], False))
+            return out
+        rec = tape.replaying()
+        vacant = dec(None if rec else vacancy())
+        cands = dec(None if rec else candidates())
         sinks = [(i, c) for (i, c, _, is_link) in cands
                  if int(sc.node_zone[int(sc.head[c]) if is_link else c - L]) == int(sc.dest_zone[i])]
         sink_ids = {i for i, _ in sinks}
         Vm = torch.full((N, L), -M, dtype=dt64)
         gm = torch.zeros((N, L), dtype=dt64)
         arrived = torch.zeros(N, dtype=dt64)
+        ri, rm, rz, rg = [], [], [], []     # (agent, link of its choice set, its zone, Gumbel)
         for (i, c, cs, is_link) in cands:
             if i in sink_ids:
                 continue
-            z = int(sc.dest_zone[i])
             for k, m in enumerate(cs):
-                Vm[i, m] = U[m] + G[m] * dest_feat[z, int(sc.head[m])]
-                gm[i, m] = gumbel(sc.seed, sc.scenario_id, int(i), t, 0, k)
+                ri.append(int(i)); rm.append(int(m)); rz.append(int(sc.dest_zone[i]))
+                rg.append(gumbel(sc.seed, sc.scenario_id, int(i), t, 0, k))
             arrived[i] = 1.0
+        if ri:
+            ti, tm = torch.tensor(ri), torch.tensor(rm)
+            hm = torch.tensor(sc.head[rm].astype(np.int64))
+            Vm = Vm.index_put((ti, tm), U[tm] + G[tm] * dest_feat[torch.tensor(rz), hm])
+            gm[ti, tm] = torch.tensor(rg, dtype=dt64)
         logz = torch.log_softmax(Vm, dim=1)
         pi = torch.softmax((logz + gm) / tau, dim=1)
         onehot = torch.zeros_like(pi)
@@ -196,11 +212,8 @@ def run(sc, T=None, ybar=None, xbarT=None, tape=None, params=None):
         lp = onehot + pi - sg(pi)
         vac_t = torch.tensor(vacant.astype(np.float64))
         l = arrived[:, None] * (vac_t[None, :] * lp)
-        src_alpha = []
-        for i in range(N):
-            j = int(vlink[i])
-            src_alpha.append(alpha[j] if j >= 0 else alpha_o)
-        alpha_src = torch.stack(src_alpha)
+        # merge priority of each agent's source: its link's alpha, alpha_origin in an origin queue
+        alpha_src = torch.cat([alpha, alpha_o.reshape(1)])[torch.tensor(np.where(vlink >= 0, vlink, L))]
         p = (alpha_src[:, None] * l).T                               # L x N
         Vp = p - M * dec((p.detach() == 0).to(dt64))
         gp = torch.tensor([gumbel(sc.seed, sc.scenario_id, i, t, 1, 0) for i in range(N)], dtype=dt64)
@@ -225,12 +238,10 @@ def run(sc, T=None, ybar=None, xbarT=None, tape=None, params=None):
         for i, c in sinks:
             X = X.index_put((torch.tensor([i]), torch.tensor([c])), X[i, c] - (M + X[i, c]))
         # discrete bookkeeping of the transfers
-        winners = {}
-        amax = a.detach()
-        for m in range(L):
-            if float(amax[m].max()) > 0.5:
-                winners[int(torch.argmax(amax[m]))] = m
-        winners = dec(winners)
+        def winner_map():
+            amax = a.detach()
+            return {int(torch.argmax(amax[m])): m for m in range(L) if float(amax[m].max()) > 0.5}
+        winners = dec(None if tape.replaying() else winner_map())
         for (i, c, cs, is_link) in cands:
             leaves = i in winners or i in sink_ids
             if not leaves:

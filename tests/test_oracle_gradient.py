@@ -116,3 +116,52 @@ def test_finite_differences_of_frozen_surrogate():
             assert abs(fd - go[k][idx]) <= 2e-6 * max(abs(go[k][idx]), 1e-3), (k, idx, fd, go[k][idx])
             checked += 1
     assert checked >= 12
+
+
+def test_finite_differences_on_the_calibration_parameterisation():
+    """The calibration workload's parameterisation (the 16-feature route-choice
+    utility w, a demand parameter lambda per origin-destination pair, counts on
+    sensor links) on a city-family network: Richardson-extrapolated central
+    differences of the frozen surrogate (dense formulation, decisions and
+    stop-gradient values replayed) against the compact oracle's reverse mode
+    for 16 lambda (every one the loss reaches, up to 16) and all 16 w."""
+    import torch
+    sc = S.city(seed=31, n_nodes=40, n_links=120, n_vehicles=240, T=120, n_origin_zones=4, n_dest_zones=6,
+                dep_window=60.0, name="calibration_tiny").copy(obs_every=40)
+    assert sc.F == 16 and sc.n_od == 24
+    rng = np.random.default_rng(100)
+    nb = (sc.T + sc.obs_every - 1) // sc.obs_every
+    sens = np.sort(rng.choice(sc.L, size=40, replace=False))
+    ybar = np.zeros((nb, sc.L))
+    ybar[:, sens] = rng.normal(size=(nb, len(sens)))
+    tape = dense_ref.Tape()
+    out, gd, _ = dense_ref.run(sc, ybar=ybar, tape=tape)
+    o = OracleSim(sc, "fp64", keep_history=True)
+    np.testing.assert_array_equal(o.rollout()["counts"], out["counts"])
+    go = o.backward(ybar)
+    base = dict(w=np.asarray(sc.w, np.float64).copy(), od_lambda=np.asarray(sc.od_lambda, np.float64).copy())
+
+    def F(params):
+        tape.rewind()
+        with torch.no_grad():
+            return dense_ref.run(sc, ybar=ybar, tape=tape, params=params)[0]["loss"]
+
+    def central(k, idx, h):
+        p1 = {kk: v.copy() for kk, v in base.items()}
+        p2 = {kk: v.copy() for kk, v in base.items()}
+        p1[k][idx] += h
+        p2[k][idx] -= h
+        return (F(p1) - F(p2)) / (2 * h)
+
+    lam = rng.permutation(np.nonzero(np.abs(go["od_lambda"]) > 1e-9)[0])[:16]
+    assert len(lam) >= 12
+    checked = {"w": 0, "od_lambda": 0}
+    for k, idxs in (("w", range(16)), ("od_lambda", lam)):
+        for idx in idxs:
+            h = 2e-6 * max(1.0, abs(base[k][idx]))
+            # lambda enters through straight-through weights, linearly: one
+            # central difference is exact; w through softmaxes: Richardson
+            fd = central(k, idx, h) if k == "od_lambda" else (4.0 * central(k, idx, h / 2) - central(k, idx, h)) / 3.0
+            assert abs(fd - go[k][idx]) <= 2e-6 * max(abs(go[k][idx]), 1e-3), (k, idx, fd, go[k][idx])
+            checked[k] += 1
+    assert checked == {"w": 16, "od_lambda": len(lam)}
