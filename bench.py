@@ -785,8 +785,8 @@ def run_ours(args):
         "x_real_time": T * sc.dt / (ms_per / 1000.0),
         "state_at_T": {"n_on": int(res["n_on"][T]), "n_arrived": int(res["n_arrived"][T]),
                        "n_waiting": int(res["n_waiting"][T]),
-                       "note": "vehicles on links, arrived and not yet departed at the end of the hour: "
-                               "the rollout is jam-dominated, most vehicle-steps are standing queues"},
+                       "note": "vehicles on links, arrived and not yet departed at the end of the rollout "
+                               "(on the hour-long one: jam-dominated, most vehicle-steps are standing queues)"},
         "active_vehicle_steps_per_s": float(np.sum(n_on)) * ws / (ms_per / 1000.0),
         "per_rollout_ms": ms,
         "roofline": {"bound": "hbm", "kernel": kdesc,
