@@ -31,6 +31,23 @@
  *  - merge noise is keyed by (vehicle, step) (one target per vehicle per step);
  *  - max(l)^T in the merge mask is a constant mask (no gradient);
  *  - min/max ties of the car-following update are resolved by a dead-band tag.
+ *
+ * What pins it (tests that run without a GPU, against facts fixed outside this
+ * file): Philox known-answer vectors; or_log32 within 2 ulp of a double log;
+ * Gumbel moments and distribution; lone-vehicle link times and the Newell
+ * capacity of a saturated entry; outflow-credit limits, conservation, FIFO and
+ * the other invariants of the node model; softmax turn frequencies; exact
+ * enumeration of a small fork and merge; closed-form bin speeds; the relaxed
+ * weights tending to the forward's one-hot as the temperature falls; the
+ * closed-form gradient and the descent outcome of the trajectory-grafting toy
+ * (SI-C); a dense N x L formulation of Alg. S1/S2 differentiated by autograd;
+ * finite differences of the frozen surrogate.
+ *
+ * Parity unpinned by the paper: the demand gradient (the paper does not
+ * differentiate demand; here a straight-through demand weight), the 16-feature
+ * utility of the calibration parameterisation, and the link speeds and travel
+ * times of the counting step, whose definitions are readings.  Their code is
+ * pinned by finite differences and closed forms; their definitions are not.
  */
 #include <stdint.h>
 #include <stdlib.h>
