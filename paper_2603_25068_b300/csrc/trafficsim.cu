@@ -140,7 +140,7 @@ struct sim_ctx {
     // the reverse kernels themselves on a high-priority stream
     cudaStream_t rstream = nullptr, vstream = nullptr;
     int recompute = SIM_RECOMPUTE_OVERLAP;
-    cudaEvent_t ev_r[2] = {nullptr, nullptr}, ev_b[2] = {nullptr, nullptr}, ev_gr[2] = {nullptr, nullptr};
+    cudaEvent_t ev_r[2] = {nullptr, nullptr}, ev_b[2] = {nullptr, nullptr};
     DevSim d{};
     // sizes
     int V = 0, L = 0, N = 0, F = 0, Z = 0, n_od = 0, S = 0;
@@ -836,7 +836,7 @@ static void release(sim_ctx *h) {
     h->stream = nullptr;
     if (h->jstream) cudaStreamSynchronize(h->jstream);
     if (h->rstream) cudaStreamSynchronize(h->rstream);
-    for (cudaEvent_t e : {h->ev_z, h->ev_g, h->ev_r[0], h->ev_r[1], h->ev_b[0], h->ev_b[1], h->ev_gr[0], h->ev_gr[1]})
+    for (cudaEvent_t e : {h->ev_z, h->ev_g, h->ev_r[0], h->ev_r[1], h->ev_b[0], h->ev_b[1]})
         if (e) cudaEventDestroy(e);
     if (h->vstream) cudaStreamSynchronize(h->vstream);
     if (h->jstream) cudaStreamDestroy(h->jstream);
@@ -844,7 +844,7 @@ static void release(sim_ctx *h) {
     if (h->vstream) cudaStreamDestroy(h->vstream);
     h->jstream = h->rstream = h->vstream = nullptr;
     h->ev_z = h->ev_g = nullptr;
-    h->ev_r[0] = h->ev_r[1] = h->ev_b[0] = h->ev_b[1] = h->ev_gr[0] = h->ev_gr[1] = nullptr;
+    h->ev_r[0] = h->ev_r[1] = h->ev_b[0] = h->ev_b[1] = nullptr;
 }
 
 extern "C" int sim_create(const sim_network *net, const sim_demand *dem, const sim_params *par,
@@ -926,24 +926,17 @@ static int ensure_T(sim_ctx *h, int T) {
     return SIM_OK;
 }
 
-// checkpoint s <-> dynamic state at the start of step s K (positions in buffer cur)
-static void ckpt_copy(sim_ctx *h, int s, int cur, bool save, cudaStream_t st = nullptr) {
-    const size_t L = h->L, S = h->S, V = h->V, N = h->N;
+// checkpoint s <-> dynamic state at the start of step s K (positions in buffer
+// (s K) & 1), one launch
+static void ckpt_copy(sim_ctx *h, int s, bool save, cudaStream_t st = nullptr) {
     if (!st) st = h->stream;
-    auto cp = [&](void *state, void *ck, size_t bytes) {
-        if (save) cudaMemcpyAsync(ck, state, bytes, cudaMemcpyDeviceToDevice, st);
-        else cudaMemcpyAsync(state, ck, bytes, cudaMemcpyDeviceToDevice, st);
-    };
-    DevSim &d = h->d;
-    cp(d.lq, h->ck.lq + s * L, L * sizeof(int4));
-    cp(d.lstat, h->ck.lstat + s * L, L * sizeof(int4));
-    cp(d.vac, h->ck.vac + s * L, L * sizeof(int));
-    cp(d.sentry, h->ck.sentry + s * S, S * sizeof(int));
-    cp(d.fifo_ptr, h->ck.fifo + s * V, V * sizeof(int));
-    cp(d.vstate, h->ck.vstate + s * N, N * sizeof(int));
-    cp(cur ? d.pos1 : d.pos0, h->ck.pos + s * S, S * sizeof(float));
-    cp(d.saux, h->ck.saux + s * S, S * sizeof(int2));
-    cp(d.lpos, h->ck.lpos + s * L, L * sizeof(longlong2));
+    CkDev c{};
+    c.K = h->K; c.L = h->L; c.S = h->S; c.V = h->V; c.N = h->N;
+    c.lq = h->ck.lq; c.lstat = h->ck.lstat; c.vac = h->ck.vac; c.sentry = h->ck.sentry; c.fifo = h->ck.fifo;
+    c.vstate = h->ck.vstate; c.pos = h->ck.pos; c.saux = h->ck.saux; c.lpos = h->ck.lpos;
+    const size_t n = std::max(std::max((size_t)h->S, (size_t)h->N), std::max((size_t)h->L, (size_t)h->V));
+    const int grid = (int)std::min<size_t>((n + 255) / 256, 148 * 16);
+    k_ckpt<<<grid, 256, 0, st>>>(h->d, c, s * h->K, save ? 1 : 0);
 }
 
 static void enqueue_reset(sim_ctx *h, int T) {
@@ -1065,7 +1058,7 @@ extern "C" int sim_rollout(sim_handle h, int32_t T, sim_outputs *out) {
         if (h->K > 0) {              // one launch per checkpoint segment, the state saved before each
             for (int t0 = 0; t0 < T; t0 += h->K) {
                 const int t1 = std::min(T, t0 + h->K);
-                ckpt_copy(h, t0 / h->K, t0 & 1, true);
+                ckpt_copy(h, t0 / h->K, true);
                 TRY(enqueue_persist(h, t0, t1, t1 == T));
             }
         } else {
@@ -1087,7 +1080,7 @@ extern "C" int sim_rollout(sim_handle h, int32_t T, sim_outputs *out) {
         CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         enqueue_reset(h, T);
         for (int t = 0; t < T; ++t) {
-            if (h->K > 0 && t % h->K == 0) ckpt_copy(h, t / h->K, t & 1, true);
+            if (h->K > 0 && t % h->K == 0) ckpt_copy(h, t / h->K, true);
             enqueue_step(h, t);
         }
         enqueue_obs_final(h, T);
@@ -1221,11 +1214,13 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     // carve the workspace: one layout routine sizes it (from base 0) and then
     // hands out the sub-arrays (from the buffer)
     const int n_gw = (L + kGwLinks - 1) / kGwLinks;
-    // recomputation beside the reverse pass (two tape sets), or before it in
-    // one persistent recording launch per segment (one tape set)
+    // recomputation beside the reverse pass, or before it in one persistent
+    // recording launch per segment.  Two tape sets, by segment parity: the
+    // Jacobian kernel of a segment reads its set while the next segment is
+    // recorded into the other.
     const bool overlap = h->recompute != SIM_RECOMPUTE_SERIAL || !use_persist(h);
     BwdDev b = h->b;
-    BwdDev bt[2] = {h->b, h->b};         // the tape sets (by segment parity when overlapping)
+    BwdDev bt[2] = {h->b, h->b};
     float2 *d_Cbar = nullptr, *d_Csuf = nullptr;
     double *d_gw_part = nullptr;
     float *d_dxT_w = nullptr, *d_gout = nullptr;
@@ -1236,15 +1231,20 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
             wp += (std::max<size_t>(n, 1) * sz + 255) & ~(size_t)255;
             return p;
         };
-        for (int ts = 0; ts < (overlap ? 2 : 1); ++ts) {
+        for (int ts = 0; ts < 2; ++ts) {
             BwdDev &q = bt[ts];
             q.tpos = (float *)take((size_t)(K + 1) * S, sizeof(float));
-            q.tvid = (int *)take((size_t)(K + 1) * S, sizeof(int));
+            q.tvid = (int *)take(S, sizeof(int));
+            q.tent = (int *)take((size_t)K * L, sizeof(int));
             q.tlq = (int4 *)take((size_t)(K + 1) * L, sizeof(int4));
             q.ttag = (int8_t *)take((size_t)K * S, 1);
             q.tcrec = (int4 *)take((size_t)K * L, sizeof(int4));
             q.tnrec = (int2 *)take((size_t)K * V, sizeof(int2));
             q.tW = (unsigned long long *)take((size_t)K * L, sizeof(unsigned long long));
+            q.Z = (double *)take((size_t)K * L, sizeof(double));
+            q.SA = (double *)take((size_t)K * L, sizeof(double));
+            q.ebuf = (float *)take((size_t)K * (L + V), sizeof(float));
+            q.abuf = (float2 *)take((size_t)K * (L + V), sizeof(float2));
         }
         b.xbar = (float2 *)take(N, sizeof(float2));
         b.cursor = (int *)take(N, sizeof(int));
@@ -1252,12 +1252,9 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         b.eadj = (float2 *)take((size_t)N * h->route_cap, sizeof(float2));
         b.gu = (double *)take(L, sizeof(double)); b.gs = (double *)take(L, sizeof(double));
         b.ga = (double *)take(L, sizeof(double)); b.gU = (double *)take(L, sizeof(double));
-        b.gG = (double *)take(L, sizeof(double)); b.Z = (double *)take(3 * (size_t)L, sizeof(double));
-        b.SA = (double *)take(3 * (size_t)L, sizeof(double));
+        b.gG = (double *)take(L, sizeof(double));
         b.gao = (double *)take(1, sizeof(double));
         b.glam = (double *)take(std::max(h->n_od, 1), sizeof(double));
-        b.ebuf = (float *)take(2 * ((size_t)L + V), sizeof(float));
-        b.abuf = (float2 *)take(2 * ((size_t)L + V), sizeof(float2));
         d_Cbar = (float2 *)take((size_t)nb * L, sizeof(float2));
         d_Csuf = (float2 *)take((size_t)(nb + 1) * L, sizeof(float2));
         d_dxT_w = (float *)take(N, sizeof(float));
@@ -1274,7 +1271,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         CU(cudaStreamCreateWithPriority(&h->rstream, cudaStreamNonBlocking, lo));
         CU(cudaEventCreateWithFlags(&h->ev_z, cudaEventDisableTiming));
         CU(cudaEventCreateWithFlags(&h->ev_g, cudaEventDisableTiming));
-        for (cudaEvent_t *e : {&h->ev_r[0], &h->ev_r[1], &h->ev_b[0], &h->ev_b[1], &h->ev_gr[0], &h->ev_gr[1]})
+        for (cudaEvent_t *e : {&h->ev_r[0], &h->ev_r[1], &h->ev_b[0], &h->ev_b[1]})
             CU(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     }
     BwdLease lease{&g_bwd_pool[h->device], bwd_take(h->device, need), {h->stream, h->vstream, h->jstream, h->rstream}};
@@ -1307,8 +1304,6 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     CU(cudaMemsetAsync(b.gao, 0, sizeof(double), h->stream));
     CU(cudaMemsetAsync(b.glam, 0, (size_t)std::max(b.n_od, 1) * sizeof(double), h->stream));
     CU(cudaMemsetAsync(b.eadj, 0, (size_t)N * h->route_cap * sizeof(float2), h->stream));
-    CU(cudaMemsetAsync(b.Z, 0, 3 * (size_t)L * sizeof(double), h->stream));
-    CU(cudaMemsetAsync(b.SA, 0, 3 * (size_t)L * sizeof(double), h->stream));
     k_bwd_init<<<(N + 255) / 256, 256, 0, h->stream>>>(h->d, b, dxT);
     k_route_scan<<<(int)(((size_t)N * 32 + 255) / 256), 256, 0, h->stream>>>(h->d, N, b);
     // recomputation: no route log, counters into a scratch array
@@ -1317,18 +1312,19 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     dr.step_delta = h->d_dummy;
     const size_t smem_a = (size_t)h->stage_max * sizeof(float);
 
-    const int gS = (std::max(S, L) + 255) / 256, gLV = (L + V + 255) / 256;
-    // Segments from the last.  The tape has two sets, by segment parity.  The
-    // recomputation of segment s - 1 (on the third stream, two-kernel executor,
-    // whose blocks share SMs with the reverse kernels) runs beside the reverse
-    // pass of segment s, which reads only its tape set and static data.  A set
-    // is rewritten only after the reverse pass that read it (ev_b); a reverse
-    // pass starts only once its set is recorded (ev_r).
+    const int gS = (std::max(S, L) + 255) / 256;
+    // Segments from the last.  The tape has two sets, by segment parity.  In
+    // overlapped mode the recomputation of segment s - 1 (on the third stream,
+    // two-kernel executor, whose blocks share SMs with the reverse kernels)
+    // runs beside the reverse pass of segment s, which reads only its tape set
+    // and static data.  A set is rewritten only after the Jacobian kernel that
+    // read it last (ev_b); a reverse pass starts only once its set is recorded
+    // (ev_r).
     auto with_set = [&](int ts) {
-        if (!overlap) ts = 0;
         BwdDev q = b;
-        q.tpos = bt[ts].tpos; q.tvid = bt[ts].tvid; q.tlq = bt[ts].tlq; q.ttag = bt[ts].ttag;
+        q.tpos = bt[ts].tpos; q.tvid = bt[ts].tvid; q.tent = bt[ts].tent; q.tlq = bt[ts].tlq; q.ttag = bt[ts].ttag;
         q.tcrec = bt[ts].tcrec; q.tnrec = bt[ts].tnrec; q.tW = bt[ts].tW;
+        q.Z = bt[ts].Z; q.SA = bt[ts].SA; q.ebuf = bt[ts].ebuf; q.abuf = bt[ts].abuf;
         return q;
     };
     auto recompute = [&](int sg) -> int {
@@ -1336,14 +1332,17 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         const cudaStream_t rs = h->rstream;
         const BwdDev q = with_set(ts);
         CU(cudaStreamWaitEvent(rs, h->ev_b[ts], 0));
-        ckpt_copy(h, sg, t0 & 1, false, rs);
+        ckpt_copy(h, sg, false, rs);
         CU(cudaMemsetAsync((t0 & 1) ? h->d.W1 : h->d.W0, 0, (size_t)L * sizeof(unsigned long long), rs));
         DevSim dq = dr;
+        dq.tape_ent = q.tent;
+        dq.tape_lq0 = q.tlq;
+        dq.tape_K = K;
         for (int t = t0; t < t1; ++t) {            // each step writes its own tape record
             const size_t r = (size_t)(t - t0);
             dq.tag_tape = q.ttag + r * S;
             dq.tape_pos = q.tpos + r * S;
-            dq.tape_vid = q.tvid + r * S;
+            dq.tape_vid = r == 0 ? q.tvid : nullptr;
             dq.tape_lq = q.tlq + r * L;
             dq.tape_crec = q.tcrec + r * L;
             dq.tape_nrec = q.tnrec + r * V;
@@ -1359,21 +1358,21 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     // the initial adjoints are read before any recomputation changes the state
     CU(cudaEventRecord(h->ev_b[0], h->stream));
     CU(cudaEventRecord(h->ev_b[1], h->stream));
-    CU(cudaEventRecord(h->ev_g, h->stream));              // nothing to wait for at the first steps
-    CU(cudaEventRecord(h->ev_gr[0], h->stream));
-    CU(cudaEventRecord(h->ev_gr[1], h->stream));
+    CU(cudaEventRecord(h->ev_g, h->stream));
     const cudaStream_t vs = h->vstream;                   // the reverse chain, high priority
     const int nlb = (L + kCfLinks - 1) / kCfLinks, npb = (V + nlb - 1) / nlb;
     CU(cudaStreamWaitEvent(vs, h->ev_g, 0));
     // one recording launch of the persistent executor for segment sg, on the
     // reverse chain's stream (serial mode)
     auto recompute_serial = [&](int sg) -> int {
-        const int t0 = sg * K, t1 = std::min(T, t0 + K);
-        const BwdDev q = with_set(0);
-        ckpt_copy(h, sg, t0 & 1, false, vs);
+        const int t0 = sg * K, t1 = std::min(T, t0 + K), ts = sg & 1;
+        const BwdDev q = with_set(ts);
+        CU(cudaStreamWaitEvent(vs, h->ev_b[ts], 0));
+        ckpt_copy(h, sg, false, vs);
         CU(cudaMemsetAsync((t0 & 1) ? h->d.W1 : h->d.W0, 0, (size_t)L * sizeof(unsigned long long), vs));
         DevSim dq = dr;
         dq.tag_tape = q.ttag; dq.tape_pos = q.tpos; dq.tape_vid = q.tvid; dq.tape_lq = q.tlq;
+        dq.tape_ent = q.tent; dq.tape_lq0 = q.tlq; dq.tape_K = K;
         dq.tape_crec = q.tcrec; dq.tape_nrec = q.tnrec; dq.tape_W = q.tW;
         TRY(enqueue_persist_d(h, dq, t0, t1, 0, true, vs));
         dq.tape_W = nullptr;
@@ -1382,7 +1381,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     };
     if (overlap) TRY(recompute(nseg - 1));
     for (int sg = nseg - 1; sg >= 0; --sg) {
-        const int t0 = sg * K, t1 = std::min(T, t0 + K), ts = overlap ? (sg & 1) : 0;
+        const int t0 = sg * K, t1 = std::min(T, t0 + K), ts = sg & 1;
         if (overlap) {
             if (sg > 0) TRY(recompute(sg - 1));
             CU(cudaStreamWaitEvent(vs, h->ev_r[ts], 0));
@@ -1391,28 +1390,39 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         }
         const BwdDev q = with_set(ts);
         // Per step on the chain's stream: the merge adjoint and car-following in
-        // one launch; then the Jacobian kernel of the step on the second stream,
-        // beside the next steps.  The merge sums of step t live in buffer t mod
-        // 3 and step t clears buffer t + 2, which the Jacobian kernel of step
-        // t + 2 read: step t waits for it (ev_gr by step parity).
+        // one launch.  The merge sums start from zero (the set's previous
+        // Jacobian kernel is done: ev_b, waited for before the recording).
+        CU(cudaMemsetAsync(q.Z, 0, (size_t)(t1 - t0) * L * sizeof(double), vs));
+        CU(cudaMemsetAsync(q.SA, 0, (size_t)(t1 - t0) * L * sizeof(double), vs));
+        // A step that follows the previous one directly is launched as its
+        // programmatic dependent: it issues its tape loads while that one ends.
         for (int t = t1 - 1; t >= t0; --t) {
             const int rec = t - t0;
-            if ((t + 1) % obs == 0 || t + 1 == T)
-                k_bwd_obs<<<(L * 32 + 255) / 256, 256, 0, vs>>>(dr, q, rec + 1, t / obs);
-            CU(cudaStreamWaitEvent(vs, h->ev_gr[t & 1], 0));
-            k_bwd_step<<<nlb, kBwdThreads, 0, vs>>>(dr, q, rec, t, t / obs, npb);
-            CU(cudaEventRecord(h->ev_z, vs));
-            CU(cudaStreamWaitEvent(h->jstream, h->ev_z, 0));
-            k_bwd_node_g<<<gLV, 256, 0, h->jstream>>>(dr, q, t, rec);
-            CU(cudaEventRecord(h->ev_gr[t & 1], h->jstream));
+            const bool at_obs = (t + 1) % obs == 0 || t + 1 == T;
+            if (at_obs) k_bwd_obs<<<(L * 32 + 255) / 256, 256, 0, vs>>>(dr, q, rec + 1, t / obs);
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(nlb);
+            cfg.blockDim = dim3(kBwdThreads);
+            cfg.stream = vs;
+            cudaLaunchAttribute pdl[1];
+            pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            pdl[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = pdl;
+            cfg.numAttrs = (t + 1 < t1 && !at_obs) ? 1 : 0;
+            CU(cudaLaunchKernelEx(&cfg, k_bwd_step, dr, q, rec, t, t / obs, npb));
         }
-        CU(cudaEventRecord(h->ev_g, h->jstream));          // the segment's Jacobian kernels read its tape
-        CU(cudaStreamWaitEvent(vs, h->ev_g, 0));
-        CU(cudaEventRecord(h->ev_b[ts], vs));              // this tape set may be rewritten
+        // the segment's Jacobians on the second stream, beside the next segment
+        CU(cudaEventRecord(h->ev_z, vs));
+        CU(cudaStreamWaitEvent(h->jstream, h->ev_z, 0));
+        const long long ng = (long long)(t1 - t0) * (L + V);
+        k_bwd_node_g<<<(unsigned)((ng + 255) / 256), 256, 0, h->jstream>>>(dr, q, t0, t1 - t0);
+        CU(cudaEventRecord(h->ev_b[ts], h->jstream));      // this tape set may be rewritten
         CU(cudaGetLastError());
     }
-    CU(cudaEventRecord(h->ev_g, vs));
-    CU(cudaStreamWaitEvent(h->stream, h->ev_g, 0));       // the handle's stream resumes after the chain
+    CU(cudaEventRecord(h->ev_z, vs));
+    CU(cudaStreamWaitEvent(h->stream, h->ev_z, 0));       // the handle's stream resumes after the chain
+    CU(cudaEventRecord(h->ev_g, h->jstream));
+    CU(cudaStreamWaitEvent(h->stream, h->ev_g, 0));       // and after the last Jacobian kernel
     // parameter gradients
     float *go = d_gout;
     float *gu = go, *gk = go + L, *ga = go + 2 * L, *gbeta = go + 3 * L, *gc = go + 4 * L, *gw = go + 5 * L;
@@ -1841,7 +1851,7 @@ static int batch_advance_solo(sim_batch_ctx *b, int k, int n_steps) {
         while (t < t_end) {                      // segments between checkpoints
             int t1 = t_end;
             if (h->K > 0) {
-                if (t % h->K == 0) ckpt_copy(h, t / h->K, t & 1, true);
+                if (t % h->K == 0) ckpt_copy(h, t / h->K, true);
                 t1 = std::min(t_end, (t / h->K + 1) * h->K);
             }
             const bool fin = t1 == T && left > t1 - h->t;

@@ -16,10 +16,13 @@
 //                 s = 5/L_j; demand weight 1 + (lambda - sg lambda)/lambda;
 //   k_bwd_node_z  per merge candidate: abar = M (Ebar - Xbar_old) - x Xbar_old
 //                 (SI-B Eq. transfer) and its merge-softmax weight; per-target
-//                 sums; the winners' entry adjoints; demand weight of exits;
+//                 sums, kept per step of the segment; the winners' entry
+//                 adjoints; demand weight of exits;
 //   k_bwd_node_g  merge softmax Jacobian -> alpha, lbar; link-choice softmax
 //                 Jacobian (Eqs. gumbel, straigththrough) -> U = beta/c + w.phi,
-//                 G = w.psi;
+//                 G = w.psi.  Nothing later in the reverse chain reads what it
+//                 writes (parameter accumulators only), so it runs once per
+//                 segment over all of the segment's steps, beside the chain;
 //   k_bwd_cf      car-following (SI-A) by branch tag: free x' = x + u dt,
 //                 congested x' = x_leader - dn/kappa, stopped x' = x; the TG clip
 //                 passes the adjoint; the winner's old entry receives its new
@@ -77,7 +80,8 @@ struct BwdDev {
     float tau, inv_tau;
     // tape of the current segment: K steps, K + 1 state records
     float *tpos;                 // [(K+1) S] positions at the start of each step
-    int *tvid;                   // [(K+1) S] vehicle of each slot
+    int *tvid;                   // [S] vehicle of each occupied slot at the segment start
+    int *tent;                   // [L K] entrant log: entrant m of link j in the segment at j K + m
     int4 *tlq;                   // [(K+1) L] queue state at the start of each step
     int8_t *ttag;                // [K S]     car-following tags
     int4 *tcrec;                 // [K L]     link candidates
@@ -97,11 +101,10 @@ struct BwdDev {
     double *gu, *gs, *ga, *gU, *gG;   // [L]
     double *gao;                 // [1]
     double *glam;                // [n_od]
-    double *Z, *SA;              // [3 L] per-target merge sums of step t in buffer t mod 3
-                                 // (step t clears buffer t + 2, read two steps earlier)
-    float *ebuf;                 // [2 (L + V)] per-source merge weight, by step parity
-    float2 *abuf;                // [2 (L + V)] per-source abar (the Jacobian kernel of
-                                 // step t runs beside the merge kernel of step t - 1)
+    // per tape set, by tape record (step t0 + rec of the segment):
+    double *Z, *SA;              // [K L] per-target merge sums (zero before the segment)
+    float *ebuf;                 // [K (L + V)] per-source merge weight
+    float2 *abuf;                // [K (L + V)] per-source abar
     const int *od;               // [N]
     const float *od_lambda;      // [n_od]
 };
@@ -175,15 +178,25 @@ __global__ void k_route_scan(DevSim d, int N, BwdDev b) {
     }
 }
 
-// copy the state at the start of step (t0 + rec) into the tape
+// copy the state at the start of step (t0 + rec) into the tape (positions and
+// queue states; the vehicles follow from the entrant log)
 __global__ void k_tape_pre(DevSim d, BwdDev b, int rec, int cur) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const float *pc = cur ? d.pos1 : d.pos0;
-    if (i < b.S) {
-        b.tpos[(size_t)rec * b.S + i] = pc[i];
-        b.tvid[(size_t)rec * b.S + i] = d.saux[i].x;
-    }
+    if (i < b.S) b.tpos[(size_t)rec * b.S + i] = pc[i];
     if (i < d.L) b.tlq[(size_t)rec * d.L + i] = d.lq[i];
+}
+
+// Vehicle with entry index e of link j (e = exits so far + queue position; a
+// link takes its entrants in FIFO order): one that was queued at the segment
+// start (queue state q0: ring slot from the start record of the tape), else
+// entrant e - (q0.w + q0.y) of the segment's entrant log.
+__device__ __forceinline__ int vid_at(const BwdDev &b, int j, int4 q0, int base, int cap, int e) {
+    const int m = e - (q0.w + q0.y);
+    if (m >= 0) return b.tent[(size_t)j * b.K + m];
+    int idx = q0.x + (e - q0.w);
+    if (idx >= cap) idx -= cap;
+    return b.tvid[base + idx];
 }
 
 // adjoint of the final positions (vehicles on a link at the end of the rollout)
@@ -202,14 +215,14 @@ __global__ void k_bwd_obs(DevSim d, BwdDev b, int rec, int bin) {
     if (j >= d.L) return;
     const float2 cb = b.Cbar[(size_t)bin * d.L + j];
     if (cb.x == 0.0f) return;
-    const int4 q = b.tlq[(size_t)rec * d.L + j];
+    const int4 q = b.tlq[(size_t)rec * d.L + j], q0 = b.tlq[j];
     const int4 st = d.lst[j];
     const float len = d.geo[j].x, s5 = __fdiv_rn(5.0f, len), half = __fmul_rn(0.5f, len);
     for (int k = lane; k < q.y; k += 32) {
         int idx = q.x + k;
         if (idx >= st.y) idx -= st.y;
         const size_t o = (size_t)rec * b.S + st.x + idx;
-        const int v = b.tvid[o];
+        const int v = vid_at(b, j, q0, st.x, st.y, q.w + k);
         const float x = b.tpos[o];
         const float a = expf(-fabsf(__fmul_rn(s5, __fsub_rn(x, half))));
         const float a1 = __fadd_rn(1.0f, a);
@@ -244,7 +257,7 @@ __device__ __forceinline__ Cand load_cand(const DevSim &d, const BwdDev &b, int 
 }
 
 // (2a) merge candidate i of step t (link, or L + origin node): abar, merge-
-// softmax weight, per-target sums (buffer t mod 3), the winner's entry
+// softmax weight, per-target sums (by tape record), the winner's entry
 // adjoint and cursor, the demand weight of exits.  z_load issues the record,
 // then in one round the target's merge word and everything that depends on the
 // vehicle only (its adjoint at t + 1 among them); z_finish does the rest.
@@ -255,6 +268,16 @@ struct ZLoad {
     float x, alpha, csuf;
 };
 
+// Programmatic dependent launch: the next kernel of the stream may start
+// (and issue its loads of the tape and of static data) while this one runs;
+// pdl_wait returns once the previous kernel has completed and its writes are
+// visible, and comes before any access to what that kernel writes.  In a
+// kernel launched without the attribute it returns at once.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// z_load: the record and what depends on the tape or static data only;
+// z_load_adj: the adjoint state the previous step wrote (after pdl_wait)
 __device__ __forceinline__ bool z_load(const DevSim &d, const BwdDev &b, int i, int rec, int bin0, ZLoad &z) {
     if (i < d.L) {
         const int4 r = b.tcrec[(size_t)rec * d.L + i];
@@ -265,15 +288,17 @@ __device__ __forceinline__ bool z_load(const DevSim &d, const BwdDev &b, int i, 
     }
     if (z.v < 0) return false;
     z.wt = z.tgt >= 0 ? b.tW[(size_t)rec * d.L + z.tgt] : 0ull;
-    z.cur = b.cursor[z.v];
-    z.xv = b.xbar[z.v];
     z.dup = b.rdup[z.v];
     z.k2 = b.od[z.v];
     z.csuf = i < d.L ? b.Csuf[(size_t)bin0 * d.L + i].x : 0.0f;
     return true;
 }
+__device__ __forceinline__ void z_load_adj(const BwdDev &b, ZLoad &z) {
+    z.cur = b.cursor[z.v];
+    z.xv = b.xbar[z.v];
+}
 
-__device__ __forceinline__ void z_finish(const DevSim &d, const BwdDev &b, int i, int t, const ZLoad &z) {
+__device__ __forceinline__ void z_finish(const DevSim &d, const BwdDev &b, int i, int t, int rec, const ZLoad &z) {
     const int v = z.v, tgt = z.tgt, cur = z.cur;
     const bool won = tgt >= 0 && z.wt != 0ull && merge_vid(z.wt) == v;
     const bool exits = i < d.L && (won || tgt == kTgtSink);         // an exit from link i
@@ -312,26 +337,29 @@ __device__ __forceinline__ void z_finish(const DevSim &d, const BwdDev &b, int i
             Xold = z.xv;
         }
         const float2 abar = ff_sub(ff_mul_f(ff_sub(Enew, Xold), d.M), ff_mul_f(Xold, z.x));
-        const size_t eo = (size_t)(t & 1) * (d.L + d.V) + i;
+        const size_t eo = (size_t)rec * (d.L + d.V) + i;
         b.ebuf[eo] = e;
         b.abuf[eo] = abar;
-        const size_t zo = (size_t)(t % 3) * d.L + tgt;
+        const size_t zo = (size_t)rec * d.L + tgt;
         atomicAdd(&b.Z[zo], (double)e);
         atomicAdd(&b.SA[zo], ff_to_double(ff_mul_f(abar, e)));
     }
     if (exits) atomicAdd(&b.glam[z.k2], (double)__fdiv_rn(z.csuf, lam));
 }
 
-// (2b) merge and link-choice Jacobians of step t
-__global__ void k_bwd_node_g(DevSim d, BwdDev b, int t, int rec) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d.L + d.V) return;
+// (2b) merge and link-choice Jacobians of steps t0 .. t0 + nrec - 1 (tape
+// records 0 .. nrec - 1), one thread per (record, candidate)
+__global__ void k_bwd_node_g(DevSim d, BwdDev b, int t0, int nrec) {
+    const int LV = d.L + d.V;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (long long)nrec * LV) return;
+    const int rec = (int)(g / LV), i = (int)(g - (long long)rec * LV), t = t0 + rec;
     const Cand c = load_cand(d, b, i, rec);
     if (c.vid < 0 || c.tgt < 0) return;
-    const size_t zo = (size_t)(t % 3) * d.L + c.tgt;
+    const size_t zo = (size_t)rec * d.L + c.tgt;
     const float2 Z = ff_from_double(b.Z[zo]);
     const float2 S = ff_div(ff_from_double(b.SA[zo]), Z);            // softmax-weighted mean of abar
-    const size_t eo = (size_t)(t & 1) * (d.L + d.V) + i;
+    const size_t eo = (size_t)rec * LV + i;
     const float pi = __fdiv_rn(b.ebuf[eo], Z.x);
     const float vbar = __fmul_rn(__fmul_rn(pi, ff_sub(b.abuf[eo], S).x), b.inv_tau);   // adjoint of V'_i
     if (i < d.L) atomicAdd(&b.ga[i], (double)vbar); else atomicAdd(b.gao, (double)vbar);
@@ -431,8 +459,7 @@ __global__ void k_bwd_node_g(DevSim d, BwdDev b, int t, int rec) {
 //     (shared memory) or, for the last position of a pass, from a look-ahead
 //     load.  The per-link parameter sums (free -> u: x' = x + u dt, congested
 //     -> s) are reduced in a fixed order.  These warps synchronise among
-//     themselves with a named barrier, and clear their links' merge sums of
-//     buffer t + 2.
+//     themselves with a named barrier.
 //   * merge warps: one thread per link candidate and per origin-queue
 //     candidate (z_load, z_finish).
 // A link's candidate is its leader, whose adjoint car-following overwrites, so
@@ -450,7 +477,7 @@ constexpr int kCfPass = kCfThreads * kCfE;
 __device__ __forceinline__ void cf_bar() { asm volatile("bar.sync 1, %0;" :: "n"(kCfThreads) : "memory"); }
 
 __global__ void __launch_bounds__(kBwdThreads) k_bwd_step(DevSim d, BwdDev b, int rec, int t, int bin0, int npb) {
-    __shared__ int4 sq[kCfLinks];
+    __shared__ int4 sq[kCfLinks], sq0[kCfLinks];
     __shared__ int sbase[kCfLinks], scap[kCfLinks], off[kCfLinks + 1];
     __shared__ int ftag[kCfThreads];
     __shared__ float2 fg[kCfThreads];
@@ -459,18 +486,26 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_step(DevSim d, BwdDev b, in
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int j0 = blockIdx.x * kCfLinks;
     const int nl = min(kCfLinks, d.L - j0);
+    pdl_trigger();
     if (tid >= kCfThreads) {                            // merge warps
         const int zi = tid - kCfThreads;
         ZLoad z;
         const bool has = zi < nl && z_load(d, b, j0 + zi, rec, bin0, z);
-        if (has) asm volatile("" :: "f"(z.xv.x), "f"(z.xv.y));   // the adjoint is in before the barrier
+        pdl_wait();
+        if (has) {
+            z_load_adj(b, z);
+            asm volatile("" :: "f"(z.xv.x), "f"(z.xv.y));   // the adjoint is in before the barrier
+        }
         __syncthreads();
-        if (has) z_finish(d, b, j0 + zi, t, z);
+        if (has) z_finish(d, b, j0 + zi, t, rec, z);
         if (zi >= kCfLinks) {                           // origin queues (not touched by car-following)
             const int n1 = min(d.V, (blockIdx.x + 1) * npb);
             for (int n = blockIdx.x * npb + zi - kCfLinks; n < n1; n += kZNodeThreads) {
                 ZLoad zn;
-                if (z_load(d, b, d.L + n, rec, bin0, zn)) z_finish(d, b, d.L + n, t, zn);
+                if (z_load(d, b, d.L + n, rec, bin0, zn)) {
+                    z_load_adj(b, zn);
+                    z_finish(d, b, d.L + n, t, rec, zn);
+                }
             }
         }
         return;
@@ -478,12 +513,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_step(DevSim d, BwdDev b, in
     if (tid < kCfLinks) {                               // queue states of the block's links
         if (tid < nl) {
             const int j = j0 + tid;
-            const size_t zo = (size_t)((t + 2) % 3) * d.L + j;      // merge sums of step t - 1 start from zero
-            b.Z[zo] = 0.0;
-            b.SA[zo] = 0.0;
             const int4 q = b.tlq[(size_t)rec * d.L + j];
             const int4 st = d.lst[j];
             sq[tid] = q;
+            sq0[tid] = b.tlq[j];
             sbase[tid] = st.x;
             scap[tid] = st.y;
         }
@@ -507,13 +540,13 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_step(DevSim d, BwdDev b, in
     cf_bar();
     const int total = off[kCfLinks];
     const float dt = d.dt;
-    const int *tvid = b.tvid + (size_t)rec * b.S;
     const int8_t *ttag = b.ttag + (size_t)rec * b.S;
     auto slot_of = [&](int li, int e) {
         int idx = sq[li].x + (e - off[li]);
         if (idx >= scap[li]) idx -= scap[li];
         return sbase[li] + idx;
     };
+    auto vid_of = [&](int li, int e) { return vid_at(b, j0 + li, sq0[li], sbase[li], scap[li], sq[li].w + (e - off[li])); };
     bool met = false;                                   // the block barrier with the merge warps
     for (int base = 0; base < total; base += kCfPass) {
         const int e0 = base + tid * kCfE;
@@ -529,18 +562,18 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_step(DevSim d, BwdDev b, in
             if (e < total) {
                 li = link_advance(off, nl, li, e);
                 lk[u] = li;
-                const int s = slot_of(li, e);
-                v[u] = tvid[s];
-                tag[u] = ttag[s];
+                v[u] = vid_of(li, e);
+                tag[u] = ttag[slot_of(li, e)];
             }
         }
         int vx = -1, tx = kTagStop;                     // the position after this pass
         const int ex = base + kCfPass;
         if (tid == kCfThreads - 1 && ex < total) {
-            const int s = slot_of(link_of(off, nl, ex), ex);
-            vx = tvid[s];
-            tx = ttag[s];
+            const int lx = link_of(off, nl, ex);
+            vx = vid_of(lx, ex);
+            tx = ttag[slot_of(lx, ex)];
         }
+        pdl_wait();                                     // adjoints of the previous step from here on
 #pragma unroll
         for (int u = 0; u < kCfE; ++u) g[u] = v[u] >= 0 ? b.xbar[v[u]] : make_float2(0.0f, 0.0f);
         const float2 gx = vx >= 0 ? b.xbar[vx] : make_float2(0.0f, 0.0f);
@@ -587,6 +620,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_step(DevSim d, BwdDev b, in
         cf_bar();                                       // before the next pass reuses the buffers
     }
     if (!met) __syncthreads();                          // no vehicles: meet the merge warps anyway
+    pdl_wait();
     if (tid < nl) {
         if (lsu[tid] != 0.0f) b.gu[j0 + tid] += (double)lsu[tid];
         if (lss[tid] != 0.0f) b.gs[j0 + tid] += (double)lss[tid];

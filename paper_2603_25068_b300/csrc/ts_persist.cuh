@@ -79,6 +79,7 @@ struct PSmem {
     int4 ld[kPLinks];              // (vehicle, zone) at queue positions 0 and 1
     int2 le[kPLinks];              // entry steps at queue positions 0 and 1
     int flags[kPLinks];            // vacancy / arrival for the coming step
+    int e0[kPLinks];               // recording: entries (exits + queued) at the segment start
     int lbase[kPLinks + 1];        // first ring slot of each link in shared memory (static)
     int voff[kPLinks + 1];         // first vehicle of each link in the CTA's queue order (step t)
     int past[kPLinks];             // bin end: vehicles past the midpoint (time t), summed over the step
@@ -365,6 +366,11 @@ __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &
                 c.P[st.x - c.base0 + idx] = 0.0f;
                 d.saux[st.x + idx] = make_int2(v, z);
                 d.sentry[st.x + idx] = tb + 1;
+                if (kTape) {                // entrant log of the segment (reverse pass)
+                    const int m = q.w + q.y - S.e0[li];
+                    if (m >= 0 && m < d.tape_K) d.tape_ent[(size_t)j * d.tape_K + m] = v;
+                    else set_error(d, SIM_EOVERFLOW, j, tb);
+                }
                 if (q.y == 0) { ld.x = v; ld.y = z; le.x = tb + 1; }
                 if (q.y == 1) { ld.z = v; ld.w = z; le.y = tb + 1; }
                 q.y += 1;
@@ -463,7 +469,10 @@ __device__ __forceinline__ int p_candidate(const DevSim &d, PSmem &S, const PCtx
         const int4 q = S.q[li];
         const int cost = q.y;                              // vehicles to update
         if (obs_only) return cost;
-        if (kTape) d.tape_lq[(size_t)r * d.L + c.j0 + li] = q;
+        if (kTape) {
+            d.tape_lq[(size_t)r * d.L + c.j0 + li] = q;
+            if (r == 0) S.e0[li] = q.w + q.y;
+        }
         const int4 st = S.st[li];
         const int credit = min(q.z + st.z, st.w);
         S.q[li].z = credit;
@@ -740,11 +749,14 @@ __device__ __forceinline__ void p_bits(const DevSim &d, PSmem &S, const PCtx &c)
     S.cr[li].z |= bits;
 }
 
-// tape: vehicle of every occupied slot at the start of step t (record r), by
-// every warp once the choice and car-following work of the step is done (the
-// decisions that follow do not depend on it).  A warp takes kTVL consecutive
-// links at a time and issues the loads of their first 32 queue positions before
-// any store, so that the L2 round trips overlap.
+// tape: vehicle of every occupied slot at the start of the segment (record r =
+// 0), by every warp once the choice and car-following work of its first step
+// is done (the decisions that follow do not depend on it).  Later steps need no
+// copy: the vehicle at queue position k of link j is entrant (exits + k) of j,
+// either one that was queued at the segment start or one of the entrant log.
+// A warp takes kTVL consecutive links at a time and issues the loads of their
+// first 32 queue positions before any store, so that the L2 round trips
+// overlap.
 constexpr int kTVL = 4;
 
 __device__ __forceinline__ void p_tape_vid(const DevSim &d, const PArgs &a, const PSmem &S, const PCtx &c, int r) {
@@ -917,7 +929,7 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         }
         p_pairs(d, S, c, t);
         __syncthreads();
-        if (kTape) p_tape_vid(d, a, S, c, t - a.t0);
+        if (kTape && t == a.t0) p_tape_vid(d, a, S, c, 0);     // vehicles of the segment start
         if (tid < 4) S.cnt[tid] = 0;
         p_decide(d, a, S, c, t, obs, false);
         p_refill(S, c, pd);

@@ -70,7 +70,12 @@ struct DevSim {
     // tape (backward); null when not recording
     int8_t *tag_tape;              // [S] car-following tag of each slot's vehicle this step
     float *tape_pos;               // [S] positions at the start of this step (occupied slots)
-    int *tape_vid;                 // [S] vehicle of each occupied slot at the start of this step
+    int *tape_vid;                 // [S] vehicle of each occupied slot at the start of the
+                                   // segment (written at its first step only; null after)
+    int *tape_ent;                 // [L tape_K] entrant log of the segment: entrant m of link j
+                                   // (counted from the segment start) at j tape_K + m
+    const int4 *tape_lq0;          // [L] queue states at the start of the segment
+    int tape_K;                    // steps of a segment
     int4 *tape_lq;                 // [L] queue state at the start of this step
     int4 *tape_crec;               // [L] link records of this step
     int2 *tape_nrec;               // [V] origin-queue records of this step

@@ -229,7 +229,7 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
                 v[u] = pc[st.x + idx];
                 if (kTape) {
                     sl[u] = st.x + idx;
-                    vd[u] = d.saux[st.x + idx].x;
+                    if (d.tape_vid) vd[u] = d.saux[st.x + idx].x;
                 }
             }
         }
@@ -240,7 +240,7 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
                 xs[e] = v[u];
                 if (kTape) {
                     d.tape_pos[sl[u]] = v[u];
-                    d.tape_vid[sl[u]] = vd[u];
+                    if (d.tape_vid) d.tape_vid[sl[u]] = vd[u];
                 }
             }
         }
@@ -515,6 +515,12 @@ __device__ __forceinline__ void step_b_core(const DevSim &d, int i, int t, int c
                 pn[st.x + idx] = 0.0f;
                 d.saux[st.x + idx] = make_int2(v, vz);
                 d.sentry[st.x + idx] = t + 1;
+                if (d.tape_ent) {                  // entrant log of the segment (reverse pass)
+                    const int4 q0 = d.tape_lq0[j];
+                    const int m = q.w + q.y - (q0.w + q0.y);
+                    if (m >= 0 && m < d.tape_K) d.tape_ent[(size_t)j * d.tape_K + m] = v;
+                    else set_error(d, SIM_EOVERFLOW, j, t);
+                }
                 q.y += 1;
                 d.vstate[v] = j;
                 entered = 1;
@@ -644,6 +650,32 @@ __device__ __forceinline__ void ckpt_member(const DevSim &d, const CkDev &c, int
     }
     for (size_t i = i0; i < (size_t)c.V; i += stride) c.fifo[s * c.V + i] = d.fifo_ptr[i];
     for (size_t i = i0; i < (size_t)c.N; i += stride) c.vstate[s * c.N + i] = d.vstate[i];
+}
+
+// the dynamic state from checkpoint t / K (the inverse of ckpt_member)
+__device__ __forceinline__ void restore_member(const DevSim &d, const CkDev &c, int t, size_t i0, size_t stride) {
+    const size_t s = t / c.K;
+    float *pc = (t & 1) ? d.pos1 : d.pos0;
+    for (size_t i = i0; i < (size_t)c.S; i += stride) {
+        pc[i] = c.pos[s * c.S + i];
+        d.saux[i] = c.saux[s * c.S + i];
+        d.sentry[i] = c.sentry[s * c.S + i];
+    }
+    for (size_t i = i0; i < (size_t)c.L; i += stride) {
+        d.lq[i] = c.lq[s * c.L + i];
+        d.lstat[i] = c.lstat[s * c.L + i];
+        d.vac[i] = c.vac[s * c.L + i];
+        d.lpos[i] = c.lpos[s * c.L + i];
+    }
+    for (size_t i = i0; i < (size_t)c.V; i += stride) d.fifo_ptr[i] = c.fifo[s * c.V + i];
+    for (size_t i = i0; i < (size_t)c.N; i += stride) d.vstate[i] = c.vstate[s * c.N + i];
+}
+
+// one instance: save (or restore) checkpoint t / K in one launch
+__global__ void k_ckpt(DevSim d, CkDev c, int t, int save) {
+    const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+    if (save) ckpt_member(d, c, t, i0, stride);
+    else restore_member(d, c, t, i0, stride);
 }
 
 __global__ void k_batch_ckpt(const DevSim *ds, const CkDev *cks, const int *tvec, const int *mode) {

@@ -150,7 +150,10 @@ class Engine:
             return 0.0
         sc = req.scenario
         slots = float(np.sum(np.floor(sc.length.astype(np.float64) * sc.kappa / sc.dn) + 2))
-        return 18.0 * (self.ckpt_every + 1) * slots + 16.0 * sc.N * self.route_cap    # two tape sets
+        # two tape sets: per step 9 B per slot, 68 B per link and 20 B per origin
+        # queue (queue states, records, merge words and merge sums)
+        return (18.0 * (self.ckpt_every + 1) * slots + 2.0 * (self.ckpt_every + 1) * (68.0 * sc.L + 20.0 * sc.V)
+                + 16.0 * sc.N * self.route_cap)
 
     def _bwd_worker(self, k: int):
         torch = self.torch
