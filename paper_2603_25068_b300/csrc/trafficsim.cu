@@ -1241,6 +1241,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
             q.tcrec = (int4 *)take((size_t)K * L, sizeof(int4));
             q.tnrec = (int2 *)take((size_t)K * V, sizeof(int2));
             q.tW = (unsigned long long *)take((size_t)K * L, sizeof(unsigned long long));
+            q.tmkey = (float *)take((size_t)K * (L + V), sizeof(float));
             q.Z = (double *)take((size_t)K * L, sizeof(double));
             q.SA = (double *)take((size_t)K * L, sizeof(double));
             q.ebuf = (float *)take((size_t)K * (L + V), sizeof(float));
@@ -1323,7 +1324,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     auto with_set = [&](int ts) {
         BwdDev q = b;
         q.tpos = bt[ts].tpos; q.tvid = bt[ts].tvid; q.tent = bt[ts].tent; q.tlq = bt[ts].tlq; q.ttag = bt[ts].ttag;
-        q.tcrec = bt[ts].tcrec; q.tnrec = bt[ts].tnrec; q.tW = bt[ts].tW;
+        q.tcrec = bt[ts].tcrec; q.tnrec = bt[ts].tnrec; q.tW = bt[ts].tW; q.tmkey = bt[ts].tmkey;
         q.Z = bt[ts].Z; q.SA = bt[ts].SA; q.ebuf = bt[ts].ebuf; q.abuf = bt[ts].abuf;
         return q;
     };
@@ -1347,6 +1348,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
             dq.tape_crec = q.tcrec + r * L;
             dq.tape_nrec = q.tnrec + r * V;
             dq.tape_W = q.tW + r * L;
+            dq.tape_mkey = q.tmkey + r * (L + V);
             k_step_a_tape<<<dq.nblk, kBlockA, smem_a, rs>>>(dq, t);
             k_step_b<<<(L + V + 255) / 256, 256, 0, rs>>>(dq, t);
         }
@@ -1372,7 +1374,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         CU(cudaMemsetAsync((t0 & 1) ? h->d.W1 : h->d.W0, 0, (size_t)L * sizeof(unsigned long long), vs));
         DevSim dq = dr;
         dq.tag_tape = q.ttag; dq.tape_pos = q.tpos; dq.tape_vid = q.tvid; dq.tape_lq = q.tlq;
-        dq.tape_ent = q.tent; dq.tape_lq0 = q.tlq; dq.tape_K = K;
+        dq.tape_ent = q.tent; dq.tape_lq0 = q.tlq; dq.tape_K = K; dq.tape_mkey = q.tmkey;
         dq.tape_crec = q.tcrec; dq.tape_nrec = q.tnrec; dq.tape_W = q.tW;
         TRY(enqueue_persist_d(h, dq, t0, t1, 0, true, vs));
         dq.tape_W = nullptr;

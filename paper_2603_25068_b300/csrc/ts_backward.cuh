@@ -87,6 +87,7 @@ struct BwdDev {
     int4 *tcrec;                 // [K L]     link candidates
     int2 *tnrec;                 // [K V]     origin-queue candidates
     unsigned long long *tW;      // [K L]     merge words
+    float *tmkey;                // [K (L+V)] merge key of each candidate with a target
     // adjoints (float2 = double-float)
     float2 *xbar;                // [N]
     float2 *eadj;                // [N cap]
@@ -265,7 +266,7 @@ struct ZLoad {
     float2 xv;                   // the vehicle's adjoint at t + 1
     unsigned long long wt;       // the target's merge word
     int v, tgt, cur, dup, k2;
-    float x, alpha, csuf;
+    float x, csuf, key;          // key: the candidate's merge key alpha + g' (recorded)
 };
 
 // Programmatic dependent launch: the next kernel of the stream may start
@@ -281,13 +282,14 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ bool z_load(const DevSim &d, const BwdDev &b, int i, int rec, int bin0, ZLoad &z) {
     if (i < d.L) {
         const int4 r = b.tcrec[(size_t)rec * d.L + i];
-        z.v = r.x; z.tgt = r.y; z.x = __int_as_float(r.w); z.alpha = d.alpha[i];
+        z.v = r.x; z.tgt = r.y; z.x = __int_as_float(r.w);
     } else {
         const int2 r = b.tnrec[(size_t)rec * d.V + (i - d.L)];
-        z.v = r.x; z.tgt = r.y; z.x = 0.0f; z.alpha = d.alpha[d.L];
+        z.v = r.x; z.tgt = r.y; z.x = 0.0f;
     }
     if (z.v < 0) return false;
     z.wt = z.tgt >= 0 ? b.tW[(size_t)rec * d.L + z.tgt] : 0ull;
+    z.key = z.tgt >= 0 ? b.tmkey[(size_t)rec * (d.L + d.V) + i] : 0.0f;
     z.dup = b.rdup[z.v];
     z.k2 = b.od[z.v];
     z.csuf = i < d.L ? b.Csuf[(size_t)bin0 * d.L + i].x : 0.0f;
@@ -308,10 +310,9 @@ __device__ __forceinline__ void z_finish(const DevSim &d, const BwdDev &b, int i
         if (cur >= 0) b.eadj[(size_t)v * b.cap + cur] = z.xv;
     }
     if (tgt >= 0) {
-        // (alpha + g') is the merge key of the forward step; the largest key of
-        // the target is in its merge word
-        const float key = __fadd_rn(z.alpha, gumbel(d.key0, d.key1, v, t, 1, 0));
-        const float e = expf(__fmul_rn(__fsub_rn(key, merge_key_of(z.wt)), b.inv_tau));
+        // (alpha + g') is the merge key of the forward step (recorded); the
+        // largest key of the target is in its merge word
+        const float e = expf(__fmul_rn(__fsub_rn(z.key, merge_key_of(z.wt)), b.inv_tau));
         float2 Enew, Xold;
         if (won) {
             Enew = z.xv;
@@ -476,31 +477,35 @@ constexpr int kCfPass = kCfThreads * kCfE;
 
 __device__ __forceinline__ void cf_bar() { asm volatile("bar.sync 1, %0;" :: "n"(kCfThreads) : "memory"); }
 
-__global__ void __launch_bounds__(kBwdThreads) k_bwd_step(DevSim d, BwdDev b, int rec, int t, int bin0, int npb) {
+__global__ void __launch_bounds__(kBwdThreads, 4) k_bwd_step(DevSim d, BwdDev b, int rec, int t, int bin0, int npb) {
     __shared__ int4 sq[kCfLinks], sq0[kCfLinks];
     __shared__ int sbase[kCfLinks], scap[kCfLinks], off[kCfLinks + 1];
     __shared__ int ftag[kCfThreads];
     __shared__ float2 fg[kCfThreads];
-    __shared__ float cu[kCfPass], cs[kCfPass];
+    __shared__ int skf[kCfThreads], skl[kCfThreads];   // link of each thread's first / last run of the pass
+    __shared__ float2 spl[kCfThreads];                  // sums of each thread's last run
     __shared__ float lsu[kCfLinks], lss[kCfLinks];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int j0 = blockIdx.x * kCfLinks;
     const int nl = min(kCfLinks, d.L - j0);
     pdl_trigger();
     if (tid >= kCfThreads) {                            // merge warps
+        // a thread's first candidate (its link, or its first origin queue) is
+        // loaded before the block barrier, the rest of its origin queues after
         const int zi = tid - kCfThreads;
+        const int n0 = blockIdx.x * npb + zi - kCfLinks, n1 = min(d.V, (blockIdx.x + 1) * npb);
+        const int i = zi < nl ? j0 + zi : (zi >= kCfLinks && n0 < n1) ? d.L + n0 : -1;
         ZLoad z;
-        const bool has = zi < nl && z_load(d, b, j0 + zi, rec, bin0, z);
+        const bool has = i >= 0 && z_load(d, b, i, rec, bin0, z);
         pdl_wait();
         if (has) {
             z_load_adj(b, z);
             asm volatile("" :: "f"(z.xv.x), "f"(z.xv.y));   // the adjoint is in before the barrier
         }
         __syncthreads();
-        if (has) z_finish(d, b, j0 + zi, t, rec, z);
+        if (has) z_finish(d, b, i, t, rec, z);
         if (zi >= kCfLinks) {                           // origin queues (not touched by car-following)
-            const int n1 = min(d.V, (blockIdx.x + 1) * npb);
-            for (int n = blockIdx.x * npb + zi - kCfLinks; n < n1; n += kZNodeThreads) {
+            for (int n = n0 + kZNodeThreads; n < n1; n += kZNodeThreads) {
                 ZLoad zn;
                 if (z_load(d, b, d.L + n, rec, bin0, zn)) {
                     z_load_adj(b, zn);
@@ -587,6 +592,14 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_step(DevSim d, BwdDev b, in
         }
         const int ntag = tid + 1 < kCfThreads ? ftag[tid + 1] : tx;
         const float2 ng = tid + 1 < kCfThreads ? fg[tid + 1] : gx;
+        // adjoints at time t, and the per-link parameter sums of the pass
+        // (free -> u, congested -> s): a run of one link's positions inside
+        // this thread is summed here, in order; a link whose positions span
+        // several threads is finished by the thread that holds its last
+        // position of the pass, which adds the last runs of the threads before
+        // it, right to left (a fixed order)
+        float su = 0.0f, ss = 0.0f, fu = 0.0f, fs = 0.0f;
+        int rl = -1, kf = -1;
 #pragma unroll
         for (int u = 0; u < kCfE; ++u) {
             const int e = e0 + u;
@@ -595,27 +608,40 @@ __global__ void __launch_bounds__(kBwdThreads) k_bwd_step(DevSim d, BwdDev b, in
             const float2 fv = u + 1 < kCfE ? g[u + 1 < kCfE ? u + 1 : u] : ng;
             const bool own = tag[u] != kTagCong, fol = e + 1 < off[lk[u] + 1] && ft == kTagCong;
             const float2 pre = own ? (fol ? ff_add(g[u], fv) : g[u]) : (fol ? fv : make_float2(0.0f, 0.0f));
-            cu[e - base] = (tag[u] == kTagFree) ? __fmul_rn(g[u].x, dt) : 0.0f;
-            cs[e - base] = (tag[u] == kTagCong) ? -g[u].x : 0.0f;
             if (v[u] >= 0) b.xbar[v[u]] = pre;
+            if (lk[u] != rl) {                          // a new run; close the previous one
+                if (rl >= 0) {
+                    if (kf < 0) { kf = rl; fu = su; fs = ss; }      // the first run
+                    else { lsu[rl] += su; lss[rl] += ss; }          // a whole link inside this thread
+                }
+                rl = lk[u];
+                su = 0.0f;
+                ss = 0.0f;
+            }
+            su = __fadd_rn(su, (tag[u] == kTagFree) ? __fmul_rn(g[u].x, dt) : 0.0f);
+            ss = __fadd_rn(ss, (tag[u] == kTagCong) ? -g[u].x : 0.0f);
         }
+        const bool single = kf < 0;                     // one run only: it is both the first and the last
+        if (single) { kf = rl; fu = su; fs = ss; }
+        skf[tid] = kf;
+        skl[tid] = rl;
+        spl[tid] = make_float2(su, ss);
         cf_bar();
-        for (int l = warp; l < nl; l += kCfWarps) {     // per-link sums of the pass, fixed order
-            const int a = max(off[l], base) - base, z = min(off[l + 1], base + kCfPass) - base;
-            float su = 0.0f, ss = 0.0f;
-            for (int k = a + lane; k < z; k += 32) {
-                su = __fadd_rn(su, cu[k]);
-                ss = __fadd_rn(ss, cs[k]);
+        const int nf = tid + 1 < kCfThreads ? skf[tid + 1] : -1;
+        if (kf >= 0 && (!single || nf != kf)) {         // the first run ends the link's positions here
+            float tu = fu, ts = fs;
+            for (int j = tid - 1; j >= 0 && skl[j] == kf; --j) {
+                const float2 p = spl[j];
+                tu = __fadd_rn(tu, p.x);
+                ts = __fadd_rn(ts, p.y);
+                if (skf[j] != kf) break;                // thread j's last run starts inside it
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                su += __shfl_xor_sync(kFull, su, o);
-                ss += __shfl_xor_sync(kFull, ss, o);
-            }
-            if (lane == 0) {
-                lsu[l] += su;
-                lss[l] += ss;
-            }
+            lsu[kf] += tu;
+            lss[kf] += ts;
+        }
+        if (!single && nf != rl) {                      // the last run ends the link here too
+            lsu[rl] += su;
+            lss[rl] += ss;
         }
         cf_bar();                                       // before the next pass reuses the buffers
     }

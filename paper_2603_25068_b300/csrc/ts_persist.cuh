@@ -686,6 +686,7 @@ __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem 
             } else {
                 tgt = p_choose(d, S, li, c.LO + nd.z, nd.w, ld.y, ld.x, t);
                 red_max_u64(Wt + tgt, p_word(S.mkey[li], ld.x, ld.y, a.packz));
+                if (d.tape_mkey) d.tape_mkey[(size_t)(t - a.t0) * (d.L + d.V) + c.j0 + li] = S.mkey[li];
             }
         }
         const float4 g = S.g[li];
@@ -719,6 +720,7 @@ __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem 
             const int4 nq = S.nq[ni];
             tgt = p_choose(d, S, kPLinks + ni, c.NO + nq.z, nq.w, nh.y, nh.x, t);
             red_max_u64(Wt + tgt, p_word(S.mkey[kPLinks + ni], nh.x, nh.y, a.packz));
+            if (d.tape_mkey) d.tape_mkey[(size_t)(t - a.t0) * (d.L + d.V) + d.L + c.n0 + ni] = S.mkey[kPLinks + ni];
         }
         S.nrec[ni] = make_int2(r.x, tgt);
     }

@@ -80,6 +80,8 @@ struct DevSim {
     int4 *tape_crec;               // [L] link records of this step
     int2 *tape_nrec;               // [V] origin-queue records of this step
     unsigned long long *tape_W;    // [L] merge words of this step
+    float *tape_mkey;              // [L + V] merge key alpha + g' of each candidate with a
+                                   // target this step (links, then origin queues)
     int2 *route_log;               // [N * route_cap] (step, link) of every entry; null = off
     int *route_len;                // [N] entries so far
     int route_cap;

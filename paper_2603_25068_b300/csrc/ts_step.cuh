@@ -359,6 +359,7 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
                 const int4 nq = S.nq[ni];
                 tgt = choose(d, S.nlo[ni], S.nkey[ni], S.nvacm[ni], d.noinfo + nq.z, nq.w - nq.z, lead.y, lead.x, t);
                 if (tgt >= 0) atomicMax(p ? &d.W1[tgt] : &d.W0[tgt], merge_word(S.nmkey[ni], lead.x));
+                if (kTape && tgt >= 0) d.tape_mkey[d.L + n] = S.nmkey[ni];
             }
         }
         d.nrec[n] = make_int2(lead.x, tgt);
@@ -404,6 +405,7 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
         } else {
             tgt = choose(d, S.lo[li], S.key[li], S.vacm[li], d.loinfo + nd.z, nd.w - nd.z, lead.y, lead.x, t);
             if (tgt >= 0) atomicMax(p ? &d.W1[tgt] : &d.W0[tgt], merge_word(S.mkey[li], lead.x));
+            if (kTape && tgt >= 0) d.tape_mkey[j] = S.mkey[li];
         }
     }
     d.lq[j].z = S.credit[li];
