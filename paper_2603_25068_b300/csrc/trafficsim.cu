@@ -1304,7 +1304,8 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     for (double *p : {b.gu, b.gs, b.ga, b.gU, b.gG}) CU(cudaMemsetAsync(p, 0, (size_t)L * sizeof(double), h->stream));
     CU(cudaMemsetAsync(b.gao, 0, sizeof(double), h->stream));
     CU(cudaMemsetAsync(b.glam, 0, (size_t)std::max(b.n_od, 1) * sizeof(double), h->stream));
-    CU(cudaMemsetAsync(b.eadj, 0, (size_t)N * h->route_cap * sizeof(float2), h->stream));
+    // eadj needs no clearing: entry r of a vehicle is undone (and its adjoint
+    // written) at the step of that entry, before any earlier step reads it
     k_bwd_init<<<(N + 255) / 256, 256, 0, h->stream>>>(h->d, b, dxT);
     k_route_scan<<<(int)(((size_t)N * 32 + 255) / 256), 256, 0, h->stream>>>(h->d, N, b);
     // recomputation: no route log, counters into a scratch array
