@@ -1248,6 +1248,7 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
             q.abuf = (float2 *)take((size_t)K * (L + V), sizeof(float2));
         }
         b.xbar = (float2 *)take(N, sizeof(float2));
+        b.A = (float2 *)take(S, sizeof(float2));
         b.cursor = (int *)take(N, sizeof(int));
         b.rdup = (unsigned char *)take(N, 1);
         b.eadj = (float2 *)take((size_t)N * h->route_cap, sizeof(float2));
@@ -1306,7 +1307,9 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     CU(cudaMemsetAsync(b.glam, 0, (size_t)std::max(b.n_od, 1) * sizeof(double), h->stream));
     // eadj needs no clearing: entry r of a vehicle is undone (and its adjoint
     // written) at the step of that entry, before any earlier step reads it
-    k_bwd_init<<<(N + 255) / 256, 256, 0, h->stream>>>(h->d, b, dxT);
+    CU(cudaMemsetAsync(b.A, 0, (size_t)S * sizeof(float2), h->stream));
+    const long long n_init = std::max((long long)N, 32LL * L);
+    k_bwd_init<<<(unsigned)((n_init + 255) / 256), 256, 0, h->stream>>>(h->d, b, dxT);
     k_route_scan<<<(int)(((size_t)N * 32 + 255) / 256), 256, 0, h->stream>>>(h->d, N, b);
     // recomputation: no route log, counters into a scratch array
     DevSim dr = h->d;

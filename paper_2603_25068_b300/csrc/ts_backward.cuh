@@ -4,12 +4,19 @@
 // the method differentiates (Methods "Optimization": jax.grad of the dense
 // formulation of SI-A Alg. S1 and SI-B Alg. S2): every discrete decision of the
 // recorded rollout is frozen and stop_gradient(v) is the recorded value.  The
-// dense state X[i, j] is represented by
-//   xbar[i]           adjoint of vehicle i's valid entry (its link, or its origin
-//                     queue, a virtual inflow link of length 0), and
+// adjoint of the dense state X[i, j] is represented by
+//   A[s]              adjoint of the valid entry of the vehicle in queue slot s
+//                     (a vehicle on a link keeps its slot from step to step, so
+//                     the car-following reads and writes it in place, in slot
+//                     order);
+//   xbar[i]           adjoint of waiting vehicle i's valid entry (its origin
+//                     queue, a virtual inflow link of length 0);
 //   eadj[i, r]        adjoint of X[i, m_r] right after vehicle i's r-th entry; an
 //                     invalid slot is the identity through time, so its adjoint at
 //                     an earlier time is that of the next entry into the link.
+// A transfer at step t moves a vehicle from its source (the head slot of a
+// link, or an origin queue) to the tail slot of its target: its adjoint at
+// t + 1 is read there (grafting passes it on unchanged to the source).
 // Per step t, in reverse (a segment of K steps is first recomputed from its
 // checkpoint, recording the tape that these kernels read):
 //   k_bwd_obs     observation at t + 1 (SI-D): dC_j/dx_i = s sigma (1 - sigma),
@@ -29,7 +36,7 @@
 //                 entry's adjoint unchanged (grafting, SI-C).
 // Precision.  FP64 arithmetic runs at a small fraction of the FP32 rate on this
 // part, so the kernels do none on the per-vehicle path.  Adjoints whose
-// differences cancel (xbar, eadj, abar, the merge sums SA / Z and the bin
+// differences cancel (A, xbar, eadj, abar, the merge sums SA / Z and the bin
 // adjoints Cbar) are double-float pairs, hi + lo with |lo| <= ulp(hi) / 2
 // (about 48 significant bits), computed with FP32 operations through the
 // error-free transformations TwoSum (Knuth), FastTwoSum (Dekker) and the
@@ -89,7 +96,8 @@ struct BwdDev {
     unsigned long long *tW;      // [K L]     merge words
     float *tmkey;                // [K (L+V)] merge key of each candidate with a target
     // adjoints (float2 = double-float)
-    float2 *xbar;                // [N]
+    float2 *A;                   // [S] adjoint of each occupied queue slot
+    float2 *xbar;                // [N] adjoint of each waiting vehicle
     float2 *eadj;                // [N cap]
     const int2 *route_log;       // [N cap]
     const int *route_len;        // [N]
@@ -200,11 +208,19 @@ __device__ __forceinline__ int vid_at(const BwdDev &b, int j, int4 q0, int base,
     return b.tvid[base + idx];
 }
 
-// adjoint of the final positions (vehicles on a link at the end of the rollout)
+// adjoints at the end of the rollout: dL/dx(T) for the vehicles on links (in
+// their slots, one warp per link of the final state), zero for waiting ones
 __global__ void k_bwd_init(DevSim d, BwdDev b, const float *dxT) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d.N) return;
-    b.xbar[i] = make_float2((dxT && d.vstate[i] >= 0) ? dxT[i] : 0.0f, 0.0f);
+    if (i < d.N) b.xbar[i] = make_float2(0.0f, 0.0f);
+    const int j = i >> 5, lane = threadIdx.x & 31;
+    if (j >= d.L) return;
+    const int4 q = d.lq[j], st = d.lst[j];
+    for (int k = lane; k < q.y; k += 32) {
+        int idx = q.x + k;
+        if (idx >= st.y) idx -= st.y;
+        b.A[st.x + idx] = make_float2(dxT ? dxT[d.saux[st.x + idx].x] : 0.0f, 0.0f);
+    }
 }
 
 // (1) observation at time t + 1 = the state of tape record rec: one warp per link.
@@ -223,14 +239,13 @@ __global__ void k_bwd_obs(DevSim d, BwdDev b, int rec, int bin) {
         int idx = q.x + k;
         if (idx >= st.y) idx -= st.y;
         const size_t o = (size_t)rec * b.S + st.x + idx;
-        const int v = vid_at(b, j, q0, st.x, st.y, q.w + k);
         const float x = b.tpos[o];
         const float a = expf(-fabsf(__fmul_rn(s5, __fsub_rn(x, half))));
         const float a1 = __fadd_rn(1.0f, a);
         const float w = __fdiv_rn(__fmul_rn(s5, a), __fmul_rn(a1, a1));
-        b.xbar[v] = ff_add(b.xbar[v], ff_mul_f(cb, w));
+        b.A[st.x + idx] = ff_add(b.A[st.x + idx], ff_mul_f(cb, w));
         if (x >= half) {
-            const int k2 = b.od[v];
+            const int k2 = b.od[vid_at(b, j, q0, st.x, st.y, q.w + k)];
             atomicAdd(&b.glam[k2], (double)__fdiv_rn(cb.x, b.od_lambda[k2]));
         }
     }
@@ -266,6 +281,9 @@ struct ZLoad {
     float2 xv;                   // the vehicle's adjoint at t + 1
     unsigned long long wt;       // the target's merge word
     int v, tgt, cur, dup, k2;
+    int aslot;                   // slot holding that adjoint (target's tail if the vehicle
+                                 // entered it, else the source's head), -1: waiting (xbar)
+    bool won;
     float x, csuf, key;          // key: the candidate's merge key alpha + g' (recorded)
 };
 
@@ -290,6 +308,16 @@ __device__ __forceinline__ bool z_load(const DevSim &d, const BwdDev &b, int i, 
     if (z.v < 0) return false;
     z.wt = z.tgt >= 0 ? b.tW[(size_t)rec * d.L + z.tgt] : 0ull;
     z.key = z.tgt >= 0 ? b.tmkey[(size_t)rec * (d.L + d.V) + i] : 0.0f;
+    z.won = z.tgt >= 0 && z.wt != 0ull && merge_vid(z.wt) == z.v;
+    z.aslot = -1;
+    if (z.won) {                 // the entrant is the last vehicle of the target's queue at t + 1
+        const int4 qm = b.tlq[(size_t)(rec + 1) * d.L + z.tgt], stm = d.lst[z.tgt];
+        int idx = qm.x + qm.y - 1;
+        if (idx >= stm.y) idx -= stm.y;
+        z.aslot = stm.x + idx;
+    } else if (i < d.L) {        // still the leader of link i
+        z.aslot = d.lst[i].x + b.tlq[(size_t)rec * d.L + i].x;
+    }
     z.dup = b.rdup[z.v];
     z.k2 = b.od[z.v];
     z.csuf = i < d.L ? b.Csuf[(size_t)bin0 * d.L + i].x : 0.0f;
@@ -297,17 +325,18 @@ __device__ __forceinline__ bool z_load(const DevSim &d, const BwdDev &b, int i, 
 }
 __device__ __forceinline__ void z_load_adj(const BwdDev &b, ZLoad &z) {
     z.cur = b.cursor[z.v];
-    z.xv = b.xbar[z.v];
+    z.xv = z.aslot >= 0 ? b.A[z.aslot] : b.xbar[z.v];
 }
 
 __device__ __forceinline__ void z_finish(const DevSim &d, const BwdDev &b, int i, int t, int rec, const ZLoad &z) {
     const int v = z.v, tgt = z.tgt, cur = z.cur;
-    const bool won = tgt >= 0 && z.wt != 0ull && merge_vid(z.wt) == v;
+    const bool won = z.won;
     const bool exits = i < d.L && (won || tgt == kTgtSink);         // an exit from link i
     const float lam = exits ? b.od_lambda[z.k2] : 1.0f;
     if (won) {                   // adjoint right after this entry: the latest one not yet undone
         b.cursor[v] = cur - 1;
         if (cur >= 0) b.eadj[(size_t)v * b.cap + cur] = z.xv;
+        if (i >= d.L) b.xbar[v] = z.xv;                  // a waiting vehicle before its entry (grafting)
     }
     if (tgt >= 0) {
         // (alpha + g') is the merge key of the forward step (recorded); the
@@ -478,8 +507,10 @@ constexpr int kCfPass = kCfThreads * kCfE;
 __device__ __forceinline__ void cf_bar() { asm volatile("bar.sync 1, %0;" :: "n"(kCfThreads) : "memory"); }
 
 __global__ void __launch_bounds__(kBwdThreads, 4) k_bwd_step(DevSim d, BwdDev b, int rec, int t, int bin0, int npb) {
-    __shared__ int4 sq[kCfLinks], sq0[kCfLinks];
+    __shared__ int4 sq[kCfLinks];
     __shared__ int sbase[kCfLinks], scap[kCfLinks], off[kCfLinks + 1];
+    __shared__ int sld[kCfLinks];                       // leader's transfer: 0 none / lost, 1 entered a link, 2 arrived
+    __shared__ float2 sen[kCfLinks];                    // adjoint at t + 1 of a leader that entered a link
     __shared__ int ftag[kCfThreads];
     __shared__ float2 fg[kCfThreads];
     __shared__ int skf[kCfThreads], skl[kCfThreads];   // link of each thread's first / last run of the pass
@@ -500,7 +531,12 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_bwd_step(DevSim d, BwdDev b,
         pdl_wait();
         if (has) {
             z_load_adj(b, z);
-            asm volatile("" :: "f"(z.xv.x), "f"(z.xv.y));   // the adjoint is in before the barrier
+            asm volatile("" :: "f"(z.xv.x), "f"(z.xv.y));   // in before the barrier: car-following
+        }                                                      // then rewrites the leader's slot
+        if (zi < nl) {                                  // for the car-following of the link's leader
+            const int f = has ? (z.won ? 1 : (z.tgt == kTgtSink ? 2 : 0)) : 0;
+            sld[zi] = f;
+            if (f == 1) sen[zi] = z.xv;
         }
         __syncthreads();
         if (has) z_finish(d, b, i, t, rec, z);
@@ -521,7 +557,6 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_bwd_step(DevSim d, BwdDev b,
             const int4 q = b.tlq[(size_t)rec * d.L + j];
             const int4 st = d.lst[j];
             sq[tid] = q;
-            sq0[tid] = b.tlq[j];
             sbase[tid] = st.x;
             scap[tid] = st.y;
         }
@@ -551,37 +586,35 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_bwd_step(DevSim d, BwdDev b,
         if (idx >= scap[li]) idx -= scap[li];
         return sbase[li] + idx;
     };
-    auto vid_of = [&](int li, int e) { return vid_at(b, j0 + li, sq0[li], sbase[li], scap[li], sq[li].w + (e - off[li])); };
     bool met = false;                                   // the block barrier with the merge warps
     for (int base = 0; base < total; base += kCfPass) {
         const int e0 = base + tid * kCfE;
-        int v[kCfE], tag[kCfE], lk[kCfE];
+        int sl[kCfE], tag[kCfE], lk[kCfE];
         float2 g[kCfE];
         int li = e0 < total ? link_of(off, nl, e0) : 0;
 #pragma unroll
         for (int u = 0; u < kCfE; ++u) {
             const int e = e0 + u;
-            v[u] = -1;
+            sl[u] = -1;
             tag[u] = kTagStop;
             lk[u] = 0;
             if (e < total) {
                 li = link_advance(off, nl, li, e);
                 lk[u] = li;
-                v[u] = vid_of(li, e);
-                tag[u] = ttag[slot_of(li, e)];
+                sl[u] = slot_of(li, e);
+                tag[u] = ttag[sl[u]];
             }
         }
-        int vx = -1, tx = kTagStop;                     // the position after this pass
+        int sx = -1, tx = kTagStop;                     // the position after this pass
         const int ex = base + kCfPass;
         if (tid == kCfThreads - 1 && ex < total) {
-            const int lx = link_of(off, nl, ex);
-            vx = vid_of(lx, ex);
-            tx = ttag[slot_of(lx, ex)];
+            sx = slot_of(link_of(off, nl, ex), ex);
+            tx = ttag[sx];
         }
         pdl_wait();                                     // adjoints of the previous step from here on
 #pragma unroll
-        for (int u = 0; u < kCfE; ++u) g[u] = v[u] >= 0 ? b.xbar[v[u]] : make_float2(0.0f, 0.0f);
-        const float2 gx = vx >= 0 ? b.xbar[vx] : make_float2(0.0f, 0.0f);
+        for (int u = 0; u < kCfE; ++u) g[u] = sl[u] >= 0 ? b.A[sl[u]] : make_float2(0.0f, 0.0f);
+        const float2 gx = sx >= 0 ? b.A[sx] : make_float2(0.0f, 0.0f);
         ftag[tid] = tag[0];
         fg[tid] = g[0];
         if (!met) {
@@ -592,6 +625,17 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_bwd_step(DevSim d, BwdDev b,
         }
         const int ntag = tid + 1 < kCfThreads ? ftag[tid + 1] : tx;
         const float2 ng = tid + 1 < kCfThreads ? fg[tid + 1] : gx;
+        // a leader that left its link at t: its adjoint at t + 1 is in its
+        // target's slot (entered, from the merge warps) or zero (arrived).  A
+        // leader is nobody's follower, so fg / ng need no such change.
+#pragma unroll
+        for (int u = 0; u < kCfE; ++u) {
+            if (e0 + u < total && e0 + u == off[lk[u]]) {
+                const int f = sld[lk[u]];
+                if (f == 1) g[u] = sen[lk[u]];
+                else if (f == 2) g[u] = make_float2(0.0f, 0.0f);
+            }
+        }
         // adjoints at time t, and the per-link parameter sums of the pass
         // (free -> u, congested -> s): a run of one link's positions inside
         // this thread is summed here, in order; a link whose positions span
@@ -608,7 +652,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_bwd_step(DevSim d, BwdDev b,
             const float2 fv = u + 1 < kCfE ? g[u + 1 < kCfE ? u + 1 : u] : ng;
             const bool own = tag[u] != kTagCong, fol = e + 1 < off[lk[u] + 1] && ft == kTagCong;
             const float2 pre = own ? (fol ? ff_add(g[u], fv) : g[u]) : (fol ? fv : make_float2(0.0f, 0.0f));
-            if (v[u] >= 0) b.xbar[v[u]] = pre;
+            b.A[sl[u]] = pre;
             if (lk[u] != rl) {                          // a new run; close the previous one
                 if (rl >= 0) {
                     if (kf < 0) { kf = rl; fu = su; fs = ss; }      // the first run
