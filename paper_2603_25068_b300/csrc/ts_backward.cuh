@@ -86,7 +86,8 @@ struct BwdDev {
     int S, K, cap, n_od;
     float tau, inv_tau;
     // tape of the current segment: K steps, K + 1 state records
-    float *tpos;                 // [(K+1) S] positions at the start of each step
+    float *tpos;                 // [(K+1) S] positions at the start of each step (written at
+                                 // bin ends only, where the observation's adjoint reads them)
     int *tvid;                   // [S] vehicle of each occupied slot at the segment start
     int *tent;                   // [L K] entrant log: entrant m of link j in the segment at j K + m
     int4 *tlq;                   // [(K+1) L] queue state at the start of each step

@@ -276,11 +276,16 @@ __device__ __forceinline__ void p_ends_post(const DevSim &d, const PArgs &a, PSm
     if (up0) c.P[lb + i0] = e.y0;
     if (up1) c.P[lb + i1] = pop ? e.y1m : e.y1f;
     if (push) c.P[lb + ie] = lead_e ? e.yem : e.yet;
-    if (kTape) {                    // tape: time-t position and branch tag of the slot
+    if (kTape) {                    // tape: branch tag of the slot, time-t position at bin ends
         const size_t o = (size_t)(t - a.t0) * a.S + c.base0 + lb;
-        if (up0) { d.tape_pos[o + i0] = e.x0; d.tag_tape[o + i0] = (int8_t)(e.tags & 3); }
-        if (up1) { d.tape_pos[o + i1] = e.x1; d.tag_tape[o + i1] = (int8_t)((e.tags >> (pop ? 2 : 4)) & 3); }
-        if (push) { d.tape_pos[o + ie] = 0.0f; d.tag_tape[o + ie] = (int8_t)((e.tags >> (lead_e ? 6 : 8)) & 3); }
+        if (up0) d.tag_tape[o + i0] = (int8_t)(e.tags & 3);
+        if (up1) d.tag_tape[o + i1] = (int8_t)((e.tags >> (pop ? 2 : 4)) & 3);
+        if (push) d.tag_tape[o + ie] = (int8_t)((e.tags >> (lead_e ? 6 : 8)) & 3);
+        if (obs) {
+            if (up0) d.tape_pos[o + i0] = e.x0;
+            if (up1) d.tape_pos[o + i1] = e.x1;
+            if (push) d.tape_pos[o + ie] = 0.0f;
+        }
     }
 }
 
@@ -632,9 +637,9 @@ __device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSm
             const float h = k == 0 ? M : __fsub_rn(ahead, x);
             int tag;
             c.P[lb + idx] = newell(x, h, g.x, g.y, g.z, g.w, tag);
-            if (kTape) {                    // tape: time-t position and branch tag of the slot
+            if (kTape) {                    // tape: branch tag of the slot, time-t position at bin ends
                 const size_t o = (size_t)r * a.S + c.base0 + lb + idx;
-                d.tape_pos[o] = x;
+                if (obs) d.tape_pos[o] = x;
                 d.tag_tape[o] = (int8_t)tag;
             }
         }

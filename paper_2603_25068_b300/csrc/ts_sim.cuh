@@ -69,7 +69,8 @@ struct DevSim {
     int *err;                      // [4]
     // tape (backward); null when not recording
     int8_t *tag_tape;              // [S] car-following tag of each slot's vehicle this step
-    float *tape_pos;               // [S] positions at the start of this step (occupied slots)
+    float *tape_pos;               // [S] positions at the start of this step (occupied slots;
+                                   // recorded at bin ends only)
     int *tape_vid;                 // [S] vehicle of each occupied slot at the start of the
                                    // segment (written at its first step only; null after)
     int *tape_ent;                 // [L tape_K] entrant log of the segment: entrant m of link j

@@ -239,7 +239,7 @@ __device__ __forceinline__ void step_block(const DevSim &d, int b, int t, bool o
             if (e < total) {
                 xs[e] = v[u];
                 if (kTape) {
-                    d.tape_pos[sl[u]] = v[u];
+                    if (obs) d.tape_pos[sl[u]] = v[u];           // read only at bin ends
                     if (d.tape_vid) d.tape_vid[sl[u]] = vd[u];
                 }
             }
