@@ -319,16 +319,19 @@ SIM_API void *sim_get_stream(sim_handle h);
 SIM_API int sim_set_stream(sim_handle h, void *stream);
 
 /* Segment recomputation of the reverse pass (sim_backward):
- *   SIM_RECOMPUTE_OVERLAP (default)  segment s - 1 is recomputed by the
- *       two-kernel executor on a low-priority stream while the reverse
- *       kernels of segment s run on a high-priority one; two tape sets
- *       (about 2 x (K + 1) x 9 bytes per queue slot);
- *   SIM_RECOMPUTE_SERIAL  each segment is recomputed by one recording launch
- *       of the persistent executor just before its reverse kernels; one tape
- *       set (half the memory).
- * Both give the same tape, so the same gradients (up to the order of the
- * double-precision atomic additions).  SERIAL falls back to OVERLAP when the
- * handle has no persistent executor.  Errors: SIM_EINVAL (unknown mode). */
+ *   SIM_RECOMPUTE_SERIAL (default)  each segment is recomputed by one
+ *       recording launch of the persistent executor just before its reverse
+ *       kernels;
+ *   SIM_RECOMPUTE_OVERLAP  segment s - 1 is recomputed by the two-kernel
+ *       executor on a low-priority stream while the reverse kernels of
+ *       segment s run on a high-priority one.
+ * Both use two tape sets (by segment parity: the Jacobian kernel of a
+ * segment reads its set while the next is recorded), about 2 x K x (1 byte per
+ * queue slot + 68 bytes per link + 20 per origin queue), positions at bin ends
+ * and the segment-start vehicle ids besides.  Both give the same tape, so the
+ * same gradients (up to the order of the double-precision atomic additions).
+ * SERIAL falls back to OVERLAP when the handle has no persistent executor.
+ * Errors: SIM_EINVAL (unknown mode). */
 #define SIM_RECOMPUTE_OVERLAP 0
 #define SIM_RECOMPUTE_SERIAL  1
 SIM_API int sim_set_recompute(sim_handle h, int32_t mode);

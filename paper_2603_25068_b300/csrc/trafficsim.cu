@@ -139,7 +139,7 @@ struct sim_ctx {
     // ... and the segment recomputation on a third stream, double-buffered tape;
     // the reverse kernels themselves on a high-priority stream
     cudaStream_t rstream = nullptr, vstream = nullptr;
-    int recompute = SIM_RECOMPUTE_OVERLAP;
+    int recompute = SIM_RECOMPUTE_SERIAL;
     cudaEvent_t ev_r[2] = {nullptr, nullptr}, ev_b[2] = {nullptr, nullptr};
     DevSim d{};
     // sizes

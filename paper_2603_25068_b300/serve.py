@@ -3,7 +3,9 @@
 Requests (nowcast rollouts, calibration-gradient rollouts, control-candidate
 rollouts) arrive over time.  The engine
   * admits waiting requests shortest remaining work first (vehicle-steps,
-    three times for a gradient request), each as soon as an upper bound of its
+    three times for a gradient request, as seconds of engine time, less the
+    time the request has already waited: a large request is not passed over
+    for longer than about its own run time), each as soon as an upper bound of its
     device memory fits in the HBM budget (replaced by sim_device_bytes of the
     handle once created, plus its reverse-pass needs) and fewer than
     max_in_flight + prefetch requests are admitted and unfinished (None:
@@ -16,9 +18,12 @@ rollouts) arrive over time.  The engine
     batch instead of stalling it,
   * runs every admitted forward rollout in one batch (sim_batch_*), a new
     request joining at the next step boundary, finished ones leaving it,
-  * runs the reverse passes of finished gradient requests on worker threads,
-    each with its own stream, so that they overlap one another and the
-    batched forward work on the device,
+  * runs the reverse pass of a finished gradient request between forward
+    chunks on the engine's stream (reversers = 0, the default: the
+    simulator's kernels each fill the GPU, so one device job at a time is
+    the fastest order), or on worker threads with streams of their own
+    (reversers > 0: reverse passes overlap one another and the forward work
+    on the device),
   * records each request's latency from arrival to result.
 Each request's result is the one it would get alone: batching changes neither
 its random key nor its state.
@@ -104,7 +109,7 @@ def handle_bytes_bound(sc, ckpt_every: int, route_cap: int) -> float:
 
 class Engine:
     def __init__(self, device: int = 0, hbm_budget: float = 150e9, chunk: int = 240, ckpt_every: int = 180,
-                 route_cap: int = 256, creators: int = 2, reversers: int = 2, max_in_flight: Optional[int] = None,
+                 route_cap: int = 256, creators: int = 2, reversers: int = 0, max_in_flight: Optional[int] = None,
                  order: str = "srw", prefetch: int = 2):
         import torch
         self.torch = torch
@@ -123,6 +128,8 @@ class Engine:
         self.stream = torch.cuda.Stream(device=device)
         self.bwd_streams = [torch.cuda.Stream(device=device) for _ in range(reversers)]
         self.active: List[tuple] = []          # (request, simulator, bytes)
+        self.reversers = reversers
+        self.pending_bwd: List[tuple] = []     # reversers = 0: (request, simulator, bytes, outputs) due
         self.batch: Optional[Batch] = None
         self.batch_members: List[int] = []
         self.used = 0.0
@@ -155,27 +162,31 @@ class Engine:
         return (18.0 * (self.ckpt_every + 1) * slots + 2.0 * (self.ckpt_every + 1) * (68.0 * sc.L + 20.0 * sc.V)
                 + 16.0 * sc.N * self.route_cap)
 
+    def _reverse(self, req, sim, nbytes, out, stream):
+        """The reverse pass of a gradient request whose forward is done; its
+        result and the release of its memory."""
+        with self.torch.cuda.device(self.device):
+            sim.set_stream(stream)                     # out of the batch
+            if out is None:
+                out = sim.outputs()
+            g = sim.backward(loss_cotangent(req, out["counts"]))
+            req.result = dict(counts=out["counts"], speed=out["speed"], travel_time=out["travel_time"], grad=g)
+            sim.close()
+        with self.lock:
+            self.used -= nbytes
+            self.in_flight -= 1
+        req.finished = self.now()
+
     def _bwd_worker(self, k: int):
-        torch = self.torch
         while True:
             item = self.bwd_q.get()
             if item is None:
                 return
-            req, sim, nbytes = item
             try:
-                with torch.cuda.device(self.device):
-                    sim.set_stream(self.bwd_streams[k])     # out of the batch: a stream of this worker
-                    out = sim.outputs()
-                    g = sim.backward(loss_cotangent(req, out["counts"]))
-                    req.result = dict(counts=out["counts"], speed=out["speed"], travel_time=out["travel_time"], grad=g)
-                    sim.close()
+                self._reverse(*item, self.bwd_streams[k])
             except Exception as e:          # reported by the main loop
                 self.worker_error = e
                 return
-            with self.lock:
-                self.used -= nbytes
-                self.in_flight -= 1
-            req.finished = self.now()
 
     def _create_worker(self, k: int):
         torch = self.torch
@@ -229,11 +240,15 @@ class Engine:
         self.create_q.put((req, reserved))
         return True
 
-    def _finish_forward(self, req, sim, nbytes):
+    def _finish_forward(self, req, sim, nbytes, out=None):
         if req.needs_grad:
-            self.bwd_q.put((req, sim, nbytes))
+            if self.reversers == 0:
+                self.pending_bwd.append((req, sim, nbytes, out))
+            else:
+                self.bwd_q.put((req, sim, nbytes, out))
             return
-        out = sim.outputs()
+        if out is None:
+            out = sim.outputs()
         req.result = dict(counts=out["counts"], speed=out["speed"], travel_time=out["travel_time"])
         sim.close()
         with self.lock:
@@ -244,8 +259,8 @@ class Engine:
     def _run_alone(self, req, sim, nbytes):
         """A request with nothing beside it: one rollout of its own simulator
         (a single persistent launch), as serial execution runs it."""
-        sim.rollout(req.scenario.T)
-        self._finish_forward(req, sim, nbytes)
+        out = sim.rollout(req.scenario.T)
+        self._finish_forward(req, sim, nbytes, out)
 
     # -------------------------------------------------------------- main loop
     def run(self, requests: List[Request], poll: float = 0.0005, max_seconds: float = 3600.0):
@@ -265,8 +280,9 @@ class Engine:
                 while k < len(pending) and pending[k].arrival <= self.now():
                     waiting.append(pending[k])
                     k += 1
+                now = self.now()
                 if self.order == "srw":
-                    waiting.sort(key=request_work)
+                    waiting.sort(key=lambda r: request_priority(r, now))
                 waiting = [req for req in waiting if not self._admit(req)]
                 while True:                              # simulators built by the creation thread
                     try:
@@ -274,7 +290,12 @@ class Engine:
                     except queue.Empty:
                         break
                 if self.order == "srw":
-                    self.ready.sort(key=lambda a: request_work(a[0]))
+                    self.ready.sort(key=lambda a: request_priority(a[0], now))
+                if self.pending_bwd:                     # a due reverse pass first: it finishes a request
+                    if self.order == "srw":
+                        self.pending_bwd.sort(key=lambda a: request_priority(a[0], now))
+                    self._reverse(*self.pending_bwd.pop(0), self.stream)
+                    continue
                 new = []
                 while self.ready and (self.max_in_flight is None or len(self.active) < self.max_in_flight):
                     req, sim, nbytes = self.ready.pop(0)
@@ -312,6 +333,17 @@ def request_work(req: Request) -> float:
     vehicle-steps, three times for a gradient request (forward, segment
     recomputation and reverse step)."""
     return float(req.vehicle_steps) * (3.0 if req.needs_grad else 1.0)
+
+
+WORK_PER_SECOND = 5e10      # request_work units the engine completes per second (measured order)
+
+
+def request_priority(req: Request, now: float) -> float:
+    """Admission order (lower first): the request's work in seconds of engine
+    time less the time it has waited since arrival, so that shortest work
+    goes first but a long request overtakes newer short ones once it has
+    waited about its own run time (no starvation)."""
+    return request_work(req) / WORK_PER_SECOND - (now - req.arrival)
 
 
 def latency_stats(reqs: List[Request]) -> dict:

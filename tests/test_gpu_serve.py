@@ -13,13 +13,17 @@ from oracle.oracle import OracleSim
 pytestmark = pytest.mark.gpu
 
 
-def test_served_results_equal_results_alone():
+@pytest.mark.parametrize("reversers", [0, 2])
+def test_served_results_equal_results_alone(reversers):
+    """reversers = 0: reverse passes between forward chunks on the engine's
+    stream; 2: on worker threads beside the forward work."""
     from paper_2603_25068_b300 import serve
-    reqs = serve.make_request_stream(n=8, rate=40.0, seed=7, sizes=(600, 1200), n_range=(3000, 20000),
+    # arrivals close enough together that several requests are ready at once
+    reqs = serve.make_request_stream(n=8, rate=400.0, seed=7, sizes=(600, 1200), n_range=(3000, 20000),
                                      horizons={"nowcast": 400, "calibration": 300, "control": 300}, n_sensors=50)
     kinds = {r.kind for r in reqs}
     assert {"nowcast"} < kinds
-    eng = serve.Engine(hbm_budget=20e9, chunk=25, ckpt_every=60)
+    eng = serve.Engine(hbm_budget=20e9, chunk=25, ckpt_every=60, reversers=reversers)
     eng.run(reqs)
     st = serve.latency_stats(reqs)
     assert st["p99_s"] >= st["p50_s"] > 0

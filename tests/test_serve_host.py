@@ -1,6 +1,6 @@
 """Host logic of the serving engine (no GPU): the requests' loss cotangents,
 the Poisson request stream and its mix, the memory bound used for admission,
-and the latency statistics."""
+the admission priority, and the latency statistics."""
 import numpy as np
 import pytest
 
@@ -78,3 +78,20 @@ def test_latency_statistics():
     st = serve.latency_stats(reqs)
     assert st["p50_s"] == pytest.approx(50.5) and st["max_s"] == 100.0 and st["mean_s"] == pytest.approx(50.5)
     assert st["p99_s"] == pytest.approx(np.percentile(np.arange(1, 101), 99))
+
+
+def test_admission_priority_is_shortest_work_with_aging():
+    """Shortest work first among requests that arrived together; a long request
+    that has waited about its own run time goes ahead of newer short ones (no
+    starvation); a gradient request counts three times its vehicle-steps."""
+    from paper_2603_25068_b300 import scenario as S
+    small = S.tiny_grid(n_vehicles=200, T=100)
+    big = S.tiny_grid(n_vehicles=1000, T=300)
+    a = serve.Request(rid=0, kind="nowcast", scenario=big, arrival=0.0)
+    b = serve.Request(rid=1, kind="nowcast", scenario=small, arrival=0.0)
+    g = serve.Request(rid=2, kind="calibration", scenario=small, arrival=0.0)
+    assert serve.request_priority(b, 0.0) < serve.request_priority(g, 0.0) < serve.request_priority(a, 0.0)
+    assert serve.request_work(g) == 3 * serve.request_work(b)
+    wait = serve.request_work(a) / serve.WORK_PER_SECOND
+    late = serve.Request(rid=3, kind="nowcast", scenario=small, arrival=1.5 * wait)
+    assert serve.request_priority(a, 1.5 * wait) < serve.request_priority(late, 1.5 * wait)
