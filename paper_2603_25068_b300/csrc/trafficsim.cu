@@ -676,36 +676,37 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
     h->no_ptr_host = no_ptr;
     h->S = (int)S;
     h->lst_host = lst;
-    // origin queues sorted by (origin, departure step, id)
     // origin queues: vehicles ordered by (origin, departure step, id), as two
     // stable counting sorts -- by departure step over the ids, then by origin
+    // -- that move whole records (id, origin, departure step, destination
+    // zone), so that neither pass gathers from the demand arrays at random
+    struct VRec { int id, origin, dep, zone; };
     std::vector<int> fifo(N), fifo_beg(V + 1, 0), fifo_dep(N), fifo_aux(2 * (size_t)N);
     {
         int max_dep = 0;
         for (int i = 0; i < N; ++i) max_dep = std::max(max_dep, dem->dep_step[i]);
-        std::vector<int> by_dep(N);
+        std::vector<VRec> by_dep(N);
         if (max_dep < (1 << 24)) {
             std::vector<int> cnt((size_t)max_dep + 2, 0);
             for (int i = 0; i < N; ++i) cnt[(size_t)dem->dep_step[i] + 1]++;
             for (int s = 0; s <= max_dep; ++s) cnt[(size_t)s + 1] += cnt[s];
-            for (int i = 0; i < N; ++i) by_dep[cnt[dem->dep_step[i]]++] = i;
+            for (int i = 0; i < N; ++i)
+                by_dep[cnt[dem->dep_step[i]]++] = VRec{i, dem->origin[i], dem->dep_step[i], dem->dest_zone[i]};
         } else {                         // departure steps too far apart for counting
-            std::iota(by_dep.begin(), by_dep.end(), 0);
-            std::stable_sort(by_dep.begin(), by_dep.end(),
-                             [&](int a, int b) { return dem->dep_step[a] < dem->dep_step[b]; });
+            for (int i = 0; i < N; ++i) by_dep[i] = VRec{i, dem->origin[i], dem->dep_step[i], dem->dest_zone[i]};
+            std::stable_sort(by_dep.begin(), by_dep.end(), [](const VRec &a, const VRec &b) { return a.dep < b.dep; });
         }
         for (int i = 0; i < N; ++i) fifo_beg[dem->origin[i] + 1]++;
         for (int n = 0; n < V; ++n) fifo_beg[n + 1] += fifo_beg[n];
         std::vector<int> fill(fifo_beg.begin(), fifo_beg.end() - 1);
         for (int k = 0; k < N; ++k) {
-            const int i = by_dep[k];
-            fifo[fill[dem->origin[i]]++] = i;
+            const VRec r = by_dep[k];
+            const int pos = fill[r.origin]++;
+            fifo[pos] = r.id;
+            fifo_dep[pos] = r.dep;
+            fifo_aux[2 * (size_t)pos] = r.id;
+            fifo_aux[2 * (size_t)pos + 1] = r.zone;
         }
-    }
-    for (int k = 0; k < N; ++k) {
-        fifo_dep[k] = dem->dep_step[fifo[k]];
-        fifo_aux[2 * k] = fifo[k];
-        fifo_aux[2 * k + 1] = dem->dest_zone[fifo[k]];
     }
     std::vector<int> fifo_end(fifo_beg.begin() + 1, fifo_beg.end());
     h->fifo_beg = fifo_beg;

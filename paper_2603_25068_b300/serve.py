@@ -32,6 +32,7 @@ from __future__ import annotations
 
 import dataclasses
 import queue
+import sys
 import threading
 import time
 from typing import List, Optional
@@ -266,6 +267,17 @@ class Engine:
     def run(self, requests: List[Request], poll: float = 0.0005, max_seconds: float = 3600.0):
         """Serve the requests (arrival times in seconds from now); returns them
         with results and timings."""
+        # the main loop and the creation threads hand the interpreter lock to
+        # one another around every library call: a short switch interval keeps
+        # each hand-over well below a millisecond (the default is 5 ms)
+        switch = sys.getswitchinterval()
+        sys.setswitchinterval(min(switch, 2e-4))
+        try:
+            return self._run(requests, poll, max_seconds)
+        finally:
+            sys.setswitchinterval(switch)
+
+    def _run(self, requests: List[Request], poll: float, max_seconds: float):
         torch = self.torch
         pending = sorted(requests, key=lambda r: r.arrival)
         self.t0 = time.perf_counter()
