@@ -17,7 +17,9 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <memory>
 #include <numeric>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -593,6 +595,44 @@ static int upload_params(sim_ctx *h, const sim_params *par) {
     return SIM_OK;
 }
 
+// ---- host set-up on several threads ----
+// f(t, T) on threads t = 0 .. T - 1 (the calling thread is t = 0)
+template <class F>
+static void host_parallel(int T, F f) {
+    if (T <= 1) { f(0, 1); return; }
+    std::vector<std::thread> th;
+    th.reserve(T - 1);
+    for (int t = 1; t < T; ++t) th.emplace_back(f, t, T);
+    f(0, T);
+    for (auto &x : th) x.join();
+}
+static int host_threads(size_t n) {
+    const size_t hw = std::max(1u, std::thread::hardware_concurrency());
+    return (int)std::max<size_t>(1, std::min<size_t>(std::min<size_t>(hw, 8), n / 65536));
+}
+// Stable counting sort of n records by key(r) in [0, K) from in to out, on T
+// threads: per-thread counts over contiguous chunks, offsets in (key, thread)
+// order, then each thread scatters its chunk in order.
+template <class R, class Key>
+static void counting_sort(const R *in, R *out, size_t n, size_t K, Key key, int T) {
+    std::vector<size_t> cnt((size_t)T * K, 0);
+    host_parallel(T, [&](int t, int nt) {
+        size_t *c = &cnt[(size_t)t * K];
+        for (size_t i = n * t / nt, e = n * (t + 1) / nt; i < e; ++i) c[key(in[i])]++;
+    });
+    size_t run = 0;
+    for (size_t k = 0; k < K; ++k)
+        for (int t = 0; t < T; ++t) {
+            const size_t c = cnt[(size_t)t * K + k];
+            cnt[(size_t)t * K + k] = run;
+            run += c;
+        }
+    host_parallel(T, [&](int t, int nt) {
+        size_t *c = &cnt[(size_t)t * K];
+        for (size_t i = n * t / nt, e = n * (t + 1) / nt; i < e; ++i) out[c[key(in[i])]++] = in[i];
+    });
+}
+
 static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem, const sim_params *par,
                        const sim_options *opt) {
     if (!net || !dem || !par || !opt) return fail(h, SIM_EINVAL, "null argument");
@@ -679,34 +719,37 @@ static int create_impl(sim_ctx *h, const sim_network *net, const sim_demand *dem
     // origin queues: vehicles ordered by (origin, departure step, id), as two
     // stable counting sorts -- by departure step over the ids, then by origin
     // -- that move whole records (id, origin, departure step, destination
-    // zone), so that neither pass gathers from the demand arrays at random
+    // zone), so that neither pass gathers from the demand arrays at random;
+    // both run on several host threads
     struct VRec { int id, origin, dep, zone; };
     std::vector<int> fifo(N), fifo_beg(V + 1, 0), fifo_dep(N), fifo_aux(2 * (size_t)N);
     {
+        const int T = host_threads((size_t)N);
+        std::unique_ptr<VRec[]> rec(new VRec[std::max(N, 1)]), tmp(new VRec[std::max(N, 1)]);
         int max_dep = 0;
         for (int i = 0; i < N; ++i) max_dep = std::max(max_dep, dem->dep_step[i]);
-        std::vector<VRec> by_dep(N);
+        host_parallel(T, [&](int t, int nt) {
+            for (size_t i = (size_t)N * t / nt, e = (size_t)N * (t + 1) / nt; i < e; ++i)
+                rec[i] = VRec{(int)i, dem->origin[i], dem->dep_step[i], dem->dest_zone[i]};
+        });
         if (max_dep < (1 << 24)) {
-            std::vector<int> cnt((size_t)max_dep + 2, 0);
-            for (int i = 0; i < N; ++i) cnt[(size_t)dem->dep_step[i] + 1]++;
-            for (int s = 0; s <= max_dep; ++s) cnt[(size_t)s + 1] += cnt[s];
-            for (int i = 0; i < N; ++i)
-                by_dep[cnt[dem->dep_step[i]]++] = VRec{i, dem->origin[i], dem->dep_step[i], dem->dest_zone[i]};
+            counting_sort(rec.get(), tmp.get(), (size_t)N, (size_t)max_dep + 1, [](const VRec &r) { return (size_t)r.dep; }, T);
         } else {                         // departure steps too far apart for counting
-            for (int i = 0; i < N; ++i) by_dep[i] = VRec{i, dem->origin[i], dem->dep_step[i], dem->dest_zone[i]};
-            std::stable_sort(by_dep.begin(), by_dep.end(), [](const VRec &a, const VRec &b) { return a.dep < b.dep; });
+            std::copy(rec.get(), rec.get() + N, tmp.get());
+            std::stable_sort(tmp.get(), tmp.get() + N, [](const VRec &a, const VRec &b) { return a.dep < b.dep; });
         }
+        counting_sort(tmp.get(), rec.get(), (size_t)N, (size_t)V, [](const VRec &r) { return (size_t)r.origin; }, T);
         for (int i = 0; i < N; ++i) fifo_beg[dem->origin[i] + 1]++;
         for (int n = 0; n < V; ++n) fifo_beg[n + 1] += fifo_beg[n];
-        std::vector<int> fill(fifo_beg.begin(), fifo_beg.end() - 1);
-        for (int k = 0; k < N; ++k) {
-            const VRec r = by_dep[k];
-            const int pos = fill[r.origin]++;
-            fifo[pos] = r.id;
-            fifo_dep[pos] = r.dep;
-            fifo_aux[2 * (size_t)pos] = r.id;
-            fifo_aux[2 * (size_t)pos + 1] = r.zone;
-        }
+        host_parallel(T, [&](int t, int nt) {
+            for (size_t k = (size_t)N * t / nt, e = (size_t)N * (t + 1) / nt; k < e; ++k) {
+                const VRec r = rec[k];
+                fifo[k] = r.id;
+                fifo_dep[k] = r.dep;
+                fifo_aux[2 * k] = r.id;
+                fifo_aux[2 * k + 1] = r.zone;
+            }
+        });
     }
     std::vector<int> fifo_end(fifo_beg.begin() + 1, fifo_beg.end());
     h->fifo_beg = fifo_beg;
