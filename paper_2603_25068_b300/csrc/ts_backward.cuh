@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_bwd_step(DevSim d, BwdDev b,
     __shared__ int skf[kCfThreads], skl[kCfThreads];   // link of each thread's first / last run of the pass
     __shared__ float2 spl[kCfThreads];                  // sums of each thread's last run
     __shared__ float lsu[kCfLinks], lss[kCfLinks];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int j0 = blockIdx.x * kCfLinks;
     const int nl = min(kCfLinks, d.L - j0);
     pdl_trigger();

@@ -655,11 +655,11 @@ __device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSm
 
 // Observation at bin ends, choice, merge, next-step bits and records of this
 // thread's link or origin queue.
+template <bool kTape>
 __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int t, bool obs,
                                          bool obs_only) {
     const int tid = threadIdx.x;
     unsigned long long *Wt = a.W3 + (size_t)(t % 3) * d.L;
-    const float M = d.M;
     if (tid < c.nl) {
         const int li = tid, j = c.j0 + li;
         const int4 q = S.q[li];
@@ -691,10 +691,9 @@ __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem 
             } else {
                 tgt = p_choose(d, S, li, c.LO + nd.z, nd.w, ld.y, ld.x, t);
                 red_max_u64(Wt + tgt, p_word(S.mkey[li], ld.x, ld.y, a.packz));
-                if (d.tape_mkey) d.tape_mkey[(size_t)(t - a.t0) * (d.L + d.V) + c.j0 + li] = S.mkey[li];
+                if (kTape) d.tape_mkey[(size_t)(t - a.t0) * (d.L + d.V) + c.j0 + li] = S.mkey[li];
             }
         }
-        const float4 g = S.g[li];
         const int4 st = S.st[li];
         const int lb = st.x - c.base0;
         auto at = [&](int k) {
@@ -725,7 +724,7 @@ __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem 
             const int4 nq = S.nq[ni];
             tgt = p_choose(d, S, kPLinks + ni, c.NO + nq.z, nq.w, nh.y, nh.x, t);
             red_max_u64(Wt + tgt, p_word(S.mkey[kPLinks + ni], nh.x, nh.y, a.packz));
-            if (d.tape_mkey) d.tape_mkey[(size_t)(t - a.t0) * (d.L + d.V) + d.L + c.n0 + ni] = S.mkey[kPLinks + ni];
+            if (kTape) d.tape_mkey[(size_t)(t - a.t0) * (d.L + d.V) + d.L + c.n0 + ni] = S.mkey[kPLinks + ni];
         }
         S.nrec[ni] = make_int2(r.x, tgt);
     }
@@ -938,7 +937,7 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         __syncthreads();
         if (kTape && t == a.t0) p_tape_vid(d, a, S, c, 0);     // vehicles of the segment start
         if (tid < 4) S.cnt[tid] = 0;
-        p_decide(d, a, S, c, t, obs, false);
+        p_decide<kTape>(d, a, S, c, t, obs, false);
         p_refill(S, c, pd);
         ++epoch;
         grid_arrive(a.bar);
@@ -964,7 +963,7 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         p_scan(S, c, v);
         p_carfollow<false, true, 0>(d, a, S, c, 0, true);
         __syncthreads();
-        p_decide(d, a, S, c, a.t1, true, true);
+        p_decide<false>(d, a, S, c, a.t1, true, true);
     }
     __syncthreads();
     // ---------------- write the group's state back ----------------
