@@ -135,7 +135,8 @@ __device__ __forceinline__ void grid_arrive(unsigned *bar) {
     if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(bar) : "memory");
 }
 __device__ __forceinline__ bool grid_wait(const DevSim &d, unsigned *bar, unsigned target, int t, int *stop) {
-    __syncthreads();
+    // thread 0 waits as soon as its own work is done; the block barrier after
+    // the wait holds every thread until both its own work and the grid's are
     if (threadIdx.x == 0) {
         const unsigned long long t_start = global_ns();
         int ok = 1;
