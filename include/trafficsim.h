@@ -199,8 +199,10 @@ SIM_API int sim_step(sim_handle h, int32_t n_steps);
 
 /* Reset, run T steps, close the last observation bin and write the outputs.
  * With options.ckpt_every > 0 it also keeps the checkpoints and route log that
- * sim_backward needs.  The steps are replayed from a CUDA graph captured on the
- * first rollout of each horizon.  Errors: as sim_reset / sim_step, SIM_ECUDA. */
+ * sim_backward needs.  The persistent executor runs the steps in one
+ * cooperative launch (one per checkpoint segment with ckpt_every > 0); the
+ * two-kernel executor replays them from a CUDA graph captured on the first
+ * rollout of each horizon.  Errors: as sim_reset / sim_step, SIM_ECUDA. */
 SIM_API int sim_rollout(sim_handle h, int32_t T, sim_outputs *out);
 
 /* Copy the outputs of the current run (bins closed so far; counters up to the
