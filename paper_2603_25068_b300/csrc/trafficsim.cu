@@ -1355,6 +1355,10 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
     const long long n_init = std::max((long long)N, 32LL * L);
     k_bwd_init<<<(unsigned)((n_init + 255) / 256), 256, 0, h->stream>>>(h->d, b, dxT);
     k_route_scan<<<(int)(((size_t)N * 32 + 255) / 256), 256, 0, h->stream>>>(h->d, N, b);
+    for (int ts = 0; ts < 2; ++ts) {                     // merge sums of both tape sets start from zero
+        CU(cudaMemsetAsync(bt[ts].Z, 0, (size_t)K * L * sizeof(double), h->stream));
+        CU(cudaMemsetAsync(bt[ts].SA, 0, (size_t)K * L * sizeof(double), h->stream));
+    }
     // recomputation: no route log, counters into a scratch array
     DevSim dr = h->d;
     dr.route_log = nullptr;
@@ -1418,9 +1422,15 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         const int t0 = sg * K, t1 = std::min(T, t0 + K), ts = sg & 1;
         const BwdDev q = with_set(ts);
         CU(cudaStreamWaitEvent(vs, h->ev_b[ts], 0));
-        ckpt_copy(h, sg, false, vs);
         CU(cudaMemsetAsync((t0 & 1) ? h->d.W1 : h->d.W0, 0, (size_t)L * sizeof(unsigned long long), vs));
+        // the recording starts from the segment's checkpoint in place, and leaves
+        // its end state there (no restore copy; no later step reads that checkpoint)
         DevSim dq = dr;
+        dq.lq = h->ck.lq + (size_t)sg * L; dq.lstat = h->ck.lstat + (size_t)sg * L;
+        dq.vac = h->ck.vac + (size_t)sg * L; dq.lpos = h->ck.lpos + (size_t)sg * L;
+        dq.sentry = h->ck.sentry + (size_t)sg * S; dq.saux = h->ck.saux + (size_t)sg * S;
+        dq.pos0 = dq.pos1 = h->ck.pos + (size_t)sg * S;
+        dq.fifo_ptr = h->ck.fifo + (size_t)sg * V; dq.vstate = h->ck.vstate + (size_t)sg * N;
         dq.tag_tape = q.ttag; dq.tape_pos = q.tpos; dq.tape_vid = q.tvid; dq.tape_lq = q.tlq;
         dq.tape_ent = q.tent; dq.tape_lq0 = q.tlq; dq.tape_K = K; dq.tape_mkey = q.tmkey;
         dq.tape_crec = q.tcrec; dq.tape_nrec = q.tnrec; dq.tape_W = q.tW;
@@ -1440,10 +1450,8 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         }
         const BwdDev q = with_set(ts);
         // Per step on the chain's stream: the merge adjoint and car-following in
-        // one launch.  The merge sums start from zero (the set's previous
-        // Jacobian kernel is done: ev_b, waited for before the recording).
-        CU(cudaMemsetAsync(q.Z, 0, (size_t)(t1 - t0) * L * sizeof(double), vs));
-        CU(cudaMemsetAsync(q.SA, 0, (size_t)(t1 - t0) * L * sizeof(double), vs));
+        // one launch.  The merge sums start from zero: zeroed at the start, and
+        // after each Jacobian kernel that read them (before ev_b).
         // A step that follows the previous one directly is launched as its
         // programmatic dependent: it issues its tape loads while that one ends.
         for (int t = t1 - 1; t >= t0; --t) {
@@ -1466,6 +1474,8 @@ extern "C" int sim_backward(sim_handle h, const float *dL_dcounts, const float *
         CU(cudaStreamWaitEvent(h->jstream, h->ev_z, 0));
         const long long ng = (long long)(t1 - t0) * (L + V);
         k_bwd_node_g<<<(unsigned)((ng + 255) / 256), 256, 0, h->jstream>>>(dr, q, t0, t1 - t0);
+        CU(cudaMemsetAsync(q.Z, 0, (size_t)K * L * sizeof(double), h->jstream));
+        CU(cudaMemsetAsync(q.SA, 0, (size_t)K * L * sizeof(double), h->jstream));
         CU(cudaEventRecord(h->ev_b[ts], h->jstream));      // this tape set may be rewritten
         CU(cudaGetLastError());
     }
