@@ -79,7 +79,7 @@ def link_occupancy(sim, T=None, samples: int = 12):
     return occ / max(n, 1)
 
 
-def balance_partition(sim, T=None, samples: int = 12, per_link: float = 1.0, occ=None):
+def balance_partition(sim, T=None, samples: int = 12, per_link: float = 20.0, occ=None):
     """Partition the persistent executor's links by measured load: weight of a
     link = its mean vehicle count over a rollout + ``per_link``.  Returns the
     weights set (None if the simulator has no persistent executor)."""
