@@ -51,6 +51,12 @@ constexpr int kPLinks = 288;                 // links per CTA at most
 constexpr int kPNodes = 128;                 // origin queues per CTA at most
 constexpr int kPNodeTid = 512;               // thread of origin queue 0 in the per-entity phases
 constexpr int kPSlot = 8;                    // choice slots per candidate evaluated in parallel
+// The last warp takes no part in the car-following: its first thread makes the
+// CTA's arrival at the grid barrier (whose release ordering waits until the
+// CTA's writes are performed) and then polls, while threads 0 .. kPCF - 1 run
+// the car-following of the barrier wait without waiting for that ordering.
+constexpr int kPCF = kPT - 32;               // car-following threads
+constexpr int kPBarTid = kPCF;               // thread of the grid barrier's arrival and wait
 constexpr int kPEnt = kPLinks + kPNodes;     // entities: links, then origin queues (index kPLinks + node)
 constexpr int kPPairs = kPEnt * (kPSlot + 1);
 static_assert(kPSlot + 1 <= 16, "a pair list entry holds the slot in 4 bits");
@@ -99,6 +105,7 @@ struct PSmem {
     int plist[kPPairs];            // entity << 4 | (0 merge key, 1 + k choice slot k)
     int wsum[32];
     int cnt[4];                    // step counters: releases, arrivals, candidates, entries
+    unsigned cbal[4][kPT / 32];    // the same counters of the step as one ballot per warp
     int npairs, ctot, stop;
 };
 
@@ -125,19 +132,20 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Grid-wide barrier number `target / gridDim.x` (counter never reset inside a
 // launch), in two halves so that a CTA can work between its arrival and the
-// wait: grid_arrive (block barrier, then one release arrival) and grid_wait.
+// wait: grid_arrive (block barrier, then one release arrival by thread
+// kPBarTid) and grid_wait (polled by the same thread).
 // Bounded: gives up after ~2 s or 2^22 polls, or as soon as another CTA has
 // recorded a timeout; returns false then (every thread of the CTA).
 __device__ __forceinline__ void grid_arrive(unsigned *bar) {
     __syncthreads();
     // release arrival: covers this CTA's writes ordered before it by the block
     // barrier; the acquire load that sees the target covers the rest
-    if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(bar) : "memory");
+    if (threadIdx.x == kPBarTid) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(bar) : "memory");
 }
 __device__ __forceinline__ bool grid_wait(const DevSim &d, unsigned *bar, unsigned target, int t, int *stop) {
-    // thread 0 waits as soon as its own work is done; the block barrier after
+    // thread kPBarTid waits as soon as it has arrived; the block barrier after
     // the wait holds every thread until both its own work and the grid's are
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == kPBarTid) {
         const unsigned long long t_start = global_ns();
         int ok = 1;
         for (unsigned it = 0;; ++it) {
@@ -464,6 +472,33 @@ __device__ __forceinline__ void p_count(PSmem &S, const int *cnt) {
     }
 }
 
+// The same counters as ballots, one word per warp and counter (a thread's
+// transfers add at most one to each: one link or origin queue per thread).
+// Every thread calls; p_count_sum adds them up later, off the phases' path.
+__device__ __forceinline__ void p_count_bal(PSmem &S, const int *cnt) {
+    const int w = threadIdx.x >> 5;
+    const unsigned b0 = __ballot_sync(kFull, cnt[0] != 0), b1 = __ballot_sync(kFull, cnt[1] != 0);
+    const unsigned b2 = __ballot_sync(kFull, cnt[2] != 0), b3 = __ballot_sync(kFull, cnt[3] != 0);
+    if ((threadIdx.x & 31) == 0) {
+        S.cbal[0][w] = b0;
+        S.cbal[1][w] = b1;
+        S.cbal[2][w] = b2;
+        S.cbal[3][w] = b3;
+    }
+}
+// the CTA's counters of step tb from the ballots, added to the step's deltas
+// (one whole warp calls)
+__device__ __forceinline__ void p_count_sum(const DevSim &d, const PSmem &S, int tb) {
+    const int lane = threadIdx.x & 31;
+    int x = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int v = (int)__reduce_add_sync(kFull, (unsigned)__popc(S.cbal[k][lane]));
+        if (lane == k) x = v;
+    }
+    if (lane < 4 && x) atomicAdd(&d.step_delta[4 * tb + lane], x);
+}
+
 // Step t of this thread's link or origin queue up to the choice: credit,
 // candidate.  Returns (choice pairs (merge key + choice slots) << 16) | the
 // link's number of queued vehicles.
@@ -569,7 +604,7 @@ __device__ __forceinline__ void p_pairs(const DevSim &d, PSmem &S, const PCtx &c
 }
 
 // Newell car-following of the queued vehicles of the CTA, in shared memory, by
-// threads 0 .. NT - 1.  The CTA's vehicles, taken in queue order link after
+// threads 0 .. NT - 1 (NT = kPCF; the other threads return at once).  The CTA's vehicles, taken in queue order link after
 // link (leader first), are cut into NT equal runs; thread c updates run c one
 // vehicle after another, walking from link to link.  The headway of a vehicle
 // uses the time-t position of the one ahead: within a run the thread keeps it
@@ -582,8 +617,9 @@ __device__ __forceinline__ void p_pairs(const DevSim &d, PSmem &S, const PCtx &c
 // vehicles (shared-memory atomics: a link may span several runs).
 template <bool kTape, bool kObsOnly, int kMin>
 __device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int r, bool obs) {
-    constexpr int NT = kPT;
+    constexpr int NT = kPCF;
     const int ct = threadIdx.x;
+    if (ct >= NT) return;
     const float M = d.M;
     const int nv = S.voff[c.nl];                             // < 2^16: ct nv fits in 32 bits
     const int v0 = (ct * nv) / NT, v1 = ((ct + 1) * nv) / NT;
@@ -924,20 +960,16 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         int cnt[4] = {0, 0, 0, 0};
         if (!first) p_apply<kTape>(d, a, S, c, t - 1, pd, cnt, true, obs);
         const int v = p_candidate<kTape>(d, S, c, t, t - a.t0, false);   // reads what this thread's p_apply wrote
-        if (!first) p_count(S, cnt);
+        if (!first) p_count_bal(S, cnt);
         p_scan(S, c, v);
-        if (!first && tid < 4) {
-            const int x = S.cnt[tid];
-            if (x) atomicAdd(&d.step_delta[4 * (t - 1) + tid], x);
-        }
         if (first) {
             p_carfollow<kTape, false, 0>(d, a, S, c, t - a.t0, obs);
             __syncthreads();
         }
         p_pairs(d, S, c, t);
+        if (!first && (tid >> 5) == kPT / 32 - 1) p_count_sum(d, S, t - 1);   // the last warp rarely holds pairs
         __syncthreads();
         if (kTape && t == a.t0) p_tape_vid(d, a, S, c, 0);     // vehicles of the segment start
-        if (tid < 4) S.cnt[tid] = 0;
         p_decide<kTape>(d, a, S, c, t, obs, false);
         p_refill(S, c, pd);
         ++epoch;
