@@ -543,6 +543,10 @@ static int enqueue_persist_d(sim_ctx *h, const DevSim &d, int t0, int t1, int fi
     a.S = h->S;
     a.bar_extra = h->bar_extra;
     h->bar_extra = 0;
+    for (int r = 0; r < 10; ++r) {               // the Philox key schedule of d's keys
+        a.rk[0][r] = d.key0 + (uint32_t)r * 0x9E3779B9u;
+        a.rk[1][r] = d.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     CU(cudaMemsetAsync(a.W3, 0, (size_t)3 * h->L * sizeof(unsigned long long), st));
     CU(cudaMemsetAsync(a.bar, 0, sizeof(unsigned), st));
     DevSim dd = d;

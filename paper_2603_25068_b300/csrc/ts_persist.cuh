@@ -73,6 +73,7 @@ struct PArgs {
     int S;                         // tape stride of the slot records (recording launches)
     int bar_extra;                 // arrivals the first barrier waits for beyond the grid (0; > 0 in
                                    // tests of the bounded wait: they never come)
+    uint32_t rk[2][10];            // Philox round keys: key0 + r 0x9E3779B9, key1 + r 0xBB67AE85 (mod 2^32)
 };
 
 struct PSmem {
@@ -178,6 +179,25 @@ __device__ __forceinline__ unsigned long long p_word(float key, int vid, int zon
 }
 __device__ __forceinline__ int p_vid(unsigned long long w, int packz) {
     return packz ? (int)((~(uint32_t)(w & 0xffffffffull)) >> 8) : merge_vid(w);
+}
+
+// Philox4x32-10 with the key schedule read from the launch's parameters
+// (a.rk): the same function as philox4x32_10(c, key0, key1), without the two
+// key additions of each round.  The Gumbel draw of (vehicle, step, stream,
+// slot) as gumbel() gives it.
+__device__ __forceinline__ uint4 p_philox(const PArgs &a, uint4 c) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ a.rk[0][r], lo1, hi0 ^ c.w ^ a.rk[1][r], lo0);
+    }
+    return c;
+}
+__device__ __forceinline__ float p_gumbel(const PArgs &a, int vid, int t, int stream, int slot) {
+    const uint4 o = p_philox(a, make_uint4((uint32_t)vid, (uint32_t)t, (uint32_t)stream, (uint32_t)(slot >> 2)));
+    const int s = slot & 3;
+    return gumbel_of_word(s == 0 ? o.x : s == 1 ? o.y : s == 2 ? o.z : o.w);
 }
 
 // argmax of the staged keys (ties to the lowest slot); slots past the stage
@@ -577,7 +597,7 @@ __device__ __forceinline__ void p_scan(PSmem &S, const PCtx &c, int v) {
 // Gumbel transform), so a warp holding both does not serialise them; the only
 // global load is the destination feature of a slot's link, issued before the
 // Gumbel draw is computed.
-__device__ __forceinline__ void p_pairs(const DevSim &d, PSmem &S, const PCtx &c, int t) {
+__device__ __forceinline__ void p_pairs(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int t) {
     const int np = S.npairs;
     for (int p = threadIdx.x; p < np; p += kPT) {
         const int e = S.plist[p];
@@ -593,7 +613,7 @@ __device__ __forceinline__ void p_pairs(const DevSim &d, PSmem &S, const PCtx &c
             info = isl ? c.LO[S.nd[en].z + k] : c.NO[S.nq[ni].z + k];
             df = d.dest_feat[(size_t)who.y * d.V + __float_as_int(info.z)];
         }
-        const float g = gumbel(d.key0, d.key1, who.x, t, sl == 0 ? 1 : 0, sl == 0 ? 0 : k);
+        const float g = p_gumbel(a, who.x, t, sl == 0 ? 1 : 0, sl == 0 ? 0 : k);
         if (sl == 0) {
             S.mkey[ei] = __fadd_rn(isl ? S.alpha[en] : d.alpha[d.L], g);
         } else {
@@ -966,7 +986,7 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
             p_carfollow<kTape, false, 0>(d, a, S, c, t - a.t0, obs);
             __syncthreads();
         }
-        p_pairs(d, S, c, t);
+        p_pairs(d, a, S, c, t);
         if (!first && (tid >> 5) == kPT / 32 - 1) p_count_sum(d, S, t - 1);   // the last warp rarely holds pairs
         __syncthreads();
         if (kTape && t == a.t0) p_tape_vid(d, a, S, c, 0);     // vehicles of the segment start
