@@ -188,9 +188,9 @@ __device__ __forceinline__ int p_vid(unsigned long long w, int packz) {
 __device__ __forceinline__ uint4 p_philox(const PArgs &a, uint4 c) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ a.rk[0][r], lo1, hi0 ^ c.w ^ a.rk[1][r], lo0);
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;   // one wide multiply each
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ a.rk[0][r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ a.rk[1][r],
+                       (uint32_t)p0);
     }
     return c;
 }
