@@ -57,9 +57,12 @@ constexpr int kPSlot = 8;                    // choice slots per candidate evalu
 // the car-following of the barrier wait without waiting for that ordering.
 constexpr int kPCF = kPT - 32;               // car-following threads
 constexpr int kPBarTid = kPCF;               // thread of the grid barrier's arrival and wait
+constexpr int kPBitsTid = 640;               // thread of link 0 in p_bits (warps with no link or origin queue)
 constexpr int kPEnt = kPLinks + kPNodes;     // entities: links, then origin queues (index kPLinks + node)
 constexpr int kPPairs = kPEnt * (kPSlot + 1);
 static_assert(kPSlot + 1 <= 16, "a pair list entry holds the slot in 4 bits");
+static_assert(kPNodeTid >= kPLinks && kPBitsTid >= kPNodeTid + kPNodes && kPBitsTid + kPLinks <= kPCF &&
+              kPBitsTid % 32 == 0, "link, origin-queue, next-step-bit and barrier threads are disjoint warps");
 
 struct PArgs {
     const int *grp_links;          // [G + 1] first link of each CTA's group
@@ -91,7 +94,8 @@ struct PSmem {
     int voff[kPLinks + 1];         // first vehicle of each link in the CTA's queue order (step t)
     int past[kPLinks];             // bin end: vehicles past the midpoint (time t), summed over the step
     float xt[kPLinks];             // position of the rearmost vehicle after the step's car-following
-    float4 bx[kPLinks];            // positions after the step's car-following at queue positions 0, 1, n-1, n-2
+    int nbits[kPLinks];            // next-step vacancy / arrival bits of the link record (p_bits)
+    int cfli[kPCF];                // link of the first vehicle of each car-following run (p_run_links)
     float mkey[kPEnt];              // merge key alpha + g' of each entity's candidate
     float alpha[kPLinks];
     unsigned long long psum[kPLinks];
@@ -337,6 +341,7 @@ __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &
         const int4 st = S.st[li];
         int4 cr = S.cr[li];
         const unsigned long long w0 = __ldcg(Wb + j);
+        cr.z |= S.nbits[li];                                 // the record's next-step bits
         unsigned long long wt = 0ull;
         int vt = 0;
         if (cr.y >= 0) {
@@ -648,13 +653,18 @@ __device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSm
     float ahead = M;
     if (v0 < v1) {
         // the link holding vehicle v0: the last li with voff[li] <= v0 (empty
-        // links before it share its offset; those after it start beyond v0)
-        int lo = 0, hi = c.nl - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (S.voff[mid] <= v0) lo = mid; else hi = mid - 1;
+        // links before it share its offset; those after it start beyond v0),
+        // listed by p_run_links for the barrier-wait runs
+        if (kMin == 2) {
+            li = S.cfli[ct];
+        } else {
+            int lo = 0, hi = c.nl - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (S.voff[mid] <= v0) lo = mid; else hi = mid - 1;
+            }
+            li = lo;
         }
-        li = lo;
         k = v0 - S.voff[li];
         const int2 qv = *reinterpret_cast<const int2 *>(&S.q[li]);
         n = qv.y;
@@ -759,15 +769,12 @@ __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem 
             return c.P[lb + idx];
         };
         const float x0 = n >= 1 ? at(0) : 0.0f;
-        const float x1 = n >= 2 ? at(1) : 0.0f;
         const float xt = n >= 1 ? at(n - 1) : 0.0f;
         S.xt[li] = xt;                      // ahead of the next entrant (p_ends_pre)
         S.past[li] = 0;                     // the sums of the next step start from zero
         S.psum[li] = 0ull;
-        const float xpt = n >= 2 ? at(n - 2) : 0.0f;
-        S.bx[li] = make_float4(x0, x1, xt, xpt);              // for p_bits
-        // the record of step t (p_bits adds the next-step bits, the transfers of
-        // step t set its final target)
+        // the record of step t (the transfers of step t add the next-step bits
+        // of p_bits and set its final target)
         S.cr[li] = make_int4(c0.x, c0.x >= 0 ? tgt : kTgtNone, c0.z << 8, __float_as_int(x0));
     } else if (!obs_only && tid >= kPNodeTid && tid < kPNodeTid + c.nn) {
         const int ni = tid - kPNodeTid;
@@ -787,19 +794,29 @@ __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem 
     }
 }
 
-// Next-step vacancy and arrival bits of this thread's link for the four (pop,
-// push) outcomes of the coming transfers, from the positions after the step's
-// car-following that p_decide kept: a vehicle entering at 0 finds the link
-// vacant after the next car-following (rearmost vehicle beyond the jam spacing,
-// SI-B) / the leader reaches the arrival line (Alg. S2).  Run while the CTA
-// waits at the grid barrier: only the transfers of the next step read them.
+// Next-step vacancy and arrival bits of link li = threadIdx.x - kPBitsTid for
+// the four (pop, push) outcomes of the coming transfers, from the positions
+// after the step's car-following at queue positions 0, 1, n - 1 and n - 2: a
+// vehicle entering at 0 finds the link vacant after the next car-following
+// (rearmost vehicle beyond the jam spacing, SI-B) / the leader reaches the
+// arrival line (Alg. S2).  Run beside the decisions by warps that hold no link
+// or origin queue; the transfers of the next step add them to the record.
 __device__ __forceinline__ void p_bits(const DevSim &d, PSmem &S, const PCtx &c) {
-    const int li = threadIdx.x;
-    if (li >= c.nl) return;
+    const int li = threadIdx.x - kPBitsTid;
+    if (li < 0 || li >= c.nl) return;
     const float M = d.M;
-    const int n = S.q[li].y;
-    const float4 x = S.bx[li];              // x0, x1, xt (rearmost), xpt (ahead of it)
+    const int4 q = S.q[li];
+    const int n = q.y;
+    const int4 st = S.st[li];
     const float4 g = S.g[li];
+    const int lb = st.x - c.base0;
+    auto at = [&](int k) {
+        int idx = q.x + k;
+        if (idx >= st.y) idx -= st.y;
+        return c.P[lb + idx];
+    };
+    const float4 x = make_float4(n >= 1 ? at(0) : 0.0f, n >= 2 ? at(1) : 0.0f,      // x0, x1,
+                                 n >= 1 ? at(n - 1) : 0.0f, n >= 2 ? at(n - 2) : 0.0f);  // xt (rearmost), xpt
     int bits = 0;
     bits |= (n == 0 || vacant_after(x.z, n >= 2 ? __fsub_rn(x.w, x.z) : M, g)) << 0;
     bits |= (n <= 1 || vacant_after(x.z, n >= 3 ? __fsub_rn(x.w, x.z) : M, g)) << 1;
@@ -809,7 +826,23 @@ __device__ __forceinline__ void p_bits(const DevSim &d, PSmem &S, const PCtx &c)
     bits |= (n >= 2 && arrives_after(x.y, g, M, d.eps_arr)) << 5;
     bits |= arrives_after(n >= 1 ? x.x : 0.0f, g, M, d.eps_arr) << 6;
     bits |= arrives_after(n >= 2 ? x.y : 0.0f, g, M, d.eps_arr) << 7;
-    S.cr[li].z |= bits;
+    S.nbits[li] = bits;
+}
+
+// First link of each car-following run of the barrier wait (p_carfollow with
+// kMin = 2): run ct starts at vehicle v0 = floor(ct nv / kPCF), and v0 >= a
+// exactly when ct >= ceil(a kPCF / nv), so link li (vehicles voff[li] ..
+// voff[li+1] - 1) holds the first vehicle of runs ceil(voff[li] kPCF / nv) ..
+// ceil(voff[li+1] kPCF / nv) - 1.  Runs without vehicles are not listed (nor
+// read).  Written beside the decisions by the threads of p_bits.
+__device__ __forceinline__ void p_run_links(PSmem &S, const PCtx &c) {
+    const int li = threadIdx.x - kPBitsTid;
+    if (li < 0 || li >= c.nl) return;
+    const int nv = S.voff[c.nl];                             // < 2^16: a kPCF fits in 32 bits
+    const int a = S.voff[li], b = S.voff[li + 1];
+    if (a == b) return;
+    const int lo = (a * kPCF + nv - 1) / nv, hi = (b * kPCF + nv - 1) / nv;
+    for (int ct = lo; ct < hi; ++ct) S.cfli[ct] = li;
 }
 
 // tape: vehicle of every occupied slot at the start of the segment (record r =
@@ -991,10 +1024,11 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         __syncthreads();
         if (kTape && t == a.t0) p_tape_vid(d, a, S, c, 0);     // vehicles of the segment start
         p_decide<kTape>(d, a, S, c, t, obs, false);
+        p_bits(d, S, c);
+        p_run_links(S, c);
         p_refill(S, c, pd);
         ++epoch;
         grid_arrive(a.bar);
-        p_bits(d, S, c);
         if (t + 1 < a.t1) {
             const bool obs1 = (t + 1) % d.obs_every == 0;
             p_carfollow<kTape, false, 2>(d, a, S, c, t + 1 - a.t0, obs1);
