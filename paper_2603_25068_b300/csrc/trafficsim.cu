@@ -514,7 +514,6 @@ static int build_groups(sim_ctx *h) {
     CU(cudaStreamSynchronize(h->stream));
     if (!h->pa.W3) {
         TRY(dalloc(h, &h->pa.W3, (size_t)3 * L));
-        TRY(dalloc(h, &h->pa.vacp, (size_t)2 * L));
         TRY(dalloc(h, &h->pa.bar, 4));
     }
     h->pa.grp_links = h->d_grp;

@@ -13,9 +13,9 @@
 //   * the merge words W[target] (64-bit atomicMax of alpha + g' over the
 //     candidates, low half ~(vehicle << 8 | zone) when the sizes allow, so that
 //     the target learns the entrant's zone with the word), three buffers
-//     indexed by step mod 3, and
-//   * the vacancy of each link at each step, published by the link's owner
-//     (two buffers by step parity).
+//     indexed by step mod 3; the owner of a link that is not vacant at the
+//     step stores kWBlocked in its word, which no candidate's word exceeds,
+//     so that the word carries the link's vacancy too.
 // A candidate is valid when its chosen link is vacant (SI-B: a link accepts
 // an entrant only if its rearmost vehicle has left the jam spacing), and every
 // candidate of one target shares that target's vacancy.  So the validity test
@@ -68,8 +68,7 @@ struct PArgs {
     const int *grp_links;          // [G + 1] first link of each CTA's group
     int npg;                       // origin queues per CTA
     int packz;                     // merge words carry the entrant's zone
-    unsigned long long *W3;        // [3 L] merge words by step mod 3
-    int *vacp;                     // [2 L] vacancy of each link at step t, index t & 1, written by its owner
+    unsigned long long *W3;        // [3 L] merge words by step mod 3 (kWBlocked: the link is not vacant)
     unsigned *bar;                 // grid barrier counter (zero at launch)
     int t0, t1;                    // steps [t0, t1)
     int final_obs;                 // close the last bin at t1 (observation-only pass)
@@ -78,6 +77,12 @@ struct PArgs {
                                    // tests of the bounded wait: they never come)
     uint32_t rk[2][10];            // Philox round keys: key0 + r 0x9E3779B9, key1 + r 0xBB67AE85 (mod 2^32)
 };
+
+// Merge word of a link that is not vacant at the step: stored by the link's
+// owner in the transfers that settle the vacancy, before or after the
+// candidates' max reductions of the step (the maximum is the same either way:
+// a real word has a float key in its high half, never all ones).
+constexpr unsigned long long kWBlocked = ~0ull;
 
 struct PSmem {
     int4 q[kPLinks];               // queue head, length, credit, exits
@@ -333,8 +338,7 @@ __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &
                                         int *cnt, bool cf, bool obs) {
     const int tid = threadIdx.x;
     const unsigned long long *Wb = a.W3 + (size_t)(tb % 3) * d.L;
-    const int *Vb = a.vacp + (size_t)(tb & 1) * d.L;           // vacancy of every link at tb
-    int *Vn = a.vacp + (size_t)((tb + 1) & 1) * d.L;           // this CTA's links at tb + 1
+    unsigned long long *Wn = a.W3 + (size_t)((tb + 1) % 3) * d.L;   // words of step tb + 1 (vacancy)
     if (tid < c.nl) {
         const int li = tid, j = c.j0 + li;
         int4 q = S.q[li];
@@ -343,11 +347,7 @@ __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &
         const unsigned long long w0 = __ldcg(Wb + j);
         cr.z |= S.nbits[li];                                 // the record's next-step bits
         unsigned long long wt = 0ull;
-        int vt = 0;
-        if (cr.y >= 0) {
-            wt = __ldcg(Wb + cr.y);
-            vt = __ldcg(Vb + cr.y);
-        }
+        if (cr.y >= 0) wt = __ldcg(Wb + cr.y);             // the target's word and its vacancy
         PEnds ends;
         if (cf) ends = p_ends_pre(d, S, c, li, q);            // while the loads are in flight
         // the candidates of a link that was not vacant at tb could not enter it:
@@ -363,7 +363,7 @@ __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &
             d.vstate[cr.x] = kVehArrived;
             cnt[1] += 1;
         } else if (cr.y >= 0) {
-            if (vt) pop = wt != 0ull && p_vid(wt, a.packz) == cr.x;
+            if (wt != kWBlocked) pop = wt != 0ull && p_vid(wt, a.packz) == cr.x;
             else cr.y = kTgtBlocked;
         }
         if (kTape) d.tape_crec[(size_t)(tb - a.t0) * d.L + j] = cr;
@@ -433,7 +433,7 @@ __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &
         const int o = (pop ? 1 : 0) | (push ? 2 : 0);
         const int fl = ((cr.z >> o) & 1) | (((cr.z >> (4 + o)) & 1) << 1);
         S.flags[li] = fl;
-        Vn[j] = fl & kFlagVacant;                            // read by the transfers of step tb + 1
+        if (!(fl & kFlagVacant)) Wn[j] = kWBlocked;         // read by the transfers of step tb + 1
         a.W3[(size_t)((tb + 2) % 3) * d.L + j] = 0ull;      // words of step tb + 2 start from zero
     } else if (tid >= kPNodeTid && tid < kPNodeTid + c.nn) {
         const int ni = tid - kPNodeTid;
@@ -446,7 +446,7 @@ __device__ __forceinline__ void p_apply(const DevSim &d, const PArgs &a, PSmem &
             cnt[1] += 1;
         } else if (cr.y >= 0) {
             const unsigned long long w = __ldcg(Wb + cr.y);
-            if (__ldcg(Vb + cr.y)) rel = w != 0ull && p_vid(w, a.packz) == cr.x;
+            if (w != kWBlocked) rel = w != 0ull && p_vid(w, a.packz) == cr.x;
             else cr.y = kTgtBlocked;
         }
         if (kTape) d.tape_nrec[(size_t)(tb - a.t0) * d.V + c.n0 + ni] = cr;
@@ -946,7 +946,8 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         S.psum[li] = 0ull;
         S.lpos[li] = d.lpos[j];
         S.flags[li] = d.vac[j];
-        a.vacp[(size_t)(a.t0 & 1) * d.L + j] = d.vac[j] & kFlagVacant;   // read by the transfers of step t0
+        if (!(d.vac[j] & kFlagVacant))                     // read by the transfers of step t0
+            a.W3[(size_t)(a.t0 % 3) * d.L + j] = kWBlocked;
         S.cr[li] = d.crec[j];
         S.alpha[li] = d.alpha[j];
         int4 ld = make_int4(-1, -1, -1, -1);
@@ -1069,7 +1070,8 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         d.vac[j] = S.flags[li];
         d.crec[j] = S.cr[li];
         if (a.t1 > a.t0) {          // a word on a link that was not vacant names no entrant
-            const unsigned long long w = a.vacp[(size_t)((a.t1 - 1) & 1) * d.L + j] ? __ldcg(Wl + j) : 0ull;
+            unsigned long long w = __ldcg(Wl + j);
+            if (w == kWBlocked) w = 0ull;
             Wlast[j] = w ? ((w & 0xffffffff00000000ull) | (unsigned long long)(~(uint32_t)p_vid(w, a.packz))) : 0ull;
         }
         Wnext[j] = 0ull;
