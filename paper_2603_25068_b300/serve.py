@@ -257,6 +257,20 @@ class Engine:
             self.in_flight -= 1
         req.finished = self.now()
 
+    def _create_and_run(self, req):
+        """A request that finds the engine idle (nothing created, ready, running
+        or reversing): its simulator built on this thread and its forward run
+        at once, with no hand-over to a creation thread."""
+        with self.lock:
+            self.in_flight += 1
+        sim = Simulator(req.scenario, device=self.device, stream=self.stream,
+                        ckpt_every=self.ckpt_every if req.needs_grad else 0, route_cap=self.route_cap)
+        nbytes = float(sim.device_bytes()) + self._estimate_extra(req)
+        with self.lock:
+            self.used += nbytes
+        req.admitted = self.now()
+        self._run_alone(req, sim, nbytes)
+
     def _run_alone(self, req, sim, nbytes):
         """A request with nothing beside it: one rollout of its own simulator
         (a single persistent launch), as serial execution runs it."""
@@ -295,6 +309,9 @@ class Engine:
                 now = self.now()
                 if self.order == "srw":
                     waiting.sort(key=lambda r: request_priority(r, now))
+                if waiting and self.in_flight == 0:      # idle: the first request as serial execution runs it
+                    self._create_and_run(waiting.pop(0))
+                    continue
                 waiting = [req for req in waiting if not self._admit(req)]
                 while True:                              # simulators built by the creation thread
                     try:
@@ -322,7 +339,15 @@ class Engine:
                 if not self.active:
                     if all(np.isfinite(r.finished) for r in requests):
                         break
-                    time.sleep(poll)
+                    # idle: wake as soon as a simulator is ready, at the next
+                    # arrival, or after `poll` seconds, whichever comes first
+                    timeout = poll
+                    if k < len(pending):
+                        timeout = min(timeout, max(pending[k].arrival - self.now(), 0.0))
+                    try:
+                        self.ready.append(self.ready_q.get(timeout=timeout))
+                    except queue.Empty:
+                        pass
                     continue
                 fin = self.batch.advance(self.chunk)
                 if fin.any():
