@@ -528,12 +528,15 @@ __device__ __forceinline__ void p_count_sum(const DevSim &d, const PSmem &S, int
 // candidate.  Returns (choice pairs (merge key + choice slots) << 16) | the
 // link's number of queued vehicles.
 template <bool kTape>
-__device__ __forceinline__ int p_candidate(const DevSim &d, PSmem &S, const PCtx &c, int t, int r, bool obs_only) {
+__device__ __forceinline__ int p_candidate(const DevSim &d, PSmem &S, const PCtx &c, int t, int r, bool obs_only,
+                                           bool all = true) {
     const int tid = threadIdx.x;
     if (tid < c.nl) {
         const int li = tid;
         const int4 q = S.q[li];
-        const int cost = q.y;                              // vehicles to update
+        // vehicles the car-following runs of the step take: every one (all),
+        // else those at queue positions >= 2 (the barrier-wait runs)
+        const int cost = all ? q.y : max(q.y - 2, 0);
         if (obs_only) return cost;
         if (kTape) {
             d.tape_lq[(size_t)r * d.L + c.j0 + li] = q;
@@ -640,7 +643,7 @@ __device__ __forceinline__ void p_pairs(const DevSim &d, const PArgs &a, PSmem &
 // transfers decide, see p_ends_pre).  At bin ends the threads also sum each
 // link's vehicles past the midpoint and their positions over the updated
 // vehicles (shared-memory atomics: a link may span several runs).
-template <bool kTape, bool kObsOnly, int kMin>
+template <bool kTape, bool kObsOnly, int kMin, bool kSkip = false>
 __device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int r, bool obs) {
     constexpr int NT = kPCF;
     const int ct = threadIdx.x;
@@ -665,7 +668,8 @@ __device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSm
             }
             li = lo;
         }
-        k = v0 - S.voff[li];
+        // kSkip: the offsets count the vehicles at queue positions >= 2 only
+        k = v0 - S.voff[li] + (kSkip ? 2 : 0);
         const int2 qv = *reinterpret_cast<const int2 *>(&S.q[li]);
         n = qv.y;
         lb = S.lbase[li];
@@ -694,14 +698,20 @@ __device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSm
             g = S.g[li];
             idx = qv.x;
             k = 0;
+            if (kSkip) {                    // from queue position 2, behind position 1
+                idx += 2;
+                if (idx >= cap) idx -= cap;
+                k = 2;
+                ahead = c.P[lb + (idx == 0 ? cap - 1 : idx - 1)];
+            }
         }
         const float x = c.P[lb + idx];
-        if (obs && k >= kMin) {             // bin end: vehicles past the midpoint, position sum (time t)
+        if (obs && (kSkip || k >= kMin)) {  // bin end: vehicles past the midpoint, position sum (time t)
             past += x >= __fmul_rn(g.x, 0.5f) ? 1 : 0;
             psum += pos_fx(x);
         }
-        if (!kObsOnly && k >= kMin) {
-            const float h = k == 0 ? M : __fsub_rn(ahead, x);
+        if (!kObsOnly && (kSkip || k >= kMin)) {
+            const float h = (!kSkip && k == 0) ? M : __fsub_rn(ahead, x);
             int tag;
             c.P[lb + idx] = newell(x, h, g.x, g.y, g.z, g.w, tag);
             if (kTape) {                    // tape: branch tag of the slot, time-t position at bin ends
@@ -1013,7 +1023,10 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         PPend pd{};
         int cnt[4] = {0, 0, 0, 0};
         if (!first) p_apply<kTape>(d, a, S, c, t - 1, pd, cnt, true, obs);
-        const int v = p_candidate<kTape>(d, S, c, t, t - a.t0, false);   // reads what this thread's p_apply wrote
+        // reads what this thread's p_apply wrote; the offsets of the scan count
+        // the vehicles the step's car-following runs take (all of them on the
+        // first step, else those at queue positions >= 2)
+        const int v = p_candidate<kTape>(d, S, c, t, t - a.t0, false, first);
         if (!first) p_count_bal(S, cnt);
         p_scan(S, c, v);
         if (first) {
@@ -1032,7 +1045,8 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         grid_arrive(a.bar);
         if (t + 1 < a.t1) {
             const bool obs1 = (t + 1) % d.obs_every == 0;
-            p_carfollow<kTape, false, 2>(d, a, S, c, t + 1 - a.t0, obs1);
+            if (first) p_carfollow<kTape, false, 2>(d, a, S, c, t + 1 - a.t0, obs1);
+            else p_carfollow<kTape, false, 2, true>(d, a, S, c, t + 1 - a.t0, obs1);
         }
         if (!grid_wait(d, a.bar, epoch * gridDim.x + (unsigned)a.bar_extra, t, &S.stop)) return;
     }
