@@ -542,6 +542,9 @@ static int enqueue_persist_d(sim_ctx *h, const DevSim &d, int t0, int t1, int fi
     a.S = h->S;
     a.bar_extra = h->bar_extra;
     h->bar_extra = 0;
+    // barrier-wait car-following over queue positions >= 2 only: on networks
+    // with 8 or more vehicles per link, whose queues are long enough for it
+    a.skip2 = (long long)h->N >= 8LL * h->L ? 1 : 0;
     for (int r = 0; r < 10; ++r) {               // the Philox key schedule of d's keys
         a.rk[0][r] = d.key0 + (uint32_t)r * 0x9E3779B9u;
         a.rk[1][r] = d.key1 + (uint32_t)r * 0xBB67AE85u;

@@ -76,6 +76,7 @@ struct PArgs {
     int bar_extra;                 // arrivals the first barrier waits for beyond the grid (0; > 0 in
                                    // tests of the bounded wait: they never come)
     uint32_t rk[2][10];            // Philox round keys: key0 + r 0x9E3779B9, key1 + r 0xBB67AE85 (mod 2^32)
+    int skip2;                     // barrier-wait runs over queue positions >= 2 only (long queues)
 };
 
 // Merge word of a link that is not vacant at the step: stored by the link's
@@ -1024,9 +1025,11 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         int cnt[4] = {0, 0, 0, 0};
         if (!first) p_apply<kTape>(d, a, S, c, t - 1, pd, cnt, true, obs);
         // reads what this thread's p_apply wrote; the offsets of the scan count
-        // the vehicles the step's car-following runs take (all of them on the
-        // first step, else those at queue positions >= 2)
-        const int v = p_candidate<kTape>(d, S, c, t, t - a.t0, false, first);
+        // the vehicles the step's car-following runs take: all of them on the
+        // first step, else those at queue positions >= 2 when the launch runs
+        // over those only (skip2: long queues; with short ones the runs would
+        // step over many links that hold no such vehicle)
+        const int v = p_candidate<kTape>(d, S, c, t, t - a.t0, false, first || !a.skip2);
         if (!first) p_count_bal(S, cnt);
         p_scan(S, c, v);
         if (first) {
@@ -1045,7 +1048,7 @@ __device__ __forceinline__ void persist_body(const DevSim &d, const PArgs &a) {
         grid_arrive(a.bar);
         if (t + 1 < a.t1) {
             const bool obs1 = (t + 1) % d.obs_every == 0;
-            if (first) p_carfollow<kTape, false, 2>(d, a, S, c, t + 1 - a.t0, obs1);
+            if (first || !a.skip2) p_carfollow<kTape, false, 2>(d, a, S, c, t + 1 - a.t0, obs1);
             else p_carfollow<kTape, false, 2, true>(d, a, S, c, t + 1 - a.t0, obs1);
         }
         if (!grid_wait(d, a.bar, epoch * gridDim.x + (unsigned)a.bar_extra, t, &S.stop)) return;
