@@ -23,19 +23,26 @@
 // takes part in the atomicMax of its chosen link; in the transfers of step t
 // the owner of a link admits the word's winner only if the link was vacant at
 // t, and the owner of a candidate pops it only if it won and its target was
-// vacant (read with the word, in the same round of loads).  Merges, winners
+// vacant (both read from the target's word, in one load).  Merges, winners
 // and transfers are exactly those of the per-step definition, while the choice
 // phase loads nothing but the destination features.  One grid-wide barrier per
 // step therefore suffices.  Epoch t of a CTA:
 //   T   transfers of step t-1 for its links and origin queues (one round of
-//       merge-word and vacancy loads), publication of its links' vacancy at t,
-//       then credit and candidates of step t;
-//   S   one block scan of the choice work -> a compact list of (candidate,
-//       choice slot) pairs;
-//   C|F choice warps evaluate the pairs (utility + Gumbel key of each slot,
-//       the merge key) while the other warps run the Newell update of every
-//       queued vehicle in shared memory, in equal runs of vehicles;
-//   P   argmax, merge atomicMax, next-step bits, records; barrier.
+//       merge-word loads), its links' vacancy at t stored into their words of
+//       step t, the car-following of each link's first two vehicles and its
+//       entrant, then credit and candidates of step t and the warp ballots of
+//       the step counters;
+//   S   one block scan: the compact list of (candidate, choice slot) pairs and
+//       each link's first vehicle in the CTA's order of the vehicles that the
+//       car-following runs take;
+//   C   every warp evaluates pairs (utility + Gumbel key of each slot, the
+//       merge key); the last warp adds up the step counters;
+//   P   argmax, merge atomicMax and records (link and origin-queue threads),
+//       beside them the next-step bits and the runs' first links (warps that
+//       hold neither); then the last warp's arrival at the grid barrier;
+//   W   while that warp polls, threads 0 .. kPCF - 1 run the car-following of
+//       step t + 1 for queue positions >= 2 (their vehicle ahead stays
+//       whatever the transfers do).
 //
 // Every floating-point operation is the one of the two-kernel path (same device
 // functions, same order), so both executors give bit-identical results.
@@ -731,8 +738,8 @@ __device__ __forceinline__ void p_carfollow(const DevSim &d, const PArgs &a, PSm
     }
 }
 
-// Observation at bin ends, choice, merge, next-step bits and records of this
-// thread's link or origin queue.
+// Observation at bin ends, choice, merge and records of this thread's link or
+// origin queue.
 template <bool kTape>
 __device__ __forceinline__ void p_decide(const DevSim &d, const PArgs &a, PSmem &S, const PCtx &c, int t, bool obs,
                                          bool obs_only) {
