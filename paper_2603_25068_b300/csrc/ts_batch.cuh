@@ -148,7 +148,7 @@ __device__ __forceinline__ void bwarp_links(const DevSim &d, int j0, int t, bool
     float *pn = p ? d.pos0 : d.pos1;
     const bool obs = obs_only || (t > 0 && t % d.obs_every == 0);
     __syncwarp();
-    // round 1: queue state and link data
+    // load round 1: queue state and link data
     int4 q = make_int4(0, 0, 0, 0), st = make_int4(0, 0, 0, 0), nd = make_int4(0, 0, 0, 0);
     float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     int flags = 0, eb = 0;
@@ -174,7 +174,7 @@ __device__ __forceinline__ void bwarp_links(const DevSim &d, int j0, int t, bool
     }
     const int excl = incl - n;
     const int total = __shfl_sync(kFull, incl, 31);
-    // round 2: leader and choice slots of a candidate, bin statistics, the
+    // load round 2: leader and choice slots of a candidate, bin statistics, the
     // positions of the first 32 vehicles of the item
     int2 lead = make_int2(-1, -1);
     int ent = 0;
@@ -194,7 +194,7 @@ __device__ __forceinline__ void bwarp_links(const DevSim &d, int j0, int t, bool
     S.past[lane] = 0;
     S.psum[lane] = 0ull;
     cp_async_wait_all();
-    // round 3: utility + Gumbel keys of the candidate's slots
+    // load round 3: utility + Gumbel keys of the candidate's slots
     float mkey = 0.0f;
     if (cand) {
         const bool choose_here = nd.y != lead.y;
